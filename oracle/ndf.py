@@ -1,0 +1,122 @@
+"""Oracle: normal binning and exhaustive footprint histograms (test infrastructure).
+
+Sec. 4.1 precomputes one NDF image for every footprint of a multi-level
+structure in which each level doubles the footprint size, until the footprint
+covers the map.  This library's reading (the paper uses Gaussian-footprint
+P-NDF images on a stride-32 grid; this path uses box footprints at every texel):
+
+* an NDF image is the integer histogram of the projected normals (n.x, n.y) on a
+  B x B grid over [-1, 1]^2 -- the "binning method" of Sec. 5.2 (Fig. 9 caption);
+* level l has a 2^l x 2^l box footprint at every texel (x, y) of the tileable
+  N x N map, with wraparound, l = 0 .. log2 N;
+* the window is centred like the paper's footprints: W_l(x, y) covers texels
+  ((x - a_l + i) mod N, (y - a_l + j) mod N), 0 <= i, j < 2^l, a_l = floor(2^l / 2).
+
+Arrays are indexed [l][y][x][s][t]; the bin s comes from n.x and t from n.y.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def bin_index(nxy: np.ndarray, bins: int):
+    """Bin (s, t) of every normal.  s = clamp(floor(fl32(fl32(n.x + 1) * fl32(B/2))),
+    0, B-1), t likewise from n.y, evaluated in FP32 with round-to-nearest and no
+    fused multiply-add.  A value on a bin edge belongs to the upper bin; n.x = 1
+    is clamped into bin B-1.  Non-finite input raises ValueError."""
+    nxy = np.asarray(nxy, dtype=np.float32)
+    if not np.all(np.isfinite(nxy)):
+        raise ValueError("non-finite normal")
+    half = np.float32(bins / 2)
+    one = np.float32(1.0)
+    s = np.floor((nxy[..., 0] + one) * half)
+    t = np.floor((nxy[..., 1] + one) * half)
+    s = np.clip(s, 0, bins - 1).astype(np.int64)
+    t = np.clip(t, 0, bins - 1).astype(np.int64)
+    return s, t
+
+
+def window_offset(level: int) -> int:
+    """a_l = floor(2^l / 2): the footprint's offset from its corner to its centre."""
+    return (1 << level) // 2
+
+
+def footprint_histograms_brute(s: np.ndarray, t: np.ndarray, levels: int, bins: int) -> np.ndarray:
+    """Definition written out with plain loops: for every level, texel and window
+    texel, add one to the window's bin.  Tiny maps only."""
+    N = s.shape[0]
+    H = np.zeros((levels, N, N, bins, bins), dtype=np.int64)
+    for l in range(levels):
+        w, a = 1 << l, window_offset(l)
+        for y in range(N):
+            for x in range(N):
+                for j in range(w):
+                    for i in range(w):
+                        u = (x - a + i) % N
+                        v = (y - a + j) % N
+                        H[l, y, x, s[v, u], t[v, u]] += 1
+    return H
+
+
+def _cyclic_window_sum(A: np.ndarray, axis: int, w: int, a: int) -> np.ndarray:
+    """out[k] = sum_{i < w} A[(k - a + i) mod n] along `axis`, exact in int64.
+    The sum is taken as a difference of running sums over two periods."""
+    n = A.shape[axis]
+    A2 = np.concatenate([A, A], axis=axis)
+    C = np.cumsum(A2, axis=axis, dtype=np.int64)
+    zero_shape = list(C.shape)
+    zero_shape[axis] = 1
+    C = np.concatenate([np.zeros(zero_shape, dtype=np.int64), C], axis=axis)
+    start = (np.arange(n) - a) % n
+    return np.take(C, start + w, axis=axis) - np.take(C, start, axis=axis)
+
+
+def level_histograms(s: np.ndarray, t: np.ndarray, level: int, bins: int) -> np.ndarray:
+    """H_l[y][x][s][t] for one level: the box window is separable, so the count
+    is a window sum of the per-bin indicator along x followed by one along y."""
+    N = s.shape[0]
+    onehot = np.zeros((N, N, bins, bins), dtype=np.int64)
+    yy, xx = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    onehot[yy, xx, s, t] = 1
+    w, a = 1 << level, window_offset(level)
+    return _cyclic_window_sum(_cyclic_window_sum(onehot, 1, w, a), 0, w, a)
+
+
+def footprint_histograms(s: np.ndarray, t: np.ndarray, levels: int, bins: int) -> np.ndarray:
+    """All levels, int64 array [levels][y][x][s][t]."""
+    N = s.shape[0]
+    H = np.empty((levels, N, N, bins, bins), dtype=np.int64)
+    for l in range(levels):
+        H[l] = level_histograms(s, t, l, bins)
+    return H
+
+
+def window_histogram(s: np.ndarray, t: np.ndarray, bins: int, x: int, y: int, level: int) -> np.ndarray:
+    """One footprint's histogram [B][B], counted directly from the texels of its
+    window (used to check single outputs of full-size builds)."""
+    N = s.shape[0]
+    w, a = 1 << level, window_offset(level)
+    xs = (x - a + np.arange(w)) % N
+    ys = (y - a + np.arange(w)) % N
+    flat = (s[np.ix_(ys, xs)] * bins + t[np.ix_(ys, xs)]).ravel()
+    return np.bincount(flat, minlength=bins * bins).reshape(bins, bins)
+
+
+def density_scale(level: int, bins: int) -> float:
+    """Counts -> NDF values.  Eq. 2 normalises the footprint weight, so an NDF
+    image is a density; over [-1,1]^2 with bin area (2/B)^2 the density of a bin
+    holding c of the 4^l footprint texels is c * B^2 / (4 * 4^l)."""
+    return bins * bins / (4.0 * float(4 ** level))
+
+
+def normalised_tensor(H: np.ndarray, bins: int) -> np.ndarray:
+    """T[l] = H[l] * B^2 / (4 * 4^l), FP64, same [l][y][x][s][t] order."""
+    T = H.astype(np.float64)
+    for l in range(H.shape[0]):
+        T[l] *= density_scale(l, bins)
+    return T
+
+
+def logical(T_phys: np.ndarray) -> np.ndarray:
+    """[l][y][x][s][t] -> logical mode order (x, y, l, s, t)."""
+    return np.transpose(T_phys, (2, 1, 0, 3, 4))
