@@ -1,0 +1,291 @@
+/*
+ * gsp.h -- C ABI of the GB300 (sm_103a) library for constant-cost
+ * spatio-angular prefiltering of glinty appearance by tensor decomposition
+ * (Constant-Cost Spatio-Angular Prefiltering of Glinty Appearance Using Tensor
+ * Decomposition, arXiv 2109.14807).
+ *
+ * The data path:
+ *   normal map --gsp_build_footprint_ndfs--> integer NDF histograms of every
+ *   2^l x 2^l footprint (Sec. 4.1)
+ *   --gsp_cp_decompose--> CP factors of the 5-mode NDF tensor (Sec. 4.2, Eq. 3)
+ *   --gsp_build_query_tables--> 1D summed-area tables (Sec. 4.4)
+ *   --gsp_range_query--> batched spatio-angular range queries (Sec. 4.4, Eq. 5)
+ *   --gsp_range_query_backward--> adjoint of the range query.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are CUDA device pointers, h_* are host pointers.  All
+ *    device buffers are allocated and owned by the caller; the library never
+ *    allocates device memory and takes scratch space only from a
+ *    caller-supplied workspace (d_ws, ws_bytes).
+ *  - `stream` is a cudaStream_t passed as an opaque pointer (NULL = legacy
+ *    default stream).  Calls enqueue work on `stream` and return without
+ *    waiting, except where a comment says the call synchronises.
+ *  - Return value: GSP_OK (0) or a negative gsp_status.  Argument errors are
+ *    detected on the host before anything is enqueued.  Errors found by the
+ *    device (a non-finite normal, a malformed query) are OR-ed into the
+ *    caller's 32-bit status word d_status (GSP_DEV_* bits) and never trap.
+ *  - Map side N is a power of two, 2 <= N <= 4096; levels = log2(N) + 1 (level
+ *    l has 2^l x 2^l footprints, l = 0 .. log2 N); bins B is a power of two,
+ *    4 <= B <= 128; rank R is 1 <= R <= 256.
+ *  - NDF tensor layout: int32 / float, C order [l][y][x][s][t]; (s, t) is the
+ *    (n.x, n.y) bin; the logical mode order is (x, y, l, s, t).
+ *  - Factor matrices are FP32, row-major [rows][R].
+ */
+#ifndef GSP_H
+#define GSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* gsp_stream; /* cudaStream_t */
+
+typedef enum gsp_status {
+  GSP_OK = 0,
+  GSP_ERR_INVALID_ARG = -1, /* a size, pointer or option is out of range      */
+  GSP_ERR_CUDA = -2,        /* a CUDA runtime call failed (see gsp_last_cuda_error) */
+  GSP_ERR_WORKSPACE = -3,   /* ws_bytes smaller than the matching *_workspace_bytes */
+  GSP_ERR_NONFINITE = -4,   /* non-finite data found (host-visible reports only) */
+  GSP_ERR_NUMERIC = -5,     /* a least-squares system could not be solved        */
+  GSP_ERR_TIMEOUT = -6,     /* a bounded device wait ran out                     */
+  GSP_ERR_UNSUPPORTED = -7  /* feature not available on this device / build      */
+} gsp_status;
+
+/* Bits OR-ed into the device status word d_status. */
+#define GSP_DEV_NONFINITE_NORMAL 0x1u /* a normal map entry was NaN or Inf     */
+#define GSP_DEV_BAD_QUERY 0x2u        /* non-finite field or material >= n_mats */
+#define GSP_DEV_NUMERIC 0x4u          /* Gram system not positive definite: the
+                                         pseudo-inverse fallback was used      */
+#define GSP_DEV_TIMEOUT 0x8u          /* a bounded wait in a kernel gave up    */
+
+#define GSP_MAX_MATERIALS 16
+#define GSP_MAX_SWEEPS 512
+
+/* ------------------------------------------------------------------------ */
+/* a1 -- binning of the normal map (Sec. 5.2 "binning method")               */
+/* ------------------------------------------------------------------------ */
+
+/* Bin every normal of the N x N map.
+ *  d_normal_xy: FP32 [N][N][2] = (n.x, n.y), row-major [y][x]; n.z > 0 implied.
+ *  d_bins:      uint16 [N][N], written: s * B + t with
+ *               s = clamp(floor(fl32(fl32(n.x + 1) * (B/2))), 0, B-1), t from n.y
+ *               (FP32, round-to-nearest, no fused multiply-add).
+ *  A non-finite normal sets GSP_DEV_NONFINITE_NORMAL and bins to 0. */
+int gsp_bin_normals(const float* d_normal_xy, int N, int bins, uint16_t* d_bins,
+                    uint32_t* d_status, gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* a2 -- exhaustive multi-level footprint histograms (Sec. 4.1)              */
+/* ------------------------------------------------------------------------ */
+
+/* Scratch bytes gsp_build_footprint_ndfs needs (the bin map). */
+size_t gsp_build_workspace_bytes(int N, int levels, int bins);
+
+/* Integer NDF histogram of every 2^l x 2^l box footprint at every texel, with
+ * wraparound (the paper precomputes NDF images of footprints that double in
+ * size per level until they cover the map, Sec. 4.1, Fig. 2).  The window of
+ * (x, y, l) covers texels ((x - a + i) mod N, (y - a + j) mod N), 0 <= i, j < 2^l,
+ * a = floor(2^l / 2).
+ *  d_hist: int32 [levels][N][N][B][B] (C order [l][y][x][s][t]), written.
+ *  Counts are exact; sum over (s, t) of every footprint is 4^l. */
+int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int levels, int bins,
+                             int32_t* d_hist, void* d_ws, size_t ws_bytes,
+                             uint32_t* d_status, gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* a3/a4 -- CP decomposition by ALS (Sec. 4.2, Eq. 3)                        */
+/* ------------------------------------------------------------------------ */
+
+typedef enum gsp_precision {
+  GSP_PREC_FP32 = 0, /* MTTKRP with FP32 FFMA on CUDA cores (the plain path)   */
+  GSP_PREC_TF32 = 1, /* MTTKRP on tcgen05 tensor cores, TF32 in, FP32 accumulate */
+  GSP_PREC_BF16 = 2  /* MTTKRP on tcgen05 tensor cores, BF16 in, FP32 accumulate */
+} gsp_precision;
+
+/* Five factor matrices and the CP weights, device pointers, FP32:
+ * fx [N][R], fy [N][R], fl [levels][R], fs [B][R], ft [B][R], lambda [R].
+ * The decomposed tensor is sum_r lambda_r fx_r o fy_r o fl_r o fs_r o ft_r. */
+typedef struct gsp_cp_factors {
+  float* fx;
+  float* fy;
+  float* fl;
+  float* fs;
+  float* ft;
+  float* lambda;
+} gsp_cp_factors;
+
+typedef struct gsp_als_opts {
+  int32_t sweeps;    /* sweeps to run (1 .. GSP_MAX_SWEEPS)                       */
+  int32_t precision; /* gsp_precision of the MTTKRP operand                       */
+  double tol;        /* stop once |fit_k - fit_(k-1)| < tol (Sec. 4.2 uses 1e-4);
+                        0 runs exactly `sweeps` sweeps                            */
+  int32_t raw_counts;/* 1: decompose the raw counts H instead of the NDF density
+                        T = H * B^2 / (4 * 4^l)                                  */
+  int32_t reserved;
+} gsp_als_opts;
+
+/* Filled by the host after the call when non-NULL (the call then synchronises
+ * `stream`).  fit_k = 1 - ||T - T_hat||_F / ||T||_F after sweep k, in FP64. */
+typedef struct gsp_als_report {
+  int32_t sweeps_done;
+  int32_t numeric_fallbacks; /* mode updates that needed the pseudo-inverse */
+  double fit[GSP_MAX_SWEEPS];
+} gsp_als_report;
+
+/* Workspace bytes for gsp_cp_prepare / gsp_cp_sweeps / gsp_cp_mttkrp. */
+size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precision);
+
+/* Build the MTTKRP operand (the NDF tensor in the precision's input type,
+ * [l][y][x][s][t]) and ||T||^2 inside the workspace.  Exactly one of d_hist
+ * (int32 histograms from gsp_build_footprint_ndfs) and d_normal_xy (the normal
+ * map: the histograms are then produced level by level straight into the
+ * operand, never stored as int32) must be non-NULL. */
+int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, int N, int levels,
+                   int bins, int rank, const gsp_als_opts* opts, void* d_ws,
+                   size_t ws_bytes, uint32_t* d_status, gsp_stream stream);
+
+/* Run ALS sweeps on the operand prepared in d_ws.  `f` holds the starting
+ * factors on entry (e.g. seeded U[0,1)) and the result on exit.  Mode order
+ * per sweep: x, y, l, s, t; each update is the exact least-squares solution
+ * A_n = M_n V^-1 with V the Hadamard product of the other modes' FP64 Gram
+ * matrices (Cholesky; pseudo-inverse fallback), then 2-norm column
+ * normalisation into lambda. */
+int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_als_opts* opts,
+                  const gsp_cp_factors* f, gsp_als_report* h_report, void* d_ws,
+                  size_t ws_bytes, gsp_stream stream);
+
+/* gsp_cp_prepare followed by gsp_cp_sweeps. */
+int gsp_cp_decompose(const int32_t* d_hist, const float* d_normal_xy, int N, int levels,
+                     int bins, int rank, const gsp_als_opts* opts, const gsp_cp_factors* f,
+                     gsp_als_report* h_report, void* d_ws, size_t ws_bytes,
+                     uint32_t* d_status, gsp_stream stream);
+
+/* The five MTTKRPs of the prepared operand for fixed factors f (lambda unused):
+ * M_n[i][r] = sum over the other four indices of T * prod_{m != n} f_m[i_m][r].
+ * d_m[0..4] = M_x [N][R], M_y [N][R], M_l [levels][R], M_s [B][R], M_t [B][R]
+ * (FP32, written).  Used to check the contraction kernels one by one. */
+int gsp_cp_mttkrp(int N, int levels, int bins, int rank, int precision,
+                  const gsp_cp_factors* f, float* const d_m[5], void* d_ws,
+                  size_t ws_bytes, gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* a5/a6 -- query tables and batched range query (Sec. 4.3-4.4, Eq. 4-5)     */
+/* ------------------------------------------------------------------------ */
+
+/* One CP-compressed material.  Factor pointers are read by the query kernels;
+ * `tables` (gsp_query_table_floats() floats, caller-owned, 16-byte aligned) is
+ * written by gsp_build_query_tables and holds, in order:
+ *   flw  [levels][R]       fl * lambda (the CP weights folded into the level factor),
+ *                          padded to a multiple of 4 floats
+ *   sats [B+1][R][4]       1D summed-area table of fs: {hi, lo, fs, 0} with
+ *                          hi + lo = sum_{k<i} fs[k] (FP64 sum split into two FP32)
+ *   satt [B+1][R][4]       the same for ft.                                       */
+typedef struct gsp_material {
+  int32_t N, levels, bins, rank;
+  const float* fx;
+  const float* fy;
+  const float* fl;
+  const float* fs;
+  const float* ft;
+  const float* lambda;
+  float* tables;
+} gsp_material;
+
+/* 32-byte query descriptor (arrays of them must be 16-byte aligned).  x, y: texel, taken mod N.  level: footprint level,
+ * clamped to [0, levels-1], blended linearly between floor(level) and the next
+ * level.  [s0, s1] x [t0, t1]: angular range in bin units (bin k = [k, k+1)),
+ * clamped to [0, B] and reordered if reversed; a zero-width side is a point
+ * query of the bin holding it.  material: index into the materials array. */
+typedef struct gsp_query {
+  int32_t x, y;
+  float level, s0, s1, t0, t1;
+  uint32_t material;
+} gsp_query;
+
+size_t gsp_query_table_floats(int levels, int bins, int rank);
+
+/* Fill h_mat->tables from its factors (1D SAT per angular factor, Sec. 4.4). */
+int gsp_build_query_tables(const gsp_material* h_mat, gsp_stream stream);
+
+/* Launch shape of the query kernels.  NULL = the library's default. */
+typedef struct gsp_query_tuning {
+  int32_t lanes_per_query; /* 4, 8, 16 or 32 */
+  int32_t blocks_per_sm;   /* persistent CTAs per SM (1 .. 32)   */
+  int32_t threads;         /* threads per CTA (64 .. 1024, multiple of 32) */
+  int32_t chunk;           /* queries a warp claims per grab (1 .. 64) */
+} gsp_query_tuning;
+
+/* Batched range queries (Eq. 5 extended to five modes):
+ *   q = sum_r fx[x,r] fy[y,r] ((1-f) flw[l0,r] + f flw[l1,r]) Sbar_r Tbar_r,
+ *   Sbar_r = (F_r(s1) - F_r(s0)) / (s1 - s0),  F_r(s) = P_r[floor s] + frac(s) fs[floor s, r],
+ * two summed-area-table look-ups per range end (Sec. 4.4).  h_mats: host array
+ * of n_mats (<= GSP_MAX_MATERIALS) materials with built tables.  d_q: n queries;
+ * d_out: n floats, written.  A malformed query writes NaN and sets
+ * GSP_DEV_BAD_QUERY.  d_ws: 16 bytes of scratch (work counter) or more.
+ * Capturable in a CUDA graph (no allocation, no synchronisation). */
+int gsp_range_query(const gsp_material* h_mats, int n_mats, const gsp_query* d_q, int64_t n,
+                    float* d_out, uint32_t* d_status, const gsp_query_tuning* tuning,
+                    void* d_ws, size_t ws_bytes, gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* a7 -- adjoint of the range query and the refinement step                  */
+/* ------------------------------------------------------------------------ */
+
+/* Gradient buffers of one material, FP32, same shapes as the factors; the
+ * level gradient is with respect to flw = fl * lambda. */
+typedef struct gsp_material_grad {
+  float* dfx;
+  float* dfy;
+  float* dflw;
+  float* dfs;
+  float* dft;
+} gsp_material_grad;
+
+size_t gsp_backward_workspace_bytes(const gsp_material* h_mats, int n_mats);
+
+/* Accumulate (+=) d(sum_i g_i q_i)/d(factors) into h_grads[m] for every
+ * material m; d_gout holds the n upstream gradients g_i.  The angular
+ * gradients go first to the summed-area-table entries the query read and are
+ * turned into factor gradients by one suffix sum per material. */
+int gsp_range_query_backward(const gsp_material* h_mats, int n_mats, const gsp_query* d_q,
+                             int64_t n, const float* d_gout, const gsp_material_grad* h_grads,
+                             void* d_ws, size_t ws_bytes, uint32_t* d_status,
+                             gsp_stream stream);
+
+/* One Adam step (Kingma & Ba 2015) on n FP32 parameters in place:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+int gsp_adam_step(float* d_param, const float* d_grad, float* d_m, float* d_v, int64_t n,
+                  int step, float lr, float beta1, float beta2, float eps, gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* misc                                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Kernel timing for measurement.  When enabled, the library records a pair of
+ * CUDA events on the launching stream around every launch of the kernels
+ * below (id = index).  gsp_profile_read synchronises those events and returns
+ * the launch count and summed device time since the last reset.  Off by
+ * default; keep it off while capturing CUDA graphs.
+ *   0 bins, 1 level0, 2 doubling, 3 cast, 4 mttkrp_xy, 5 mttkrp_lst,
+ *   6 als_small, 7 tables, 8 range_query, 9 range_query_backward, 10 adam */
+#define GSP_PROFILE_SLOTS 11
+int gsp_profile_enable(int on);
+void gsp_profile_reset(void);
+int gsp_profile_read(int id, int64_t* h_launches, double* h_total_ms);
+const char* gsp_profile_name(int id);
+/* Kernel launches issued by this library since the process started. */
+uint64_t gsp_kernel_launches(void);
+
+const char* gsp_strerror(int status);
+/* cudaError_t value of the last failing CUDA call in this thread (0 if none). */
+int gsp_last_cuda_error(void);
+int gsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSP_H */

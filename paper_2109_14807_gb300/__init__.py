@@ -1,0 +1,18 @@
+"""GB300-native footprint-NDF binning, CP-ALS and constant-cost spatio-angular
+range queries (Constant-Cost Spatio-Angular Prefiltering of Glinty Appearance
+Using Tensor Decomposition, arXiv 2109.14807).
+
+The compute lives in the CUDA library libgsp.so (C ABI: include/gsp.h); this
+package is its Python binding.  Build it with ``paper_2109_14807_gb300.build.build()``.
+"""
+from .api import (CPWorkspace, QueryMaterial, RangeQueryFn, adam_step, backward_workspace_bytes,
+                  bin_normals, build_footprint_ndfs, build_query_tables, cp_decompose,
+                  init_factors_to_device, new_status, queries_to_device, range_query,
+                  range_query_autograd, range_query_backward, status_bits)
+
+__all__ = [
+    "CPWorkspace", "QueryMaterial", "RangeQueryFn", "adam_step", "backward_workspace_bytes",
+    "bin_normals", "build_footprint_ndfs", "build_query_tables", "cp_decompose",
+    "init_factors_to_device", "new_status", "queries_to_device", "range_query",
+    "range_query_autograd", "range_query_backward", "status_bits",
+]

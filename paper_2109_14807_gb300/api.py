@@ -1,0 +1,299 @@
+"""Python binding of the C ABI: the same calls, with torch tensors for device
+memory and torch's current CUDA stream.  Nothing here computes; every step of
+the path runs in libgsp.so.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (AlsOpts, AlsReport, CpFactors, Material, MaterialGrad, QueryTuning, check,
+                   load)
+
+QUERY_WORDS = 8  # a query descriptor is 32 bytes = 8 int32 words
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def new_status(device="cuda"):
+    """Device status word (uint32 semantics, stored as int32)."""
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def status_bits(status: torch.Tensor) -> int:
+    return int(status.item()) & 0xFFFFFFFF
+
+
+def queries_to_device(q: np.ndarray, device="cuda") -> torch.Tensor:
+    """numpy array of 32-byte descriptors -> int32 tensor [n][8] on the device."""
+    words = np.frombuffer(np.ascontiguousarray(q).tobytes(), dtype=np.int32).reshape(-1, QUERY_WORDS)
+    return torch.from_numpy(words.copy()).to(device)
+
+
+# ------------------------------------------------------------ a1 / a2 --
+
+def bin_normals(normal_xy: torch.Tensor, bins: int, status=None) -> torch.Tensor:
+    lib = load()
+    N = normal_xy.shape[0]
+    out = torch.empty((N, N), dtype=torch.int16, device=normal_xy.device)
+    check("gsp_bin_normals", lib.gsp_bin_normals(_ptr(normal_xy, torch.float32, "normal_xy"), N,
+                                                 bins, _ptr(out), _ptr(status), _stream()))
+    return out
+
+
+def build_footprint_ndfs(normal_xy: torch.Tensor, levels: int, bins: int, out=None, status=None,
+                         workspace=None) -> torch.Tensor:
+    """int32 histograms [levels][N][N][B][B] (C order [l][y][x][s][t])."""
+    lib = load()
+    N = normal_xy.shape[0]
+    if out is None:
+        out = torch.empty((levels, N, N, bins, bins), dtype=torch.int32, device=normal_xy.device)
+    need = lib.gsp_build_workspace_bytes(N, levels, bins)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=normal_xy.device)
+    check("gsp_build_footprint_ndfs", lib.gsp_build_footprint_ndfs(
+        _ptr(normal_xy, torch.float32, "normal_xy"), N, levels, bins, _ptr(out, torch.int32, "out"),
+        _ptr(workspace), workspace.numel(), _ptr(status), _stream()))
+    return out
+
+
+# ------------------------------------------------------------ a3 / a4 --
+
+FACTOR_NAMES = ("fx", "fy", "fl", "fs", "ft")
+
+
+def _factors_struct(f: dict) -> CpFactors:
+    return CpFactors(*(_ptr(f[k], torch.float32, k) for k in FACTOR_NAMES),
+                     _ptr(f["lambda"], torch.float32, "lambda"))
+
+
+class CPWorkspace:
+    """Device workspace of one CP decomposition (operand tensor + scratch)."""
+
+    def __init__(self, N, levels, bins, rank, precision="fp32", device="cuda"):
+        lib = load()
+        self.N, self.levels, self.bins, self.rank = N, levels, bins, rank
+        self.precision = _lib.PREC[precision] if isinstance(precision, str) else int(precision)
+        nbytes = lib.gsp_cp_workspace_bytes(N, levels, bins, rank, self.precision)
+        if nbytes == 0:
+            raise ValueError("unsupported CP shape")
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    def _opts(self, sweeps=1, tol=0.0, raw_counts=False):
+        return AlsOpts(int(sweeps), self.precision, float(tol), int(bool(raw_counts)), 0)
+
+    def prepare(self, hist=None, normal_xy=None, raw_counts=False, status=None):
+        lib = load()
+        opts = self._opts(raw_counts=raw_counts)
+        check("gsp_cp_prepare", lib.gsp_cp_prepare(
+            _ptr(hist, torch.int32, "hist"), _ptr(normal_xy, torch.float32, "normal_xy"),
+            self.N, self.levels, self.bins, self.rank, ctypes.byref(opts), _ptr(self.buf),
+            self.buf.numel(), _ptr(status), _stream()))
+
+    def sweeps(self, factors: dict, sweeps: int, tol=0.0, report=True):
+        """Run ALS sweeps in place on `factors`; returns the list of fits (or None)."""
+        lib = load()
+        opts = self._opts(sweeps, tol)
+        rep = AlsReport() if report else None
+        fs = _factors_struct(factors)
+        check("gsp_cp_sweeps", lib.gsp_cp_sweeps(
+            self.N, self.levels, self.bins, self.rank, ctypes.byref(opts), ctypes.byref(fs),
+            ctypes.byref(rep) if rep is not None else None, _ptr(self.buf), self.buf.numel(),
+            _stream()))
+        if rep is None:
+            return None
+        return [rep.fit[i] for i in range(rep.sweeps_done)], rep.numeric_fallbacks
+
+    def mttkrp(self, factors: dict):
+        """The five MTTKRPs of the prepared operand for fixed factors (FP32)."""
+        lib = load()
+        dev = self.buf.device
+        rows = (self.N, self.N, self.levels, self.bins, self.bins)
+        outs = [torch.empty((n, self.rank), dtype=torch.float32, device=dev) for n in rows]
+        arr = (ctypes.c_void_p * 5)(*[o.data_ptr() for o in outs])
+        f = dict(factors)
+        f.setdefault("lambda", torch.ones(self.rank, dtype=torch.float32, device=dev))
+        fs = _factors_struct(f)
+        check("gsp_cp_mttkrp", lib.gsp_cp_mttkrp(
+            self.N, self.levels, self.bins, self.rank, self.precision, ctypes.byref(fs), arr,
+            _ptr(self.buf), self.buf.numel(), _stream()))
+        return outs
+
+
+def init_factors_to_device(init: dict, device="cuda") -> dict:
+    """numpy init factors (synth.init_factors) -> FP32 device tensors + lambda."""
+    out = {k: torch.from_numpy(np.asarray(init[k], dtype=np.float32)).to(device).contiguous()
+           for k in FACTOR_NAMES}
+    out["lambda"] = torch.ones(out["fx"].shape[1], dtype=torch.float32, device=device)
+    return out
+
+
+def cp_decompose(rank, init: dict, hist=None, normal_xy=None, levels=None, bins=None,
+                 sweeps=20, precision="fp32", tol=0.0, raw_counts=False, status=None):
+    """CP-ALS of the footprint NDF tensor.  Returns (factors, fits, fallbacks)."""
+    src = hist if hist is not None else normal_xy
+    if hist is not None:
+        levels, N, _, bins, _ = hist.shape
+    else:
+        N = normal_xy.shape[0]
+    ws = CPWorkspace(N, levels, bins, rank, precision, device=src.device)
+    ws.prepare(hist=hist, normal_xy=normal_xy, raw_counts=raw_counts, status=status)
+    f = init_factors_to_device(init, src.device) if not isinstance(init["fx"], torch.Tensor) else init
+    fits, fallbacks = ws.sweeps(f, sweeps, tol)
+    return f, fits, fallbacks
+
+
+# ------------------------------------------------------------ a5 / a6 --
+
+@dataclass
+class QueryMaterial:
+    """One CP-compressed material: device factor tensors plus its query tables."""
+    fx: torch.Tensor
+    fy: torch.Tensor
+    fl: torch.Tensor
+    fs: torch.Tensor
+    ft: torch.Tensor
+    lam: torch.Tensor
+    tables: torch.Tensor = field(default=None)
+
+    @property
+    def N(self):
+        return self.fx.shape[0]
+
+    @property
+    def levels(self):
+        return self.fl.shape[0]
+
+    @property
+    def bins(self):
+        return self.fs.shape[0]
+
+    @property
+    def rank(self):
+        return self.fx.shape[1]
+
+    def struct(self) -> Material:
+        if self.tables is None:
+            n = load().gsp_query_table_floats(self.levels, self.bins, self.rank)
+            self.tables = torch.empty(n, dtype=torch.float32, device=self.fx.device)
+        return Material(self.N, self.levels, self.bins, self.rank,
+                        *(_ptr(getattr(self, k), torch.float32, k) for k in
+                          ("fx", "fy", "fl", "fs", "ft", "lam")), _ptr(self.tables))
+
+    @staticmethod
+    def from_factors(f: dict) -> "QueryMaterial":
+        return QueryMaterial(f["fx"], f["fy"], f["fl"], f["fs"], f["ft"], f["lambda"])
+
+
+def build_query_tables(mat: QueryMaterial) -> None:
+    lib = load()
+    m = mat.struct()
+    check("gsp_build_query_tables", lib.gsp_build_query_tables(ctypes.byref(m), _stream()))
+
+
+def _mats(materials):
+    if isinstance(materials, QueryMaterial):
+        materials = [materials]
+    arr = (Material * len(materials))(*[m.struct() for m in materials])
+    return arr, len(materials)
+
+
+def range_query(materials, queries: torch.Tensor, out=None, status=None, tuning=None,
+                workspace=None) -> torch.Tensor:
+    """Batched range queries; `queries` is an int32 [n][8] tensor of descriptors."""
+    lib = load()
+    arr, nm = _mats(materials)
+    n = queries.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=queries.device)
+    if workspace is None:
+        workspace = torch.empty(16, dtype=torch.uint8, device=queries.device)
+    tn = QueryTuning(*tuning) if tuning is not None else None
+    check("gsp_range_query", lib.gsp_range_query(
+        arr, nm, _ptr(queries, torch.int32, "queries"), n, _ptr(out, torch.float32, "out"),
+        _ptr(status), ctypes.byref(tn) if tn is not None else None, _ptr(workspace),
+        workspace.numel(), _stream()))
+    return out
+
+
+def backward_workspace_bytes(materials) -> int:
+    arr, nm = _mats(materials)
+    return load().gsp_backward_workspace_bytes(arr, nm)
+
+
+def range_query_backward(materials, queries, gout, grads, status=None, workspace=None):
+    """Accumulate factor gradients: grads[m] = dict(dfx, dfy, dflw, dfs, dft)."""
+    lib = load()
+    arr, nm = _mats(materials)
+    garr = (MaterialGrad * nm)(*[MaterialGrad(*(_ptr(g[k], torch.float32, k) for k in
+                                                ("dfx", "dfy", "dflw", "dfs", "dft")))
+                                 for g in grads])
+    need = lib.gsp_backward_workspace_bytes(arr, nm)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=queries.device)
+    check("gsp_range_query_backward", lib.gsp_range_query_backward(
+        arr, nm, _ptr(queries, torch.int32, "queries"), queries.shape[0],
+        _ptr(gout, torch.float32, "gout"), garr, _ptr(workspace), workspace.numel(), _ptr(status),
+        _stream()))
+
+
+def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    lib = load()
+    check("gsp_adam_step", lib.gsp_adam_step(_ptr(param, torch.float32), _ptr(grad, torch.float32),
+                                             _ptr(m, torch.float32), _ptr(v, torch.float32),
+                                             param.numel(), int(step), float(lr), float(beta1),
+                                             float(beta2), float(eps), _stream()))
+
+
+# ----------------------------------------------------------------- a7 --
+
+class RangeQueryFn(torch.autograd.Function):
+    """q = range_query(fx, fy, flw, fs, ft; queries) with a hand-written adjoint.
+
+    The CP weights are folded into flw (lambda = 1), the parameterisation the
+    query tables use, so gradients come back for all five factor matrices."""
+
+    @staticmethod
+    def forward(ctx, queries, fx, fy, flw, fs, ft):
+        ones = torch.ones(fx.shape[1], dtype=torch.float32, device=fx.device)
+        mat = QueryMaterial(fx.contiguous(), fy.contiguous(), flw.contiguous(), fs.contiguous(),
+                            ft.contiguous(), ones)
+        build_query_tables(mat)
+        out = range_query(mat, queries)
+        ctx.mat = mat
+        ctx.save_for_backward(queries)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        (queries,) = ctx.saved_tensors
+        mat = ctx.mat
+        g = {k: torch.zeros_like(getattr(mat, a)) for k, a in
+             (("dfx", "fx"), ("dfy", "fy"), ("dflw", "fl"), ("dfs", "fs"), ("dft", "ft"))}
+        range_query_backward(mat, queries, gout.contiguous().float(), [g])
+        return None, g["dfx"], g["dfy"], g["dflw"], g["dfs"], g["dft"]
+
+
+def range_query_autograd(queries, fx, fy, flw, fs, ft):
+    return RangeQueryFn.apply(queries, fx, fy, flw, fs, ft)

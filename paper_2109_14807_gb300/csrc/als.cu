@@ -1,0 +1,706 @@
+// Rows a3-a4: CP decomposition of the footprint NDF tensor by alternating
+// least squares (Sec. 4.2, Eq. 3; CP-ALS of Kolda & Bader 2009).
+//
+// Per sweep, modes in the order x, y, l, s, t:
+//   Y'  = T contracted with fl (.) fs (.) ft          (one pass over T)
+//   x:  M_x = sum_y Y' fy      -> solve -> normalise
+//   y:  M_y = sum_x Y' fx_new  -> solve -> normalise
+//   Z'  = T contracted with fx_new (.) fy_new         (one pass over T)
+//   l:  M_l = sum_st Z' fs ft           -> solve -> normalise
+//   s:  M_s = sum_{l,t} Z' fl_new ft    -> solve -> normalise
+//   t:  M_t = sum_{l,s} Z' fl_new fs_new-> solve -> normalise -> fit
+// "solve" is A_n = M_n V^-1 with V the Hadamard product of the other four FP64
+// Gram matrices (FP64 Cholesky; pseudo-inverse by Jacobi eigendecomposition
+// when V is not numerically positive definite); "normalise" divides every
+// column by its 2-norm, which becomes lambda.  All small linear algebra is
+// FP64; the two passes over T are the MTTKRP kernels (FP32 FFMA or tcgen05).
+#include <math.h>
+
+#include "mttkrp.cuh"
+#include "ndf_build.cuh"
+
+namespace gsp {
+namespace {
+
+constexpr int kMaxCpRank = 128;
+constexpr int kJacobiMaxRank = 64;
+
+struct CpLayout {
+  size_t T, ping, bins, Yp, Zp, Zpart, KR, M, G, W, lam, fit, sumsq, norm2, flags, total;
+};
+
+size_t esize(int prec) { return prec == GSP_PREC_BF16 ? 2 : 4; }
+
+CpLayout cp_layout(const MttkrpDims& d, int prec) {
+  CpLayout o;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  const size_t N2 = static_cast<size_t>(d.N2()), B2 = static_cast<size_t>(d.B2());
+  const size_t L = d.L, R = d.R;
+  o.T = take(N2 * L * B2 * esize(prec));
+  o.ping = take(2 * N2 * B2 * sizeof(int32_t));
+  o.bins = take(N2 * sizeof(uint16_t));
+  o.Yp = take(N2 * R * sizeof(float));
+  o.Zp = take(L * B2 * R * sizeof(float));
+  o.Zpart = take(L * static_cast<size_t>(lst_chunks(d, prec)) * B2 * R * sizeof(float));
+  o.KR = take(R * L * B2 * sizeof(float));
+  size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
+  o.M = take(imax * R * sizeof(double));
+  o.G = take(5 * R * R * sizeof(double));
+  o.W = take(R * R * sizeof(double));
+  o.lam = take(R * sizeof(double));
+  o.fit = take(GSP_MAX_SWEEPS * sizeof(double));
+  o.sumsq = take(L * sizeof(unsigned long long));
+  o.norm2 = take(sizeof(double));
+  o.flags = take(16);
+  o.total = off;
+  return o;
+}
+
+bool valid_cp(int N, int L, int B, int R, int prec) {
+  return valid_map(N, L, B) && N >= 8 && B >= 8 && is_pow2(R) && R >= 8 && R <= kMaxCpRank &&
+         prec >= GSP_PREC_FP32 && prec <= GSP_PREC_BF16;
+}
+
+// --------------------------------------------------------------- kernels --
+
+// KR[(l*B2 + s*B + t)][r] = fl[l][r] fs[s][r] ft[t][r]   (row layout, FP32)
+__global__ void k_kr_rows(const float* __restrict__ fl, const float* __restrict__ fs,
+                          const float* __restrict__ ft, int L, int B, int R,
+                          float* __restrict__ out) {
+  long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  long long total = static_cast<long long>(L) * B * B * R;
+  if (i >= total) return;
+  int r = static_cast<int>(i % R);
+  long long k = i / R;
+  int t = static_cast<int>(k % B);
+  int s = static_cast<int>((k / B) % B);
+  int l = static_cast<int>(k / (static_cast<long long>(B) * B));
+  out[i] = fl[l * R + r] * fs[s * R + r] * ft[t * R + r];
+}
+
+// KRt[r][l*B2 + s*B + t] in the operand type (the K-major B operand of the
+// tensor-core pass)
+template <typename OutT>
+__global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict__ fs,
+                          const float* __restrict__ ft, int L, int B, int R,
+                          OutT* __restrict__ out) {
+  long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  long long K = static_cast<long long>(L) * B * B;
+  if (i >= K * R) return;
+  long long k = i % K;
+  int r = static_cast<int>(i / K);
+  int t = static_cast<int>(k % B);
+  int s = static_cast<int>((k / B) % B);
+  int l = static_cast<int>(k / (static_cast<long long>(B) * B));
+  float v = fl[l * R + r] * fs[s * R + r] * ft[t * R + r];
+  if constexpr (sizeof(OutT) == 2)
+    out[i] = __float2bfloat16_rn(v);
+  else
+    out[i] = v;
+}
+
+// Zp[l][st][r] = sum_c Zpart[l*C + c][st][r], fixed order
+__global__ void k_zreduce(const float* __restrict__ Zpart, float* __restrict__ Zp, int L, int C,
+                          long long per_level) {
+  long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (e >= per_level * L) return;
+  long long l = e / per_level, rem = e % per_level;
+  const float* p = Zpart + (l * C) * per_level + rem;
+  float acc = 0.0f;
+  for (int c = 0; c < C; ++c) acc += p[static_cast<long long>(c) * per_level];
+  Zp[e] = acc;
+}
+
+// M[i][r] = sum_{j1 < J1, j2 < J2} W[(i*wi + j1*w1 + j2*w2)][r] * A1[j1][r] * A2[j2][r]
+struct CParams {
+  const float* W;
+  long long wi, w1, w2;
+  int J1, J2;
+  const float* A1;
+  const float* A2;
+  int R;
+  double* M;
+  float* Mf;
+};
+
+__global__ void __launch_bounds__(256) k_contract(CParams p) {
+  __shared__ double red[256];
+  const int i = blockIdx.x;
+  const int R = p.R;
+  const int r = threadIdx.x % R;
+  const int jl = threadIdx.x / R;
+  const int JL = blockDim.x / R;
+  const long long J = static_cast<long long>(p.J1) * p.J2;
+  double acc = 0.0;
+  for (long long j = jl; j < J; j += JL) {
+    int j1 = static_cast<int>(j / p.J2), j2 = static_cast<int>(j % p.J2);
+    double v = static_cast<double>(p.W[(i * p.wi + j1 * p.w1 + j2 * p.w2) * R + r]);
+    if (p.A1) v *= static_cast<double>(p.A1[j1 * R + r]);
+    if (p.A2) v *= static_cast<double>(p.A2[j2 * R + r]);
+    acc += v;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = JL / 2; w > 0; w >>= 1) {
+    if (jl < w) red[threadIdx.x] += red[threadIdx.x + w * R];
+    __syncthreads();
+  }
+  if (jl == 0) {
+    if (p.M) p.M[i * R + r] = red[threadIdx.x];
+    if (p.Mf) p.Mf[i * R + r] = static_cast<float>(red[threadIdx.x]);
+  }
+}
+
+// G[r1][r2] = sum_i A[i][r1] A[i][r2], FP64
+__global__ void k_gram(const float* __restrict__ A, int I, int R, double* __restrict__ G) {
+  const int r1 = blockIdx.x, r2 = threadIdx.x;
+  double acc = 0.0;
+  for (int i = 0; i < I; ++i)
+    acc += static_cast<double>(A[i * R + r1]) * static_cast<double>(A[i * R + r2]);
+  G[r1 * R + r2] = acc;
+}
+
+// Hadamard product of the four Gram matrices other than `skip`.
+__device__ void hadamard_v(const double* __restrict__ G, int R, int skip, double* V) {
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    double v = 1.0;
+    for (int m = 0; m < 5; ++m)
+      if (m != skip) v *= G[m * R * R + e];
+    V[e] = v;
+  }
+}
+
+// Symmetric eigendecomposition by parallel cyclic Jacobi (Golub & Van Loan,
+// Alg. 8.4.2/8.4.3 with round-robin ordering).  V is overwritten by a
+// near-diagonal matrix, Q by the eigenvectors (columns).
+__device__ void jacobi_eigen(double* V, double* Q, int R) {
+  __shared__ double cs_c[kJacobiMaxRank / 2], cs_s[kJacobiMaxRank / 2];
+  __shared__ int cs_p[kJacobiMaxRank / 2], cs_q[kJacobiMaxRank / 2];
+  __shared__ int done;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Q[e] = (e / R == e % R) ? 1.0 : 0.0;
+  __syncthreads();
+  const int H = R / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) {
+      double off = 0.0, tot = 0.0;
+      for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b) {
+          double v = V[a * R + b] * V[a * R + b];
+          tot += v;
+          if (a != b) off += v;
+        }
+      done = off <= 1e-30 * tot;
+    }
+    __syncthreads();
+    if (done) break;
+    for (int k = 0; k < R - 1; ++k) {
+      for (int p = threadIdx.x; p < H; p += blockDim.x) {
+        int a = (k + p) % (R - 1), b = (k - p + R - 1) % (R - 1);
+        if (p == 0) b = R - 1;
+        int P = a < b ? a : b, Qi = a < b ? b : a;
+        double app = V[P * R + P], aqq = V[Qi * R + Qi], apq = V[P * R + Qi];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300) {
+          double tau = (aqq - app) / (2.0 * apq);
+          double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs_c[p] = c;
+        cs_s[p] = s;
+        cs_p[p] = P;
+        cs_q[p] = Qi;
+      }
+      __syncthreads();
+      for (int w = threadIdx.x; w < H * R; w += blockDim.x) {  // rows: V <- J^T V
+        int p = w / R, col = w % R;
+        int P = cs_p[p], Qi = cs_q[p];
+        double c = cs_c[p], s = cs_s[p];
+        double vp = V[P * R + col], vq = V[Qi * R + col];
+        V[P * R + col] = c * vp - s * vq;
+        V[Qi * R + col] = s * vp + c * vq;
+      }
+      __syncthreads();
+      for (int w = threadIdx.x; w < H * R; w += blockDim.x) {  // columns: V <- V J, Q <- Q J
+        int p = w / R, row = w % R;
+        int P = cs_p[p], Qi = cs_q[p];
+        double c = cs_c[p], s = cs_s[p];
+        double vp = V[row * R + P], vq = V[row * R + Qi];
+        V[row * R + P] = c * vp - s * vq;
+        V[row * R + Qi] = s * vp + c * vq;
+        double qp = Q[row * R + P], qq = Q[row * R + Qi];
+        Q[row * R + P] = c * qp - s * qq;
+        Q[row * R + Qi] = s * qp + c * qq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// In-place lower Cholesky factor of V (block-cooperative).  Returns false when
+// a pivot is not above thresh; block-uniform result.
+__device__ bool cholesky_inplace(double* V, int R, double thresh) {
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < R; ++j) {
+    if (threadIdx.x == 0) {
+      double d = V[j * R + j];
+      for (int k = 0; k < j; ++k) d -= V[j * R + k] * V[j * R + k];
+      if (!(d > thresh)) fail = 1;
+      else V[j * R + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (fail) return false;
+    const double djj = V[j * R + j];
+    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) {
+      double v = V[i * R + j];
+      for (int k = 0; k < j; ++k) v -= V[i * R + k] * V[j * R + k];
+      V[i * R + j] = v / djj;
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+__device__ double max_diag(const double* V, int R) {
+  __shared__ double mx;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int a = 0; a < R; ++a) m = fmax(m, fabs(V[a * R + a]));
+    mx = m;
+  }
+  __syncthreads();
+  return mx;
+}
+
+// One block: W = V^-1 by Cholesky.  When V is not numerically positive
+// definite, W = V^+ from a Jacobi eigendecomposition (R <= 64), or for larger
+// R the inverse of V + delta I with the smallest delta in 1e-12..1e-6 x
+// max diag that factorises; the fallback is flagged GSP_DEV_NUMERIC.
+__global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ G, int R, int skip,
+                                                  double* __restrict__ W, uint32_t* flags) {
+  extern __shared__ double smem[];
+  double* V = smem;          // [R][R]
+  double* Q = smem + R * R;  // [R][R] (eigenvectors, R <= 64 only)
+  const double eps = 2.220446049250313e-16;
+  hadamard_v(G, R, skip, V);
+  __syncthreads();
+  double mx = max_diag(V, R);
+  bool ok = cholesky_inplace(V, R, R * eps * mx);
+  if (!ok) {
+    if (threadIdx.x == 0 && flags) atomicOr(flags, GSP_DEV_NUMERIC);
+    if (R <= kJacobiMaxRank) {
+      hadamard_v(G, R, skip, V);
+      __syncthreads();
+      jacobi_eigen(V, Q, R);
+      double lmax = max_diag(V, R);
+      double cutoff = R * eps * lmax;
+      for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        int a = e / R, b = e % R;
+        double acc = 0.0;
+        for (int k = 0; k < R; ++k) {
+          double lam = V[k * R + k];
+          if (lam > cutoff) acc += Q[a * R + k] * Q[b * R + k] / lam;
+        }
+        W[e] = acc;
+      }
+      return;
+    }
+    const double deltas[3] = {1e-12, 1e-9, 1e-6};
+    for (int a = 0; a < 3 && !ok; ++a) {
+      hadamard_v(G, R, skip, V);
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int k = 0; k < R; ++k) V[k * R + k] += deltas[a] * mx;
+      __syncthreads();
+      ok = cholesky_inplace(V, R, R * eps * mx);
+    }
+    if (!ok) {  // leave the factor unchanged in scale: W = 0 makes A = 0 -> lambda = 0
+      for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = 0.0;
+      return;
+    }
+  }
+  // W = L^-T L^-1, one column per thread (column c is scratch for its solves)
+  for (int c = threadIdx.x; c < R; c += blockDim.x) {
+    for (int k = 0; k < R; ++k) {
+      double y = (k == c) ? 1.0 : 0.0;
+      for (int j = 0; j < k; ++j) y -= V[k * R + j] * W[j * R + c];
+      W[k * R + c] = y / V[k * R + k];
+    }
+    for (int k = R - 1; k >= 0; --k) {
+      double w = W[k * R + c];
+      for (int j = k + 1; j < R; ++j) w -= V[j * R + k] * W[j * R + c];
+      W[k * R + c] = w / V[k * R + k];
+    }
+  }
+}
+
+// A[i][c] = sum_k M[i][k] W[k][c]   (FP64 accumulate, FP32 out)
+__global__ void k_apply(const double* __restrict__ M, const double* __restrict__ W, int I, int R,
+                        float* __restrict__ A) {
+  long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (e >= static_cast<long long>(I) * R) return;
+  int i = static_cast<int>(e / R), c = static_cast<int>(e % R);
+  double acc = 0.0;
+  for (int k = 0; k < R; ++k) acc += M[i * R + k] * W[k * R + c];
+  A[e] = static_cast<float>(acc);
+}
+
+// lambda_c = ||A[:, c]||_2; A[:, c] /= lambda_c (left alone if zero)
+__global__ void __launch_bounds__(256) k_colnorm(float* __restrict__ A, int I, int R,
+                                                 double* __restrict__ lam64,
+                                                 float* __restrict__ lam32) {
+  __shared__ double red[256];
+  __shared__ double nrm;
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < I; i += blockDim.x) {
+    double v = A[i * R + c];
+    acc += v * v;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    nrm = sqrt(red[0]);
+    lam64[c] = nrm;
+    if (lam32) lam32[c] = static_cast<float>(nrm);
+  }
+  __syncthreads();
+  if (nrm > 0.0) {
+    for (int i = threadIdx.x; i < I; i += blockDim.x)
+      A[i * R + c] = static_cast<float>(static_cast<double>(A[i * R + c]) / nrm);
+  }
+}
+
+__global__ void k_norm2(const unsigned long long* __restrict__ sumsq, int L, int B, int raw,
+                        double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double acc = 0.0;
+  for (int l = 0; l < L; ++l) {
+    double sc = raw ? 1.0 : static_cast<double>(B) * B / (4.0 * ldexp(1.0, 2 * l));
+    acc += static_cast<double>(sumsq[l]) * sc * sc;
+  }
+  *out = acc;
+}
+
+// fit = 1 - sqrt(max(0, ||T||^2 + ||T_hat||^2 - 2 <T, T_hat>)) / ||T||
+__global__ void __launch_bounds__(256) k_fit(const double* __restrict__ Mt,
+                                             const float* __restrict__ ft,
+                                             const double* __restrict__ lam,
+                                             const double* __restrict__ G, int B, int R,
+                                             const double* __restrict__ norm2,
+                                             double* __restrict__ fit_out) {
+  __shared__ double ri[256], rh[256];
+  double inner = 0.0, hat = 0.0;
+  for (int e = threadIdx.x; e < B * R; e += blockDim.x) {
+    int r = e % R;
+    inner += lam[r] * Mt[e] * static_cast<double>(ft[e]);
+  }
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    int a = e / R, b = e % R;
+    double g = 1.0;
+    for (int m = 0; m < 5; ++m) g *= G[m * R * R + e];
+    hat += lam[a] * lam[b] * g;
+  }
+  ri[threadIdx.x] = inner;
+  rh[threadIdx.x] = hat;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      ri[threadIdx.x] += ri[threadIdx.x + w];
+      rh[threadIdx.x] += rh[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double n2 = *norm2;
+    double res = n2 + rh[0] - 2.0 * ri[0];
+    *fit_out = 1.0 - sqrt(res > 0.0 ? res : 0.0) / sqrt(n2);
+  }
+}
+
+// ------------------------------------------------------------ host side --
+
+struct Ctx {
+  MttkrpDims d;
+  int prec;
+  CpLayout lay;
+  char* ws;
+  cudaStream_t s;
+  template <typename T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+
+int ensure_smem_attr() {
+  static int done_dev = -1;
+  int dev = 0;
+  GSP_CUDA(cudaGetDevice(&dev));
+  if (done_dev != dev) {
+    // k_chol_inv: V (R*R doubles) plus eigenvectors for R <= 64: at most 128 KB
+    GSP_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxCpRank * kMaxCpRank * static_cast<int>(sizeof(double))));
+    done_dev = dev;
+  }
+  return GSP_OK;
+}
+
+int run_xy(const Ctx& c, const float* fl, const float* fs, const float* ft) {
+  const MttkrpDims& d = c.d;
+  long long K = static_cast<long long>(d.L) * d.B2();
+  if (c.prec == GSP_PREC_FP32) {
+    k_kr_rows<<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.R, c.at<float>(c.lay.KR));
+    GSP_CHECK_LAUNCH();
+    return simt_mttkrp_xy(c.at<float>(c.lay.T), c.at<float>(c.lay.KR), c.at<float>(c.lay.Yp), d, c.s);
+  }
+  if (c.prec == GSP_PREC_BF16)
+    k_kr_cols<__nv_bfloat16><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(
+        fl, fs, ft, d.L, d.B, d.R, c.at<__nv_bfloat16>(c.lay.KR));
+  else
+    k_kr_cols<float><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.R,
+                                                               c.at<float>(c.lay.KR));
+  GSP_CHECK_LAUNCH();
+  return tc_mttkrp_xy(c.ws + c.lay.T, c.ws + c.lay.KR, c.at<float>(c.lay.Yp), d, c.prec, c.s);
+}
+
+int run_lst(const Ctx& c, const float* fx, const float* fy) {
+  const MttkrpDims& d = c.d;
+  int C = lst_chunks(d, c.prec);
+  if (c.prec == GSP_PREC_FP32)
+    GSP_TRY(simt_mttkrp_lst(c.at<float>(c.lay.T), fx, fy, c.at<float>(c.lay.Zpart), d, C, c.s));
+  else
+    GSP_TRY(tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.at<float>(c.lay.Zpart), d, c.prec, C, c.s));
+  long long per_level = static_cast<long long>(d.B2()) * d.R;
+  k_zreduce<<<grid_for(per_level * d.L, 256), 256, 0, c.s>>>(c.at<float>(c.lay.Zpart),
+                                                             c.at<float>(c.lay.Zp), d.L, C, per_level);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+// mode 0..4 = x, y, l, s, t
+int contract(const Ctx& c, int mode, const gsp_cp_factors& f, double* M, float* Mf) {
+  const MttkrpDims& d = c.d;
+  CParams p{};
+  p.R = d.R;
+  p.M = M;
+  p.Mf = Mf;
+  int I = 0;
+  const long long B = d.B, B2 = d.B2(), N = d.N;
+  switch (mode) {
+    case 0:  // x: W = Y'[(y*N + x)]
+      p.W = c.at<float>(c.lay.Yp); p.wi = 1; p.w1 = N; p.w2 = 0; p.J1 = d.N; p.J2 = 1;
+      p.A1 = f.fy; p.A2 = nullptr; I = d.N;
+      break;
+    case 1:  // y
+      p.W = c.at<float>(c.lay.Yp); p.wi = N; p.w1 = 1; p.w2 = 0; p.J1 = d.N; p.J2 = 1;
+      p.A1 = f.fx; p.A2 = nullptr; I = d.N;
+      break;
+    case 2:  // l: W = Z'[l][s*B + t]
+      p.W = c.at<float>(c.lay.Zp); p.wi = B2; p.w1 = B; p.w2 = 1; p.J1 = d.B; p.J2 = d.B;
+      p.A1 = f.fs; p.A2 = f.ft; I = d.L;
+      break;
+    case 3:  // s
+      p.W = c.at<float>(c.lay.Zp); p.wi = B; p.w1 = B2; p.w2 = 1; p.J1 = d.L; p.J2 = d.B;
+      p.A1 = f.fl; p.A2 = f.ft; I = d.B;
+      break;
+    default:  // t
+      p.W = c.at<float>(c.lay.Zp); p.wi = 1; p.w1 = B2; p.w2 = B; p.J1 = d.L; p.J2 = d.B;
+      p.A1 = f.fl; p.A2 = f.fs; I = d.B;
+      break;
+  }
+  prof_begin(PROF_ALS_SMALL, c.s);
+  k_contract<<<I, 256, 0, c.s>>>(p);
+  prof_end(PROF_ALS_SMALL, c.s);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+float* factor_ptr(const gsp_cp_factors& f, int mode) {
+  switch (mode) {
+    case 0: return f.fx;
+    case 1: return f.fy;
+    case 2: return f.fl;
+    case 3: return f.fs;
+    default: return f.ft;
+  }
+}
+
+int mode_rows(const MttkrpDims& d, int mode) {
+  return mode < 2 ? d.N : mode == 2 ? d.L : d.B;
+}
+
+int gram(const Ctx& c, const gsp_cp_factors& f, int mode) {
+  const int R = c.d.R;
+  k_gram<<<R, R, 0, c.s>>>(factor_ptr(f, mode), mode_rows(c.d, mode), R,
+                           c.at<double>(c.lay.G) + static_cast<size_t>(mode) * R * R);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+int update(const Ctx& c, const gsp_cp_factors& f, int mode) {
+  const int R = c.d.R;
+  const int I = mode_rows(c.d, mode);
+  size_t smem = static_cast<size_t>(R) * R * sizeof(double) * (R <= kJacobiMaxRank ? 2 : 1);
+  prof_begin(PROF_ALS_SMALL, c.s);
+  k_chol_inv<<<1, 256, smem, c.s>>>(c.at<double>(c.lay.G), R, mode, c.at<double>(c.lay.W),
+                                    c.at<uint32_t>(c.lay.flags));
+  GSP_CHECK_LAUNCH();
+  float* A = factor_ptr(f, mode);
+  k_apply<<<grid_for(static_cast<long long>(I) * R, 256), 256, 0, c.s>>>(
+      c.at<double>(c.lay.M), c.at<double>(c.lay.W), I, R, A);
+  GSP_CHECK_LAUNCH();
+  k_colnorm<<<R, 256, 0, c.s>>>(A, I, R, c.at<double>(c.lay.lam), f.lambda);
+  GSP_CHECK_LAUNCH();
+  GSP_TRY(gram(c, f, mode));
+  prof_end(PROF_ALS_SMALL, c.s);
+  return GSP_OK;
+}
+
+int make_ctx(int N, int L, int B, int R, int prec, void* d_ws, size_t ws_bytes, gsp_stream st,
+             Ctx& c) {
+  if (!valid_cp(N, L, B, R, prec)) return GSP_ERR_INVALID_ARG;
+  c.d = MttkrpDims{N, L, B, R};
+  c.prec = prec;
+  if (prec != GSP_PREC_FP32 && !tc_supported(c.d, prec)) return GSP_ERR_UNSUPPORTED;
+  c.lay = cp_layout(c.d, prec);
+  if (!d_ws || ws_bytes < c.lay.total) return GSP_ERR_WORKSPACE;
+  c.ws = static_cast<char*>(d_ws);
+  c.s = to_stream(st);
+  return ensure_smem_attr();
+}
+
+bool valid_factors(const gsp_cp_factors* f) {
+  return f && f->fx && f->fy && f->fl && f->fs && f->ft && f->lambda;
+}
+
+}  // namespace
+}  // namespace gsp
+
+using namespace gsp;
+
+extern "C" size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precision) {
+  if (!valid_cp(N, levels, bins, rank, precision)) return 0;
+  MttkrpDims d{N, levels, bins, rank};
+  if (precision != GSP_PREC_FP32 && !tc_supported(d, precision)) return 0;
+  return cp_layout(d, precision).total;
+}
+
+extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, int N, int levels,
+                              int bins, int rank, const gsp_als_opts* opts, void* d_ws,
+                              size_t ws_bytes, uint32_t* d_status, gsp_stream stream) {
+  if (!opts || (d_hist == nullptr) == (d_normal_xy == nullptr)) return GSP_ERR_INVALID_ARG;
+  Ctx c;
+  GSP_TRY(make_ctx(N, levels, bins, rank, opts->precision, d_ws, ws_bytes, stream, c));
+  const MttkrpDims& d = c.d;
+  const long long slice = d.N2() * d.B2();
+  unsigned long long* sumsq = c.at<unsigned long long>(c.lay.sumsq);
+  GSP_CUDA(cudaMemsetAsync(sumsq, 0, sizeof(unsigned long long) * levels, c.s));
+  GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
+  auto sink_for = [&](int l, int32_t* h) {
+    LevelSink o{h, nullptr, nullptr, 1.0f, sumsq + l};
+    float sc = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
+    o.scale = sc;
+    if (c.prec == GSP_PREC_BF16)
+      o.bf16 = c.at<__nv_bfloat16>(c.lay.T) + slice * l;
+    else
+      o.f32 = c.at<float>(c.lay.T) + slice * l;
+    return o;
+  };
+  if (d_hist) {
+    for (int l = 0; l < levels; ++l)
+      GSP_TRY(launch_cast(d_hist + slice * l, N, bins, sink_for(l, nullptr), c.s));
+  } else {
+    uint16_t* bm = c.at<uint16_t>(c.lay.bins);
+    int32_t* ping[2] = {c.at<int32_t>(c.lay.ping), c.at<int32_t>(c.lay.ping) + slice};
+    GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, c.s));
+    GSP_TRY(launch_level0(bm, N, bins, sink_for(0, levels > 1 ? ping[0] : nullptr), c.s));
+    for (int l = 1; l < levels; ++l)
+      GSP_TRY(launch_double(ping[(l - 1) & 1], N, bins, l - 1,
+                            sink_for(l, l + 1 < levels ? ping[l & 1] : nullptr), c.s));
+  }
+  k_norm2<<<1, 32, 0, c.s>>>(sumsq, levels, bins, opts->raw_counts, c.at<double>(c.lay.norm2));
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+extern "C" int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_als_opts* opts,
+                             const gsp_cp_factors* f, gsp_als_report* h_report, void* d_ws,
+                             size_t ws_bytes, gsp_stream stream) {
+  if (!opts || !valid_factors(f) || opts->sweeps < 1 || opts->sweeps > GSP_MAX_SWEEPS ||
+      !(opts->tol >= 0.0))
+    return GSP_ERR_INVALID_ARG;
+  Ctx c;
+  GSP_TRY(make_ctx(N, levels, bins, rank, opts->precision, d_ws, ws_bytes, stream, c));
+  double* M = c.at<double>(c.lay.M);
+  double* fits = c.at<double>(c.lay.fit);
+  GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
+  for (int m = 0; m < 5; ++m) GSP_TRY(gram(c, *f, m));
+  int done = 0;
+  double prev = 0.0;
+  for (int sweep = 0; sweep < opts->sweeps; ++sweep) {
+    GSP_TRY(run_xy(c, f->fl, f->fs, f->ft));
+    GSP_TRY(contract(c, 0, *f, M, nullptr));
+    GSP_TRY(update(c, *f, 0));
+    GSP_TRY(contract(c, 1, *f, M, nullptr));
+    GSP_TRY(update(c, *f, 1));
+    GSP_TRY(run_lst(c, f->fx, f->fy));
+    for (int m = 2; m < 5; ++m) {
+      GSP_TRY(contract(c, m, *f, M, nullptr));
+      GSP_TRY(update(c, *f, m));
+    }
+    k_fit<<<1, 256, 0, c.s>>>(M, f->ft, c.at<double>(c.lay.lam), c.at<double>(c.lay.G), bins,
+                              rank, c.at<double>(c.lay.norm2), fits + sweep);
+    GSP_CHECK_LAUNCH();
+    done = sweep + 1;
+    if (opts->tol > 0.0) {
+      double cur = 0.0;
+      GSP_CUDA(cudaMemcpyAsync(&cur, fits + sweep, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      GSP_CUDA(cudaStreamSynchronize(c.s));
+      if (sweep > 0 && fabs(cur - prev) < opts->tol) break;
+      prev = cur;
+    }
+  }
+  if (h_report) {
+    h_report->sweeps_done = done;
+    uint32_t flags = 0;
+    GSP_CUDA(cudaMemcpyAsync(h_report->fit, fits, sizeof(double) * done, cudaMemcpyDeviceToHost, c.s));
+    GSP_CUDA(cudaMemcpyAsync(&flags, c.ws + c.lay.flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.s));
+    GSP_CUDA(cudaStreamSynchronize(c.s));
+    h_report->numeric_fallbacks = (flags & GSP_DEV_NUMERIC) ? 1 : 0;
+  }
+  return GSP_OK;
+}
+
+extern "C" int gsp_cp_decompose(const int32_t* d_hist, const float* d_normal_xy, int N,
+                                int levels, int bins, int rank, const gsp_als_opts* opts,
+                                const gsp_cp_factors* f, gsp_als_report* h_report, void* d_ws,
+                                size_t ws_bytes, uint32_t* d_status, gsp_stream stream) {
+  GSP_TRY(gsp_cp_prepare(d_hist, d_normal_xy, N, levels, bins, rank, opts, d_ws, ws_bytes,
+                         d_status, stream));
+  return gsp_cp_sweeps(N, levels, bins, rank, opts, f, h_report, d_ws, ws_bytes, stream);
+}
+
+extern "C" int gsp_cp_mttkrp(int N, int levels, int bins, int rank, int precision,
+                             const gsp_cp_factors* f, float* const d_m[5], void* d_ws,
+                             size_t ws_bytes, gsp_stream stream) {
+  if (!f || !f->fx || !f->fy || !f->fl || !f->fs || !f->ft || !d_m) return GSP_ERR_INVALID_ARG;
+  for (int m = 0; m < 5; ++m)
+    if (!d_m[m]) return GSP_ERR_INVALID_ARG;
+  Ctx c;
+  GSP_TRY(make_ctx(N, levels, bins, rank, precision, d_ws, ws_bytes, stream, c));
+  GSP_TRY(run_xy(c, f->fl, f->fs, f->ft));
+  GSP_TRY(contract(c, 0, *f, nullptr, d_m[0]));
+  GSP_TRY(contract(c, 1, *f, nullptr, d_m[1]));
+  GSP_TRY(run_lst(c, f->fx, f->fy));
+  for (int m = 2; m < 5; ++m) GSP_TRY(contract(c, m, *f, nullptr, d_m[m]));
+  return GSP_OK;
+}

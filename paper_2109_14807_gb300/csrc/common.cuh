@@ -1,0 +1,79 @@
+// Shared helpers of the CUDA library (host and device).  No method arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gsp.h"
+
+namespace gsp {
+
+// Last failing cudaError_t of this host thread (read by gsp_last_cuda_error).
+int& last_cuda_error();
+
+inline int cuda_fail(cudaError_t e) {
+  last_cuda_error() = static_cast<int>(e);
+  return GSP_ERR_CUDA;
+}
+
+#define GSP_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t gsp_e_ = (call);                         \
+    if (gsp_e_ != cudaSuccess) return gsp::cuda_fail(gsp_e_); \
+  } while (0)
+
+// Every kernel launch is followed by GSP_CHECK_LAUNCH(): it counts the launch
+// and turns a launch error into GSP_ERR_CUDA.
+void count_launch();
+#define GSP_CHECK_LAUNCH() \
+  do {                     \
+    gsp::count_launch();   \
+    GSP_CUDA(cudaGetLastError()); \
+  } while (0)
+
+enum ProfId {
+  PROF_BINS = 0, PROF_LEVEL0, PROF_DOUBLE, PROF_CAST, PROF_MTTKRP_XY, PROF_MTTKRP_LST,
+  PROF_ALS_SMALL, PROF_TABLES, PROF_QUERY, PROF_QUERY_BWD, PROF_ADAM, PROF_COUNT
+};
+// Event pair around one launch (no-ops unless profiling is enabled).
+void prof_begin(int id, cudaStream_t s);
+void prof_end(int id, cudaStream_t s);
+
+#define GSP_TRY(expr)               \
+  do {                              \
+    int gsp_rc_ = (expr);           \
+    if (gsp_rc_ != GSP_OK) return gsp_rc_; \
+  } while (0)
+
+inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+inline int ilog2(long long v) {
+  int l = 0;
+  while ((1LL << (l + 1)) <= v) ++l;
+  return l;
+}
+
+inline cudaStream_t to_stream(gsp_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Streaming-multiprocessor count of the current device (cached per device).
+int sm_count();
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline unsigned grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return static_cast<unsigned>(b < 1 ? 1 : b);
+}
+
+// Checks shared by the NDF-building calls.
+inline bool valid_map(int N, int levels, int bins) {
+  return is_pow2(N) && N >= 2 && N <= 4096 && levels >= 1 && levels <= ilog2(N) + 1 &&
+         is_pow2(bins) && bins >= 4 && bins <= 128;
+}
+
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {
+  if (status) atomicOr(status, bits);
+}
+
+}  // namespace gsp

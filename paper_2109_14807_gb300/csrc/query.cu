@@ -1,0 +1,480 @@
+// Rows a5-a7: query tables (1D summed-area tables, Sec. 4.4), the batched
+// spatio-angular range query (Eq. 5 over five modes, Sec. 4.3-4.4), its adjoint
+// and the Adam refinement step.
+//
+// Query mapping: a group of LANES consecutive lanes serves one query, lane j
+// handling ranks j, j + LANES, ...; the rank sum is a butterfly shuffle inside
+// the group.  Every table row a query touches is read by the group as one
+// contiguous run (coalesced), and the small per-material tables stay resident
+// in L1/L2.  Warps claim `chunk` groups of queries at a time from a global
+// counter (persistent CTAs, dynamic balance over uneven materials).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace gsp {
+namespace {
+
+struct MatParams {
+  gsp_material m[GSP_MAX_MATERIALS];
+  int n;
+};
+
+// The SAT region starts after flw, padded to a multiple of 4 floats so that
+// its float4 rows are 16-byte aligned.
+__host__ __device__ __forceinline__ size_t flw_floats(int L, int R) {
+  return (static_cast<size_t>(L) * R + 3) / 4 * 4;
+}
+
+struct GradParams {
+  gsp_material_grad g[GSP_MAX_MATERIALS];
+  float* dps[GSP_MAX_MATERIALS];  // [B+1][R] gradient w.r.t. the s-table prefix sums
+  float* dpt[GSP_MAX_MATERIALS];
+};
+
+// ---------------------------------------------------------------- tables --
+__global__ void k_tables(const float* __restrict__ fl, const float* __restrict__ lambda,
+                         const float* __restrict__ fs, const float* __restrict__ ft, int L,
+                         int B, int R, float* __restrict__ tables) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const float lam = lambda[r];
+  for (int l = 0; l < L; ++l) tables[l * R + r] = fl[l * R + r] * lam;
+  float4* sat = reinterpret_cast<float4*>(tables + flw_floats(L, R));
+  for (int side = 0; side < 2; ++side) {
+    const float* f = side == 0 ? fs : ft;
+    float4* t = sat + static_cast<size_t>(side) * (B + 1) * R;
+    double P = 0.0;  // running prefix sum, FP64
+    for (int i = 0; i <= B; ++i) {
+      float hi = static_cast<float>(P);
+      float lo = static_cast<float>(P - static_cast<double>(hi));
+      float fi = i < B ? f[i * R + r] : 0.0f;
+      t[static_cast<size_t>(i) * R + r] = make_float4(hi, lo, fi, 0.0f);
+      if (i < B) P += static_cast<double>(fi);
+    }
+  }
+}
+
+// ----------------------------------------------------------- query terms --
+// Everything a query needs besides per-rank table reads.
+struct QTerms {
+  int x, y, l0, l1;
+  float f;          // level blend weight of l1
+  int is0, is1, it0, it1;
+  float fs0, fs1, ft0, ft1;  // fractional parts of the range ends
+  float inv_ws, inv_wt;      // 1 / width, 0 for a zero-width side
+  int isz, itz;              // bin of a zero-width side
+  bool ok;
+};
+
+__device__ __forceinline__ void load_query(const gsp_query* __restrict__ q, long long i,
+                                           gsp_query& d) {
+  const int4* p = reinterpret_cast<const int4*>(q + i);
+  int4 a = __ldg(p), b = __ldg(p + 1);
+  d.x = a.x;
+  d.y = a.y;
+  d.level = __int_as_float(a.z);
+  d.s0 = __int_as_float(a.w);
+  d.s1 = __int_as_float(b.x);
+  d.t0 = __int_as_float(b.y);
+  d.t1 = __int_as_float(b.z);
+  d.material = static_cast<uint32_t>(b.w);
+}
+
+__device__ __forceinline__ void range_side(float a, float b, int B, int& i0, int& i1, float& f0,
+                                           float& f1, float& inv_w, int& iz) {
+  a = fminf(fmaxf(a, 0.0f), static_cast<float>(B));
+  b = fminf(fmaxf(b, 0.0f), static_cast<float>(B));
+  if (b < a) {
+    float t = a;
+    a = b;
+    b = t;
+  }
+  float fa = floorf(a), fb = floorf(b);
+  i0 = static_cast<int>(fa);
+  i1 = static_cast<int>(fb);
+  f0 = a - fa;
+  f1 = b - fb;
+  float w = b - a;
+  inv_w = w > 0.0f ? 1.0f / w : 0.0f;
+  iz = min(i0, B - 1);
+}
+
+__device__ __forceinline__ QTerms query_terms(const gsp_query& d, const gsp_material& M) {
+  QTerms t;
+  const int N = M.N, L = M.levels, B = M.bins;
+  t.ok = isfinite(d.level) && isfinite(d.s0) && isfinite(d.s1) && isfinite(d.t0) &&
+         isfinite(d.t1);
+  t.x = d.x & (N - 1);  // N is a power of two: two's complement wrap
+  t.y = d.y & (N - 1);
+  float lev = t.ok ? fminf(fmaxf(d.level, 0.0f), static_cast<float>(L - 1)) : 0.0f;
+  float fl0 = floorf(lev);
+  t.l0 = static_cast<int>(fl0);
+  t.f = lev - fl0;
+  t.l1 = min(t.l0 + 1, L - 1);
+  range_side(t.ok ? d.s0 : 0.f, t.ok ? d.s1 : 0.f, B, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
+  range_side(t.ok ? d.t0 : 0.f, t.ok ? d.t1 : 0.f, B, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
+  return t;
+}
+
+// Range average of one rank from two SAT rows (hi/lo split prefix sums).
+__device__ __forceinline__ float sat_mean(const float4* __restrict__ sat, int R, int r, int i0,
+                                          int i1, float f0, float f1, float inv_w, int iz) {
+  if (inv_w > 0.0f) {
+    float4 p0 = __ldg(sat + static_cast<size_t>(i0) * R + r);
+    float4 p1 = __ldg(sat + static_cast<size_t>(i1) * R + r);
+    float dh = p1.x - p0.x;
+    float dl = fmaf(f1, p1.z, p1.y) - fmaf(f0, p0.z, p0.y);
+    return (dh + dl) * inv_w;
+  }
+  return __ldg(reinterpret_cast<const float*>(sat + static_cast<size_t>(iz) * R + r) + 2);
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ MatParams mp,
+                                                     const gsp_query* __restrict__ q,
+                                                     long long n, float* __restrict__ out,
+                                                     uint32_t* status,
+                                                     unsigned long long* counter, int chunk) {
+  constexpr int QPW = 32 / LANES;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LANES;
+  const int j = lane % LANES;
+  const long long per_grab = static_cast<long long>(chunk) * QPW;
+  const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+  const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  long long grab = 0;
+  for (;;) {
+    long long base;
+    if (counter) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(counter, static_cast<unsigned long long>(per_grab));
+      base = static_cast<long long>(__shfl_sync(0xffffffffu, b, 0));
+    } else {
+      base = (warp_id + grab * n_warps) * per_grab;
+      ++grab;
+    }
+    if (base >= n) break;
+    for (int c = 0; c < chunk; ++c) {
+      const long long qi = base + static_cast<long long>(c) * QPW + sub;
+      float v = 0.0f;
+      bool bad = false;
+      if (qi < n) {
+        gsp_query d;
+        load_query(q, qi, d);
+        if (d.material >= static_cast<uint32_t>(mp.n)) {
+          bad = true;
+        } else {
+          const gsp_material& M = mp.m[d.material];
+          QTerms t = query_terms(d, M);
+          bad = !t.ok;
+          const int R = M.rank;
+          const float* __restrict__ flw = M.tables;
+          const float4* sats = reinterpret_cast<const float4*>(M.tables + flw_floats(M.levels, R));
+          const float4* satt = sats + static_cast<size_t>(M.bins + 1) * R;
+          const float* __restrict__ fxr = M.fx + static_cast<size_t>(t.x) * R;
+          const float* __restrict__ fyr = M.fy + static_cast<size_t>(t.y) * R;
+          const float* __restrict__ fl0 = flw + static_cast<size_t>(t.l0) * R;
+          const float* __restrict__ fl1 = flw + static_cast<size_t>(t.l1) * R;
+          const float g0 = 1.0f - t.f;
+          for (int r = j; r < R; r += LANES) {
+            float lv = fmaf(t.f, __ldg(fl1 + r), g0 * __ldg(fl0 + r));
+            float S = sat_mean(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
+            float T = sat_mean(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
+            v = fmaf(__ldg(fxr + r) * __ldg(fyr + r), lv * S * T, v);
+          }
+        }
+      }
+#pragma unroll
+      for (int off = LANES / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (qi < n && j == 0) {
+        if (bad) {
+          out[qi] = __int_as_float(0x7fc00000);
+          set_status(status, GSP_DEV_BAD_QUERY);
+        } else {
+          out[qi] = v;
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------- adjoint --
+template <int LANES>
+__global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__ MatParams mp,
+                                                         const __grid_constant__ GradParams gp,
+                                                         const gsp_query* __restrict__ q,
+                                                         long long n,
+                                                         const float* __restrict__ gout,
+                                                         uint32_t* status) {
+  constexpr int QPW = 32 / LANES;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LANES;
+  const int j = lane % LANES;
+  const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+  const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  for (long long base = warp_id * QPW; base < n; base += n_warps * QPW) {
+    const long long qi = base + sub;
+    if (qi >= n) continue;
+    gsp_query d;
+    load_query(q, qi, d);
+    if (d.material >= static_cast<uint32_t>(mp.n)) {
+      if (j == 0) set_status(status, GSP_DEV_BAD_QUERY);
+      continue;
+    }
+    const int m = d.material;
+    const gsp_material& M = mp.m[m];
+    QTerms t = query_terms(d, M);
+    if (!t.ok) {
+      if (j == 0) set_status(status, GSP_DEV_BAD_QUERY);
+      continue;
+    }
+    const float g = __ldg(gout + qi);
+    if (g == 0.0f) continue;
+    const int R = M.rank;
+    const float* flw = M.tables;
+    const float4* sats = reinterpret_cast<const float4*>(M.tables + flw_floats(M.levels, R));
+    const float4* satt = sats + static_cast<size_t>(M.bins + 1) * R;
+    const gsp_material_grad& G = gp.g[m];
+    float* dps = gp.dps[m];
+    float* dpt = gp.dpt[m];
+    const float g0 = 1.0f - t.f;
+    for (int r = j; r < R; r += LANES) {
+      float a0 = __ldg(flw + t.l0 * R + r), a1 = __ldg(flw + t.l1 * R + r);
+      float lv = fmaf(t.f, a1, g0 * a0);
+      float S = sat_mean(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
+      float T = sat_mean(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
+      float xv = __ldg(M.fx + t.x * R + r), yv = __ldg(M.fy + t.y * R + r);
+      float xy = xv * yv;
+      float st = S * T;
+      atomicAdd(G.dfx + t.x * R + r, g * yv * lv * st);
+      atomicAdd(G.dfy + t.y * R + r, g * xv * lv * st);
+      atomicAdd(G.dflw + t.l0 * R + r, g * g0 * xy * st);
+      if (t.f != 0.0f) atomicAdd(G.dflw + t.l1 * R + r, g * t.f * xy * st);
+      // Sbar = (F(s1) - F(s0)) / w with F(s) = P[floor s] + frac(s) fs[floor s]
+      float cs = g * xy * lv * T;
+      if (t.inv_ws > 0.0f) {
+        float a = cs * t.inv_ws;
+        atomicAdd(dps + t.is1 * R + r, a);
+        atomicAdd(dps + t.is0 * R + r, -a);
+        if (t.fs1 != 0.0f) atomicAdd(G.dfs + t.is1 * R + r, a * t.fs1);
+        if (t.fs0 != 0.0f) atomicAdd(G.dfs + t.is0 * R + r, -a * t.fs0);
+      } else {
+        atomicAdd(G.dfs + t.isz * R + r, cs);
+      }
+      float ct = g * xy * lv * S;
+      if (t.inv_wt > 0.0f) {
+        float a = ct * t.inv_wt;
+        atomicAdd(dpt + t.it1 * R + r, a);
+        atomicAdd(dpt + t.it0 * R + r, -a);
+        if (t.ft1 != 0.0f) atomicAdd(G.dft + t.it1 * R + r, a * t.ft1);
+        if (t.ft0 != 0.0f) atomicAdd(G.dft + t.it0 * R + r, -a * t.ft0);
+      } else {
+        atomicAdd(G.dft + t.itz * R + r, ct);
+      }
+    }
+  }
+}
+
+// dP[i] is the gradient w.r.t. P[i] = sum_{k<i} f[k]; so df[k] += sum_{i>k} dP[i].
+__global__ void k_suffix(const float* __restrict__ dp, float* __restrict__ df, int B, int R) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  float acc = 0.0f;
+  for (int i = B; i >= 1; --i) {
+    acc += dp[i * R + r];
+    df[(i - 1) * R + r] += acc;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+  float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+  m[i] = mi;
+  v[i] = vi;
+  float mh = mi / c1, vh = vi / c2;
+  p[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+bool valid_material(const gsp_material& m) {
+  return is_pow2(m.N) && m.N >= 1 && m.N <= (1 << 20) && m.levels >= 1 && m.levels <= 64 &&
+         m.bins >= 1 && m.bins <= 4096 && m.rank >= 1 && m.rank <= 256 && m.fx && m.fy &&
+         m.tables && (reinterpret_cast<uintptr_t>(m.tables) & 15) == 0;
+}
+
+int pick_lanes(const gsp_material* mats, int n_mats, const gsp_query_tuning* tn) {
+  if (tn && tn->lanes_per_query) return tn->lanes_per_query;
+  int rmax = 1;
+  for (int i = 0; i < n_mats; ++i) rmax = rmax > mats[i].rank ? rmax : mats[i].rank;
+  int lanes = 4;
+  while (lanes < rmax && lanes < 32) lanes *= 2;
+  return lanes;
+}
+
+}  // namespace
+}  // namespace gsp
+
+using namespace gsp;
+
+extern "C" size_t gsp_query_table_floats(int levels, int bins, int rank) {
+  if (levels < 1 || bins < 1 || rank < 1) return 0;
+  return flw_floats(levels, rank) + 8 * static_cast<size_t>(bins + 1) * rank;
+}
+
+extern "C" int gsp_build_query_tables(const gsp_material* h_mat, gsp_stream stream) {
+  if (!h_mat) return GSP_ERR_INVALID_ARG;
+  const gsp_material& m = *h_mat;
+  if (!valid_material(m) || !m.fl || !m.fs || !m.ft || !m.lambda) return GSP_ERR_INVALID_ARG;
+  int threads = 64;
+  prof_begin(PROF_TABLES, to_stream(stream));
+  k_tables<<<grid_for(m.rank, threads), threads, 0, to_stream(stream)>>>(
+      m.fl, m.lambda, m.fs, m.ft, m.levels, m.bins, m.rank, m.tables);
+  prof_end(PROF_TABLES, to_stream(stream));
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+extern "C" int gsp_range_query(const gsp_material* h_mats, int n_mats, const gsp_query* d_q,
+                               int64_t n, float* d_out, uint32_t* d_status,
+                               const gsp_query_tuning* tuning, void* d_ws, size_t ws_bytes,
+                               gsp_stream stream) {
+  if (!h_mats || n_mats < 1 || n_mats > GSP_MAX_MATERIALS || n < 0) return GSP_ERR_INVALID_ARG;
+  if (n > 0 && (!d_q || !d_out || (reinterpret_cast<uintptr_t>(d_q) & 15))) return GSP_ERR_INVALID_ARG;
+  MatParams mp;
+  mp.n = n_mats;
+  for (int i = 0; i < n_mats; ++i) {
+    if (!valid_material(h_mats[i])) return GSP_ERR_INVALID_ARG;
+    mp.m[i] = h_mats[i];
+  }
+  if (n == 0) return GSP_OK;
+  int lanes = pick_lanes(h_mats, n_mats, tuning);
+  int threads = tuning && tuning->threads ? tuning->threads : 256;
+  int bpsm = tuning && tuning->blocks_per_sm ? tuning->blocks_per_sm : 8;
+  int chunk = tuning && tuning->chunk ? tuning->chunk : 4;
+  if (threads < 32 || threads > 256 || threads % 32 || bpsm < 1 || bpsm > 32 || chunk < 1 ||
+      chunk > 64)
+    return GSP_ERR_INVALID_ARG;
+  cudaStream_t s = to_stream(stream);
+  unsigned long long* counter = nullptr;
+  if (d_ws) {
+    if (ws_bytes < 16) return GSP_ERR_WORKSPACE;
+    counter = static_cast<unsigned long long*>(d_ws);
+    GSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+  }
+  long long warps_needed = (n + (32 / lanes) * chunk - 1) / ((32 / lanes) * chunk);
+  long long blocks = static_cast<long long>(sm_count()) * bpsm;
+  long long need = (warps_needed * 32 + threads - 1) / threads;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  prof_begin(PROF_QUERY, s);
+  switch (lanes) {
+    case 4:
+      k_range_query<4><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+    case 8:
+      k_range_query<8><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+    case 16:
+      k_range_query<16><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+    case 32:
+      k_range_query<32><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+    default:
+      return GSP_ERR_INVALID_ARG;
+  }
+  prof_end(PROF_QUERY, s);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+extern "C" size_t gsp_backward_workspace_bytes(const gsp_material* h_mats, int n_mats) {
+  if (!h_mats || n_mats < 1 || n_mats > GSP_MAX_MATERIALS) return 0;
+  size_t total = 0;
+  for (int i = 0; i < n_mats; ++i)
+    total += 2 * align_up(static_cast<size_t>(h_mats[i].bins + 1) * h_mats[i].rank * sizeof(float), 256);
+  return total;
+}
+
+extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
+                                        const gsp_query* d_q, int64_t n, const float* d_gout,
+                                        const gsp_material_grad* h_grads, void* d_ws,
+                                        size_t ws_bytes, uint32_t* d_status, gsp_stream stream) {
+  if (!h_mats || !h_grads || n_mats < 1 || n_mats > GSP_MAX_MATERIALS || n < 0)
+    return GSP_ERR_INVALID_ARG;
+  if (n > 0 && (!d_q || !d_gout || (reinterpret_cast<uintptr_t>(d_q) & 15))) return GSP_ERR_INVALID_ARG;
+  size_t need = gsp_backward_workspace_bytes(h_mats, n_mats);
+  if (!d_ws || ws_bytes < need) return GSP_ERR_WORKSPACE;
+  MatParams mp;
+  GradParams gp;
+  mp.n = n_mats;
+  char* w = static_cast<char*>(d_ws);
+  for (int i = 0; i < n_mats; ++i) {
+    const gsp_material& m = h_mats[i];
+    const gsp_material_grad& g = h_grads[i];
+    if (!valid_material(m) || !g.dfx || !g.dfy || !g.dflw || !g.dfs || !g.dft)
+      return GSP_ERR_INVALID_ARG;
+    mp.m[i] = m;
+    gp.g[i] = g;
+    size_t b = align_up(static_cast<size_t>(m.bins + 1) * m.rank * sizeof(float), 256);
+    gp.dps[i] = reinterpret_cast<float*>(w);
+    gp.dpt[i] = reinterpret_cast<float*>(w + b);
+    w += 2 * b;
+  }
+  cudaStream_t s = to_stream(stream);
+  GSP_CUDA(cudaMemsetAsync(d_ws, 0, need, s));
+  if (n > 0) {
+    int lanes = pick_lanes(h_mats, n_mats, nullptr);
+    const int threads = 256;
+    long long warps = (n + (32 / lanes) - 1) / (32 / lanes);
+    long long blocks = (warps * 32 + threads - 1) / threads;
+    long long cap = static_cast<long long>(sm_count()) * 8;
+    if (blocks > cap) blocks = cap;
+    prof_begin(PROF_QUERY_BWD, s);
+    switch (lanes) {
+      case 4:
+        k_range_query_bwd<4><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        break;
+      case 8:
+        k_range_query_bwd<8><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        break;
+      case 16:
+        k_range_query_bwd<16><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        break;
+      default:
+        k_range_query_bwd<32><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        break;
+    }
+    prof_end(PROF_QUERY_BWD, s);
+    GSP_CHECK_LAUNCH();
+  }
+  for (int i = 0; i < n_mats; ++i) {
+    int R = h_mats[i].rank;
+    k_suffix<<<grid_for(R, 64), 64, 0, s>>>(gp.dps[i], h_grads[i].dfs, h_mats[i].bins, R);
+    GSP_CHECK_LAUNCH();
+    k_suffix<<<grid_for(R, 64), 64, 0, s>>>(gp.dpt[i], h_grads[i].dft, h_mats[i].bins, R);
+    GSP_CHECK_LAUNCH();
+  }
+  return GSP_OK;
+}
+
+extern "C" int gsp_adam_step(float* d_param, const float* d_grad, float* d_m, float* d_v,
+                             int64_t n, int step, float lr, float beta1, float beta2, float eps,
+                             gsp_stream stream) {
+  if (n < 0 || step < 1 || (n > 0 && (!d_param || !d_grad || !d_m || !d_v)))
+    return GSP_ERR_INVALID_ARG;
+  if (n == 0) return GSP_OK;
+  float c1 = static_cast<float>(1.0 - pow(static_cast<double>(beta1), step));
+  float c2 = static_cast<float>(1.0 - pow(static_cast<double>(beta2), step));
+  prof_begin(PROF_ADAM, to_stream(stream));
+  k_adam<<<grid_for(n, 256), 256, 0, to_stream(stream)>>>(d_param, d_grad, d_m, d_v, n, lr, beta1,
+                                                          beta2, eps, c1, c2);
+  prof_end(PROF_ADAM, to_stream(stream));
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}

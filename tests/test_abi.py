@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol
+include/gsp.h declares; host-side argument checks answer without a GPU."""
+import ctypes
+import shutil
+
+import pytest
+
+from paper_2109_14807_gb300 import _lib, build
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not build.up_to_date(),
+                                reason="nvcc not available to build libgsp.so")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _lib.header_symbols()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # every declared function has a ctypes signature in the binding
+    assert set(names) == set(_lib._SIGS)
+
+
+def test_struct_sizes_match_header():
+    assert ctypes.sizeof(_lib.Material) == 16 + 7 * 8
+    assert ctypes.sizeof(_lib.AlsOpts) == 24
+    assert ctypes.sizeof(_lib.AlsReport) == 8 + 8 * _lib.MAX_SWEEPS
+    assert ctypes.sizeof(_lib.QueryTuning) == 16
+    assert ctypes.sizeof(_lib.CpFactors) == 6 * 8
+    import synth
+    assert synth.QUERY_DTYPE.itemsize == 32
+
+
+def test_host_side_sizes_and_validation(lib):
+    assert lib.gsp_version() >= 10000
+    assert lib.gsp_strerror(0) == b"ok"
+    assert lib.gsp_strerror(-3) == b"workspace too small"
+    # sizes
+    assert lib.gsp_build_workspace_bytes(32, 6, 16) >= 32 * 32 * 2
+    assert lib.gsp_build_workspace_bytes(33, 6, 16) == 0          # N not a power of two
+    assert lib.gsp_build_workspace_bytes(32, 7, 16) == 0          # too many levels
+    assert lib.gsp_query_table_floats(6, 16, 8) == 6 * 8 + 8 * 17 * 8
+    assert lib.gsp_query_table_floats(5, 8, 3) == 16 + 8 * 9 * 3   # flw padded to 4 floats
+    assert lib.gsp_cp_workspace_bytes(32, 6, 16, 8, 0) > 32 * 32 * 6 * 256 * 4
+    assert lib.gsp_cp_workspace_bytes(32, 6, 16, 12, 0) == 0      # rank not a power of two
+    assert lib.gsp_cp_workspace_bytes(32, 6, 16, 8, 3) == 0       # unknown precision
+    # argument errors are returned before anything is enqueued
+    assert lib.gsp_build_footprint_ndfs(None, 32, 6, 16, None, None, 0, None, None) == -1
+    assert lib.gsp_range_query(None, 1, None, 10, None, None, None, None, 0, None) == -1
+    m = _lib.Material()
+    assert lib.gsp_range_query(ctypes.byref(m), 0, None, 0, None, None, None, None, 0, None) == -1
+    assert lib.gsp_range_query(ctypes.byref(m), 17, None, 0, None, None, None, None, 0, None) == -1
+    assert lib.gsp_adam_step(None, None, None, None, 5, 1, 1e-3, 0.9, 0.999, 1e-8, None) == -1
+    opts = _lib.AlsOpts(0, 0, 0.0, 0, 0)
+    f = _lib.CpFactors()
+    assert lib.gsp_cp_sweeps(32, 6, 16, 8, ctypes.byref(opts), ctypes.byref(f), None, None, 0,
+                             None) == -1

@@ -1,0 +1,133 @@
+"""GPU parity of the CP-ALS path (rows a3-a4): the five MTTKRPs element by
+element against the oracle's dense MTTKRP, and ALS fits against the FP64
+oracle's CP-ALS from the same initial factors."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cp, ndf
+from _gpu import dev, lib, oracle_material, query_error, QUERY_TOL
+
+pytestmark = pytest.mark.gpu
+
+# MTTKRP tolerance relative to the magnitude scale sum |X| prod |A| of each entry:
+# FP32 accumulation / TF32 (11-bit significand) / BF16 (8-bit significand) inputs
+MTTKRP_TOL = {"fp32": 2e-5, "tf32": 3e-3, "bf16": 1.5e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    return lib()
+
+
+def _tensor(N, L, B, kind, seed):
+    m = synth.flake_map(N, max(4, N * N // 16), 0.3, seed) if kind == "flakes" else \
+        synth.brushed_map(N, 0.05, 0.3, 6, seed)
+    s, t = ndf.bin_index(m, B)
+    H = ndf.footprint_histograms(s, t, L, B)
+    return m, H, ndf.logical(ndf.normalised_tensor(H, B))
+
+
+def _supported(prec, N, L, B, R):
+    from paper_2109_14807_gb300 import _lib
+    return _lib.load().gsp_cp_workspace_bytes(N, L, B, R, _lib.PREC[prec]) > 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("N,L,B,R", [(32, 6, 16, 8), (32, 6, 16, 16), (64, 7, 32, 32), (64, 7, 16, 64)])
+def test_mttkrp_parity(prec, N, L, B, R):
+    import paper_2109_14807_gb300 as g
+    m, H, X = _tensor(N, L, B, "flakes", 20 + N + R)
+    ws = g.CPWorkspace(N, L, B, R, prec) if _supported(prec, N, L, B, R) else None
+    if ws is None:
+        pytest.skip(f"{prec} MTTKRP does not support rank {R}")
+    ws.prepare(hist=dev(H, torch.int32))
+    u = [synth.uniform(300 + R, k, n * R).reshape(n, R).astype(np.float32)
+         for k, n in enumerate((N, N, L, B, B))]
+    f = {k: dev(a) for k, a in zip(("fx", "fy", "fl", "fs", "ft"), u)}
+    outs = ws.mttkrp(f)
+    torch.cuda.synchronize()
+    A = [a.astype(np.float64) for a in u]
+    for n in range(5):
+        ref = cp.mttkrp_dense(X, A, n)  # factors >= 0 and X >= 0: ref is its own scale
+        got = outs[n].double().cpu().numpy()
+        err = np.max(np.abs(got - ref) / np.maximum(ref, 1e-30 + np.max(ref) * 1e-6))
+        assert err <= MTTKRP_TOL[prec], (n, err)
+
+
+def _oracle_fits(X, R, init, sweeps):
+    A0 = [init[k].astype(np.float32).astype(np.float64) for k in ("fx", "fy", "fl", "fs", "ft")]
+    return cp.cp_als(X, R, A0, sweeps)
+
+
+def test_als_fp32_flakes32_matches_oracle():
+    import paper_2109_14807_gb300 as g
+    w = synth.WORKLOADS["flakes32"]
+    N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
+    m = synth.make_map(w)
+    s, t = ndf.bin_index(m, B)
+    H = ndf.footprint_histograms(s, t, L, B)
+    X = ndf.logical(ndf.normalised_tensor(H, B))
+    init = synth.init_factors(N, L, B, R, 2001)
+    _, _, ofits = _oracle_fits(X, R, init, w["sweeps"])
+    f, fits, fb = g.cp_decompose(R, init, hist=dev(H, torch.int32), sweeps=w["sweeps"], precision="fp32")
+    assert fb == 0
+    fits = np.array(fits)
+    rel = np.abs(fits - ofits) / np.abs(ofits)
+    assert np.max(rel) <= 1e-5, (fits, ofits)
+    # the same factors answer queries like the oracle does
+    mat = g.QueryMaterial.from_factors(f)
+    g.build_query_tables(mat)
+    q = synth.queries_integer(N, L, B, w["queries"], 1001)
+    got = g.range_query(mat, g.queries_to_device(q)).cpu().numpy()
+    err, _ = query_error(got, oracle_material(f), q)
+    assert err <= QUERY_TOL
+
+
+def test_als_from_normals_equals_from_histograms():
+    import paper_2109_14807_gb300 as g
+    w = synth.WORKLOADS["flakes32"]
+    N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
+    m = synth.make_map(w)
+    init = synth.init_factors(N, L, B, R, 2001)
+    H = g.build_footprint_ndfs(dev(m), L, B)
+    _, fits1, _ = g.cp_decompose(R, init, hist=H, sweeps=5)
+    _, fits2, _ = g.cp_decompose(R, init, normal_xy=dev(m), levels=L, bins=B, sweeps=5)
+    assert fits1 == fits2
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_als_tensor_core_fit_matches_oracle_mid(prec):
+    import paper_2109_14807_gb300 as g
+    N, L, B, R = 64, 7, 32, 32
+    if not _supported(prec, N, L, B, R):
+        pytest.skip(f"{prec} path unavailable")
+    m, H, X = _tensor(N, L, B, "brushed", 77)
+    init = synth.init_factors(N, L, B, R, 2077)
+    sweeps = 8
+    _, _, ofits = _oracle_fits(X, R, init, sweeps)
+    _, fits, _ = g.cp_decompose(R, init, hist=dev(H, torch.int32), sweeps=sweeps, precision=prec)
+    rel = np.abs(np.array(fits) - ofits) / np.abs(ofits)
+    assert np.max(rel) <= 1e-4, (fits, ofits)
+
+
+def test_als_resume_is_bit_identical():
+    import paper_2109_14807_gb300 as g
+    w = synth.WORKLOADS["flakes32"]
+    N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
+    H = dev(ndf.footprint_histograms(*ndf.bin_index(synth.make_map(w), B), L, B), torch.int32)
+    init = synth.init_factors(N, L, B, R, 2001)
+    ws = g.CPWorkspace(N, L, B, R, "fp32")
+    ws.prepare(hist=H)
+    fa = g.init_factors_to_device(init)
+    fits_a, _ = ws.sweeps(fa, 6)
+    fb = g.init_factors_to_device(init)
+    fits_b1, _ = ws.sweeps(fb, 3)
+    saved = {k: v.clone() for k, v in fb.items()}  # checkpoint
+    fc = {k: v.clone() for k, v in saved.items()}
+    fits_b2, _ = ws.sweeps(fc, 3)
+    assert fits_a[:3] == fits_b1
+    assert fits_a[3:] == fits_b2
+    for k in fa:
+        assert torch.equal(fa[k], fc[k])
