@@ -345,7 +345,7 @@ def run_gsp(args, rank, world):
     st_bits = g.status_bits(status)
 
     # parity gate: a sample of this run's queries against the FP64 oracle
-    parity = query_parity(mat, q_np, out)
+    parity = query_parity(g, mat, qd, q_np, out)
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -419,9 +419,13 @@ def roofline(prof, w, prec, peaks, peak_src):
             if peak_src == "measured" else "fallback"}
 
 
-def query_parity(mat, q_np, out, n_sample=100_000):
+def query_parity(g, mat, qd, q_np, out, n_sample=100_000):
+    """Rebuild the tables from the current factors, answer the step's queries
+    with the timed launch configuration, and check a sample against the oracle."""
     from oracle import query as oq
     import torch
+    g.build_query_tables(mat)
+    g.range_query(mat, qd, out=out)
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.float64)
     f = {k: getattr(mat, k).double().cpu().numpy() for k in ("fx", "fy", "fl", "fs", "ft", "lam")}
@@ -429,7 +433,7 @@ def query_parity(mat, q_np, out, n_sample=100_000):
     idx = np.sort((synth.uniform(77, 1, n_sample) * len(q_np)).astype(np.int64))
     ref = oq.cp_range_query(om, q_np[idx])
     kap = oq.condition_scale(om, q_np[idx])
-    err = float(np.max(np.abs(got[idx] - ref) / np.maximum(np.abs(ref), kap)))
+    err = float(np.max(oq.kappa_relative_error(got[idx], ref, kap)))
     return {"max_kappa_rel_err": err, "sampled": n_sample, "pass_1e-5": err <= 1e-5}
 
 

@@ -125,6 +125,18 @@ def condition_scale(materials, q: np.ndarray) -> np.ndarray:
     return out
 
 
+def kappa_relative_error(got, ref, kappa) -> np.ndarray:
+    """|got - ref| / max(|ref|, kappa) per query; a query whose reference and
+    condition scale are both exactly zero (a range over empty bins) counts as
+    exact when got is zero too and as infinitely wrong otherwise."""
+    got = np.asarray(got, dtype=np.float64)
+    denom = np.maximum(np.abs(ref), kappa)
+    diff = np.abs(got - ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        err = diff / denom
+    return np.where(denom > 0, err, np.where(diff == 0, 0.0, np.inf))
+
+
 def cp_point_query(mat: dict, x: int, y: int, l: int, s: int, t: int) -> float:
     """Eq. 4: D(x, y, z) = sum_r C_r X_r(x) Y_r(y) Z_r(z), five integer indices."""
     return float(np.sum(mat["fx"][x] * mat["fy"][y] * mat["flw"][l] * mat["fs"][s] * mat["ft"][t]))

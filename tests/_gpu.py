@@ -44,5 +44,4 @@ def query_error(got, mats, q):
     """max over queries of |got - ref| / max(|ref|, kappa)."""
     ref = oq.cp_range_query(mats, q)
     kap = oq.condition_scale(mats, q)
-    got = np.asarray(got, dtype=np.float64)
-    return float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), kap))), ref
+    return float(np.max(oq.kappa_relative_error(got, ref, kap))), ref

@@ -157,3 +157,11 @@ def test_adjoint_is_transpose_of_linear_map_in_fs():
     g = synth.uniform(1, 1, len(q))
     G = oq.cp_range_query_adjoint(mat, q, g)
     assert abs(g @ oq.cp_range_query(mat, q) - np.sum(G["fs"] * mat["fs"])) < 1e-12
+
+
+def test_kappa_relative_error_zero_scale():
+    got = np.array([0.0, 1e-3, 2.0, 0.0])
+    ref = np.array([0.0, 0.0, 2.0 + 1e-6, 0.0])
+    kap = np.array([0.0, 0.0, 4.0, 1.0])
+    e = oq.kappa_relative_error(got, ref, kap)
+    assert e[0] == 0.0 and np.isinf(e[1]) and abs(e[2] - 1e-6 / 4.0) < 1e-15 and e[3] == 0.0
