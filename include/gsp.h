@@ -255,6 +255,31 @@ int gsp_range_query_backward(const gsp_material* h_mats, int n_mats, const gsp_q
                              void* d_ws, size_t ws_bytes, uint32_t* d_status,
                              gsp_stream stream);
 
+/* gsp_range_query_backward without a caller workspace, for callers that cannot
+ * allocate device memory: a shading or sampling plugin that only receives the
+ * device pointers its host application hands it and has no allocator of its
+ * own, or a frame loop that must not call cudaMalloc because it synchronises
+ * the whole device.  The paper has no counterpart; this is a calling
+ * convention of this library.
+ *  The scratch (the per-material gradients of the summed-area-table prefix
+ *  sums, gsp_backward_workspace_bytes() of them) comes from one fixed array of
+ *  GSP_BACKWARD_NOALLOC_MAX_BYTES in device memory that the library defines;
+ *  every GPU that loads the library holds it until the process exits.  Larger
+ *  material sets are rejected with GSP_ERR_WORKSPACE before anything is
+ *  enqueued.  The call allocates nothing and calls no allocating routine.
+ *  The first call on a device looks up the array's device address with that
+ *  device current (no work is enqueued by that step); make that first call
+ *  before any stream capture.  All calls share the one array and it keeps the
+ *  last call's contents: each call clears the part it uses on `stream` before
+ *  its kernels run, so calls must not overlap on the GPU (two streams running
+ *  this call at the same time race on the array).  Arguments and results are
+ *  those of gsp_range_query_backward. */
+#define GSP_BACKWARD_NOALLOC_MAX_BYTES (4u << 20)
+int gsp_range_query_backward_noalloc(const gsp_material* h_mats, int n_mats,
+                                     const gsp_query* d_q, int64_t n, const float* d_gout,
+                                     const gsp_material_grad* h_grads, uint32_t* d_status,
+                                     gsp_stream stream);
+
 /* One Adam step (Kingma & Ba 2015) on n FP32 parameters in place:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */

@@ -82,6 +82,9 @@ _SIGS = {
     "gsp_range_query_backward": (c_int, [POINTER(Material), c_int, c_void_p, c_int64, c_void_p,
                                          POINTER(MaterialGrad), c_void_p, c_size_t, c_void_p,
                                          c_void_p]),
+    "gsp_range_query_backward_noalloc": (c_int, [POINTER(Material), c_int, c_void_p, c_int64,
+                                                 c_void_p, POINTER(MaterialGrad), c_void_p,
+                                                 c_void_p]),
     "gsp_adam_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int, c_float,
                               c_float, c_float, c_float, c_void_p]),
     "gsp_profile_enable": (c_int, [c_int]),

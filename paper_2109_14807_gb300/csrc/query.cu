@@ -10,6 +10,8 @@
 // counter (persistent CTAs, dynamic balance over uneven materials).
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace gsp {
@@ -461,6 +463,52 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
     GSP_CHECK_LAUNCH();
   }
   return GSP_OK;
+}
+
+// ------------------------------------------------ no-allocation backward --
+// Fixed device scratch for gsp_range_query_backward_noalloc: the prefix-sum
+// gradient tables of the adjoint, for callers that cannot allocate.  Every
+// device that loads the library holds this array until the process exits.
+namespace gsp {
+namespace {
+constexpr size_t kNoAllocFloats = GSP_BACKWARD_NOALLOC_MAX_BYTES / sizeof(float);
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+// Device address of the array, looked up once per device with that device
+// current (host code cannot use the symbol's host-side name as a pointer).
+int noalloc_scratch(void** out) {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  int dev = 0;
+  GSP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GSP_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    GSP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return GSP_OK;
+}
+}  // namespace
+}  // namespace gsp
+
+extern "C" int gsp_range_query_backward_noalloc(const gsp_material* h_mats, int n_mats,
+                                                const gsp_query* d_q, int64_t n,
+                                                const float* d_gout,
+                                                const gsp_material_grad* h_grads,
+                                                uint32_t* d_status, gsp_stream stream) {
+  if (!h_mats || !h_grads || n_mats < 1 || n_mats > GSP_MAX_MATERIALS || n < 0)
+    return GSP_ERR_INVALID_ARG;
+  const size_t need = gsp_backward_workspace_bytes(h_mats, n_mats);
+  if (need == 0) return GSP_ERR_INVALID_ARG;
+  if (need > GSP_BACKWARD_NOALLOC_MAX_BYTES) return GSP_ERR_WORKSPACE;
+  void* scratch = nullptr;
+  GSP_TRY(noalloc_scratch(&scratch));
+  // the workspace version clears the part it uses on `stream` before its kernels
+  return gsp_range_query_backward(h_mats, n_mats, d_q, n, d_gout, h_grads, scratch,
+                                  GSP_BACKWARD_NOALLOC_MAX_BYTES, d_status, stream);
 }
 
 extern "C" int gsp_adam_step(float* d_param, const float* d_grad, float* d_m, float* d_v,
