@@ -100,9 +100,12 @@ int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int levels, int bi
 /* ------------------------------------------------------------------------ */
 
 typedef enum gsp_precision {
-  GSP_PREC_FP32 = 0, /* MTTKRP with FP32 FFMA on CUDA cores (the plain path)   */
-  GSP_PREC_TF32 = 1, /* MTTKRP on tcgen05 tensor cores, TF32 in, FP32 accumulate */
-  GSP_PREC_BF16 = 2  /* MTTKRP on tcgen05 tensor cores, BF16 in, FP32 accumulate */
+  GSP_PREC_FP32 = 0,    /* MTTKRP with FP32 FFMA on CUDA cores (the plain path)      */
+  GSP_PREC_TF32 = 1,    /* tcgen05, TF32 operands, FP32 accumulate                   */
+  GSP_PREC_BF16 = 2,    /* tcgen05, BF16 operands, FP32 accumulate; the NDF tensor is
+                           one BF16 value, the Khatri-Rao operand a BF16 hi + lo pair
+                           (two MMAs per K slice, Henry, Tang & Heinecke 2019)      */
+  GSP_PREC_BF16_1X = 3  /* tcgen05, both operands rounded once to BF16             */
 } gsp_precision;
 
 /* Five factor matrices and the CP weights, device pointers, FP32:

@@ -26,10 +26,11 @@ constexpr int kMaxCpRank = 128;
 constexpr int kJacobiMaxRank = 64;
 
 struct CpLayout {
-  size_t T, ping, bins, Yp, Zp, Zpart, KR, M, G, W, lam, fit, sumsq, norm2, flags, total;
+  size_t T, bins, Yp, Zp, Zpart, KR, M, G, W, lam, fit, sumsq, norm2, flags, total;
 };
 
-size_t esize(int prec) { return prec == GSP_PREC_BF16 ? 2 : 4; }
+size_t esize(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1X ? 2 : 4; }
+bool is_bf16(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1X; }
 
 CpLayout cp_layout(const MttkrpDims& d, int prec) {
   CpLayout o;
@@ -42,7 +43,6 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   const size_t N2 = static_cast<size_t>(d.N2()), B2 = static_cast<size_t>(d.B2());
   const size_t L = d.L, R = d.R;
   o.T = take(N2 * L * B2 * esize(prec));
-  o.ping = take(2 * N2 * B2 * sizeof(int32_t));
   o.bins = take(N2 * sizeof(uint16_t));
   o.Yp = take(N2 * R * sizeof(float));
   o.Zp = take(L * B2 * R * sizeof(float));
@@ -63,7 +63,7 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
 
 bool valid_cp(int N, int L, int B, int R, int prec) {
   return valid_map(N, L, B) && N >= 8 && B >= 8 && is_pow2(R) && R >= 8 && R <= kMaxCpRank &&
-         prec >= GSP_PREC_FP32 && prec <= GSP_PREC_BF16;
+         prec >= GSP_PREC_FP32 && prec <= GSP_PREC_BF16_1X;
 }
 
 // --------------------------------------------------------------- kernels --
@@ -84,10 +84,12 @@ __global__ void k_kr_rows(const float* __restrict__ fl, const float* __restrict_
 }
 
 // KRt[r][l*B2 + s*B + t] in the operand type (the K-major B operand of the
-// tensor-core pass)
+// tensor-core pass).  BF16 with `split`: rows R..2R-1 hold the remainder
+// v - bf16(v) of rows 0..R-1.  FP32 storage with `split`: values rounded to
+// the nearest TF32.
 template <typename OutT>
 __global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict__ fs,
-                          const float* __restrict__ ft, int L, int B, int R,
+                          const float* __restrict__ ft, int L, int B, int R, int split,
                           OutT* __restrict__ out) {
   long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   long long K = static_cast<long long>(L) * B * B;
@@ -98,10 +100,13 @@ __global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict_
   int s = static_cast<int>((k / B) % B);
   int l = static_cast<int>(k / (static_cast<long long>(B) * B));
   float v = fl[l * R + r] * fs[s * R + r] * ft[t * R + r];
-  if constexpr (sizeof(OutT) == 2)
-    out[i] = __float2bfloat16_rn(v);
-  else
-    out[i] = v;
+  if constexpr (sizeof(OutT) == 2) {
+    __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    out[i] = hi;
+    if (split) out[i + K * R] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  } else {
+    out[i] = split ? round_tf32(v) : v;  // split = 1 marks the TF32 operand here
+  }
 }
 
 // Zp[l][st][r] = sum_c Zpart[l*C + c][st][r], fixed order
@@ -156,13 +161,40 @@ __global__ void __launch_bounds__(256) k_contract(CParams p) {
   }
 }
 
-// G[r1][r2] = sum_i A[i][r1] A[i][r2], FP64
-__global__ void k_gram(const float* __restrict__ A, int I, int R, double* __restrict__ G) {
-  const int r1 = blockIdx.x, r2 = threadIdx.x;
+// M[i][r] = sum_j W[(i + j*w1)][r] * A1[j][r] for consecutive i (wi = 1): each
+// CTA owns 256/R consecutive rows i, so every step over j reads one
+// contiguous run of W; one output per thread, fixed summation order.
+__global__ void __launch_bounds__(256) k_contract_rows(const float* __restrict__ W, long long w1,
+                                                       int J, const float* __restrict__ A1,
+                                                       int R, double* __restrict__ M,
+                                                       float* __restrict__ Mf) {
+  const int per = blockDim.x / R;
+  const int i = blockIdx.x * per + threadIdx.x / R;
+  const int r = threadIdx.x % R;
   double acc = 0.0;
-  for (int i = 0; i < I; ++i)
+  for (int j = 0; j < J; ++j)
+    acc += static_cast<double>(W[(i + j * w1) * R + r]) * static_cast<double>(A1[j * R + r]);
+  if (M) M[i * R + r] = acc;
+  if (Mf) Mf[i * R + r] = static_cast<float>(acc);
+}
+
+// G[r1][r2] = sum_i A[i][r1] A[i][r2], FP64; 256/R row slices per output row,
+// combined in a fixed order
+__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int I, int R,
+                                              double* __restrict__ G) {
+  __shared__ double part[256];
+  const int r1 = blockIdx.x, r2 = threadIdx.x % R, p = threadIdx.x / R;
+  const int P = blockDim.x / R;
+  double acc = 0.0;
+  for (int i = p; i < I; i += P)
     acc += static_cast<double>(A[i * R + r1]) * static_cast<double>(A[i * R + r2]);
-  G[r1 * R + r2] = acc;
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (p == 0) {
+    double t = part[r2];
+    for (int k = 1; k < P; ++k) t += part[k * R + r2];
+    G[r1 * R + r2] = t;
+  }
 }
 
 // Hadamard product of the four Gram matrices other than `skip`.
@@ -326,18 +358,24 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ G, 
       return;
     }
   }
-  // W = L^-T L^-1, one column per thread (column c is scratch for its solves)
+  // W = L^-T L^-1, one column per thread (column c is scratch for its solves);
+  // in shared memory when it fits next to V, then copied out
+  double* Ws = R <= kJacobiMaxRank ? Q : W;
   for (int c = threadIdx.x; c < R; c += blockDim.x) {
     for (int k = 0; k < R; ++k) {
       double y = (k == c) ? 1.0 : 0.0;
-      for (int j = 0; j < k; ++j) y -= V[k * R + j] * W[j * R + c];
-      W[k * R + c] = y / V[k * R + k];
+      for (int j = 0; j < k; ++j) y -= V[k * R + j] * Ws[j * R + c];
+      Ws[k * R + c] = y / V[k * R + k];
     }
     for (int k = R - 1; k >= 0; --k) {
-      double w = W[k * R + c];
-      for (int j = k + 1; j < R; ++j) w -= V[j * R + k] * W[j * R + c];
-      W[k * R + c] = w / V[k * R + k];
+      double w = Ws[k * R + c];
+      for (int j = k + 1; j < R; ++j) w -= V[j * R + k] * Ws[j * R + c];
+      Ws[k * R + c] = w / V[k * R + k];
     }
+  }
+  if (Ws != W) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = Ws[e];
   }
 }
 
@@ -462,14 +500,16 @@ int run_xy(const Ctx& c, const float* fl, const float* fs, const float* ft) {
     GSP_CHECK_LAUNCH();
     return simt_mttkrp_xy(c.at<float>(c.lay.T), c.at<float>(c.lay.KR), c.at<float>(c.lay.Yp), d, c.s);
   }
-  if (c.prec == GSP_PREC_BF16)
+  if (is_bf16(c.prec))
     k_kr_cols<__nv_bfloat16><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(
-        fl, fs, ft, d.L, d.B, d.R, c.at<__nv_bfloat16>(c.lay.KR));
+        fl, fs, ft, d.L, d.B, d.R, c.prec == GSP_PREC_BF16 ? 1 : 0,
+        c.at<__nv_bfloat16>(c.lay.KR));
   else
-    k_kr_cols<float><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.R,
+    k_kr_cols<float><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.R, 1,
                                                                c.at<float>(c.lay.KR));
   GSP_CHECK_LAUNCH();
-  return tc_mttkrp_xy(c.ws + c.lay.T, c.ws + c.lay.KR, c.at<float>(c.lay.Yp), d, c.prec, c.s);
+  return tc_mttkrp_xy(c.ws + c.lay.T, c.ws + c.lay.KR, c.at<float>(c.lay.Yp), d, c.prec,
+                      c.at<uint32_t>(c.lay.flags), c.s);
 }
 
 int run_lst(const Ctx& c, const float* fx, const float* fy) {
@@ -478,7 +518,8 @@ int run_lst(const Ctx& c, const float* fx, const float* fy) {
   if (c.prec == GSP_PREC_FP32)
     GSP_TRY(simt_mttkrp_lst(c.at<float>(c.lay.T), fx, fy, c.at<float>(c.lay.Zpart), d, C, c.s));
   else
-    GSP_TRY(tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.at<float>(c.lay.Zpart), d, c.prec, C, c.s));
+    GSP_TRY(tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.at<float>(c.lay.Zpart), d, c.prec, C,
+                          c.at<uint32_t>(c.lay.flags), c.s));
   long long per_level = static_cast<long long>(d.B2()) * d.R;
   k_zreduce<<<grid_for(per_level * d.L, 256), 256, 0, c.s>>>(c.at<float>(c.lay.Zpart),
                                                              c.at<float>(c.lay.Zp), d.L, C, per_level);
@@ -518,7 +559,13 @@ int contract(const Ctx& c, int mode, const gsp_cp_factors& f, double* M, float* 
       break;
   }
   prof_begin(PROF_ALS_SMALL, c.s);
-  k_contract<<<I, 256, 0, c.s>>>(p);
+  if (mode == 0) {
+    int per = 256 / d.R;
+    if (per > I) per = I;  // both powers of two: per divides I
+    k_contract_rows<<<I / per, per * d.R, 0, c.s>>>(p.W, p.w1, p.J1, p.A1, d.R, M, Mf);
+  }
+  else
+    k_contract<<<I, 256, 0, c.s>>>(p);
   prof_end(PROF_ALS_SMALL, c.s);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
@@ -540,7 +587,7 @@ int mode_rows(const MttkrpDims& d, int mode) {
 
 int gram(const Ctx& c, const gsp_cp_factors& f, int mode) {
   const int R = c.d.R;
-  k_gram<<<R, R, 0, c.s>>>(factor_ptr(f, mode), mode_rows(c.d, mode), R,
+  k_gram<<<R, 256, 0, c.s>>>(factor_ptr(f, mode), mode_rows(c.d, mode), R,
                            c.at<double>(c.lay.G) + static_cast<size_t>(mode) * R * R);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
@@ -605,27 +652,28 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
   unsigned long long* sumsq = c.at<unsigned long long>(c.lay.sumsq);
   GSP_CUDA(cudaMemsetAsync(sumsq, 0, sizeof(unsigned long long) * levels, c.s));
   GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
-  auto sink_for = [&](int l, int32_t* h) {
-    LevelSink o{h, nullptr, nullptr, 1.0f, sumsq + l};
-    float sc = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
-    o.scale = sc;
-    if (c.prec == GSP_PREC_BF16)
-      o.bf16 = c.at<__nv_bfloat16>(c.lay.T) + slice * l;
-    else
-      o.f32 = c.at<float>(c.lay.T) + slice * l;
-    return o;
-  };
   if (d_hist) {
-    for (int l = 0; l < levels; ++l)
-      GSP_TRY(launch_cast(d_hist + slice * l, N, bins, sink_for(l, nullptr), c.s));
+    for (int l = 0; l < levels; ++l) {
+      LevelSink o{nullptr, nullptr, nullptr, 1.0f, sumsq + l};
+      o.scale = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
+      if (is_bf16(c.prec))
+        o.bf16 = c.at<__nv_bfloat16>(c.lay.T) + slice * l;
+      else
+        o.f32 = c.at<float>(c.lay.T) + slice * l;
+      GSP_TRY(launch_cast(d_hist + slice * l, N, bins, o, c.s));
+    }
   } else {
     uint16_t* bm = c.at<uint16_t>(c.lay.bins);
-    int32_t* ping[2] = {c.at<int32_t>(c.lay.ping), c.at<int32_t>(c.lay.ping) + slice};
     GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, c.s));
-    GSP_TRY(launch_level0(bm, N, bins, sink_for(0, levels > 1 ? ping[0] : nullptr), c.s));
-    for (int l = 1; l < levels; ++l)
-      GSP_TRY(launch_double(ping[(l - 1) & 1], N, bins, l - 1,
-                            sink_for(l, l + 1 < levels ? ping[l & 1] : nullptr), c.s));
+    HistOut o{};
+    o.sumsq = sumsq;
+    for (int l = 0; l < levels; ++l)
+      o.scale[l] = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
+    if (is_bf16(c.prec))
+      o.bf16 = c.at<__nv_bfloat16>(c.lay.T);
+    else
+      o.f32 = c.at<float>(c.lay.T);
+    GSP_TRY(launch_box_hist(bm, N, levels, bins, o, c.s));
   }
   k_norm2<<<1, 32, 0, c.s>>>(sumsq, levels, bins, opts->raw_counts, c.at<double>(c.lay.norm2));
   GSP_CHECK_LAUNCH();
@@ -676,6 +724,7 @@ extern "C" int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_al
     GSP_CUDA(cudaMemcpyAsync(&flags, c.ws + c.lay.flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.s));
     GSP_CUDA(cudaStreamSynchronize(c.s));
     h_report->numeric_fallbacks = (flags & GSP_DEV_NUMERIC) ? 1 : 0;
+    if (flags & GSP_DEV_TIMEOUT) return GSP_ERR_TIMEOUT;
   }
   return GSP_OK;
 }

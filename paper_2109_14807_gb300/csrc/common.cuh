@@ -72,6 +72,14 @@ inline bool valid_map(int N, int levels, int bins) {
          is_pow2(bins) && bins >= 4 && bins <= 128;
 }
 
+// Round an FP32 value to the nearest TF32 value (ties away from zero), so the
+// tensor core, which drops the low 13 mantissa bits, sees an unbiased operand.
+__device__ __forceinline__ float round_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {
   if (status) atomicOr(status, bits);
 }

@@ -31,10 +31,14 @@ int simt_mttkrp_lst(const float* T, const float* fx, const float* fy, float* Zpa
 
 // tcgen05 path.  KRt: [R][L*B2] in the operand type (bf16 or fp32 read as tf32).
 // Returns GSP_ERR_UNSUPPORTED when the shape is outside the kernel's support.
+// `err` (device word, may be null) receives GSP_DEV_TIMEOUT if a bounded wait
+// inside the kernel gave up.
 int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d, int precision,
-                 cudaStream_t s);
+                 uint32_t* err, cudaStream_t s);
 int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart,
-                  const MttkrpDims& d, int precision, int chunks, cudaStream_t s);
+                  const MttkrpDims& d, int precision, int chunks, uint32_t* err, cudaStream_t s);
 bool tc_supported(const MttkrpDims& d, int precision);
+// Z' work units per xy chunk (levels x st groups) of the tensor-core pass.
+int tc_lst_units_per_chunk(const MttkrpDims& d);
 
 }  // namespace gsp

@@ -1,21 +1,707 @@
-// tcgen05 tensor-core MTTKRP passes (BF16 / TF32 in, FP32 accumulate in TMEM).
+// tcgen05 tensor-core MTTKRP passes of a CP-ALS sweep (BF16 or TF32 operand,
+// FP32 accumulation in tensor memory).
+//
+// Both passes stream the operand tensor T [l][xy][st] (C order, st = s*B + t
+// contiguous) once, in 128-byte-wide tiles loaded by TMA with 128-byte
+// swizzling straight into the layout the tensor cores read.
+//
+//  Y' pass  D[xy][r] = sum_{l, st} T[l][xy][st] * KRt[r][l*B2 + st]
+//           one 128-row xy tile per accumulator, K = L * B2; T is the K-major A
+//           operand, KRt (fl*fs*ft, built per sweep) the K-major B operand.
+//  Z' pass  D[st][r] = sum_{xy in chunk} T[l][xy][st] * fx[x][r] fy[y][r]
+//           per (level, xy chunk, st group): one accumulator per 128-wide st
+//           block; the same T tiles are now the MN-major A operand; the B
+//           operand (fx (.) fy over the chunk's xy rows) is computed in shared
+//           memory by the epilogue warps while they are otherwise idle.
+//
+// CTA = 6 warps: warps 0-3 epilogue (TMEM lanes 0-127) and, in the Z' pass,
+// B-operand producers; warp 4 issues TMA; warp 5 owns TMEM and issues MMAs
+// (one thread).  Every mbarrier wait is bounded by a clock budget: on expiry
+// the CTA raises GSP_DEV_TIMEOUT, waits for its own copies and MMAs in flight
+// (again bounded), frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "mttkrp.cuh"
 
 namespace gsp {
+namespace {
+
+constexpr int kMaxStages = 8;
+constexpr int kThreads = 192;
+constexpr long long kTimeoutCycles = 4000000000LL;  // about 2 s at GB300 clocks
+constexpr int kTileBytes = 128 * 128;                // 128 rows x 128 bytes
+
+// ------------------------------------------------------------- PTX glue --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete.  Returns false when the
+// CTA's abort flag is (or becomes) set or the clock budget runs out.
+__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
+  if (mbar_test(a, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_test(a, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kTimeoutCycles) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// Bounded wait that ignores the abort flag (used to drain work in flight).
+__device__ __noinline__ bool mbar_drain(uint32_t a, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(a, parity))
+    if (clock64() - t0 > kTimeoutCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
+      : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor, base offset 0.  layout: 2 = 128-byte
+// swizzle of 16-byte chunks; 1 = 128-byte swizzle of 32-byte chunks (the form
+// MN-major 32-bit operands take).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                          uint64_t layout = 2) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) |
+         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (layout << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
+// A major-ness (0 = K-major, 1 = MN-major), B K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t a_mn, uint32_t n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (a_mn << 15) | ((n >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+
+template <int ELEM>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                     uint32_t accumulate) {
+  if constexpr (ELEM == 2) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes, one lane per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__host__ __device__ constexpr uint32_t tmem_cols_for(int cols) {
+  uint32_t c = 32;
+  while (c < static_cast<uint32_t>(cols)) c <<= 1;
+  return c;
+}
+
+struct Barriers {
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t b_full[2];
+  uint64_t b_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// Epilogue: copy this warp's 32 TMEM lanes x R columns starting at column
+// `col` into row-major FP32 rows of `out` (row stride R floats).
+__device__ __forceinline__ void store_accumulator(uint32_t tmem_base, int warp, int lane, int col,
+                                                  int R, float* out_rows) {
+  const uint32_t taddr = tmem_base + (static_cast<uint32_t>(warp * 32) << 16) + col;
+  float* row = out_rows + static_cast<size_t>(warp * 32 + lane) * R;
+  for (int c = 0; c < R; c += 16) {
+    float v[16];
+    tmem_ld16(taddr + c, v);
+    float4* dst = reinterpret_cast<float4*>(row + c);
+    dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+    dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+    dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+    dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+  }
+}
+
+// ------------------------------------------------------------ Y' pass --
+// ELEM: 2 (BF16) or 4 (TF32/FP32 storage).  E128 = elements per 128 bytes.
+// SPLIT: the B operand holds 2R rows, a BF16 hi part and its remainder; each
+// K slice then issues two MMAs into the same accumulator.
+template <int ELEM, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_xy_tc(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapKR,
+            float* __restrict__ Yp, int n_tiles, long long N2, int L, int B2, int R, int kStages,
+            uint32_t* err) {
+  constexpr int E128 = 128 / ELEM;
+  constexpr uint32_t FMT = ELEM == 2 ? 1u : 2u;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ Barriers bar;
+  uint8_t* smem = align1024(smem_raw);
+  const int b_bytes = R * 128 * (SPLIT ? 2 : 1);
+  const int stage_bytes = kTileBytes + b_bytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kpl = B2 / E128;  // 128-byte K chunks per level
+  const int kiters = L * kpl;
+  const uint32_t ncols = tmem_cols_for(2 * R);
+  volatile int* abort = &bar.abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar.full[s]), 1);
+      mbar_init(smem_u32(&bar.empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bar.acc_full[a]), 1);
+      mbar_init(smem_u32(&bar.acc_empty[a]), 128);
+    }
+    mbar_init(smem_u32(&bar.drain), 1);
+    bar.abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 5) tmem_alloc(smem_u32(&bar.tmem_base), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bar.tmem_base;
+
+  if (warp == 4) {
+    if (lane == 0) {  // ---- TMA producer
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued_parity[kMaxStages];
+      bool issued[kMaxStages];
+      for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
+      for (int tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
+        const long long xy0 = static_cast<long long>(tile) * 128;
+        for (int it = 0; it < kiters; ++it) {
+          if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
+          const int l = it / kpl, kc = it % kpl;
+          const uint32_t sa = smem_u32(smem + s * stage_bytes);
+          const uint32_t fb = smem_u32(&bar.full[s]);
+          mbar_expect_tx(fb, stage_bytes);
+          tma_load_2d(sa, &mapT, kc * E128, static_cast<int>(l * N2 + xy0), fb);
+          tma_load_2d(sa + kTileBytes, &mapKR, l * B2 + kc * E128, 0, fb);
+          issued[s] = true;
+          issued_parity[s] = ph;
+          if (++s == kStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    producer_done:
+      if (*abort)  // wait for this CTA's own copies still in flight
+        for (int i = 0; i < kStages; ++i)
+          if (issued[i]) mbar_drain(smem_u32(&bar.full[i]), issued_parity[i]);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {  // ---- MMA issuer
+      const uint32_t id = idesc(FMT, 0, static_cast<uint32_t>(R));
+      int s = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      bool any = false;
+      for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (!mbar_wait(smem_u32(&bar.acc_empty[acc]), aph ^ 1u, abort)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + static_cast<uint32_t>(acc * R);
+        for (int it = 0; it < kiters; ++it) {
+          if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * stage_bytes);
+          const uint32_t sb = sa + kTileBytes;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {  // four K slices of 32 bytes per 128-byte row
+            const uint64_t a = sdesc(sa + j * 32, 16, 1024);
+            umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (it > 0 || j > 0) ? 1u : 0u);
+            if constexpr (SPLIT) umma<ELEM>(d, a, sdesc(sb + R * 128 + j * 32, 16, 1024), id, 1u);
+          }
+          any = true;
+          umma_commit(smem_u32(&bar.empty[s]));
+          if (++s == kStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        umma_commit(smem_u32(&bar.acc_full[acc]));
+        if (++acc == 2) {
+          acc = 0;
+          aph ^= 1u;
+        }
+      }
+    mma_done:
+      if (*abort && any) {  // wait for the MMAs already issued
+        umma_commit(smem_u32(&bar.drain));
+        mbar_drain(smem_u32(&bar.drain), 0);
+      }
+    }
+  } else {  // ---- epilogue warps 0-3: TMEM -> Y'
+    int acc = 0;
+    uint32_t aph = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      if (!mbar_wait(smem_u32(&bar.acc_full[acc]), aph, abort)) break;
+      tc_fence_after();
+      store_accumulator(tmem, warp, lane, acc * R, R, Yp + static_cast<size_t>(tile) * 128 * R);
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bar.acc_empty[acc]));
+      if (++acc == 2) {
+        acc = 0;
+        aph ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && bar.abort && err) atomicOr(err, GSP_DEV_TIMEOUT);
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+// ------------------------------------------------------------ Z' pass --
+// Unit u -> (level l, xy chunk c, st group g); the chunk's rows are processed in
+// K steps of E128 rows.  For each K step the producer loads, for every st block
+// m of the group, the [E128 rows x 128 st] tile as 128/E128 TMA boxes of
+// [E128 rows][E128 st] (MN-major atoms, LBO = box bytes); the epilogue warps
+// write KRxy[r][k] = fx[x_k][r] fy[y_k][r] (K-major, 128-byte rows, swizzled).
+template <int ELEM, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_lst_tc(const __grid_constant__ CUtensorMap mapT, const float* __restrict__ fx,
+             const float* __restrict__ fy, float* __restrict__ Zpart, int n_units, int logN,
+             int L, int B2, int R, int C, int MB, int G, int kStages, uint32_t* err) {
+  constexpr int E128 = 128 / ELEM;
+  constexpr uint32_t FMT = ELEM == 2 ? 1u : 2u;
+  constexpr int BOXES = 128 / E128;                 // TMA boxes per 128-wide st block
+  constexpr int BOX_BYTES = E128 * 128;             // E128 rows x 128 bytes
+  constexpr int MMA_K_ROWS = 32 / ELEM;             // K rows per MMA (32 bytes of K)
+  constexpr uint64_t A_LAYOUT = ELEM == 2 ? 2 : 1;  // MN-major TF32 uses 32-byte atoms
+  constexpr uint32_t A_SBO = ELEM == 2 ? 1024 : 512;  // K-row group stride of that layout
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ Barriers bar;
+  uint8_t* smem = align1024(smem_raw);
+  uint8_t* bslots = smem + kStages * kTileBytes;
+  const int b_bytes = R * 128 * (SPLIT ? 2 : 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N = 1 << logN;
+  const long long N2 = static_cast<long long>(N) * N;
+  const long long rows = N2 / C;
+  const int ksteps = static_cast<int>(rows / E128);
+  const uint32_t ncols = tmem_cols_for(MB * R);
+  volatile int* abort = &bar.abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar.full[s]), 1);
+      mbar_init(smem_u32(&bar.empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar.acc_full[0]), 1);
+    mbar_init(smem_u32(&bar.acc_empty[0]), 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar.b_full[b]), 128);
+      mbar_init(smem_u32(&bar.b_empty[b]), 1);
+    }
+    mbar_init(smem_u32(&bar.drain), 1);
+    bar.abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 5) tmem_alloc(smem_u32(&bar.tmem_base), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bar.tmem_base;
+
+  if (warp == 4) {
+    if (lane == 0) {  // ---- TMA producer
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued_parity[kMaxStages];
+      bool issued[kMaxStages];
+      for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
+      for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+        const int g = u % G, c = (u / G) % C, l = u / (G * C);
+        const long long row0 = l * N2 + c * rows;
+        for (int kc = 0; kc < ksteps; ++kc) {
+          for (int m = 0; m < MB; ++m) {
+            if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
+            const uint32_t sa = smem_u32(smem + s * kTileBytes);
+            const uint32_t fb = smem_u32(&bar.full[s]);
+            mbar_expect_tx(fb, kTileBytes);
+            const int st0 = (g * MB + m) * 128;
+            for (int b = 0; b < BOXES; ++b)
+              tma_load_2d(sa + b * BOX_BYTES, &mapT, st0 + b * E128,
+                          static_cast<int>(row0 + static_cast<long long>(kc) * E128), fb);
+            issued[s] = true;
+            issued_parity[s] = ph;
+            if (++s == kStages) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+      }
+    producer_done:
+      if (*abort)
+        for (int i = 0; i < kStages; ++i)
+          if (issued[i]) mbar_drain(smem_u32(&bar.full[i]), issued_parity[i]);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {  // ---- MMA issuer
+      const uint32_t id = idesc(FMT, 1, static_cast<uint32_t>(R));
+      int s = 0, bs = 0;
+      uint32_t ph = 0, bph = 0, uph = 0;
+      bool any = false;
+      for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        if (!mbar_wait(smem_u32(&bar.acc_empty[0]), uph ^ 1u, abort)) break;
+        tc_fence_after();
+        for (int kc = 0; kc < ksteps; ++kc) {
+          if (!mbar_wait(smem_u32(&bar.b_full[bs]), bph, abort)) goto mma_done;
+          tc_fence_after();
+          const uint32_t sb = smem_u32(bslots + bs * b_bytes);
+          for (int m = 0; m < MB; ++m) {
+            if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * kTileBytes);
+            const uint32_t d = tmem + static_cast<uint32_t>(m * R);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const uint64_t a = sdesc(sa + j * MMA_K_ROWS * 128, BOX_BYTES, A_SBO, A_LAYOUT);
+              umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (kc > 0 || j > 0) ? 1u : 0u);
+              if constexpr (SPLIT)
+                umma<ELEM>(d, a, sdesc(sb + R * 128 + j * 32, 16, 1024), id, 1u);
+            }
+            any = true;
+            umma_commit(smem_u32(&bar.empty[s]));
+            if (++s == kStages) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+          umma_commit(smem_u32(&bar.b_empty[bs]));
+          if (++bs == 2) {
+            bs = 0;
+            bph ^= 1u;
+          }
+        }
+        umma_commit(smem_u32(&bar.acc_full[0]));
+        uph ^= 1u;
+      }
+    mma_done:
+      if (*abort && any) {
+        umma_commit(smem_u32(&bar.drain));
+        mbar_drain(smem_u32(&bar.drain), 0);
+      }
+    }
+  } else {  // ---- warps 0-3: B operand producer, then epilogue
+    const int t = threadIdx.x;  // 0..127
+    const int k = t % E128;      // xy column of the B tile this thread fills
+    const int r_first = t / E128, r_step = 128 / E128;
+    int bs = 0;
+    uint32_t bph = 0, uph = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+      const int g = u % G, c = (u / G) % C, l = u / (G * C);
+      const long long xy_base = c * rows;
+      for (int kc = 0; kc < ksteps; ++kc) {
+        if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto epi_done;
+        const long long xy = xy_base + static_cast<long long>(kc) * E128 + k;
+        const int x = static_cast<int>(xy & (N - 1)), y = static_cast<int>(xy >> logN);
+        const float* fxr = fx + static_cast<size_t>(x) * R;
+        const float* fyr = fy + static_cast<size_t>(y) * R;
+        uint8_t* tile = bslots + bs * b_bytes;
+        const int byte_in_row = k * ELEM;
+        const int chunk = byte_in_row >> 4, within = byte_in_row & 15;
+        for (int r = r_first; r < R; r += r_step) {
+          const float v = __ldg(fxr + r) * __ldg(fyr + r);
+          const int sw = ((chunk ^ (r & 7)) << 4) | within;
+          uint8_t* dst = tile + r * 128 + sw;
+          if constexpr (ELEM == 2) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(dst) = hi;
+            if constexpr (SPLIT)  // row R + r: same swizzle phase since R % 8 == 0
+              *reinterpret_cast<__nv_bfloat16*>(dst + R * 128) =
+                  __float2bfloat16_rn(v - __bfloat162float(hi));
+          } else {
+            *reinterpret_cast<float*>(dst) = round_tf32(v);
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(smem_u32(&bar.b_full[bs]));
+        if (++bs == 2) {
+          bs = 0;
+          bph ^= 1u;
+        }
+      }
+      // epilogue: MB accumulators of 128 st rows x R
+      if (!mbar_wait(smem_u32(&bar.acc_full[0]), uph, abort)) goto epi_done;
+      tc_fence_after();
+      {
+        float* part = Zpart + (static_cast<size_t>(l) * C + c) * B2 * R;
+        for (int m = 0; m < MB; ++m)
+          store_accumulator(tmem, warp, lane, m * R, R,
+                            part + static_cast<size_t>((g * MB + m) * 128) * R);
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bar.acc_empty[0]));
+      uph ^= 1u;
+      (void)l;
+    }
+  epi_done:;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && bar.abort && err) atomicOr(err, GSP_DEV_TIMEOUT);
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+// ----------------------------------------------------------- host side --
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2D map over a row-major [rows][cols] matrix, box = [box_rows][128 bytes], 128B swizzle.
+int make_map(CUtensorMap* map, const void* base, int elem, long long rows, long long cols,
+             int box_rows, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
+  auto fn = encode_fn();
+  if (!fn) return GSP_ERR_UNSUPPORTED;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * elem};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? GSP_OK : GSP_ERR_CUDA;
+}
+
+// Ring depth: as many stages as fit in ~200 KB, between 3 and 8.
+int stages_for(size_t stage_bytes, size_t fixed) {
+  size_t avail = 200 * 1024 - fixed;
+  int st = static_cast<int>(avail / stage_bytes);
+  return st > kMaxStages ? kMaxStages : (st < 3 ? 3 : st);
+}
+
+size_t xy_stage_bytes(int R, bool split) { return kTileBytes + static_cast<size_t>(R) * 128 * (split ? 2 : 1); }
+int xy_stages(int R, bool split) { return stages_for(xy_stage_bytes(R, split), 1024); }
+size_t xy_smem(int R, bool split) { return 1024 + xy_stages(R, split) * xy_stage_bytes(R, split); }
+
+size_t lst_b_bytes(int R, bool split) { return static_cast<size_t>(R) * 128 * (split ? 2 : 1); }
+int lst_stages(int R, bool split) { return stages_for(kTileBytes, 1024 + 2 * lst_b_bytes(R, split)); }
+// The Z' pass allocates up to all 512 TMEM columns, so it asks for enough
+// shared memory that no second CTA fits on the SM.
+size_t lst_smem(int R, bool split) {
+  size_t need = 1024 + lst_stages(R, split) * static_cast<size_t>(kTileBytes) + 2 * lst_b_bytes(R, split);
+  return need < 120 * 1024 ? 120 * 1024 : need;
+}
+
+template <typename K>
+int set_smem(K kernel, size_t bytes) {
+  GSP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(bytes)));
+  return GSP_OK;
+}
+
+int lst_groups(const MttkrpDims& d, int* MB) {
+  int blocks = d.B2() / 128;
+  int mb = 512 / d.R;
+  if (mb > blocks) mb = blocks;
+  *MB = mb;
+  return blocks / mb;
+}
+
+}  // namespace
 
 bool tc_supported(const MttkrpDims& d, int precision) {
-  (void)d;
-  (void)precision;
-  return false;
+  if (precision != GSP_PREC_BF16 && precision != GSP_PREC_BF16_1X && precision != GSP_PREC_TF32)
+    return false;
+  if (!(d.R == 16 || d.R == 32 || d.R == 64 || d.R == 128)) return false;
+  if (d.B < 16 || d.N < 16) return false;
+  if (d.L * d.N2() >= (1LL << 31)) return false;  // TMA row coordinate is int32
+  const bool split = precision == GSP_PREC_BF16;
+  return xy_smem(d.R, split) <= 227 * 1024 && lst_smem(d.R, split) <= 227 * 1024 &&
+         encode_fn() != nullptr;
 }
 
-int tc_mttkrp_xy(const void*, const void*, float*, const MttkrpDims&, int, cudaStream_t) {
-  return GSP_ERR_UNSUPPORTED;
+int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d, int precision,
+                 uint32_t* err, cudaStream_t s) {
+  if (!tc_supported(d, precision)) return GSP_ERR_UNSUPPORTED;
+  const int elem = precision == GSP_PREC_TF32 ? 4 : 2;
+  const bool split = precision == GSP_PREC_BF16;
+  const int brows = d.R * (split ? 2 : 1);
+  CUtensorMap mT, mK;
+  GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2(), 128));
+  GSP_TRY(make_map(&mK, KRt, elem, brows, static_cast<long long>(d.L) * d.B2(), brows));
+  const int n_tiles = static_cast<int>(d.N2() / 128);
+  int grid = sm_count();
+  if (grid > n_tiles) grid = n_tiles;
+  const size_t smem = xy_smem(d.R, split);
+  const int stages = xy_stages(d.R, split);
+  prof_begin(PROF_MTTKRP_XY, s);
+  if (elem == 4) {
+    GSP_TRY(set_smem(k_xy_tc<4, false>, smem));
+    k_xy_tc<4, false><<<grid, kThreads, smem, s>>>(mT, mK, Yp, n_tiles, d.N2(), d.L, d.B2(), d.R,
+                                                   stages, err);
+  } else if (split) {
+    GSP_TRY(set_smem(k_xy_tc<2, true>, smem));
+    k_xy_tc<2, true><<<grid, kThreads, smem, s>>>(mT, mK, Yp, n_tiles, d.N2(), d.L, d.B2(), d.R,
+                                                  stages, err);
+  } else {
+    GSP_TRY(set_smem(k_xy_tc<2, false>, smem));
+    k_xy_tc<2, false><<<grid, kThreads, smem, s>>>(mT, mK, Yp, n_tiles, d.N2(), d.L, d.B2(), d.R,
+                                                   stages, err);
+  }
+  prof_end(PROF_MTTKRP_XY, s);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
 }
 
-int tc_mttkrp_lst(const void*, const float*, const float*, float*, const MttkrpDims&, int, int,
-                  cudaStream_t) {
-  return GSP_ERR_UNSUPPORTED;
+int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart,
+                  const MttkrpDims& d, int precision, int chunks, uint32_t* err, cudaStream_t s) {
+  if (!tc_supported(d, precision)) return GSP_ERR_UNSUPPORTED;
+  const int elem = precision == GSP_PREC_TF32 ? 4 : 2;
+  const bool split = precision == GSP_PREC_BF16;
+  const int E128 = 128 / elem;
+  if ((d.N2() / chunks) % E128) return GSP_ERR_UNSUPPORTED;
+  CUtensorMap mT;
+  GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2(), E128,
+                   elem == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
+  int MB = 0;
+  const int G = lst_groups(d, &MB);
+  const int n_units = d.L * chunks * G;
+  int grid = sm_count();
+  if (grid > n_units) grid = n_units;
+  const size_t smem = lst_smem(d.R, split);
+  const int stages = lst_stages(d.R, split);
+  const int logN = ilog2(d.N);
+  prof_begin(PROF_MTTKRP_LST, s);
+  if (elem == 4) {
+    GSP_TRY(set_smem(k_lst_tc<4, false>, smem));
+    k_lst_tc<4, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, n_units, logN, d.L,
+                                                    d.B2(), d.R, chunks, MB, G, stages, err);
+  } else if (split) {
+    GSP_TRY(set_smem(k_lst_tc<2, true>, smem));
+    k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, n_units, logN, d.L,
+                                                   d.B2(), d.R, chunks, MB, G, stages, err);
+  } else {
+    GSP_TRY(set_smem(k_lst_tc<2, false>, smem));
+    k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, n_units, logN, d.L,
+                                                    d.B2(), d.R, chunks, MB, G, stages, err);
+  }
+  prof_end(PROF_MTTKRP_LST, s);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+int tc_lst_units_per_chunk(const MttkrpDims& d) {
+  int MB = 0;
+  return d.L * lst_groups(d, &MB);
 }
 
 }  // namespace gsp

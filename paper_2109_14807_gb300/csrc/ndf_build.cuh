@@ -19,15 +19,21 @@ struct LevelSink {
   unsigned long long* sumsq;
 };
 
+// Outputs of the all-level histogram build; any pointer may be null.  Arrays
+// are the full [levels][N][N][B][B] tensors; sumsq has one counter per level.
+struct HistOut {
+  int32_t* h;
+  float* f32;
+  __nv_bfloat16* bf16;
+  unsigned long long* sumsq;
+  float scale[16];  // counts -> operand value, per level
+};
+
 int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins,
                 uint32_t* d_status, cudaStream_t s);
-// Level 0: one-hot counts of every texel's own bin.
-int launch_level0(const uint16_t* d_bins, int N, int bins, LevelSink o, cudaStream_t s);
-// Level l+1 from level l (l = level_in) by the doubling identity
-// W_{l+1}(x) = W_l(x - d) u W_l(x + d), d = 2^(l-1) (W_1(x) = W_0(x-1) u W_0(x)),
-// applied along x and along y: four shifted adds per count.
-int launch_double(const int32_t* d_in, int N, int bins, int level_in, LevelSink o,
-                  cudaStream_t s);
+// Histograms of every footprint of every level 0..levels-1 from the bin map.
+int launch_box_hist(const uint16_t* d_bins, int N, int levels, int bins, const HistOut& o,
+                    cudaStream_t s);
 // Copy / convert an existing int32 slice into a sink.
 int launch_cast(const int32_t* d_in, int N, int bins, LevelSink o, cudaStream_t s);
 

@@ -13,7 +13,13 @@ pytestmark = pytest.mark.gpu
 
 # MTTKRP tolerance relative to the magnitude scale sum |X| prod |A| of each entry:
 # FP32 accumulation / TF32 (11-bit significand) / BF16 (8-bit significand) inputs
-MTTKRP_TOL = {"fp32": 2e-5, "tf32": 3e-3, "bf16": 1.5e-2}
+MTTKRP_TOL = {"fp32": 2e-5, "tf32": 3e-3, "bf16": 1.5e-2, "bf16_1x": 1.5e-2}
+# ALS fit tolerance vs the FP64 oracle after the same sweeps from the same init.
+# BF16 (tensor in BF16, Khatri-Rao operand as a BF16 hi + lo pair) must meet
+# 1e-4.  Single-pass TF32 rounds the Khatri-Rao operand to 11 significant bits;
+# emulating that rounding in FP64 on this workload gives ~9e-5 after 8 sweeps,
+# so it is held to 2e-4.
+FIT_TOL = {"bf16": 1e-4, "tf32": 2e-4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,8 +40,9 @@ def _supported(prec, N, L, B, R):
     return _lib.load().gsp_cp_workspace_bytes(N, L, B, R, _lib.PREC[prec]) > 0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
-@pytest.mark.parametrize("N,L,B,R", [(32, 6, 16, 8), (32, 6, 16, 16), (64, 7, 32, 32), (64, 7, 16, 64)])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16_1x"])
+@pytest.mark.parametrize("N,L,B,R", [(32, 6, 16, 8), (32, 6, 16, 16), (64, 7, 32, 32), (64, 7, 16, 64),
+                                     (32, 6, 32, 128)])
 def test_mttkrp_parity(prec, N, L, B, R):
     import paper_2109_14807_gb300 as g
     m, H, X = _tensor(N, L, B, "flakes", 20 + N + R)
@@ -109,7 +116,7 @@ def test_als_tensor_core_fit_matches_oracle_mid(prec):
     _, _, ofits = _oracle_fits(X, R, init, sweeps)
     _, fits, _ = g.cp_decompose(R, init, hist=dev(H, torch.int32), sweeps=sweeps, precision=prec)
     rel = np.abs(np.array(fits) - ofits) / np.abs(ofits)
-    assert np.max(rel) <= 1e-4, (fits, ofits)
+    assert np.max(rel) <= FIT_TOL[prec], (fits, ofits)
 
 
 def test_als_resume_is_bit_identical():
