@@ -24,9 +24,11 @@
  *    detected on the host before anything is enqueued.  Errors found by the
  *    device (a non-finite normal, a malformed query) are OR-ed into the
  *    caller's 32-bit status word d_status (GSP_DEV_* bits) and never trap.
- *  - Map side N is a power of two, 2 <= N <= 4096; levels = log2(N) + 1 (level
- *    l has 2^l x 2^l footprints, l = 0 .. log2 N); bins B is a power of two,
- *    4 <= B <= 128; rank R is 1 <= R <= 256.
+ *  - Map side N is a power of two, 2 <= N <= 1024 for the NDF build and CP
+ *    decomposition (any power of two up to 2^20 for queries); levels <= log2(N) + 1
+ *    (level l has 2^l x 2^l footprints, l = 0 .. log2 N); bins B is a power of two,
+ *    4 <= B <= 128; rank R is 1 <= R <= 256 for queries and a power of two
+ *    8 <= R <= 64 for the CP decomposition (16 <= R for the tensor-core paths).
  *  - NDF tensor layout: int32 / float, C order [l][y][x][s][t]; (s, t) is the
  *    (n.x, n.y) bin; the logical mode order is (x, y, l, s, t).
  *  - Factor matrices are FP32, row-major [rows][R].
@@ -298,7 +300,7 @@ int gsp_adam_step(float* d_param, const float* d_grad, float* d_m, float* d_v, i
  * below (id = index).  gsp_profile_read synchronises those events and returns
  * the launch count and summed device time since the last reset.  Off by
  * default; keep it off while capturing CUDA graphs.
- *   0 bins, 1 level0, 2 doubling, 3 cast, 4 mttkrp_xy, 5 mttkrp_lst,
+ *   0 bins, 1 (unused), 2 box_hist, 3 cast, 4 mttkrp_xy, 5 mttkrp_lst,
  *   6 als_small, 7 tables, 8 range_query, 9 range_query_backward, 10 adam */
 #define GSP_PROFILE_SLOTS 11
 int gsp_profile_enable(int on);

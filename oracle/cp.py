@@ -69,22 +69,40 @@ def fit_dense(X: np.ndarray, lam: np.ndarray, factors) -> float:
     return 1.0 - np.linalg.norm((X - reconstruct(lam, factors)).ravel()) / np.linalg.norm(X.ravel())
 
 
-def cp_als(X, rank: int, init, sweeps: int, tol: float = 0.0):
+def fit_gram(normX2: float, lam: np.ndarray, factors, M_last: np.ndarray) -> float:
+    """The same fit from inner products only (Kolda & Bader, Sec. 3.4):
+    ||X - Xhat||^2 = ||X||^2 + lambda^T (*_m A_m^T A_m) lambda - 2 <X, Xhat>, with
+    <X, Xhat> = sum_r lambda_r <M_N[:, r], A_N[:, r]> from the last mode's MTTKRP."""
+    V = np.ones((len(lam), len(lam)))
+    for A in factors:
+        V *= A.T @ A
+    inner = float(np.sum(lam * np.sum(M_last * factors[-1], axis=0)))
+    res2 = normX2 + float(lam @ V @ lam) - 2.0 * inner
+    return 1.0 - np.sqrt(max(res2, 0.0) / normX2)
+
+
+def cp_als(X, rank: int, init, sweeps: int, tol: float = 0.0, fit_method: str = "explicit"):
     """CP-ALS on a dense numpy tensor or on a FootprintTensor.  `init` is a list
     of one [I_m][rank] matrix per mode.  Returns (lambda, factors, fits), one fit
-    per sweep done."""
+    per sweep done; fit_method "gram" uses fit_gram instead of the residual."""
     dense = isinstance(X, np.ndarray)
     A = [np.array(f, dtype=np.float64, copy=True) for f in init]
     for f in A:
         assert f.shape[1] == rank
     lam = np.ones(rank)
     fits = []
+    normX2 = None
     for _ in range(sweeps):
         for n in range(len(A)):
             V = gram_hadamard(A, n)
             M = mttkrp_dense(X, A, n) if dense else X.mttkrp(A, n)
             A[n], lam = ls_update(M, V)
-        fits.append(fit_dense(X, lam, A) if dense else X.fit(lam, A))
+        if fit_method == "gram":
+            if normX2 is None:
+                normX2 = float(np.sum(X * X)) if dense else X.norm2()
+            fits.append(fit_gram(normX2, lam, A, M))
+        else:
+            fits.append(fit_dense(X, lam, A) if dense else X.fit(lam, A))
         if tol > 0 and len(fits) > 1 and abs(fits[-1] - fits[-2]) < tol:
             break
     return lam, A, fits

@@ -22,7 +22,7 @@
 namespace gsp {
 namespace {
 
-constexpr int kMaxCpRank = 128;
+constexpr int kMaxCpRank = 64;
 constexpr int kJacobiMaxRank = 64;
 
 struct CpLayout {
@@ -43,7 +43,7 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   const size_t N2 = static_cast<size_t>(d.N2()), B2 = static_cast<size_t>(d.B2());
   const size_t L = d.L, R = d.R;
   o.T = take(N2 * L * B2 * esize(prec));
-  o.bins = take(N2 * sizeof(uint16_t));
+  o.bins = take(N2 * sizeof(uint16_t) + kGroupBytes);
   o.Yp = take(N2 * R * sizeof(float));
   o.Zp = take(L * B2 * R * sizeof(float));
   o.Zpart = take(L * static_cast<size_t>(lst_chunks(d, prec)) * B2 * R * sizeof(float));
@@ -51,7 +51,7 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
   o.M = take(imax * R * sizeof(double));
   o.G = take(5 * R * R * sizeof(double));
-  o.W = take(R * R * sizeof(double));
+  o.W = take((3 * R * R + R) * sizeof(double) + 16);  // L, Z^T, 1/diag(L), mode, then W
   o.lam = take(R * sizeof(double));
   o.fit = take(GSP_MAX_SWEEPS * sizeof(double));
   o.sumsq = take(L * sizeof(unsigned long long));
@@ -141,15 +141,28 @@ __global__ void __launch_bounds__(256) k_contract(CParams p) {
   const int jl = threadIdx.x / R;
   const int JL = blockDim.x / R;
   const long long J = static_cast<long long>(p.J1) * p.J2;
-  double acc = 0.0;
-  for (long long j = jl; j < J; j += JL) {
-    int j1 = static_cast<int>(j / p.J2), j2 = static_cast<int>(j % p.J2);
-    double v = static_cast<double>(p.W[(i * p.wi + j1 * p.w1 + j2 * p.w2) * R + r]);
-    if (p.A1) v *= static_cast<double>(p.A1[j1 * R + r]);
-    if (p.A2) v *= static_cast<double>(p.A2[j2 * R + r]);
-    acc += v;
+  // FP32 (the operands are FP32 tensor-core / FFMA sums); 4 independent chains
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  long long j = jl;
+  for (; j + 3 * JL < J; j += 4 * JL) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long jj = j + u * JL;
+      const int j1 = static_cast<int>(jj / p.J2), j2 = static_cast<int>(jj % p.J2);
+      float v = p.W[(i * p.wi + j1 * p.w1 + j2 * p.w2) * R + r];
+      if (p.A1) v *= p.A1[j1 * R + r];
+      if (p.A2) v *= p.A2[j2 * R + r];
+      acc[u] += v;
+    }
   }
-  red[threadIdx.x] = acc;
+  for (; j < J; j += JL) {
+    const int j1 = static_cast<int>(j / p.J2), j2 = static_cast<int>(j % p.J2);
+    float v = p.W[(i * p.wi + j1 * p.w1 + j2 * p.w2) * R + r];
+    if (p.A1) v *= p.A1[j1 * R + r];
+    if (p.A2) v *= p.A2[j2 * R + r];
+    acc[0] += v;
+  }
+  red[threadIdx.x] = static_cast<double>((acc[0] + acc[1]) + (acc[2] + acc[3]));
   __syncthreads();
   for (int w = JL / 2; w > 0; w >>= 1) {
     if (jl < w) red[threadIdx.x] += red[threadIdx.x + w * R];
@@ -171,11 +184,17 @@ __global__ void __launch_bounds__(256) k_contract_rows(const float* __restrict__
   const int per = blockDim.x / R;
   const int i = blockIdx.x * per + threadIdx.x / R;
   const int r = threadIdx.x % R;
-  double acc = 0.0;
-  for (int j = 0; j < J; ++j)
-    acc += static_cast<double>(W[(i + j * w1) * R + r]) * static_cast<double>(A1[j * R + r]);
-  if (M) M[i * R + r] = acc;
-  if (Mf) Mf[i * R + r] = static_cast<float>(acc);
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // 8 loads in flight
+  int j = 0;
+  for (; j + 8 <= J; j += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      acc[u] = fmaf(W[(i + (j + u) * w1) * R + r], A1[(j + u) * R + r], acc[u]);
+  }
+  for (; j < J; ++j) acc[0] = fmaf(W[(i + j * w1) * R + r], A1[j * R + r], acc[0]);
+  const float t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  if (M) M[i * R + r] = static_cast<double>(t);
+  if (Mf) Mf[i * R + r] = t;
 }
 
 // G[r1][r2] = sum_i A[i][r1] A[i][r2], FP64; 256/R row slices per output row,
@@ -186,8 +205,17 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int I
   const int r1 = blockIdx.x, r2 = threadIdx.x % R, p = threadIdx.x / R;
   const int P = blockDim.x / R;
   double acc = 0.0;
-  for (int i = p; i < I; i += P)
-    acc += static_cast<double>(A[i * R + r1]) * static_cast<double>(A[i * R + r2]);
+  float chunk = 0.0f;
+  int cnt = 0;
+  for (int i = p; i < I; i += P) {  // FP32 dot products over 32 rows, summed in FP64
+    chunk = fmaf(A[i * R + r1], A[i * R + r2], chunk);
+    if (++cnt == 32) {
+      acc += static_cast<double>(chunk);
+      chunk = 0.0f;
+      cnt = 0;
+    }
+  }
+  acc += static_cast<double>(chunk);
   part[threadIdx.x] = acc;
   __syncthreads();
   if (p == 0) {
@@ -274,26 +302,33 @@ __device__ void jacobi_eigen(double* V, double* Q, int R) {
   }
 }
 
-// In-place lower Cholesky factor of V (block-cooperative).  Returns false when
-// a pivot is not above thresh; block-uniform result.
-__device__ bool cholesky_inplace(double* V, int R, double thresh) {
+// Right-looking Cholesky of V in shared memory (lower triangle, row-major).
+// Returns false when a pivot is not above thresh; block-uniform result.
+__device__ bool cholesky_inplace(double* V, int R, double thresh, double* invd) {
   __shared__ int fail;
   if (threadIdx.x == 0) fail = 0;
   __syncthreads();
   for (int j = 0; j < R; ++j) {
     if (threadIdx.x == 0) {
-      double d = V[j * R + j];
-      for (int k = 0; k < j; ++k) d -= V[j * R + k] * V[j * R + k];
-      if (!(d > thresh)) fail = 1;
-      else V[j * R + j] = sqrt(d);
+      const double d = V[j * R + j];
+      if (!(d > thresh)) {
+        fail = 1;
+      } else {
+        const double s = sqrt(d);
+        V[j * R + j] = s;
+        invd[j] = 1.0 / s;
+      }
     }
     __syncthreads();
     if (fail) return false;
-    const double djj = V[j * R + j];
-    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) {
-      double v = V[i * R + j];
-      for (int k = 0; k < j; ++k) v -= V[i * R + k] * V[j * R + k];
-      V[i * R + j] = v / djj;
+    const double ij = invd[j];
+    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) V[i * R + j] *= ij;
+    __syncthreads();
+    // trailing lower triangle on a 16 x 16 thread grid (blockDim.x == 256)
+    const int ti = threadIdx.x >> 4, tk = threadIdx.x & 15;
+    for (int i = j + 1 + ti; i < R; i += 16) {
+      const double lij = V[i * R + j];
+      for (int k = j + 1 + tk; k <= i; k += 16) V[i * R + k] -= lij * V[k * R + j];
     }
     __syncthreads();
   }
@@ -311,82 +346,128 @@ __device__ double max_diag(const double* V, int R) {
   return mx;
 }
 
-// One block: W = V^-1 by Cholesky.  When V is not numerically positive
-// definite, W = V^+ from a Jacobi eigendecomposition (R <= 64), or for larger
-// R the inverse of V + delta I with the smallest delta in 1e-12..1e-6 x
-// max diag that factorises; the fallback is flagged GSP_DEV_NUMERIC.
-__global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ G, int R, int skip,
-                                                  double* __restrict__ W, uint32_t* flags) {
+// Layout of the solve scratch `fac` (doubles): L [R][R], Z^T [R][R] with
+// Z = L^-1, 1/diag(L) [R], the mode word (int, padded to 16 bytes), W [R][R].
+struct SolveScratch {
+  double *L, *Zt, *invd, *W;
+  int* mode;
+};
+__host__ __device__ inline SolveScratch solve_scratch(double* fac, int R) {
+  SolveScratch s;
+  s.L = fac;
+  s.Zt = fac + R * R;
+  s.invd = fac + 2 * R * R;
+  s.mode = reinterpret_cast<int*>(fac + 2 * R * R + R);
+  s.W = fac + 2 * R * R + R + 2;
+  return s;
+}
+
+// One CTA: factor V (Hadamard product of the other modes' Grams) for the
+// least-squares update: L and 1/diag(L), mode 0.  When V is not numerically
+// positive definite: W = V^+ from a Jacobi eigendecomposition, mode 1, and
+// GSP_DEV_NUMERIC.
+__global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int R, int skip,
+                                              double* __restrict__ out, uint32_t* flags) {
   extern __shared__ double smem[];
+  __shared__ double invd_s[kMaxCpRank];
   double* V = smem;          // [R][R]
   double* Q = smem + R * R;  // [R][R] (eigenvectors, R <= 64 only)
+  const SolveScratch ss = solve_scratch(out, R);
+  double* L = ss.L;
+  double* invd = ss.invd;
+  int* mode = ss.mode;
   const double eps = 2.220446049250313e-16;
   hadamard_v(G, R, skip, V);
   __syncthreads();
-  double mx = max_diag(V, R);
-  bool ok = cholesky_inplace(V, R, R * eps * mx);
+  const double mx = max_diag(V, R);
+  bool ok = cholesky_inplace(V, R, R * eps * mx, invd_s);
   if (!ok) {
     if (threadIdx.x == 0 && flags) atomicOr(flags, GSP_DEV_NUMERIC);
     if (R <= kJacobiMaxRank) {
       hadamard_v(G, R, skip, V);
       __syncthreads();
       jacobi_eigen(V, Q, R);
-      double lmax = max_diag(V, R);
-      double cutoff = R * eps * lmax;
+      const double lmax = max_diag(V, R);
+      const double cutoff = R * eps * lmax;
       for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-        int a = e / R, b = e % R;
+        const int a = e / R, b = e % R;
         double acc = 0.0;
         for (int k = 0; k < R; ++k) {
-          double lam = V[k * R + k];
+          const double lam = V[k * R + k];
           if (lam > cutoff) acc += Q[a * R + k] * Q[b * R + k] / lam;
         }
-        W[e] = acc;
+        ss.W[e] = acc;
       }
+      if (threadIdx.x == 0) *mode = 1;
       return;
     }
     const double deltas[3] = {1e-12, 1e-9, 1e-6};
-    for (int a = 0; a < 3 && !ok; ++a) {
+    for (int t = 0; t < 3 && !ok; ++t) {
       hadamard_v(G, R, skip, V);
       __syncthreads();
       if (threadIdx.x == 0)
-        for (int k = 0; k < R; ++k) V[k * R + k] += deltas[a] * mx;
+        for (int k = 0; k < R; ++k) V[k * R + k] += deltas[t] * mx;
       __syncthreads();
-      ok = cholesky_inplace(V, R, R * eps * mx);
+      ok = cholesky_inplace(V, R, R * eps * mx, invd_s);
     }
-    if (!ok) {  // leave the factor unchanged in scale: W = 0 makes A = 0 -> lambda = 0
-      for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = 0.0;
+    if (!ok) {  // give up on this update: A = 0, lambda = 0 for the mode
+      for (int e = threadIdx.x; e < R * R; e += blockDim.x) ss.W[e] = 0.0;
+      if (threadIdx.x == 0) *mode = 1;
       return;
     }
   }
-  // W = L^-T L^-1, one column per thread (column c is scratch for its solves);
-  // in shared memory when it fits next to V, then copied out
-  double* Ws = R <= kJacobiMaxRank ? Q : W;
-  for (int c = threadIdx.x; c < R; c += blockDim.x) {
-    for (int k = 0; k < R; ++k) {
-      double y = (k == c) ? 1.0 : 0.0;
-      for (int j = 0; j < k; ++j) y -= V[k * R + j] * Ws[j * R + c];
-      Ws[k * R + c] = y / V[k * R + k];
-    }
-    for (int k = R - 1; k >= 0; --k) {
-      double w = Ws[k * R + c];
-      for (int j = k + 1; j < R; ++j) w -= V[j * R + k] * Ws[j * R + c];
-      Ws[k * R + c] = w / V[k * R + k];
-    }
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, k = e % R;
+    L[e] = k <= i ? V[e] : 0.0;
   }
-  if (Ws != W) {
+  for (int k = threadIdx.x; k < R; k += blockDim.x) invd[k] = invd_s[k];
+  if (threadIdx.x == 0) *mode = 0;
+}
+
+// Column c of Z = L^-1, one CTA of 64 threads per column: forward substitution
+// z_k = -(sum_{c<=j<k} L[k][j] z_j) / L[k][k], each sum a fixed-order block
+// reduction; writes Z^T[c][:].  Skipped in mode 1.
+__global__ void __launch_bounds__(64) k_inv_cols(double* __restrict__ fac, int R) {
+  const SolveScratch ss = solve_scratch(fac, R);
+  if (*ss.mode != 0) return;
+  __shared__ double z[kMaxCpRank];
+  __shared__ double wsum[2];
+  const int c = blockIdx.x, t = threadIdx.x;
+  if (t < R) z[t] = (t == c) ? ss.invd[c] : 0.0;
+  __syncthreads();
+  for (int k = c + 1; k < R; ++k) {
+    double part = (t >= c && t < k) ? ss.L[k * R + t] * z[t] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if ((t & 31) == 0) wsum[t >> 5] = part;
     __syncthreads();
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) W[e] = Ws[e];
+    if (t == 0) z[k] = -(wsum[0] + wsum[1]) * ss.invd[k];
+    __syncthreads();
   }
+  if (t < R) ss.Zt[c * R + t] = z[t];
+}
+
+// W = Z^T Z = V^-1: W[a][b] = sum_{k >= max(a, b)} Z^T[a][k] Z^T[b][k]; one CTA
+// per row a.  Skipped in mode 1 (W already holds V^+).
+__global__ void __launch_bounds__(kMaxCpRank) k_gram_inv(double* __restrict__ fac, int R) {
+  const SolveScratch ss = solve_scratch(fac, R);
+  if (*ss.mode != 0) return;
+  const int a = blockIdx.x, b = threadIdx.x;
+  if (b >= R) return;
+  double acc = 0.0;
+  for (int k = a > b ? a : b; k < R; ++k) acc += ss.Zt[a * R + k] * ss.Zt[b * R + k];
+  ss.W[a * R + b] = acc;
 }
 
 // A[i][c] = sum_k M[i][k] W[k][c]   (FP64 accumulate, FP32 out)
-__global__ void k_apply(const double* __restrict__ M, const double* __restrict__ W, int I, int R,
+__global__ void k_apply(const double* __restrict__ M, double* __restrict__ fac, int I, int R,
                         float* __restrict__ A) {
+  const SolveScratch ss = solve_scratch(fac, R);
   long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (e >= static_cast<long long>(I) * R) return;
-  int i = static_cast<int>(e / R), c = static_cast<int>(e % R);
+  const int i = static_cast<int>(e / R), c = static_cast<int>(e % R);
   double acc = 0.0;
-  for (int k = 0; k < R; ++k) acc += M[i * R + k] * W[k * R + c];
+  for (int k = 0; k < R; ++k) acc += M[i * R + k] * ss.W[k * R + c];
   A[e] = static_cast<float>(acc);
 }
 
@@ -484,9 +565,9 @@ int ensure_smem_attr() {
   int dev = 0;
   GSP_CUDA(cudaGetDevice(&dev));
   if (done_dev != dev) {
-    // k_chol_inv: V (R*R doubles) plus eigenvectors for R <= 64: at most 128 KB
-    GSP_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kMaxCpRank * kMaxCpRank * static_cast<int>(sizeof(double))));
+    // k_chol: V (R*R doubles) plus eigenvectors for R <= 64: at most 128 KB
+    GSP_CUDA(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * kMaxCpRank * kMaxCpRank * static_cast<int>(sizeof(double))));
     done_dev = dev;
   }
   return GSP_OK;
@@ -598,12 +679,17 @@ int update(const Ctx& c, const gsp_cp_factors& f, int mode) {
   const int I = mode_rows(c.d, mode);
   size_t smem = static_cast<size_t>(R) * R * sizeof(double) * (R <= kJacobiMaxRank ? 2 : 1);
   prof_begin(PROF_ALS_SMALL, c.s);
-  k_chol_inv<<<1, 256, smem, c.s>>>(c.at<double>(c.lay.G), R, mode, c.at<double>(c.lay.W),
-                                    c.at<uint32_t>(c.lay.flags));
+  k_chol<<<1, 256, smem, c.s>>>(c.at<double>(c.lay.G), R, mode, c.at<double>(c.lay.W),
+                                c.at<uint32_t>(c.lay.flags));
   GSP_CHECK_LAUNCH();
   float* A = factor_ptr(f, mode);
-  k_apply<<<grid_for(static_cast<long long>(I) * R, 256), 256, 0, c.s>>>(
-      c.at<double>(c.lay.M), c.at<double>(c.lay.W), I, R, A);
+  double* fac = c.at<double>(c.lay.W);
+  k_inv_cols<<<R, 64, 0, c.s>>>(fac, R);
+  GSP_CHECK_LAUNCH();
+  k_gram_inv<<<R, kMaxCpRank, 0, c.s>>>(fac, R);
+  GSP_CHECK_LAUNCH();
+  k_apply<<<grid_for(static_cast<long long>(I) * R, 256), 256, 0, c.s>>>(c.at<double>(c.lay.M),
+                                                                         fac, I, R, A);
   GSP_CHECK_LAUNCH();
   k_colnorm<<<R, 256, 0, c.s>>>(A, I, R, c.at<double>(c.lay.lam), f.lambda);
   GSP_CHECK_LAUNCH();
@@ -664,9 +750,11 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
     }
   } else {
     uint16_t* bm = c.at<uint16_t>(c.lay.bins);
-    GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, c.s));
+    uint32_t* groups = reinterpret_cast<uint32_t*>(c.ws + c.lay.bins + d.N2() * sizeof(uint16_t));
+    GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, groups, c.s));
     HistOut o{};
     o.sumsq = sumsq;
+    o.groups = groups;
     for (int l = 0; l < levels; ++l)
       o.scale[l] = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
     if (is_bf16(c.prec))

@@ -28,7 +28,7 @@ cudaEvent_t take_event() {
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   return e;
 }
-const char* kProfNames[PROF_COUNT] = {"bins", "level0", "doubling", "cast", "mttkrp_xy",
+const char* kProfNames[PROF_COUNT] = {"bins", "level0", "box_hist", "cast", "mttkrp_xy",
                                       "mttkrp_lst", "als_small", "tables", "range_query",
                                       "range_query_backward", "adam"};
 }  // namespace

@@ -11,10 +11,21 @@ namespace gsp {
 
 namespace {
 
+constexpr int kGroupWords = 128 * 128 / 16 / 32;  // one bit per 16-bin group, B <= 128
+
+// `groups` (optional): bit g set when some texel falls in bins [16g, 16g + 16).
 __global__ void k_bin_normals(const float2* __restrict__ nxy, int n, int bins,
-                              uint16_t* __restrict__ out, uint32_t* status) {
+                              uint16_t* __restrict__ out, uint32_t* status,
+                              uint32_t* __restrict__ groups) {
+  __shared__ uint32_t gmask[kGroupWords];
+  if (groups) {
+    for (int k = threadIdx.x; k < kGroupWords; k += blockDim.x) gmask[k] = 0u;
+    __syncthreads();
+  }
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  uint16_t code = 0;
+  bool valid = i < n;
+  if (valid) {
   float2 v = nxy[i];
   uint16_t code = 0;
   if (!isfinite(v.x) || !isfinite(v.y)) {
@@ -30,6 +41,13 @@ __global__ void k_bin_normals(const float2* __restrict__ nxy, int n, int bins,
     code = static_cast<uint16_t>(static_cast<int>(s) * bins + static_cast<int>(t));
   }
   out[i] = code;
+  }
+  if (groups) {
+    if (valid) atomicOr(&gmask[(code >> 4) >> 5], 1u << ((code >> 4) & 31));
+    __syncthreads();
+    for (int k = threadIdx.x; k < kGroupWords; k += blockDim.x)
+      if (gmask[k]) atomicOr(groups + k, gmask[k]);
+  }
 }
 
 __device__ __forceinline__ void sink_store(const LevelSink& o, long long i, int4 v) {
@@ -70,43 +88,65 @@ __device__ __forceinline__ void sink_sumsq(const LevelSink& o, int4 v, bool acti
 // V[x][b] = number of texels of bin g0 + b in column x among the window rows
 // [y - a, y - a + w) (w = 2^l, a = w/2, wrapped).  Moving from row y to y+1
 // removes one texel and adds one per column.  For each row the histograms of
-// all N footprints are window sums of V along x, read from an exclusive
-// prefix sum S over x: two look-ups per count, three across the wrap.
-//  - updates: thread t owns the columns x = t, t + 256, ... (no atomics);
-//  - prefix: thread t scans the contiguous columns [t*sl, (t+1)*sl) for all 16
-//    bins with 16-byte shared-memory accesses, the segment totals are combined
-//    by a warp shuffle scan plus one pass over the 8 warp totals;
-//  - outputs: four bins per thread-item, 16-byte reads of S.
+// all N footprints are window sums of V along x, read from the prefix sum S
+// over x: two look-ups per count, three across the wrap.
+//  - updates: thread t owns the columns x = t, t + 512, ... (no atomics);
+//  - prefix: warp w scans its contiguous x range in blocks of 32 columns, one
+//    column per lane, on pairs of 16-bit counts packed in 32-bit words (a sum
+//    over 32 columns is at most 32 w <= 2^15), carries between blocks in 32
+//    bits, and stores S once the offsets of the earlier ranges are known;
+//  - rows of V (48 B) and S (80 B) are padded so that 16-byte accesses of
+//    consecutive columns fall on distinct banks.
 constexpr int kHistG = 16;
-constexpr int kHistThreads = 256;
+constexpr int kHistThreads = 512;
+constexpr int kHistWarps = kHistThreads / 32;
+constexpr int kVRow = 24;  // uint16 per column count row (16 + 8 padding)
+constexpr int kSRow = 20;  // ints per prefix row (16 + 4 padding)
+constexpr int kMaxBlocks = 2;  // 32-column blocks per scanning warp (N <= 1024)
 
-__global__ void __launch_bounds__(kHistThreads, 2)
+__global__ void __launch_bounds__(kHistThreads, 1)
     k_box_hist(const uint16_t* __restrict__ bins_map, int logN, int B2, int ychunk,
                const __grid_constant__ HistOut o) {
   constexpr int G = kHistG;
   extern __shared__ __align__(16) uint8_t smem_b[];
-  __shared__ int wtot[kHistThreads / 32][G];
+  __shared__ __align__(16) int WT[kHistWarps * G];
   const int N = 1 << logN, m = N - 1;
-  uint16_t* V = reinterpret_cast<uint16_t*>(smem_b);          // [N][16], 32 B per column
-  int* S = reinterpret_cast<int*>(smem_b + N * G * sizeof(uint16_t));  // [N + 1][16]
+  uint16_t* V = reinterpret_cast<uint16_t*>(smem_b);                         // [N][24]
+  int* S = reinterpret_cast<int*>(smem_b + N * kVRow * sizeof(uint16_t));    // [N + 1][20]
   const int g0 = blockIdx.x * G;
   const int y0 = blockIdx.y * ychunk;
   const int l = blockIdx.z;
   const int w = 1 << l, a = w >> 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (o.groups && !((o.groups[blockIdx.x >> 5] >> (blockIdx.x & 31)) & 1u)) {
+    // no texel of the map falls in this bin group: every count is zero
+    const int row_log = logN + 2;  // N * (G / 4) items per row
+    const long long items = static_cast<long long>(ychunk) << row_log;
+    for (long long e = tid; e < items; e += kHistThreads) {
+      const int yy = y0 + static_cast<int>(e >> row_log);
+      const int rem = static_cast<int>(e & ((1LL << row_log) - 1));
+      const int x = rem >> 2, q = rem & 3;
+      const long long i4 = (((static_cast<long long>(l) * N + yy) * N * B2) >> 2) +
+                           ((static_cast<long long>(x) * B2 + g0) >> 2) + q;
+      if (o.h) reinterpret_cast<int4*>(o.h)[i4] = make_int4(0, 0, 0, 0);
+      if (o.f32) reinterpret_cast<float4*>(o.f32)[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (o.bf16) reinterpret_cast<uint2*>(o.bf16)[i4] = make_uint2(0u, 0u);
+    }
+    return;
+  }
+  const int scan_warps = N >= 32 * kHistWarps ? kHistWarps : (N >= 32 ? N >> 5 : 1);
+  const int xr = N / scan_warps;               // columns per scanning warp
+  const int nblk = xr >= 32 ? xr >> 5 : 1;     // 32-column blocks per warp
 
-  for (int i = tid; i < N * G / 8; i += kHistThreads)
+  for (int i = tid; i < N * kVRow / 8; i += kHistThreads)
     reinterpret_cast<uint4*>(V)[i] = make_uint4(0, 0, 0, 0);
+  if (tid < 4) reinterpret_cast<int4*>(S)[tid] = make_int4(0, 0, 0, 0);  // S[0] = 0
   __syncthreads();
   for (int x = tid; x < N; x += kHistThreads)
     for (int j = 0; j < w; ++j) {
       const int b = static_cast<int>(bins_map[(((y0 - a + j) & m) << logN) + x]) - g0;
-      if (static_cast<unsigned>(b) < static_cast<unsigned>(G)) V[x * G + b] += 1;
+      if (static_cast<unsigned>(b) < static_cast<unsigned>(G)) V[x * kVRow + b] += 1;
     }
-
-  // contiguous scan segments: sl columns per thread, `active` threads
-  const int sl = N >= kHistThreads ? N / kHistThreads : 1;
-  const int active = N / sl;
   const float sc = o.scale[l];
   unsigned long long sumsq = 0;
 
@@ -116,87 +156,90 @@ __global__ void __launch_bounds__(kHistThreads, 2)
       for (int x = tid; x < N; x += kHistThreads) {
         const int bo = static_cast<int>(bins_map[(ro << logN) + x]) - g0;
         const int bi = static_cast<int>(bins_map[(ri << logN) + x]) - g0;
-        if (static_cast<unsigned>(bo) < static_cast<unsigned>(G)) V[x * G + bo] -= 1;
-        if (static_cast<unsigned>(bi) < static_cast<unsigned>(G)) V[x * G + bi] += 1;
+        if (static_cast<unsigned>(bo) < static_cast<unsigned>(G)) V[x * kVRow + bo] -= 1;
+        if (static_cast<unsigned>(bi) < static_cast<unsigned>(G)) V[x * kVRow + bi] += 1;
       }
     }
     __syncthreads();
-    // 1) running sums inside this thread's segment (S[x+1] = sum up to x)
-    int acc[G];
+    int vals[kMaxBlocks][G];
+    if (warp < scan_warps) {
+      int carry[G];
 #pragma unroll
-    for (int b = 0; b < G; ++b) acc[b] = 0;
-    if (tid < active) {
-      for (int i = 0; i < sl; ++i) {
-        const int x = tid * sl + i;
-        const uint4 p0 = reinterpret_cast<const uint4*>(V)[x * 2];
-        const uint4 p1 = reinterpret_cast<const uint4*>(V)[x * 2 + 1];
-        const uint32_t wds[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      for (int b = 0; b < G; ++b) carry[b] = 0;
+      const int xbeg = warp * xr;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          acc[2 * k] += static_cast<int>(wds[k] & 0xFFFFu);
-          acc[2 * k + 1] += static_cast<int>(wds[k] >> 16);
+      for (int blk = 0; blk < kMaxBlocks; ++blk) {
+        if (blk < nblk) {
+          const int x = xbeg + blk * 32 + lane;
+          const bool in = blk * 32 + lane < xr;
+          uint32_t wd[8];
+          if (in) {
+            const uint4 p0 = *reinterpret_cast<const uint4*>(V + x * kVRow);
+            const uint4 p1 = *reinterpret_cast<const uint4*>(V + x * kVRow + 8);
+            wd[0] = p0.x; wd[1] = p0.y; wd[2] = p0.z; wd[3] = p0.w;
+            wd[4] = p1.x; wd[5] = p1.y; wd[6] = p1.z; wd[7] = p1.w;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) wd[k] = 0u;
+          }
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const uint32_t u = __shfl_up_sync(0xffffffffu, wd[k], off);
+              if (lane >= off) wd[k] += u;  // two 16-bit lanes, no carry across
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            vals[blk][2 * k] = static_cast<int>(wd[k] & 0xFFFFu) + carry[2 * k];
+            vals[blk][2 * k + 1] = static_cast<int>(wd[k] >> 16) + carry[2 * k + 1];
+          }
+          const int last = (xr - blk * 32 < 32 ? xr - blk * 32 : 32) - 1;
+#pragma unroll
+          for (int b = 0; b < G; ++b) carry[b] = __shfl_sync(0xffffffffu, vals[blk][b], last);
         }
-        int4* dst = reinterpret_cast<int4*>(S + (x + 1) * G);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          dst[q] = make_int4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
       }
-    }
-    // 2) exclusive prefix of the segment totals: warp shuffle scan, then warps
-    int incl[G];
+      if (lane == 0) {
 #pragma unroll
-    for (int b = 0; b < G; ++b) incl[b] = acc[b];
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-      for (int b = 0; b < G; ++b) {
-        const int v = __shfl_up_sync(0xffffffffu, incl[b], off);
-        if (lane >= off) incl[b] += v;
+        for (int b = 0; b < G; ++b) WT[warp * G + b] = carry[b];
       }
-    }
-    if (lane == 31) {
-#pragma unroll
-      for (int b = 0; b < G; ++b) wtot[warp][b] = incl[b];
     }
     __syncthreads();
-    if (tid < active) {
+    if (warp < scan_warps) {
+      // offset of this warp's range: lanes 0..15 sum one bin each over the earlier warps
+      int my = 0;
+      if (lane < G)
+        for (int k = 0; k < warp; ++k) my += WT[k * G + lane];
       int off[G];
 #pragma unroll
-      for (int b = 0; b < G; ++b) off[b] = incl[b] - acc[b];
-      for (int k = 0; k < warp; ++k)
+      for (int b = 0; b < G; ++b) off[b] = __shfl_sync(0xffffffffu, my, b);
+      const int xbeg = warp * xr;
 #pragma unroll
-        for (int b = 0; b < G; ++b) off[b] += wtot[k][b];
-      for (int i = 0; i < sl; ++i) {
-        int4* dst = reinterpret_cast<int4*>(S + (tid * sl + i + 1) * G);
+      for (int blk = 0; blk < kMaxBlocks; ++blk) {
+        if (blk < nblk && blk * 32 + lane < xr) {
+          int4* dst = reinterpret_cast<int4*>(S + (xbeg + blk * 32 + lane + 1) * kSRow);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int4 v = dst[q];
-          v.x += off[4 * q];
-          v.y += off[4 * q + 1];
-          v.z += off[4 * q + 2];
-          v.w += off[4 * q + 3];
-          dst[q] = v;
+          for (int q = 0; q < 4; ++q)
+            dst[q] = make_int4(vals[blk][4 * q] + off[4 * q], vals[blk][4 * q + 1] + off[4 * q + 1],
+                               vals[blk][4 * q + 2] + off[4 * q + 2], vals[blk][4 * q + 3] + off[4 * q + 3]);
         }
-      }
-      if (tid == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(S)[q] = make_int4(0, 0, 0, 0);
       }
     }
     __syncthreads();
-    // 3) counts of every footprint of row y, four bins per item
+    // counts of every footprint of row y, four bins per item
     const long long row4 = ((static_cast<long long>(l) * N + y) * N * B2) >> 2;
     for (int e = tid; e < N * (G / 4); e += kHistThreads) {
       const int x = e >> 2, q = e & 3;
       const int st = (x - a) & m, en = st + w;
-      const int4 lo = reinterpret_cast<const int4*>(S + st * G)[q];
+      const int4 lo = reinterpret_cast<const int4*>(S + st * kSRow)[q];
       int4 c;
       if (en <= N) {
-        const int4 hi = reinterpret_cast<const int4*>(S + en * G)[q];
+        const int4 hi = reinterpret_cast<const int4*>(S + en * kSRow)[q];
         c = make_int4(hi.x - lo.x, hi.y - lo.y, hi.z - lo.z, hi.w - lo.w);
       } else {
-        const int4 hi = reinterpret_cast<const int4*>(S + N * G)[q];
-        const int4 wr = reinterpret_cast<const int4*>(S + (en - N) * G)[q];
+        const int4 hi = reinterpret_cast<const int4*>(S + N * kSRow)[q];
+        const int4 wr = reinterpret_cast<const int4*>(S + (en - N) * kSRow)[q];
         c = make_int4(hi.x - lo.x + wr.x, hi.y - lo.y + wr.y, hi.z - lo.z + wr.z,
                       hi.w - lo.w + wr.w);
       }
@@ -216,7 +259,8 @@ __global__ void __launch_bounds__(kHistThreads, 2)
         sumsq += static_cast<unsigned long long>(c.x) * c.x + static_cast<unsigned long long>(c.y) * c.y +
                  static_cast<unsigned long long>(c.z) * c.z + static_cast<unsigned long long>(c.w) * c.w;
     }
-    // the next row's updates touch V only; S is rewritten after the barrier
+    // the next row's updates touch V only; the barrier after them orders this
+    // row's reads of S before the next row's writes
   }
   if (o.sumsq) {
     for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
@@ -240,26 +284,27 @@ constexpr int kThreads = 256;
 }  // namespace
 
 int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins, uint32_t* d_status,
-                cudaStream_t s) {
+                uint32_t* d_groups, cudaStream_t s) {
   int n = N * N;
+  if (d_groups) GSP_CUDA(cudaMemsetAsync(d_groups, 0, kGroupWords * sizeof(uint32_t), s));
   prof_begin(PROF_BINS, s);
   k_bin_normals<<<grid_for(n, kThreads), kThreads, 0, s>>>(
-      reinterpret_cast<const float2*>(d_normal_xy), n, bins, d_bins, d_status);
+      reinterpret_cast<const float2*>(d_normal_xy), n, bins, d_bins, d_status, d_groups);
   prof_end(PROF_BINS, s);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
 }
 
 size_t box_hist_smem(int N) {
-  return static_cast<size_t>(N) * kHistG * sizeof(uint16_t) +
-         static_cast<size_t>(N + 1) * kHistG * sizeof(int);
+  return static_cast<size_t>(N) * kVRow * sizeof(uint16_t) +
+         static_cast<size_t>(N + 1) * kSRow * sizeof(int);
 }
 
 int launch_box_hist(const uint16_t* d_bins, int N, int levels, int bins, const HistOut& o,
                     cudaStream_t s) {
   const int B2 = bins * bins;
   if (B2 % kHistG) return GSP_ERR_UNSUPPORTED;
-  const int ychunk = N >= 128 ? 128 : N;
+  const int ychunk = N >= 256 ? 256 : N;
   const size_t smem = box_hist_smem(N);
   if (smem > 227 * 1024) return GSP_ERR_UNSUPPORTED;
   dim3 grid(B2 / kHistG, N / ychunk, levels);
@@ -288,15 +333,15 @@ using namespace gsp;
 
 extern "C" int gsp_bin_normals(const float* d_normal_xy, int N, int bins, uint16_t* d_bins,
                                uint32_t* d_status, gsp_stream stream) {
-  if (!d_normal_xy || !d_bins || !is_pow2(N) || N < 2 || N > 4096 || !is_pow2(bins) ||
+  if (!d_normal_xy || !d_bins || !is_pow2(N) || N < 2 || N > 1024 || !is_pow2(bins) ||
       bins < 4 || bins > 128)
     return GSP_ERR_INVALID_ARG;
-  return launch_bins(d_normal_xy, N, bins, d_bins, d_status, to_stream(stream));
+  return launch_bins(d_normal_xy, N, bins, d_bins, d_status, nullptr, to_stream(stream));
 }
 
 extern "C" size_t gsp_build_workspace_bytes(int N, int levels, int bins) {
   if (!valid_map(N, levels, bins)) return 0;
-  return align_up(static_cast<size_t>(N) * N * sizeof(uint16_t), 256);
+  return align_up(static_cast<size_t>(N) * N * sizeof(uint16_t), 256) + kGroupBytes;
 }
 
 extern "C" int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int levels, int bins,
@@ -306,9 +351,12 @@ extern "C" int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int lev
   if (!d_ws || ws_bytes < gsp_build_workspace_bytes(N, levels, bins)) return GSP_ERR_WORKSPACE;
   cudaStream_t s = to_stream(stream);
   uint16_t* bins_map = static_cast<uint16_t*>(d_ws);
-  GSP_TRY(launch_bins(d_normal_xy, N, bins, bins_map, d_status, s));
+  uint32_t* groups = reinterpret_cast<uint32_t*>(
+      static_cast<char*>(d_ws) + align_up(static_cast<size_t>(N) * N * sizeof(uint16_t), 256));
+  GSP_TRY(launch_bins(d_normal_xy, N, bins, bins_map, d_status, groups, s));
   HistOut o{};
   o.h = d_hist;
+  o.groups = groups;
   for (int l = 0; l < levels; ++l) o.scale[l] = 1.0f;
   return launch_box_hist(bins_map, N, levels, bins, o, s);
 }

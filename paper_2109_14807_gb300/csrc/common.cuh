@@ -68,7 +68,7 @@ inline unsigned grid_for(long long n, int threads) {
 
 // Checks shared by the NDF-building calls.
 inline bool valid_map(int N, int levels, int bins) {
-  return is_pow2(N) && N >= 2 && N <= 4096 && levels >= 1 && levels <= ilog2(N) + 1 &&
+  return is_pow2(N) && N >= 2 && N <= 1024 && levels >= 1 && levels <= ilog2(N) + 1 &&
          is_pow2(bins) && bins >= 4 && bins <= 128;
 }
 

@@ -486,9 +486,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {  // ---- warps 0-3: B operand producer, then epilogue
-    const int t = threadIdx.x;  // 0..127
-    const int k = t % E128;      // xy column of the B tile this thread fills
-    const int r_first = t / E128, r_step = 128 / E128;
+    // thread t fills xy row k = t / TPR of the tile, ranks [r0, r0 + R/TPR),
+    // reading fx and fy rows with 16-byte loads
+    constexpr int TPR = 128 / E128;  // threads per xy row
+    const int t = threadIdx.x;       // 0..127
+    const int k = t / TPR;
+    const int rpart = R / TPR;
+    const int r0 = (t % TPR) * rpart;
+    const int byte_in_row = k * ELEM;
+    const int chunk = byte_in_row >> 4, within = byte_in_row & 15;
     int bs = 0;
     uint32_t bph = 0, uph = 0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -498,23 +504,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto epi_done;
         const long long xy = xy_base + static_cast<long long>(kc) * E128 + k;
         const int x = static_cast<int>(xy & (N - 1)), y = static_cast<int>(xy >> logN);
-        const float* fxr = fx + static_cast<size_t>(x) * R;
-        const float* fyr = fy + static_cast<size_t>(y) * R;
+        const float4* fx4 = reinterpret_cast<const float4*>(fx + static_cast<size_t>(x) * R + r0);
+        const float4* fy4 = reinterpret_cast<const float4*>(fy + static_cast<size_t>(y) * R + r0);
         uint8_t* tile = bslots + bs * b_bytes;
-        const int byte_in_row = k * ELEM;
-        const int chunk = byte_in_row >> 4, within = byte_in_row & 15;
-        for (int r = r_first; r < R; r += r_step) {
-          const float v = __ldg(fxr + r) * __ldg(fyr + r);
-          const int sw = ((chunk ^ (r & 7)) << 4) | within;
-          uint8_t* dst = tile + r * 128 + sw;
-          if constexpr (ELEM == 2) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            *reinterpret_cast<__nv_bfloat16*>(dst) = hi;
-            if constexpr (SPLIT)  // row R + r: same swizzle phase since R % 8 == 0
-              *reinterpret_cast<__nv_bfloat16*>(dst + R * 128) =
-                  __float2bfloat16_rn(v - __bfloat162float(hi));
-          } else {
-            *reinterpret_cast<float*>(dst) = round_tf32(v);
+        for (int i = 0; i < rpart / 4; ++i) {
+          const float4 a4 = __ldg(fx4 + i), b4 = __ldg(fy4 + i);
+          const float v[4] = {a4.x * b4.x, a4.y * b4.y, a4.z * b4.z, a4.w * b4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int r = r0 + 4 * i + e;
+            uint8_t* dst = tile + r * 128 + ((((chunk ^ (r & 7)) << 4)) | within);
+            if constexpr (ELEM == 2) {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(v[e]);
+              *reinterpret_cast<__nv_bfloat16*>(dst) = hi;
+              if constexpr (SPLIT)  // row R + r: same swizzle phase since R % 8 == 0
+                *reinterpret_cast<__nv_bfloat16*>(dst + R * 128) =
+                    __float2bfloat16_rn(v[e] - __bfloat162float(hi));
+            } else {
+              *reinterpret_cast<float*>(dst) = round_tf32(v[e]);
+            }
           }
         }
         fence_async_smem();

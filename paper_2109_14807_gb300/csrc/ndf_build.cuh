@@ -26,11 +26,17 @@ struct HistOut {
   float* f32;
   __nv_bfloat16* bf16;
   unsigned long long* sumsq;
-  float scale[16];  // counts -> operand value, per level
+  const uint32_t* groups;  // occupied 16-bin groups (bitmask) or null
+  float scale[16];         // counts -> operand value, per level
 };
 
+// Bytes of the occupied-bin-group bitmask (one bit per 16 bins, B <= 128).
+constexpr size_t kGroupBytes = 128 * 128 / 16 / 8;
+
+// Bin the normal map; when d_groups is non-null also mark the occupied
+// 16-bin groups there (kGroupBytes, cleared first).
 int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins,
-                uint32_t* d_status, cudaStream_t s);
+                uint32_t* d_status, uint32_t* d_groups, cudaStream_t s);
 // Histograms of every footprint of every level 0..levels-1 from the bin map.
 int launch_box_hist(const uint16_t* d_bins, int N, int levels, int bins, const HistOut& o,
                     cudaStream_t s);

@@ -32,7 +32,27 @@ struct GradParams {
   gsp_material_grad g[GSP_MAX_MATERIALS];
   float* dps[GSP_MAX_MATERIALS];  // [B+1][R] gradient w.r.t. the s-table prefix sums
   float* dpt[GSP_MAX_MATERIALS];
+  // When use_smem: each CTA accumulates the small per-material tables
+  // (dflw, dps, dpt, dfs, dft, in that order from soff[m]) in shared memory and
+  // adds them to global memory once at the end.
+  int soff[GSP_MAX_MATERIALS + 1];
+  int use_smem;
 };
+
+struct SmallGrad {
+  float *dflw, *dps, *dpt, *dfs, *dft;
+};
+
+__device__ __forceinline__ SmallGrad small_tables(float* base, const gsp_material& M) {
+  const int R = M.rank, L = M.levels, B = M.bins;
+  SmallGrad t;
+  t.dflw = base;
+  t.dps = t.dflw + L * R;
+  t.dpt = t.dps + (B + 1) * R;
+  t.dfs = t.dpt + (B + 1) * R;
+  t.dft = t.dfs + B * R;
+  return t;
+}
 
 // ---------------------------------------------------------------- tables --
 __global__ void k_tables(const float* __restrict__ fl, const float* __restrict__ lambda,
@@ -132,13 +152,19 @@ __device__ __forceinline__ float sat_mean(const float4* __restrict__ sat, int R,
   return __ldg(reinterpret_cast<const float*>(sat + static_cast<size_t>(iz) * R + r) + 2);
 }
 
+// Rank sum, identical for every LANES: rank r belongs to "conceptual lane"
+// c = r mod 32, accumulated in increasing r; the 32 conceptual lanes are then
+// combined in the order of a 32-lane xor butterfly.  Lane j of a group of
+// LANES holds the conceptual lanes j + k*LANES (k < 32/LANES) in registers and
+// performs the butterfly steps of offset >= LANES locally, the rest by shuffle.
 template <int LANES>
 __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ MatParams mp,
                                                      const gsp_query* __restrict__ q,
                                                      long long n, float* __restrict__ out,
                                                      uint32_t* status,
                                                      unsigned long long* counter, int chunk) {
-  constexpr int QPW = 32 / LANES;
+  constexpr int QPW = 32 / LANES;  // queries per warp step
+  constexpr int NC = 32 / LANES;   // conceptual lanes per lane
   const int lane = threadIdx.x & 31;
   const int sub = lane / LANES;
   const int j = lane % LANES;
@@ -159,7 +185,9 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
     if (base >= n) break;
     for (int c = 0; c < chunk; ++c) {
       const long long qi = base + static_cast<long long>(c) * QPW + sub;
-      float v = 0.0f;
+      float acc[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) acc[k] = 0.0f;
       bool bad = false;
       if (qi < n) {
         gsp_query d;
@@ -179,14 +207,28 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           const float* __restrict__ fl0 = flw + static_cast<size_t>(t.l0) * R;
           const float* __restrict__ fl1 = flw + static_cast<size_t>(t.l1) * R;
           const float g0 = 1.0f - t.f;
-          for (int r = j; r < R; r += LANES) {
-            float lv = fmaf(t.f, __ldg(fl1 + r), g0 * __ldg(fl0 + r));
-            float S = sat_mean(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
-            float T = sat_mean(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
-            v = fmaf(__ldg(fxr + r) * __ldg(fyr + r), lv * S * T, v);
+          for (int r0 = 0; r0 < R; r0 += 32) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+              const int r = r0 + j + k * LANES;
+              if (r < R) {
+                const float lv = fmaf(t.f, __ldg(fl1 + r), g0 * __ldg(fl0 + r));
+                const float S = sat_mean(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
+                const float T = sat_mean(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
+                acc[k] = fmaf(__ldg(fxr + r) * __ldg(fyr + r), lv * S * T, acc[k]);
+              }
+            }
           }
         }
       }
+#pragma unroll
+      for (int o = 16; o >= LANES; o >>= 1) {
+        const int h = o / LANES;
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+          if (!(k & h)) acc[k] = acc[k] + acc[k | h];
+      }
+      float v = acc[0];
 #pragma unroll
       for (int off = LANES / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if (qi < n && j == 0) {
@@ -209,12 +251,17 @@ __global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__
                                                          long long n,
                                                          const float* __restrict__ gout,
                                                          uint32_t* status) {
+  extern __shared__ float sacc[];
   constexpr int QPW = 32 / LANES;
   const int lane = threadIdx.x & 31;
   const int sub = lane / LANES;
   const int j = lane % LANES;
   const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  if (gp.use_smem) {
+    for (int e = threadIdx.x; e < gp.soff[mp.n]; e += blockDim.x) sacc[e] = 0.0f;
+    __syncthreads();
+  }
   for (long long base = warp_id * QPW; base < n; base += n_warps * QPW) {
     const long long qi = base + sub;
     if (qi >= n) continue;
@@ -238,8 +285,16 @@ __global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__
     const float4* sats = reinterpret_cast<const float4*>(M.tables + flw_floats(M.levels, R));
     const float4* satt = sats + static_cast<size_t>(M.bins + 1) * R;
     const gsp_material_grad& G = gp.g[m];
-    float* dps = gp.dps[m];
-    float* dpt = gp.dpt[m];
+    SmallGrad sg;
+    if (gp.use_smem) {
+      sg = small_tables(sacc + gp.soff[m], M);
+    } else {
+      sg.dflw = G.dflw;
+      sg.dps = gp.dps[m];
+      sg.dpt = gp.dpt[m];
+      sg.dfs = G.dfs;
+      sg.dft = G.dft;
+    }
     const float g0 = 1.0f - t.f;
     for (int r = j; r < R; r += LANES) {
       float a0 = __ldg(flw + t.l0 * R + r), a1 = __ldg(flw + t.l1 * R + r);
@@ -251,28 +306,47 @@ __global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__
       float st = S * T;
       atomicAdd(G.dfx + t.x * R + r, g * yv * lv * st);
       atomicAdd(G.dfy + t.y * R + r, g * xv * lv * st);
-      atomicAdd(G.dflw + t.l0 * R + r, g * g0 * xy * st);
-      if (t.f != 0.0f) atomicAdd(G.dflw + t.l1 * R + r, g * t.f * xy * st);
+      atomicAdd(sg.dflw + t.l0 * R + r, g * g0 * xy * st);
+      if (t.f != 0.0f) atomicAdd(sg.dflw + t.l1 * R + r, g * t.f * xy * st);
       // Sbar = (F(s1) - F(s0)) / w with F(s) = P[floor s] + frac(s) fs[floor s]
       float cs = g * xy * lv * T;
       if (t.inv_ws > 0.0f) {
         float a = cs * t.inv_ws;
-        atomicAdd(dps + t.is1 * R + r, a);
-        atomicAdd(dps + t.is0 * R + r, -a);
-        if (t.fs1 != 0.0f) atomicAdd(G.dfs + t.is1 * R + r, a * t.fs1);
-        if (t.fs0 != 0.0f) atomicAdd(G.dfs + t.is0 * R + r, -a * t.fs0);
+        atomicAdd(sg.dps + t.is1 * R + r, a);
+        atomicAdd(sg.dps + t.is0 * R + r, -a);
+        if (t.fs1 != 0.0f) atomicAdd(sg.dfs + t.is1 * R + r, a * t.fs1);
+        if (t.fs0 != 0.0f) atomicAdd(sg.dfs + t.is0 * R + r, -a * t.fs0);
       } else {
-        atomicAdd(G.dfs + t.isz * R + r, cs);
+        atomicAdd(sg.dfs + t.isz * R + r, cs);
       }
       float ct = g * xy * lv * S;
       if (t.inv_wt > 0.0f) {
         float a = ct * t.inv_wt;
-        atomicAdd(dpt + t.it1 * R + r, a);
-        atomicAdd(dpt + t.it0 * R + r, -a);
-        if (t.ft1 != 0.0f) atomicAdd(G.dft + t.it1 * R + r, a * t.ft1);
-        if (t.ft0 != 0.0f) atomicAdd(G.dft + t.it0 * R + r, -a * t.ft0);
+        atomicAdd(sg.dpt + t.it1 * R + r, a);
+        atomicAdd(sg.dpt + t.it0 * R + r, -a);
+        if (t.ft1 != 0.0f) atomicAdd(sg.dft + t.it1 * R + r, a * t.ft1);
+        if (t.ft0 != 0.0f) atomicAdd(sg.dft + t.it0 * R + r, -a * t.ft0);
       } else {
-        atomicAdd(G.dft + t.itz * R + r, ct);
+        atomicAdd(sg.dft + t.itz * R + r, ct);
+      }
+    }
+  }
+  if (gp.use_smem) {
+    __syncthreads();
+    for (int m = 0; m < mp.n; ++m) {
+      const gsp_material& M = mp.m[m];
+      const int R = M.rank, L = M.levels, B = M.bins;
+      const SmallGrad sg = small_tables(sacc + gp.soff[m], M);
+      const gsp_material_grad& G = gp.g[m];
+      for (int e = threadIdx.x; e < L * R; e += blockDim.x)
+        if (sg.dflw[e] != 0.0f) atomicAdd(G.dflw + e, sg.dflw[e]);
+      for (int e = threadIdx.x; e < (B + 1) * R; e += blockDim.x) {
+        if (sg.dps[e] != 0.0f) atomicAdd(gp.dps[m] + e, sg.dps[e]);
+        if (sg.dpt[e] != 0.0f) atomicAdd(gp.dpt[m] + e, sg.dpt[e]);
+      }
+      for (int e = threadIdx.x; e < B * R; e += blockDim.x) {
+        if (sg.dfs[e] != 0.0f) atomicAdd(G.dfs + e, sg.dfs[e]);
+        if (sg.dft[e] != 0.0f) atomicAdd(G.dft + e, sg.dft[e]);
       }
     }
   }
@@ -428,28 +502,47 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
     gp.dpt[i] = reinterpret_cast<float*>(w + b);
     w += 2 * b;
   }
+  // small tables of all materials in shared memory when they fit in 96 KB
+  int off = 0;
+  for (int i = 0; i < n_mats; ++i) {
+    gp.soff[i] = off;
+    const gsp_material& m = h_mats[i];
+    off += m.rank * (m.levels + 2 * (m.bins + 1) + 2 * m.bins);
+  }
+  gp.soff[n_mats] = off;
+  const size_t smem = static_cast<size_t>(off) * sizeof(float);
+  gp.use_smem = smem <= 96 * 1024 ? 1 : 0;
   cudaStream_t s = to_stream(stream);
   GSP_CUDA(cudaMemsetAsync(d_ws, 0, need, s));
   if (n > 0) {
     int lanes = pick_lanes(h_mats, n_mats, nullptr);
     const int threads = 256;
+    const size_t dyn = gp.use_smem ? smem : 0;
     long long warps = (n + (32 / lanes) - 1) / (32 / lanes);
     long long blocks = (warps * 32 + threads - 1) / threads;
-    long long cap = static_cast<long long>(sm_count()) * 8;
+    // CTAs per SM: as many as the shared-memory tables allow, up to 8
+    long long per_sm = gp.use_smem ? static_cast<long long>((228 * 1024) / (smem + 1024)) : 8;
+    if (per_sm > 8) per_sm = 8;
+    if (per_sm < 1) per_sm = 1;
+    long long cap = static_cast<long long>(sm_count()) * per_sm;
     if (blocks > cap) blocks = cap;
     prof_begin(PROF_QUERY_BWD, s);
     switch (lanes) {
       case 4:
-        k_range_query_bwd<4><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        k_range_query_bwd<4><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
         break;
       case 8:
-        k_range_query_bwd<8><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        k_range_query_bwd<8><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
         break;
       case 16:
-        k_range_query_bwd<16><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        k_range_query_bwd<16><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
         break;
       default:
-        k_range_query_bwd<32><<<blocks, threads, 0, s>>>(mp, gp, d_q, n, d_gout, d_status);
+        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        k_range_query_bwd<32><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
         break;
     }
     prof_end(PROF_QUERY_BWD, s);

@@ -178,3 +178,46 @@ def test_no_workspace_static_schedule_matches():
     assert rc == 0
     torch.cuda.synchronize()
     assert torch.equal(a, out)
+
+
+def test_results_do_not_depend_on_launch_shape():
+    # the rank sum has one fixed order, so every tuning gives the same bits
+    import paper_2109_14807_gb300 as g
+    f = random_factors(128, 8, 32, 64, 21)
+    mat = _material(f)
+    q = synth.queries_fractional(128, 8, 32, 50_000, 22, frac_level=True)
+    qd = g.queries_to_device(q)
+    ref = g.range_query(mat, qd, tuning=(32, 8, 256, 4)).clone()
+    for tn in [(16, 8, 256, 4), (8, 4, 128, 1), (4, 16, 256, 8), (32, 1, 64, 64), (16, 2, 256, 2)]:
+        got = g.range_query(mat, qd, tuning=tn)
+        assert torch.equal(got, ref), tn
+    f2 = random_factors(64, 7, 16, 37, 23)  # rank not a multiple of 32
+    m2 = _material(f2)
+    q2 = g.queries_to_device(synth.queries_fractional(64, 7, 16, 20_000, 24, frac_level=True))
+    r2 = g.range_query(m2, q2, tuning=(32, 8, 256, 4)).clone()
+    for lanes in (4, 8, 16):
+        assert torch.equal(g.range_query(m2, q2, tuning=(lanes, 8, 256, 4)), r2), lanes
+
+
+def test_graph_replay_and_autotuner():
+    import paper_2109_14807_gb300 as g
+    from paper_2109_14807_gb300 import tune
+    shapes = [(256, 16, 32), (512, 64, 32)]
+    mats = []
+    for i, (N, R, B) in enumerate(shapes):
+        mats.append(_material(random_factors(N, int(np.log2(N)) + 1, B, R, 70 + i)))
+    q = synth.queries_camera([(N, int(np.log2(N)) + 1, B) for N, R, B in shapes], 300_000, 71)
+    qd = g.queries_to_device(q)
+    tn = tune.autotune_query(mats, qd, sample=100_000, repeats=1, cache_path=None)
+    assert len(tn) == 4
+    eager = g.range_query(mats, qd, tuning=tn).clone()
+    out = torch.empty_like(eager)
+    graph = tune.QueryGraph(mats, qd, out, tuning=tn)
+    out.zero_()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+    err, _ = query_error(out.cpu().numpy(), [oracle_material(random_factors(N, int(np.log2(N)) + 1, B, R, 70 + i))
+                                             for i, (N, R, B) in enumerate(shapes)], q)
+    assert err <= QUERY_TOL

@@ -117,3 +117,18 @@ def test_to_material_folds_weights():
     fac = [np.ones((2, 2)), np.ones((2, 2)), np.array([[1.0, 1.0], [0.5, 2.0]]), np.ones((3, 2)), np.ones((3, 2))]
     m = cp.to_material(lam, fac)
     assert np.array_equal(m["flw"], np.array([[2.0, 3.0], [1.0, 6.0]]))
+
+
+def test_gram_fit_equals_explicit_fit():
+    w = synth.WORKLOADS["flakes32"]
+    s, t = ndf.bin_index(synth.make_map(w), w["bins"])
+    H = ndf.footprint_histograms(s, t, w["levels"], w["bins"])
+    X = ndf.logical(ndf.normalised_tensor(H, w["bins"]))
+    f = synth.init_factors(w["N"], w["levels"], w["bins"], 6, 2001)
+    init = [f[k][:, :6] for k in ("fx", "fy", "fl", "fs", "ft")]
+    _, _, fe = cp.cp_als(X, 6, init, sweeps=5)
+    _, _, fg = cp.cp_als(X, 6, init, sweeps=5, fit_method="gram")
+    FT = cp.FootprintTensor(H, w["bins"])
+    _, _, ff = cp.cp_als(FT, 6, init, sweeps=5, fit_method="gram")
+    assert np.allclose(fe, fg, rtol=0, atol=1e-9)
+    assert np.allclose(fe, ff, rtol=0, atol=1e-9)
