@@ -49,13 +49,21 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gsp", "reference"], default="gsp")
     p.add_argument("--precision", choices=["auto", "bf16", "tf32", "fp32"], default="auto")
+    p.add_argument("--workload", choices=["flakes1024", "flakes256", "brushed512"],
+                   default="flakes1024",
+                   help="flakes1024 is the benchmark; the others are smaller cases of the "
+                        "same step for profiling")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
 
-def workload():
+def workload(name=None):
+    global WORKLOAD
+    if name:
+        WORKLOAD = name
     w = dict(synth.WORKLOADS[WORKLOAD])
+    w.setdefault("queries", 1_000_000)
     return w
 
 
@@ -153,6 +161,23 @@ def ncu_traffic(kernel, precision):
     return None
 
 
+# ------------------------------------------------------------ replicas --
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """Slowest rank's time (replicas run independently; no data-path
+    collective, only this reduction of the timing)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Units all ranks processed per second (weak scaling: fixed work per rank)."""
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
 # ------------------------------------------------------------------ oracle --
 def oracle_sample_step(w, m, q, f_init):
     """Time the FP64 oracle on a bounded sample of one step and extrapolate to
@@ -201,10 +226,10 @@ def host_cores():
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = workload()
+    w = workload(args.workload)
     m = synth.make_map(w)
-    q = synth.queries_fractional(w["N"], w["levels"], w["bins"], w["queries"], 1003)
-    f_init = synth.init_factors(w["N"], w["levels"], w["bins"], w["rank"], 2003)
+    q = synth.queries_fractional(w["N"], w["levels"], w["bins"], w["queries"], 1000 + w["seed"])
+    f_init = synth.init_factors(w["N"], w["levels"], w["bins"], w["rank"], 2000 + w["seed"])
     times = []
     desc = ""
     for i in range(args.warmup + args.steps):
@@ -228,8 +253,9 @@ def run_reference(args, rank, world):
 
 
 def config_block(w, prec):
-    return {"workload": f"{WORKLOAD}: {w['N']}x{w['N']} Voronoi flakes ({w['cells']} cells, "
-                        f"Beckmann alpha {w['alpha']}), levels 0..{w['levels'] - 1}, "
+    kind = (f"Voronoi flakes ({w['cells']} cells, Beckmann alpha {w['alpha']})" if w["map"] == "flakes"
+            else f"brushed (slope sd {w['sigma_x']}/{w['sigma_y']}, {w['scratches']} scratches)")
+    return {"workload": f"{WORKLOAD}: {w['N']}x{w['N']} {kind}, levels 0..{w['levels'] - 1}, "
                         f"{w['bins']}x{w['bins']} bins, CP rank {w['rank']}, "
                         f"{w['queries']} fractional range queries",
             "N": w["N"], "levels": w["levels"], "bins": w["bins"], "rank": w["rank"],
@@ -248,15 +274,15 @@ def run_gsp(args, rank, world):
     lib = _lib.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w = workload()
+    w = workload(args.workload)
     N, L, B, R, nq = w["N"], w["levels"], w["bins"], w["rank"], w["queries"]
     prec = args.precision
     if prec == "auto":
         prec = "bf16" if lib.gsp_cp_workspace_bytes(N, L, B, R, _lib.PREC["bf16"]) else "fp32"
 
     m_np = synth.make_map(w)
-    q_np = synth.queries_fractional(N, L, B, nq, 1003)
-    f_init = synth.init_factors(N, L, B, R, 2003)
+    q_np = synth.queries_fractional(N, L, B, nq, 1000 + w["seed"])
+    f_init = synth.init_factors(N, L, B, R, 2000 + w["seed"])
 
     normals = torch.from_numpy(m_np).to(dev)
     qd = g.queries_to_device(q_np, dev)
@@ -330,11 +356,7 @@ def run_gsp(args, rank, world):
     launches = lib.gsp_kernel_launches() - launches0
     lib.gsp_profile_enable(0)
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     ms_step = total_ms / args.steps
     stages = {name: statistics.median(stage_ev[k][i].elapsed_time(stage_ev[k][i + 1])
                                       for k in range(args.steps))
@@ -369,7 +391,7 @@ def run_gsp(args, rank, world):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": nq * world / (ms_step / 1e3), "unit": "queries/s",
+            "metric": METRIC, "value": whole_job_rate(nq, world, ms_step), "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",

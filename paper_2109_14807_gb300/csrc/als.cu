@@ -46,7 +46,9 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   o.bins = take(N2 * sizeof(uint16_t) + kGroupBytes);
   o.Yp = take(N2 * R * sizeof(float));
   o.Zp = take(L * B2 * R * sizeof(float));
-  o.Zpart = take(L * static_cast<size_t>(lst_chunks(d, prec)) * B2 * R * sizeof(float));
+  const size_t simt_part = L * static_cast<size_t>(lst_chunks(d, GSP_PREC_FP32)) * B2 * R;
+  const size_t tc_part = static_cast<size_t>(kLstMaxRanges) * 2 * B2 * R;
+  o.Zpart = take((prec == GSP_PREC_FP32 ? simt_part : tc_part) * sizeof(float));
   o.KR = take(R * L * B2 * sizeof(float));
   size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
   o.M = take(imax * R * sizeof(double));
@@ -595,12 +597,11 @@ int run_xy(const Ctx& c, const float* fl, const float* fs, const float* ft) {
 
 int run_lst(const Ctx& c, const float* fx, const float* fy) {
   const MttkrpDims& d = c.d;
-  int C = lst_chunks(d, c.prec);
-  if (c.prec == GSP_PREC_FP32)
-    GSP_TRY(simt_mttkrp_lst(c.at<float>(c.lay.T), fx, fy, c.at<float>(c.lay.Zpart), d, C, c.s));
-  else
-    GSP_TRY(tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.at<float>(c.lay.Zpart), d, c.prec, C,
-                          c.at<uint32_t>(c.lay.flags), c.s));
+  if (c.prec != GSP_PREC_FP32)
+    return tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.at<float>(c.lay.Zpart), c.at<float>(c.lay.Zp),
+                         d, c.prec, c.at<uint32_t>(c.lay.flags), c.s);
+  const int C = lst_chunks(d, c.prec);
+  GSP_TRY(simt_mttkrp_lst(c.at<float>(c.lay.T), fx, fy, c.at<float>(c.lay.Zpart), d, C, c.s));
   long long per_level = static_cast<long long>(d.B2()) * d.R;
   k_zreduce<<<grid_for(per_level * d.L, 256), 256, 0, c.s>>>(c.at<float>(c.lay.Zpart),
                                                              c.at<float>(c.lay.Zp), d.L, C, per_level);

@@ -22,25 +22,24 @@ __global__ void k_bin_normals(const float2* __restrict__ nxy, int n, int bins,
     for (int k = threadIdx.x; k < kGroupWords; k += blockDim.x) gmask[k] = 0u;
     __syncthreads();
   }
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < n;
   uint16_t code = 0;
-  bool valid = i < n;
   if (valid) {
-  float2 v = nxy[i];
-  uint16_t code = 0;
-  if (!isfinite(v.x) || !isfinite(v.y)) {
-    set_status(status, GSP_DEV_NONFINITE_NORMAL);
-  } else {
-    const float half = static_cast<float>(bins >> 1);
-    const float hi = static_cast<float>(bins - 1);
-    // fl32(fl32(n + 1) * B/2), explicit roundings, no contraction into an FMA
-    float s = floorf(__fmul_rn(__fadd_rn(v.x, 1.0f), half));
-    float t = floorf(__fmul_rn(__fadd_rn(v.y, 1.0f), half));
-    s = fminf(fmaxf(s, 0.0f), hi);
-    t = fminf(fmaxf(t, 0.0f), hi);
-    code = static_cast<uint16_t>(static_cast<int>(s) * bins + static_cast<int>(t));
-  }
-  out[i] = code;
+    const float2 v = nxy[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) {
+      set_status(status, GSP_DEV_NONFINITE_NORMAL);
+    } else {
+      const float half = static_cast<float>(bins >> 1);
+      const float hi = static_cast<float>(bins - 1);
+      // fl32(fl32(n + 1) * B/2), explicit roundings, no contraction into an FMA
+      float s = floorf(__fmul_rn(__fadd_rn(v.x, 1.0f), half));
+      float t = floorf(__fmul_rn(__fadd_rn(v.y, 1.0f), half));
+      s = fminf(fmaxf(s, 0.0f), hi);
+      t = fminf(fmaxf(t, 0.0f), hi);
+      code = static_cast<uint16_t>(static_cast<int>(s) * bins + static_cast<int>(t));
+    }
+    out[i] = code;
   }
   if (groups) {
     if (valid) atomicOr(&gmask[(code >> 4) >> 5], 1u << ((code >> 4) & 31));

@@ -133,10 +133,8 @@ __global__ void __launch_bounds__(256) k_lst_simt(const float* __restrict__ T,
 
 int lst_chunks(const MttkrpDims& d, int precision) {
   long long per_chunk_blocks;
-  if (precision == GSP_PREC_FP32 || !tc_supported(d, precision))
-    per_chunk_blocks = static_cast<long long>(d.B2() / BM) * ((d.R + BN - 1) / BN) * d.L;
-  else
-    per_chunk_blocks = tc_lst_units_per_chunk(d);  // one tensor-core CTA per unit
+  (void)precision;
+  per_chunk_blocks = static_cast<long long>(d.B2() / BM) * ((d.R + BN - 1) / BN) * d.L;
   long long target = 4LL * 148;
   long long C = 1;
   while (C * per_chunk_blocks < target && C * 2 * 256 <= d.N2()) C *= 2;

@@ -30,6 +30,7 @@ namespace gsp {
 namespace {
 
 constexpr int kMaxStages = 8;
+constexpr int kMaxRankTc = 64;  // CP ranks served by the tensor-core passes
 constexpr int kThreads = 192;
 constexpr long long kTimeoutCycles = 4000000000LL;  // about 2 s at GB300 clocks
 constexpr int kTileBytes = 128 * 128;                // 128 rows x 128 bytes
@@ -353,16 +354,36 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------ Z' pass --
-// Unit u -> (level l, xy chunk c, st group g); the chunk's rows are processed in
-// K steps of E128 rows.  For each K step the producer loads, for every st block
-// m of the group, the [E128 rows x 128 st] tile as 128/E128 TMA boxes of
-// [E128 rows][E128 st] (MN-major atoms, LBO = box bytes); the epilogue warps
-// write KRxy[r][k] = fx[x_k][r] fy[y_k][r] (K-major, 128-byte rows, swizzled).
+// The K steps (E128 xy rows each) of all levels form one sequence of
+// L * N^2 / E128 steps; CTA p of st group g takes the contiguous range
+// [p K / P, (p+1) K / P).  A range is shorter than a level, so it holds at most
+// two segments (the part in its first level and the part in the next); each
+// segment's accumulators go to partial slice 2p + seg of the group's st rows
+// and a fixed-order reduce adds the slices of each level.  Within a K step the
+// producer loads, for every st block m of the group, the [E128 rows x 128 st]
+// tile as 128/E128 TMA boxes (MN-major atoms, LBO = box bytes); the epilogue
+// warps write KRxy[r][k] = fx[x_k][r] fy[y_k][r] (K-major, 128-byte rows).
+struct LstRange {
+  long long k0, k1;     // this CTA's steps
+  long long mid;        // end of the first segment
+  int level0;
+};
+
+__device__ __forceinline__ LstRange lst_range(int p, int P, long long K, long long spl) {
+  LstRange r;
+  r.k0 = K * p / P;
+  r.k1 = K * (p + 1) / P;
+  r.level0 = static_cast<int>(r.k0 / spl);
+  const long long lend = (r.level0 + 1) * spl;
+  r.mid = r.k1 < lend ? r.k1 : lend;
+  return r;
+}
+
 template <int ELEM, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_lst_tc(const __grid_constant__ CUtensorMap mapT, const float* __restrict__ fx,
-             const float* __restrict__ fy, float* __restrict__ Zpart, int n_units, int logN,
-             int L, int B2, int R, int C, int MB, int G, int kStages, uint32_t* err) {
+             const float* __restrict__ fy, float* __restrict__ Zpart, int P, int logN, int L,
+             int B2, int R, int MB, int G, int kStages, uint32_t* err) {
   constexpr int E128 = 128 / ELEM;
   constexpr uint32_t FMT = ELEM == 2 ? 1u : 2u;
   constexpr int BOXES = 128 / E128;                 // TMA boxes per 128-wide st block
@@ -378,8 +399,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = 1 << logN;
   const long long N2 = static_cast<long long>(N) * N;
-  const long long rows = N2 / C;
-  const int ksteps = static_cast<int>(rows / E128);
+  const long long spl = N2 / E128;        // steps per level
+  const long long K = spl * L;
+  const int g = blockIdx.x % G, p = blockIdx.x / G;
+  const LstRange rg = lst_range(p, P, K, spl);
   const uint32_t ncols = tmem_cols_for(MB * R);
   volatile int* abort = &bar.abort;
 
@@ -411,25 +434,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_parity[kMaxStages];
       bool issued[kMaxStages];
       for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
-      for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
-        const int g = u % G, c = (u / G) % C, l = u / (G * C);
-        const long long row0 = l * N2 + c * rows;
-        for (int kc = 0; kc < ksteps; ++kc) {
-          for (int m = 0; m < MB; ++m) {
-            if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
-            const uint32_t sa = smem_u32(smem + s * kTileBytes);
-            const uint32_t fb = smem_u32(&bar.full[s]);
-            mbar_expect_tx(fb, kTileBytes);
-            const int st0 = (g * MB + m) * 128;
-            for (int b = 0; b < BOXES; ++b)
-              tma_load_2d(sa + b * BOX_BYTES, &mapT, st0 + b * E128,
-                          static_cast<int>(row0 + static_cast<long long>(kc) * E128), fb);
-            issued[s] = true;
-            issued_parity[s] = ph;
-            if (++s == kStages) {
-              s = 0;
-              ph ^= 1u;
-            }
+      for (long long k = rg.k0; k < rg.k1 && !*abort; ++k) {
+        for (int m = 0; m < MB; ++m) {
+          if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
+          const uint32_t sa = smem_u32(smem + s * kTileBytes);
+          const uint32_t fb = smem_u32(&bar.full[s]);
+          mbar_expect_tx(fb, kTileBytes);
+          const int st0 = (g * MB + m) * 128;
+          for (int b = 0; b < BOXES; ++b)
+            tma_load_2d(sa + b * BOX_BYTES, &mapT, st0 + b * E128, static_cast<int>(k * E128), fb);
+          issued[s] = true;
+          issued_parity[s] = ph;
+          if (++s == kStages) {
+            s = 0;
+            ph ^= 1u;
           }
         }
       }
@@ -444,10 +462,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       int s = 0, bs = 0;
       uint32_t ph = 0, bph = 0, uph = 0;
       bool any = false;
-      for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+      for (int seg = 0; seg < 2; ++seg) {
+        const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
+        if (kb >= ke) continue;
         if (!mbar_wait(smem_u32(&bar.acc_empty[0]), uph ^ 1u, abort)) break;
         tc_fence_after();
-        for (int kc = 0; kc < ksteps; ++kc) {
+        for (long long k = kb; k < ke; ++k) {
           if (!mbar_wait(smem_u32(&bar.b_full[bs]), bph, abort)) goto mma_done;
           tc_fence_after();
           const uint32_t sb = smem_u32(bslots + bs * b_bytes);
@@ -459,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const uint64_t a = sdesc(sa + j * MMA_K_ROWS * 128, BOX_BYTES, A_SBO, A_LAYOUT);
-              umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (kc > 0 || j > 0) ? 1u : 0u);
+              umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (k > kb || j > 0) ? 1u : 0u);
               if constexpr (SPLIT)
                 umma<ELEM>(d, a, sdesc(sb + R * 128 + j * 32, 16, 1024), id, 1u);
             }
@@ -485,43 +505,55 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_drain(smem_u32(&bar.drain), 0);
       }
     }
-  } else {  // ---- warps 0-3: B operand producer, then epilogue
+  } else {  // ---- warps 0-3: B operand producer, then epilogue per segment
     // thread t fills xy row k = t / TPR of the tile, ranks [r0, r0 + R/TPR),
-    // reading fx and fy rows with 16-byte loads
+    // all its fx and fy loads issued before any product is formed
     constexpr int TPR = 128 / E128;  // threads per xy row
+    constexpr int MAXV = kMaxRankTc / 4 / TPR;  // float4 per operand row part
     const int t = threadIdx.x;       // 0..127
-    const int k = t / TPR;
+    const int kk = t / TPR;
     const int rpart = R / TPR;
     const int r0 = (t % TPR) * rpart;
-    const int byte_in_row = k * ELEM;
+    const int byte_in_row = kk * ELEM;
     const int chunk = byte_in_row >> 4, within = byte_in_row & 15;
     int bs = 0;
     uint32_t bph = 0, uph = 0;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-      const int g = u % G, c = (u / G) % C, l = u / (G * C);
-      const long long xy_base = c * rows;
-      for (int kc = 0; kc < ksteps; ++kc) {
+    for (int seg = 0; seg < 2; ++seg) {
+      const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
+      if (kb >= ke) continue;
+      const int l = rg.level0 + seg;
+      for (long long k = kb; k < ke; ++k) {
         if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto epi_done;
-        const long long xy = xy_base + static_cast<long long>(kc) * E128 + k;
+        const long long xy = k * E128 + kk - l * N2;
         const int x = static_cast<int>(xy & (N - 1)), y = static_cast<int>(xy >> logN);
         const float4* fx4 = reinterpret_cast<const float4*>(fx + static_cast<size_t>(x) * R + r0);
         const float4* fy4 = reinterpret_cast<const float4*>(fy + static_cast<size_t>(y) * R + r0);
-        uint8_t* tile = bslots + bs * b_bytes;
-        for (int i = 0; i < rpart / 4; ++i) {
-          const float4 a4 = __ldg(fx4 + i), b4 = __ldg(fy4 + i);
-          const float v[4] = {a4.x * b4.x, a4.y * b4.y, a4.z * b4.z, a4.w * b4.w};
+        float4 av[MAXV], bv[MAXV];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int r = r0 + 4 * i + e;
-            uint8_t* dst = tile + r * 128 + ((((chunk ^ (r & 7)) << 4)) | within);
-            if constexpr (ELEM == 2) {
-              const __nv_bfloat16 hi = __float2bfloat16_rn(v[e]);
-              *reinterpret_cast<__nv_bfloat16*>(dst) = hi;
-              if constexpr (SPLIT)  // row R + r: same swizzle phase since R % 8 == 0
-                *reinterpret_cast<__nv_bfloat16*>(dst + R * 128) =
-                    __float2bfloat16_rn(v[e] - __bfloat162float(hi));
-            } else {
-              *reinterpret_cast<float*>(dst) = round_tf32(v[e]);
+        for (int i = 0; i < MAXV; ++i)
+          if (i < rpart / 4) {
+            av[i] = __ldg(fx4 + i);
+            bv[i] = __ldg(fy4 + i);
+          }
+        uint8_t* tile = bslots + bs * b_bytes;
+#pragma unroll
+        for (int i = 0; i < MAXV; ++i) {
+          if (i < rpart / 4) {
+            const float v[4] = {av[i].x * bv[i].x, av[i].y * bv[i].y, av[i].z * bv[i].z,
+                                av[i].w * bv[i].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int r = r0 + 4 * i + e;
+              uint8_t* dst = tile + r * 128 + ((((chunk ^ (r & 7)) << 4)) | within);
+              if constexpr (ELEM == 2) {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(v[e]);
+                *reinterpret_cast<__nv_bfloat16*>(dst) = hi;
+                if constexpr (SPLIT)  // row R + r: same swizzle phase since R % 8 == 0
+                  *reinterpret_cast<__nv_bfloat16*>(dst + R * 128) =
+                      __float2bfloat16_rn(v[e] - __bfloat162float(hi));
+              } else {
+                *reinterpret_cast<float*>(dst) = round_tf32(v[e]);
+              }
             }
           }
         }
@@ -532,11 +564,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           bph ^= 1u;
         }
       }
-      // epilogue: MB accumulators of 128 st rows x R
+      // epilogue: MB accumulators of 128 st rows x R -> partial slice 2p + seg
       if (!mbar_wait(smem_u32(&bar.acc_full[0]), uph, abort)) goto epi_done;
       tc_fence_after();
       {
-        float* part = Zpart + (static_cast<size_t>(l) * C + c) * B2 * R;
+        float* part = Zpart + (static_cast<size_t>(p) * 2 + seg) * B2 * R;
         for (int m = 0; m < MB; ++m)
           store_accumulator(tmem, warp, lane, m * R, R,
                             part + static_cast<size_t>((g * MB + m) * 128) * R);
@@ -544,7 +576,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(smem_u32(&bar.acc_empty[0]));
       uph ^= 1u;
-      (void)l;
     }
   epi_done:;
   }
@@ -555,6 +586,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem, ncols);
   }
+}
+
+// Z'[l][st][r] = sum over CTAs p (in order) of the partial slices whose segment
+// lies in level l.
+__global__ void k_lst_reduce(const float* __restrict__ Zpart, float* __restrict__ Zp, int P,
+                             int L, long long spl, long long per_level) {
+  const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (e >= per_level * L) return;
+  const int l = static_cast<int>(e / per_level);
+  const long long rem = e % per_level;
+  const long long K = spl * L;
+  float acc = 0.0f;
+  for (int p = 0; p < P; ++p) {
+    const long long k0 = K * p / P, k1 = K * (p + 1) / P;
+    if (k0 >= k1) continue;
+    const int l0 = static_cast<int>(k0 / spl);
+    const long long mid = k1 < (l0 + 1) * spl ? k1 : (l0 + 1) * spl;
+    if (l0 == l) acc += Zpart[(static_cast<long long>(p) * 2) * per_level + rem];
+    else if (l0 + 1 == l && mid < k1) acc += Zpart[(static_cast<long long>(p) * 2 + 1) * per_level + rem];
+  }
+  Zp[e] = acc;
 }
 
 // ----------------------------------------------------------- host side --
@@ -629,7 +681,7 @@ int lst_groups(const MttkrpDims& d, int* MB) {
 bool tc_supported(const MttkrpDims& d, int precision) {
   if (precision != GSP_PREC_BF16 && precision != GSP_PREC_BF16_1X && precision != GSP_PREC_TF32)
     return false;
-  if (!(d.R == 16 || d.R == 32 || d.R == 64 || d.R == 128)) return false;
+  if (!(d.R == 16 || d.R == 32 || d.R == 64)) return false;
   if (d.B < 16 || d.N < 16) return false;
   if (d.L * d.N2() >= (1LL << 31)) return false;  // TMA row coordinate is int32
   const bool split = precision == GSP_PREC_BF16;
@@ -670,46 +722,54 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
   return GSP_OK;
 }
 
-int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart,
-                  const MttkrpDims& d, int precision, int chunks, uint32_t* err, cudaStream_t s) {
+int tc_lst_ctas(const MttkrpDims& d) {
+  int MB = 0;
+  const int G = lst_groups(d, &MB);
+  int P = sm_count() / G;
+  if (P < 1) P = 1;
+  if (P > kLstMaxRanges) P = kLstMaxRanges;
+  return P;
+}
+
+int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart, float* Zp,
+                  const MttkrpDims& d, int precision, uint32_t* err, cudaStream_t s) {
   if (!tc_supported(d, precision)) return GSP_ERR_UNSUPPORTED;
   const int elem = precision == GSP_PREC_TF32 ? 4 : 2;
   const bool split = precision == GSP_PREC_BF16;
   const int E128 = 128 / elem;
-  if ((d.N2() / chunks) % E128) return GSP_ERR_UNSUPPORTED;
   CUtensorMap mT;
   GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2(), E128,
                    elem == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
   int MB = 0;
   const int G = lst_groups(d, &MB);
-  const int n_units = d.L * chunks * G;
-  int grid = sm_count();
-  if (grid > n_units) grid = n_units;
+  const int P = tc_lst_ctas(d);
+  const int grid = P * G;
   const size_t smem = lst_smem(d.R, split);
   const int stages = lst_stages(d.R, split);
   const int logN = ilog2(d.N);
   prof_begin(PROF_MTTKRP_LST, s);
   if (elem == 4) {
     GSP_TRY(set_smem(k_lst_tc<4, false>, smem));
-    k_lst_tc<4, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, n_units, logN, d.L,
-                                                    d.B2(), d.R, chunks, MB, G, stages, err);
+    k_lst_tc<4, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+                                                    MB, G, stages, err);
   } else if (split) {
     GSP_TRY(set_smem(k_lst_tc<2, true>, smem));
-    k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, n_units, logN, d.L,
-                                                   d.B2(), d.R, chunks, MB, G, stages, err);
+    k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+                                                   MB, G, stages, err);
   } else {
     GSP_TRY(set_smem(k_lst_tc<2, false>, smem));
-    k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, n_units, logN, d.L,
-                                                    d.B2(), d.R, chunks, MB, G, stages, err);
+    k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+                                                    MB, G, stages, err);
   }
   prof_end(PROF_MTTKRP_LST, s);
+  GSP_CHECK_LAUNCH();
+  const long long per_level = static_cast<long long>(d.B2()) * d.R;
+  k_lst_reduce<<<grid_for(per_level * d.L, 256), 256, 0, s>>>(Zpart, Zp, P, d.L, d.N2() / E128,
+                                                              per_level);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
 }
 
-int tc_lst_units_per_chunk(const MttkrpDims& d) {
-  int MB = 0;
-  return d.L * lst_groups(d, &MB);
-}
+
 
 }  // namespace gsp
