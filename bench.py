@@ -45,7 +45,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gsp", "reference"], default="gsp")
     p.add_argument("--precision", choices=["auto", "bf16", "tf32", "fp32"], default="auto")
@@ -53,6 +53,9 @@ def parse_args():
                    default="flakes1024",
                    help="flakes1024 is the benchmark; the others are smaller cases of the "
                         "same step for profiling")
+    p.add_argument("--query-tuning", default=None,
+                   help="lanes,blocks_per_sm,threads,chunk for the query kernel instead of the "
+                        "autotuner's choice")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -83,7 +86,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -305,7 +308,10 @@ def run_gsp(args, rank, world):
     # not depend on it)
     from paper_2109_14807_gb300 import tune
     g.build_query_tables(mat)
-    q_tuning = tune.autotune_query(mat, qd, sample=2_000_000, repeats=2)
+    if args.query_tuning:
+        q_tuning = tuple(int(v) for v in args.query_tuning.split(","))
+    else:
+        q_tuning = tune.autotune_query(mat, qd, sample=2_000_000, repeats=2)
 
     def step(stage_events=None):
         ev = stage_events

@@ -143,22 +143,26 @@ __global__ void __launch_bounds__(256) k_contract(CParams p) {
   const int jl = threadIdx.x / R;
   const int JL = blockDim.x / R;
   const long long J = static_cast<long long>(p.J1) * p.J2;
-  // FP32 (the operands are FP32 tensor-core / FFMA sums); 4 independent chains
+  // FP32 (the operands are FP32 tensor-core / FFMA sums); 4 independent chains.
+  // J2 is a power of two, so j splits into (j1, j2) by shift and mask.
+  const int j2_log = 31 - __clz(p.J2);
+  const int j2_mask = p.J2 - 1;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  long long j = jl;
-  for (; j + 3 * JL < J; j += 4 * JL) {
+  int j = jl;
+  const int Ji = static_cast<int>(J);
+  for (; j + 3 * JL < Ji; j += 4 * JL) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const long long jj = j + u * JL;
-      const int j1 = static_cast<int>(jj / p.J2), j2 = static_cast<int>(jj % p.J2);
+      const int jj = j + u * JL;
+      const int j1 = jj >> j2_log, j2 = jj & j2_mask;
       float v = p.W[(i * p.wi + j1 * p.w1 + j2 * p.w2) * R + r];
       if (p.A1) v *= p.A1[j1 * R + r];
       if (p.A2) v *= p.A2[j2 * R + r];
       acc[u] += v;
     }
   }
-  for (; j < J; j += JL) {
-    const int j1 = static_cast<int>(j / p.J2), j2 = static_cast<int>(j % p.J2);
+  for (; j < Ji; j += JL) {
+    const int j1 = j >> j2_log, j2 = j & j2_mask;
     float v = p.W[(i * p.wi + j1 * p.w1 + j2 * p.w2) * R + r];
     if (p.A1) v *= p.A1[j1 * R + r];
     if (p.A2) v *= p.A2[j2 * R + r];

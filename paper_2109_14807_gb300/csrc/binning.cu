@@ -119,17 +119,25 @@ __global__ void __launch_bounds__(kHistThreads, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (o.groups && !((o.groups[blockIdx.x >> 5] >> (blockIdx.x & 31)) & 1u)) {
     // no texel of the map falls in this bin group: every count is zero
-    const int row_log = logN + 2;  // N * (G / 4) items per row
+    // items of 8 bins (16-byte BF16 stores; two 16-byte stores for 32-bit outputs)
+    const int row_log = logN + 1;  // N * (G / 8) items per row
     const long long items = static_cast<long long>(ychunk) << row_log;
+    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
     for (long long e = tid; e < items; e += kHistThreads) {
       const int yy = y0 + static_cast<int>(e >> row_log);
       const int rem = static_cast<int>(e & ((1LL << row_log) - 1));
-      const int x = rem >> 2, q = rem & 3;
-      const long long i4 = (((static_cast<long long>(l) * N + yy) * N * B2) >> 2) +
-                           ((static_cast<long long>(x) * B2 + g0) >> 2) + q;
-      if (o.h) reinterpret_cast<int4*>(o.h)[i4] = make_int4(0, 0, 0, 0);
-      if (o.f32) reinterpret_cast<float4*>(o.f32)[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (o.bf16) reinterpret_cast<uint2*>(o.bf16)[i4] = make_uint2(0u, 0u);
+      const int x = rem >> 1, h = rem & 1;
+      const long long i8 = (((static_cast<long long>(l) * N + yy) * N * B2) >> 3) +
+                           ((static_cast<long long>(x) * B2 + g0) >> 3) + h;
+      if (o.h) {
+        reinterpret_cast<uint4*>(o.h)[2 * i8] = z4;
+        reinterpret_cast<uint4*>(o.h)[2 * i8 + 1] = z4;
+      }
+      if (o.f32) {
+        reinterpret_cast<uint4*>(o.f32)[2 * i8] = z4;
+        reinterpret_cast<uint4*>(o.f32)[2 * i8 + 1] = z4;
+      }
+      if (o.bf16) reinterpret_cast<uint4*>(o.bf16)[i8] = z4;
     }
     return;
   }
@@ -141,23 +149,46 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     reinterpret_cast<uint4*>(V)[i] = make_uint4(0, 0, 0, 0);
   if (tid < 4) reinterpret_cast<int4*>(S)[tid] = make_int4(0, 0, 0, 0);  // S[0] = 0
   __syncthreads();
-  for (int x = tid; x < N; x += kHistThreads)
-    for (int j = 0; j < w; ++j) {
-      const int b = static_cast<int>(bins_map[(((y0 - a + j) & m) << logN) + x]) - g0;
-      if (static_cast<unsigned>(b) < static_cast<unsigned>(G)) V[x * kVRow + b] += 1;
+  for (int x = tid; x < N; x += kHistThreads) {
+    // the window's rows, eight independent loads at a time
+    for (int j0 = 0; j0 < w; j0 += 8) {
+      uint16_t code[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        code[u] = j0 + u < w ? bins_map[(((y0 - a + j0 + u) & m) << logN) + x] : 0xFFFFu;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = static_cast<int>(code[u]) - g0;
+        if (j0 + u < w && static_cast<unsigned>(b) < static_cast<unsigned>(G)) V[x * kVRow + b] += 1;
+      }
     }
+  }
   const float sc = o.scale[l];
+  // codes leaving / entering the window at the next row step, loaded one row
+  // ahead so the L2 latency overlaps this row's work (N <= 2 * kHistThreads)
+  int nxt_out[2], nxt_in[2];
+  auto fetch = [&](int yn) {
+    const int ro = (yn - 1 - a) & m, ri = (yn - 1 - a + w) & m;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int x = tid + k * kHistThreads;
+      nxt_out[k] = x < N ? static_cast<int>(bins_map[(ro << logN) + x]) : 0xFFFF;
+      nxt_in[k] = x < N ? static_cast<int>(bins_map[(ri << logN) + x]) : 0xFFFF;
+    }
+  };
+  fetch(y0 + 1);
   unsigned long long sumsq = 0;
 
   for (int y = y0; y < y0 + ychunk; ++y) {
     if (y > y0) {
-      const int ro = (y - 1 - a) & m, ri = (y - 1 - a + w) & m;
-      for (int x = tid; x < N; x += kHistThreads) {
-        const int bo = static_cast<int>(bins_map[(ro << logN) + x]) - g0;
-        const int bi = static_cast<int>(bins_map[(ri << logN) + x]) - g0;
-        if (static_cast<unsigned>(bo) < static_cast<unsigned>(G)) V[x * kVRow + bo] -= 1;
-        if (static_cast<unsigned>(bi) < static_cast<unsigned>(G)) V[x * kVRow + bi] += 1;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int x = tid + k * kHistThreads;
+        const int bo = nxt_out[k] - g0, bi = nxt_in[k] - g0;
+        if (x < N && static_cast<unsigned>(bo) < static_cast<unsigned>(G)) V[x * kVRow + bo] -= 1;
+        if (x < N && static_cast<unsigned>(bi) < static_cast<unsigned>(G)) V[x * kVRow + bi] += 1;
       }
+      if (y + 1 < y0 + ychunk) fetch(y + 1);
     }
     __syncthreads();
     int vals[kMaxBlocks][G];

@@ -588,23 +588,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Level of each CTA's two partial slices (-1: slice not written).
+struct LstSegments {
+  int8_t level[kLstMaxRanges][2];
+};
+
 // Z'[l][st][r] = sum over CTAs p (in order) of the partial slices whose segment
 // lies in level l.
 __global__ void k_lst_reduce(const float* __restrict__ Zpart, float* __restrict__ Zp, int P,
-                             int L, long long spl, long long per_level) {
+                             int L, long long per_level, const __grid_constant__ LstSegments sg) {
   const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (e >= per_level * L) return;
   const int l = static_cast<int>(e / per_level);
-  const long long rem = e % per_level;
-  const long long K = spl * L;
+  const long long rem = e - l * per_level;
   float acc = 0.0f;
   for (int p = 0; p < P; ++p) {
-    const long long k0 = K * p / P, k1 = K * (p + 1) / P;
-    if (k0 >= k1) continue;
-    const int l0 = static_cast<int>(k0 / spl);
-    const long long mid = k1 < (l0 + 1) * spl ? k1 : (l0 + 1) * spl;
-    if (l0 == l) acc += Zpart[(static_cast<long long>(p) * 2) * per_level + rem];
-    else if (l0 + 1 == l && mid < k1) acc += Zpart[(static_cast<long long>(p) * 2 + 1) * per_level + rem];
+    if (sg.level[p][0] == l) acc += Zpart[(static_cast<long long>(p) * 2) * per_level + rem];
+    if (sg.level[p][1] == l) acc += Zpart[(static_cast<long long>(p) * 2 + 1) * per_level + rem];
   }
   Zp[e] = acc;
 }
@@ -764,8 +764,17 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart,
   prof_end(PROF_MTTKRP_LST, s);
   GSP_CHECK_LAUNCH();
   const long long per_level = static_cast<long long>(d.B2()) * d.R;
-  k_lst_reduce<<<grid_for(per_level * d.L, 256), 256, 0, s>>>(Zpart, Zp, P, d.L, d.N2() / E128,
-                                                              per_level);
+  LstSegments sg;
+  const long long spl = d.N2() / E128, K = spl * d.L;
+  for (int p = 0; p < kLstMaxRanges; ++p) sg.level[p][0] = sg.level[p][1] = -1;
+  for (int p = 0; p < P; ++p) {  // the same split as lst_range() in the kernel
+    const long long k0 = K * p / P, k1 = K * (p + 1) / P;
+    if (k0 >= k1) continue;
+    const int l0 = static_cast<int>(k0 / spl);
+    sg.level[p][0] = static_cast<int8_t>(l0);
+    if (k1 > (l0 + 1) * spl) sg.level[p][1] = static_cast<int8_t>(l0 + 1);
+  }
+  k_lst_reduce<<<grid_for(per_level * d.L, 256), 256, 0, s>>>(Zpart, Zp, P, d.L, per_level, sg);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
 }
