@@ -109,6 +109,13 @@ typedef enum gsp_precision {
                            (two MMAs per K slice, Henry, Tang & Heinecke 2019)      */
   GSP_PREC_BF16_1X = 3  /* tcgen05, both operands rounded once to BF16             */
 } gsp_precision;
+/* Tensor-core precisions round the NDF tensor without bias: a value between two
+ * BF16 (TF32) neighbours goes to the upper one when frac(i * phi) (i = the
+ * element's index in [l][y][x][s][t], phi = the golden ratio, 32-bit fixed point)
+ * is below its relative distance from the lower one, so representable values,
+ * e.g. every count up to 256 (2048), are exact.  Tensor-memory accumulators
+ * restart every 16 K steps (64 MMAs per operand part) and their partial sums
+ * are added with round-to-nearest FP32 adds. */
 
 /* Five factor matrices and the CP weights, device pointers, FP32:
  * fx [N][R], fy [N][R], fl [levels][R], fs [B][R], ft [B][R], lambda [R].
@@ -144,7 +151,9 @@ typedef struct gsp_als_report {
 size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precision);
 
 /* Build the MTTKRP operand (the NDF tensor in the precision's input type,
- * [l][y][x][s][t]) and ||T||^2 inside the workspace.  Exactly one of d_hist
+ * [l][y][x][s][t]: BF16 for GSP_PREC_BF16 / _BF16_1X, else FP32, on the TF32
+ * grid for GSP_PREC_TF32; it occupies the first levels*N*N*B*B elements of
+ * d_ws) and ||T||^2 inside the workspace.  Exactly one of d_hist
  * (int32 histograms from gsp_build_footprint_ndfs) and d_normal_xy (the normal
  * map: the histograms are then produced level by level straight into the
  * operand, never stored as int32) must be non-NULL. */

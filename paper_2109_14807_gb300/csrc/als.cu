@@ -745,7 +745,7 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
   GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
   if (d_hist) {
     for (int l = 0; l < levels; ++l) {
-      LevelSink o{nullptr, nullptr, nullptr, 1.0f, sumsq + l};
+      LevelSink o{nullptr, nullptr, nullptr, 1.0f, sumsq + l, c.prec == GSP_PREC_TF32, slice * l};
       o.scale = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
       if (is_bf16(c.prec))
         o.bf16 = c.at<__nv_bfloat16>(c.lay.T) + slice * l;
@@ -766,6 +766,7 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
       o.bf16 = c.at<__nv_bfloat16>(c.lay.T);
     else
       o.f32 = c.at<float>(c.lay.T);
+    o.tf32 = c.prec == GSP_PREC_TF32;
     GSP_TRY(launch_box_hist(bm, N, levels, bins, o, c.s));
   }
   k_norm2<<<1, 32, 0, c.s>>>(sumsq, levels, bins, opts->raw_counts, c.at<double>(c.lay.norm2));

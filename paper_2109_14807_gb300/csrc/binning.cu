@@ -51,19 +51,20 @@ __global__ void k_bin_normals(const float2* __restrict__ nxy, int n, int bins,
 
 __device__ __forceinline__ void sink_store(const LevelSink& o, long long i, int4 v) {
   if (o.h) reinterpret_cast<int4*>(o.h)[i] = v;
+  const float f0 = static_cast<float>(v.x) * o.scale, f1 = static_cast<float>(v.y) * o.scale;
+  const float f2 = static_cast<float>(v.z) * o.scale, f3 = static_cast<float>(v.w) * o.scale;
+  const uint32_t d = weyl_dither(static_cast<unsigned long long>(o.base + 4 * i));
   if (o.f32) {
-    float4 f = make_float4(static_cast<float>(v.x) * o.scale, static_cast<float>(v.y) * o.scale,
-                           static_cast<float>(v.z) * o.scale, static_cast<float>(v.w) * o.scale);
+    float4 f = make_float4(f0, f1, f2, f3);
+    if (o.tf32)
+      f = make_float4(tf32_dither(f0, d), tf32_dither(f1, d + kWeyl), tf32_dither(f2, d + 2 * kWeyl),
+                      tf32_dither(f3, d + 3 * kWeyl));
     reinterpret_cast<float4*>(o.f32)[i] = f;
   }
   if (o.bf16) {
-    __nv_bfloat162 a = __floats2bfloat162_rn(static_cast<float>(v.x) * o.scale,
-                                             static_cast<float>(v.y) * o.scale);
-    __nv_bfloat162 b = __floats2bfloat162_rn(static_cast<float>(v.z) * o.scale,
-                                             static_cast<float>(v.w) * o.scale);
     uint2 p;
-    p.x = *reinterpret_cast<uint32_t*>(&a);
-    p.y = *reinterpret_cast<uint32_t*>(&b);
+    p.x = bf16_pair_dither(f0, d, f1, d + kWeyl);
+    p.y = bf16_pair_dither(f2, d + 2 * kWeyl, f3, d + 3 * kWeyl);
     reinterpret_cast<uint2*>(o.bf16)[i] = p;
   }
 }
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     }
   }
   const float sc = o.scale[l];
+  const float nb = -8388608.0f * sc;  // -2^23 * scale, exact
   // codes leaving / entering the window at the next row step, loaded one row
   // ahead so the L2 latency overlaps this row's work (N <= 2 * kHistThreads)
   int nxt_out[2], nxt_in[2];
@@ -257,37 +259,71 @@ __global__ void __launch_bounds__(kHistThreads, 1)
       }
     }
     __syncthreads();
-    // counts of every footprint of row y, four bins per item
-    const long long row4 = ((static_cast<long long>(l) * N + y) * N * B2) >> 2;
-    for (int e = tid; e < N * (G / 4); e += kHistThreads) {
-      const int x = e >> 2, q = e & 3;
+    // counts of every footprint of row y, eight bins per item; the lanes of a
+    // warp take consecutive x, so their 16-byte prefix reads (80-byte rows)
+    // fall on distinct banks
+    const long long row8 = ((static_cast<long long>(l) * N + y) * N * B2) >> 3;
+    for (int e = tid; e < 2 * N; e += kHistThreads) {
+      const int h = e >> logN, x = e & m;
       const int st = (x - a) & m, en = st + w;
-      const int4 lo = reinterpret_cast<const int4*>(S + st * kSRow)[q];
-      int4 c;
-      if (en <= N) {
-        const int4 hi = reinterpret_cast<const int4*>(S + en * kSRow)[q];
-        c = make_int4(hi.x - lo.x, hi.y - lo.y, hi.z - lo.z, hi.w - lo.w);
-      } else {
-        const int4 hi = reinterpret_cast<const int4*>(S + N * kSRow)[q];
-        const int4 wr = reinterpret_cast<const int4*>(S + (en - N) * kSRow)[q];
-        c = make_int4(hi.x - lo.x + wr.x, hi.y - lo.y + wr.y, hi.z - lo.z + wr.z,
-                      hi.w - lo.w + wr.w);
+      const int4* lo4 = reinterpret_cast<const int4*>(S + st * kSRow + 8 * h);
+      int c[8];
+      {
+        const int4 l0 = lo4[0], l1 = lo4[1];
+        int4 h0, h1;
+        if (en <= N) {
+          const int4* hi4 = reinterpret_cast<const int4*>(S + en * kSRow + 8 * h);
+          h0 = hi4[0];
+          h1 = hi4[1];
+        } else {  // window wraps: S[N] - S[st] + S[en - N]
+          const int4* tp = reinterpret_cast<const int4*>(S + N * kSRow + 8 * h);
+          const int4* wr = reinterpret_cast<const int4*>(S + (en - N) * kSRow + 8 * h);
+          const int4 t0 = tp[0], t1 = tp[1], w0 = wr[0], w1 = wr[1];
+          h0 = make_int4(t0.x + w0.x, t0.y + w0.y, t0.z + w0.z, t0.w + w0.w);
+          h1 = make_int4(t1.x + w1.x, t1.y + w1.y, t1.z + w1.z, t1.w + w1.w);
+        }
+        c[0] = h0.x - l0.x; c[1] = h0.y - l0.y; c[2] = h0.z - l0.z; c[3] = h0.w - l0.w;
+        c[4] = h1.x - l1.x; c[5] = h1.y - l1.y; c[6] = h1.z - l1.z; c[7] = h1.w - l1.w;
       }
-      const long long i4 = row4 + ((static_cast<long long>(x) * B2 + g0) >> 2) + q;
-      if (o.h) reinterpret_cast<int4*>(o.h)[i4] = c;
-      if (o.f32)
-        reinterpret_cast<float4*>(o.f32)[i4] = make_float4(c.x * sc, c.y * sc, c.z * sc, c.w * sc);
+      const long long i8 = row8 + ((static_cast<long long>(x) * B2 + g0) >> 3) + h;
+      if (o.h) {
+        reinterpret_cast<int4*>(o.h)[2 * i8] = make_int4(c[0], c[1], c[2], c[3]);
+        reinterpret_cast<int4*>(o.h)[2 * i8 + 1] = make_int4(c[4], c[5], c[6], c[7]);
+      }
+      // c * scale, exactly: 2^23 + c as a float (c < 2^23), times the
+      // power-of-two scale, minus 2^23 * scale, in one rounding
+      float f[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = fmaf(__int_as_float(c[k] | 0x4B000000), sc, nb);
+      const uint32_t d = weyl_dither(static_cast<unsigned long long>(i8) * 8);
+      if (o.f32) {
+        if (o.tf32) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) f[k] = tf32_dither(f[k], d + k * kWeyl);
+        }
+        reinterpret_cast<float4*>(o.f32)[2 * i8] = make_float4(f[0], f[1], f[2], f[3]);
+        reinterpret_cast<float4*>(o.f32)[2 * i8 + 1] = make_float4(f[4], f[5], f[6], f[7]);
+      }
       if (o.bf16) {
-        __nv_bfloat162 p0 = __floats2bfloat162_rn(c.x * sc, c.y * sc);
-        __nv_bfloat162 p1 = __floats2bfloat162_rn(c.z * sc, c.w * sc);
-        uint2 p;
-        p.x = *reinterpret_cast<uint32_t*>(&p0);
-        p.y = *reinterpret_cast<uint32_t*>(&p1);
-        reinterpret_cast<uint2*>(o.bf16)[i4] = p;
+        uint4 p;
+        p.x = bf16_pair_dither(f[0], d, f[1], d + kWeyl);
+        p.y = bf16_pair_dither(f[2], d + 2 * kWeyl, f[3], d + 3 * kWeyl);
+        p.z = bf16_pair_dither(f[4], d + 4 * kWeyl, f[5], d + 5 * kWeyl);
+        p.w = bf16_pair_dither(f[6], d + 6 * kWeyl, f[7], d + 7 * kWeyl);
+        reinterpret_cast<uint4*>(o.bf16)[i8] = p;
       }
-      if (o.sumsq)
-        sumsq += static_cast<unsigned long long>(c.x) * c.x + static_cast<unsigned long long>(c.y) * c.y +
-                 static_cast<unsigned long long>(c.z) * c.z + static_cast<unsigned long long>(c.w) * c.w;
+      if (o.sumsq) {
+        if (l <= 7) {  // counts <= 4^7: eight squares fit in 32 bits
+          uint32_t q = 0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) q += static_cast<uint32_t>(c[k]) * static_cast<uint32_t>(c[k]);
+          sumsq += q;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            sumsq += static_cast<unsigned long long>(static_cast<uint32_t>(c[k])) * static_cast<uint32_t>(c[k]);
+        }
+      }
     }
     // the next row's updates touch V only; the barrier after them orders this
     // row's reads of S before the next row's writes

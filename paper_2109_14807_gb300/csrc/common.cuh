@@ -80,6 +80,43 @@ __device__ __forceinline__ float round_tf32(float v) {
   return __uint_as_float(r);
 }
 
+// Unbiased rounding of the NDF operand tensor to fewer significand bits.
+// Round-to-nearest of counts drawn from a decreasing distribution (most
+// footprint counts are small) errs low on average, and that bias, not the
+// rounding noise, is what moves an ALS fit.  Instead a dither d in [0, 2^drop)
+// is added below the kept bits and the sum truncated, so that a value between
+// two representable neighbours goes up with probability equal to its distance
+// from the lower one.  d is the Weyl sequence frac(i * phi) of the element's
+// linear index i (32-bit fixed point, phi = golden ratio; Knuth, TAOCP vol. 3,
+// Sec. 6.4): equidistributed, cheap and the same wherever element i is
+// produced.  Representable values (low bits zero) are unchanged, so counts
+// with at most 8 (BF16) or 11 (TF32) significant bits stay exact.
+constexpr uint32_t kWeyl = 0x9E3779B9u;
+
+__device__ __forceinline__ uint32_t weyl_dither(unsigned long long i) {
+  return static_cast<uint32_t>(i) * kWeyl;
+}
+
+// FP32 bits of v >= 0 rounded to keep 32 - drop bits, dither d (full 32 bits).
+__device__ __forceinline__ uint32_t dither_round(float v, uint32_t d, int drop) {
+  return (__float_as_uint(v) + (d >> (32 - drop))) & ~((1u << drop) - 1u);
+}
+
+// BF16 bits of v >= 0 rounded without bias.
+__device__ __forceinline__ uint32_t bf16_dither(float v, uint32_t d) {
+  return (__float_as_uint(v) + (d >> 16)) >> 16;
+}
+
+// Two BF16 values (element 0 in the low half) as one 32-bit word.
+__device__ __forceinline__ uint32_t bf16_pair_dither(float v0, uint32_t d0, float v1, uint32_t d1) {
+  return __byte_perm(__float_as_uint(v0) + (d0 >> 16), __float_as_uint(v1) + (d1 >> 16), 0x7632);
+}
+
+// v >= 0 on the TF32 grid (10 fraction bits), rounded without bias.
+__device__ __forceinline__ float tf32_dither(float v, uint32_t d) {
+  return __uint_as_float(dither_round(v, d, 13));
+}
+
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {
   if (status) atomicOr(status, bits);
 }

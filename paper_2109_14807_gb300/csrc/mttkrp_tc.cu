@@ -14,6 +14,15 @@
 //           operand (fx (.) fy over the chunk's xy rows) is computed in shared
 //           memory by the epilogue warps while they are otherwise idle.
 //
+// Accumulation is chunked: the tensor core's FP32 accumulation does not round
+// to nearest, and over a chain of thousands of MMAs into one accumulator the
+// sums drift low by a few parts in 10^5 (measured: ~5e-8 relative per
+// accumulating MMA).  So every chunk of kChunk K steps starts a fresh TMEM
+// accumulator, and the epilogue adds the chunk sums with round-to-nearest FP32
+// adds in a fixed order: for Y' into registers, from double-buffered chunk
+// accumulators; for Z' into a running-sum region of tensor memory beside the
+// one chunk accumulator (the MMAs wait for that add, once per kChunkZ steps).
+//
 // CTA = 6 warps: warps 0-3 epilogue (TMEM lanes 0-127) and, in the Z' pass,
 // B-operand producers; warp 4 issues TMA; warp 5 owns TMEM and issues MMAs
 // (one thread).  Every mbarrier wait is bounded by a clock budget: on expiry
@@ -34,6 +43,8 @@ constexpr int kMaxRankTc = 64;  // CP ranks served by the tensor-core passes
 constexpr int kThreads = 192;
 constexpr long long kTimeoutCycles = 4000000000LL;  // about 2 s at GB300 clocks
 constexpr int kTileBytes = 128 * 128;                // 128 rows x 128 bytes
+constexpr int kChunk = 16;   // Y' K steps (4 MMAs each) per tensor-memory accumulator chunk
+constexpr int kChunkZ = 64;  // Z' K steps per chunk
 
 // ------------------------------------------------------------- PTX glue --
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -94,6 +105,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "%3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
       : "memory");
+}
+
+// The same load with an L2 eviction-priority hint (the streamed operand tensor
+// is read once per pass and should not push reused data out of L2).
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int c0,
+                                                 int c1, uint32_t mbar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 
 // tcgen05 shared-memory matrix descriptor, base offset 0.  layout: 2 = 128-byte
@@ -171,6 +199,39 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without the wait, so that several can be in flight.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes from registers.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -199,23 +260,6 @@ struct Barriers {
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
-}
-
-// Epilogue: copy this warp's 32 TMEM lanes x R columns starting at column
-// `col` into row-major FP32 rows of `out` (row stride R floats).
-__device__ __forceinline__ void store_accumulator(uint32_t tmem_base, int warp, int lane, int col,
-                                                  int R, float* out_rows) {
-  const uint32_t taddr = tmem_base + (static_cast<uint32_t>(warp * 32) << 16) + col;
-  float* row = out_rows + static_cast<size_t>(warp * 32 + lane) * R;
-  for (int c = 0; c < R; c += 16) {
-    float v[16];
-    tmem_ld16(taddr + c, v);
-    float4* dst = reinterpret_cast<float4*>(row + c);
-    dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-    dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-    dst[2] = make_float4(v[8], v[9], v[10], v[11]);
-    dst[3] = make_float4(v[12], v[13], v[14], v[15]);
-  }
 }
 
 // ------------------------------------------------------------ Y' pass --
@@ -266,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_parity[kMaxStages];
       bool issued[kMaxStages];
       for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
+      const uint64_t stream_policy = policy_evict_first();
       for (int tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
         const long long xy0 = static_cast<long long>(tile) * 128;
         for (int it = 0; it < kiters; ++it) {
@@ -274,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t sa = smem_u32(smem + s * stage_bytes);
           const uint32_t fb = smem_u32(&bar.full[s]);
           mbar_expect_tx(fb, stage_bytes);
-          tma_load_2d(sa, &mapT, kc * E128, static_cast<int>(l * N2 + xy0), fb);
+          tma_load_2d_hint(sa, &mapT, kc * E128, static_cast<int>(l * N2 + xy0), fb, stream_policy);
           tma_load_2d(sa + kTileBytes, &mapKR, l * B2 + kc * E128, 0, fb);
           issued[s] = true;
           issued_parity[s] = ph;
@@ -296,10 +341,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t ph = 0, aph = 0;
       bool any = false;
       for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        if (!mbar_wait(smem_u32(&bar.acc_empty[acc]), aph ^ 1u, abort)) break;
-        tc_fence_after();
-        const uint32_t d = tmem + static_cast<uint32_t>(acc * R);
+        uint32_t d = tmem;
         for (int it = 0; it < kiters; ++it) {
+          const int c = it % kChunk;
+          if (c == 0) {  // a fresh accumulator for each chunk of K steps
+            if (!mbar_wait(smem_u32(&bar.acc_empty[acc]), aph ^ 1u, abort)) goto mma_done;
+            tc_fence_after();
+            d = tmem + static_cast<uint32_t>(acc * R);
+          }
           if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + s * stage_bytes);
@@ -307,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {  // four K slices of 32 bytes per 128-byte row
             const uint64_t a = sdesc(sa + j * 32, 16, 1024);
-            umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (it > 0 || j > 0) ? 1u : 0u);
+            umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (c > 0 || j > 0) ? 1u : 0u);
             if constexpr (SPLIT) umma<ELEM>(d, a, sdesc(sb + R * 128 + j * 32, 16, 1024), id, 1u);
           }
           any = true;
@@ -316,11 +365,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             s = 0;
             ph ^= 1u;
           }
-        }
-        umma_commit(smem_u32(&bar.acc_full[acc]));
-        if (++acc == 2) {
-          acc = 0;
-          aph ^= 1u;
+          if (c == kChunk - 1 || it == kiters - 1) {
+            umma_commit(smem_u32(&bar.acc_full[acc]));
+            if (++acc == 2) {
+              acc = 0;
+              aph ^= 1u;
+            }
+          }
         }
       }
     mma_done:
@@ -329,20 +380,42 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_drain(smem_u32(&bar.drain), 0);
       }
     }
-  } else {  // ---- epilogue warps 0-3: TMEM -> Y'
+  } else {  // ---- epilogue warps 0-3: chunk sums -> registers -> Y'
     int acc = 0;
     uint32_t aph = 0;
+    const int nch = (kiters + kChunk - 1) / kChunk;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-      if (!mbar_wait(smem_u32(&bar.acc_full[acc]), aph, abort)) break;
-      tc_fence_after();
-      store_accumulator(tmem, warp, lane, acc * R, R, Yp + static_cast<size_t>(tile) * 128 * R);
-      tc_fence_before();
-      mbar_arrive(smem_u32(&bar.acc_empty[acc]));
-      if (++acc == 2) {
-        acc = 0;
-        aph ^= 1u;
+      float sum[kMaxRankTc];
+#pragma unroll
+      for (int i = 0; i < kMaxRankTc; ++i) sum[i] = 0.0f;
+      for (int ch = 0; ch < nch; ++ch) {
+        if (!mbar_wait(smem_u32(&bar.acc_full[acc]), aph, abort)) goto epi_done;
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < kMaxRankTc / 16; ++c) {
+          if (c * 16 < R) {
+            float v[16];
+            tmem_ld16(lane_base + acc * R + c * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sum[c * 16 + i] += v[i];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bar.acc_empty[acc]));
+        if (++acc == 2) {
+          acc = 0;
+          aph ^= 1u;
+        }
       }
+      float* row = Yp + (static_cast<size_t>(tile) * 128 + warp * 32 + lane) * R;
+#pragma unroll
+      for (int c = 0; c < kMaxRankTc / 4; ++c)
+        if (c * 4 < R)
+          reinterpret_cast<float4*>(row)[c] =
+              make_float4(sum[4 * c], sum[4 * c + 1], sum[4 * c + 2], sum[4 * c + 3]);
     }
+  epi_done:;
   }
   tc_fence_before();
   __syncthreads();
@@ -403,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long K = spl * L;
   const int g = blockIdx.x % G, p = blockIdx.x / G;
   const LstRange rg = lst_range(p, P, K, spl);
-  const uint32_t ncols = tmem_cols_for(MB * R);
+  const uint32_t ncols = tmem_cols_for(2 * MB * R);  // chunk accumulator + running sums
   volatile int* abort = &bar.abort;
 
   if (threadIdx.x == 0) {
@@ -434,6 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_parity[kMaxStages];
       bool issued[kMaxStages];
       for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
+      const uint64_t stream_policy = policy_evict_first();
       for (long long k = rg.k0; k < rg.k1 && !*abort; ++k) {
         for (int m = 0; m < MB; ++m) {
           if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
@@ -442,7 +516,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_expect_tx(fb, kTileBytes);
           const int st0 = (g * MB + m) * 128;
           for (int b = 0; b < BOXES; ++b)
-            tma_load_2d(sa + b * BOX_BYTES, &mapT, st0 + b * E128, static_cast<int>(k * E128), fb);
+            tma_load_2d_hint(sa + b * BOX_BYTES, &mapT, st0 + b * E128, static_cast<int>(k * E128),
+                             fb, stream_policy);
           issued[s] = true;
           issued_parity[s] = ph;
           if (++s == kStages) {
@@ -465,9 +540,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int seg = 0; seg < 2; ++seg) {
         const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
         if (kb >= ke) continue;
-        if (!mbar_wait(smem_u32(&bar.acc_empty[0]), uph ^ 1u, abort)) break;
-        tc_fence_after();
         for (long long k = kb; k < ke; ++k) {
+          const int c = static_cast<int>((k - kb) % kChunkZ);
+          if (c == 0) {  // a fresh accumulator for each chunk of K steps
+            if (!mbar_wait(smem_u32(&bar.acc_empty[0]), uph ^ 1u, abort)) goto mma_done;
+            tc_fence_after();
+          }
           if (!mbar_wait(smem_u32(&bar.b_full[bs]), bph, abort)) goto mma_done;
           tc_fence_after();
           const uint32_t sb = smem_u32(bslots + bs * b_bytes);
@@ -479,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const uint64_t a = sdesc(sa + j * MMA_K_ROWS * 128, BOX_BYTES, A_SBO, A_LAYOUT);
-              umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (k > kb || j > 0) ? 1u : 0u);
+              umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (c > 0 || j > 0) ? 1u : 0u);
               if constexpr (SPLIT)
                 umma<ELEM>(d, a, sdesc(sb + R * 128 + j * 32, 16, 1024), id, 1u);
             }
@@ -495,9 +573,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             bs = 0;
             bph ^= 1u;
           }
+          if (c == kChunkZ - 1 || k == ke - 1) {
+            umma_commit(smem_u32(&bar.acc_full[0]));
+            uph ^= 1u;
+          }
         }
-        umma_commit(smem_u32(&bar.acc_full[0]));
-        uph ^= 1u;
       }
     mma_done:
       if (*abort && any) {
@@ -518,10 +598,62 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int chunk = byte_in_row >> 4, within = byte_in_row & 15;
     int bs = 0;
     uint32_t bph = 0, uph = 0;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    const uint32_t sum_col = static_cast<uint32_t>(MB * R);
+    // Add chunk j of the accumulators (TMEM columns [0, MB R)) to the running
+    // sums (columns [MB R, 2 MB R)); the last chunk of a segment goes to
+    // partial slice 2p + seg instead.  32 columns per tensor-memory round trip.
+    auto drain = [&](long long j, bool last, int seg) -> bool {
+      if (!mbar_wait(smem_u32(&bar.acc_full[0]), uph, abort)) return false;
+      tc_fence_after();
+      float* part = Zpart + (static_cast<size_t>(p) * 2 + seg) * B2 * R;
+      for (int m = 0; m < MB; ++m) {
+        float* row = part + (static_cast<size_t>((g * MB + m) * 128) + warp * 32 + lane) * R;
+        for (int c = 0; c < R; c += 32) {
+          const uint32_t col = static_cast<uint32_t>(m * R + c);
+          const bool two = c + 16 < R;  // R = 16 has one 16-column group
+          uint32_t a[32], b[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) b[i] = 0u;
+          tmem_ld16_nowait(lane_base + col, a);
+          if (two) tmem_ld16_nowait(lane_base + col + 16, a + 16);
+          if (j > 0) {
+            tmem_ld16_nowait(lane_base + sum_col + col, b);
+            if (two) tmem_ld16_nowait(lane_base + sum_col + col + 16, b + 16);
+          }
+          tmem_ld_wait();
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            v[i] = j > 0 ? __uint_as_float(b[i]) + __uint_as_float(a[i]) : __uint_as_float(a[i]);
+          if (last) {
+            float4* dst = reinterpret_cast<float4*>(row + c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            if (two) {
+#pragma unroll
+              for (int i = 4; i < 8; ++i)
+                dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+          } else {
+            tmem_st16(lane_base + sum_col + col, v);
+            if (two) tmem_st16(lane_base + sum_col + col + 16, v + 16);
+          }
+        }
+      }
+      if (!last) tmem_st_wait();
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bar.acc_empty[0]));
+      uph ^= 1u;
+      return true;
+    };
     for (int seg = 0; seg < 2; ++seg) {
       const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
       if (kb >= ke) continue;
       const int l = rg.level0 + seg;
+      const long long nch = (ke - kb + kChunkZ - 1) / kChunkZ;
+      long long drained = 0;
       for (long long k = kb; k < ke; ++k) {
         if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto epi_done;
         const long long xy = k * E128 + kk - l * N2;
@@ -563,19 +695,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           bs = 0;
           bph ^= 1u;
         }
+        // chunk j is added once the B operand of the next chunk's first step
+        // is ready, so the MMAs resume as soon as the accumulator is free
+        if (drained < nch - 1 && k >= kb + (drained + 1) * kChunkZ) {
+          if (!drain(drained, false, seg)) goto epi_done;
+          ++drained;
+        }
       }
-      // epilogue: MB accumulators of 128 st rows x R -> partial slice 2p + seg
-      if (!mbar_wait(smem_u32(&bar.acc_full[0]), uph, abort)) goto epi_done;
-      tc_fence_after();
-      {
-        float* part = Zpart + (static_cast<size_t>(p) * 2 + seg) * B2 * R;
-        for (int m = 0; m < MB; ++m)
-          store_accumulator(tmem, warp, lane, m * R, R,
-                            part + static_cast<size_t>((g * MB + m) * 128) * R);
-      }
-      tc_fence_before();
-      mbar_arrive(smem_u32(&bar.acc_empty[0]));
-      uph ^= 1u;
+      for (; drained < nch; ++drained)
+        if (!drain(drained, drained == nch - 1, seg)) goto epi_done;
     }
   epi_done:;
   }
@@ -668,9 +796,11 @@ int set_smem(K kernel, size_t bytes) {
   return GSP_OK;
 }
 
+// st blocks per CTA (MB) and st groups (G): the chunk accumulators and the
+// running sums take 2 MB R <= 512 tensor-memory columns.
 int lst_groups(const MttkrpDims& d, int* MB) {
   int blocks = d.B2() / 128;
-  int mb = 512 / d.R;
+  int mb = 256 / d.R;
   if (mb > blocks) mb = blocks;
   *MB = mb;
   return blocks / mb;
@@ -726,7 +856,7 @@ int tc_lst_ctas(const MttkrpDims& d) {
   int MB = 0;
   const int G = lst_groups(d, &MB);
   int P = sm_count() / G;
-  if (P < 1) P = 1;
+  if (P < d.L) P = d.L;  // a range is then at most one level long: <= 2 segments
   if (P > kLstMaxRanges) P = kLstMaxRanges;
   return P;
 }

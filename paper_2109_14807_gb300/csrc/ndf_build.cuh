@@ -8,19 +8,25 @@ namespace gsp {
 
 // Where one level slice of counts goes.  Any pointer may be null.
 //  h:     int32 counts [N][N][B][B]
-//  f32:   counts * scale as FP32
-//  bf16:  counts * scale rounded to BF16 (round to nearest even)
+//  f32:   counts * scale as FP32 (exact; on the TF32 grid when tf32 is set)
+//  bf16:  counts * scale rounded to BF16
 //  sumsq: one 64-bit counter receiving sum of counts^2 (exact)
+// BF16 and TF32 values are rounded without bias (dither_round), the dither
+// indexed by base + the element's index in the slice.
 struct LevelSink {
   int32_t* h;
   float* f32;
   __nv_bfloat16* bf16;
   float scale;
   unsigned long long* sumsq;
+  int tf32;
+  long long base;
 };
 
 // Outputs of the all-level histogram build; any pointer may be null.  Arrays
 // are the full [levels][N][N][B][B] tensors; sumsq has one counter per level.
+// Rounding as for LevelSink, the dither indexed by the element's index in the
+// full tensor.
 struct HistOut {
   int32_t* h;
   float* f32;
@@ -28,6 +34,7 @@ struct HistOut {
   unsigned long long* sumsq;
   const uint32_t* groups;  // occupied 16-bin groups (bitmask) or null
   float scale[16];         // counts -> operand value, per level
+  int tf32;                // f32 values rounded to the TF32 grid without bias
 };
 
 // Bytes of the occupied-bin-group bitmask (one bit per 16 bins, B <= 128).

@@ -19,8 +19,8 @@ MTTKRP_TOL = {"fp32": 2e-5, "tf32": 3e-3, "bf16": 1.5e-2, "bf16_1x": 1.5e-2}
 # ALS fit tolerance vs the FP64 oracle after the same sweeps from the same init.
 # BF16 (tensor in BF16, Khatri-Rao operand as a BF16 hi + lo pair) must meet
 # 1e-4.  Single-pass TF32 rounds the Khatri-Rao operand to 11 significant bits;
-# emulating that rounding in FP64 on this workload gives ~9e-5 after 8 sweeps,
-# so it is held to 2e-4.
+# emulating that rounding in FP64 on the 64^2 brushed workload gives ~9e-5 after
+# 8 sweeps, so it is held to 2e-4.
 FIT_TOL = {"bf16": 1e-4, "tf32": 2e-4}
 
 
@@ -94,16 +94,61 @@ def test_als_fp32_flakes32_matches_oracle():
     assert err <= QUERY_TOL
 
 
-def test_als_from_normals_equals_from_histograms():
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
+def test_als_from_normals_equals_from_histograms(prec):
+    # both ways of preparing the operand give the same values (the rounding of
+    # the tensor-core operands depends only on the element index)
     import paper_2109_14807_gb300 as g
-    w = synth.WORKLOADS["flakes32"]
-    N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
-    m = synth.make_map(w)
+    N, L, B, R = 32, 6, 16, 16
+    if not _supported(prec, N, L, B, R):
+        pytest.skip(f"{prec} path unavailable")
+    m = synth.make_map(synth.WORKLOADS["flakes32"])
     init = synth.init_factors(N, L, B, R, 2001)
     H = g.build_footprint_ndfs(dev(m), L, B)
-    _, fits1, _ = g.cp_decompose(R, init, hist=H, sweeps=5)
-    _, fits2, _ = g.cp_decompose(R, init, normal_xy=dev(m), levels=L, bins=B, sweeps=5)
+    _, fits1, _ = g.cp_decompose(R, init, hist=H, sweeps=5, precision=prec)
+    _, fits2, _ = g.cp_decompose(R, init, normal_xy=dev(m), levels=L, bins=B, sweeps=5,
+                                 precision=prec)
     assert fits1 == fits2
+
+
+@pytest.mark.parametrize("prec,drop", [("bf16", 16), ("tf32", 13)])
+def test_operand_rounding_is_exact_or_neighbour_and_unbiased(prec, drop):
+    # The tensor-core operand (documented as the first levels*N^2*B^2 elements
+    # of the workspace) holds every exactly representable density unchanged and
+    # every other one as its lower or upper neighbour on the BF16 / TF32 grid,
+    # without bias: the summed rounding error stays within six standard
+    # deviations of a sum of independent zero-mean errors of at most one ulp.
+    # 16 large flakes put thousands of texels of one bin in the coarse
+    # footprints (counts above 256 and 2048 are not representable).
+    import paper_2109_14807_gb300 as g
+    N, L, B, R = 128, 8, 16, 16
+    if not _supported(prec, N, L, B, R):
+        pytest.skip(f"{prec} path unavailable")
+    m = synth.flake_map(N, 16, 0.1, 77)
+    H = ndf.footprint_histograms(*ndf.bin_index(m, B), L, B)
+    exact = ndf.normalised_tensor(H, B).astype(np.float32).ravel()  # exact: counts * 2^k
+    ws = g.CPWorkspace(N, L, B, R, prec)
+    ws.prepare(normal_xy=dev(m))
+    torch.cuda.synchronize()
+    n = exact.size
+    if prec == "bf16":
+        raw = ws.buf[: 2 * n].cpu().numpy().view(np.uint16).astype(np.uint64) << 16
+    else:
+        raw = ws.buf[: 4 * n].cpu().numpy().view(np.uint32).astype(np.uint64)
+    u = exact.view(np.uint32).astype(np.uint64)
+    lo = (u >> drop) << drop
+    up = lo + (1 << drop)
+    representable = lo == u
+    assert np.all(raw[representable] == u[representable])
+    assert np.all((raw == lo) | (raw == up))
+    f = lambda b: b.astype(np.uint32).view(np.float32).astype(np.float64)
+    err = f(raw) - exact.astype(np.float64)
+    ulp = f(up) - f(lo)
+    inexact = ~representable
+    assert np.count_nonzero(inexact) > 10_000  # the case exercises the rounding
+    del H
+    bound = 6.0 * np.sqrt(np.sum(ulp[inexact] ** 2) / 4.0)
+    assert abs(np.sum(err)) <= bound, (np.sum(err), bound)
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
