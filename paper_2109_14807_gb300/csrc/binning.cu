@@ -95,14 +95,24 @@ __device__ __forceinline__ void sink_sumsq(const LevelSink& o, int4 v, bool acti
 //    column per lane, on pairs of 16-bit counts packed in 32-bit words (a sum
 //    over 32 columns is at most 32 w <= 2^15), carries between blocks in 32
 //    bits, and stores S once the offsets of the earlier ranges are known;
-//  - rows of V (48 B) and S (80 B) are padded so that 16-byte accesses of
-//    consecutive columns fall on distinct banks.
+//  - rows of V (48 B) are padded so that 16-byte accesses of consecutive
+//    columns fall on distinct banks; S is kept as two planes of 8 bins (32-byte
+//    rows) whose offsets differ by 16 mod 128 bytes, so the output's reads
+//    (lane pairs per column, one plane each) fall on distinct banks;
+//  - S is double-buffered, so the scan of row y and the output of row y - 1
+//    share one phase: two barriers per row.
 constexpr int kHistG = 16;
 constexpr int kHistThreads = 512;
 constexpr int kHistWarps = kHistThreads / 32;
 constexpr int kVRow = 24;  // uint16 per column count row (16 + 8 padding)
-constexpr int kSRow = 20;  // ints per prefix row (16 + 4 padding)
+constexpr int kSRow = 8;   // ints per prefix row of one 8-bin plane
 constexpr int kMaxBlocks = 2;  // 32-column blocks per scanning warp (N <= 1024)
+
+// Ints per S plane: N + 1 rows of 8, padded so that the second plane starts 4
+// ints (16 bytes) past a multiple of 32 ints from the first.
+__host__ __device__ constexpr int s_plane_ints(int N) {
+  return (N + 1) * kSRow + (((4 - (N + 1) * kSRow) % 32) + 32) % 32;
+}
 
 __global__ void __launch_bounds__(kHistThreads, 1)
     k_box_hist(const uint16_t* __restrict__ bins_map, int logN, int B2, int ychunk,
@@ -112,7 +122,8 @@ __global__ void __launch_bounds__(kHistThreads, 1)
   __shared__ __align__(16) int WT[kHistWarps * G];
   const int N = 1 << logN, m = N - 1;
   uint16_t* V = reinterpret_cast<uint16_t*>(smem_b);                         // [N][24]
-  int* S = reinterpret_cast<int*>(smem_b + N * kVRow * sizeof(uint16_t));    // [N + 1][20]
+  int* S = reinterpret_cast<int*>(smem_b + N * kVRow * sizeof(uint16_t));    // [2][2][N + 1][8]
+  const int plane = s_plane_ints(N), sbuf = 2 * plane;
   const int g0 = blockIdx.x * G;
   const int y0 = blockIdx.y * ychunk;
   const int l = blockIdx.z;
@@ -148,7 +159,9 @@ __global__ void __launch_bounds__(kHistThreads, 1)
 
   for (int i = tid; i < N * kVRow / 8; i += kHistThreads)
     reinterpret_cast<uint4*>(V)[i] = make_uint4(0, 0, 0, 0);
-  if (tid < 4) reinterpret_cast<int4*>(S)[tid] = make_int4(0, 0, 0, 0);  // S[0] = 0
+  if (tid < 8)  // S[0] = 0 in both planes of both buffers
+    reinterpret_cast<int4*>(S + (tid >> 2) * sbuf + ((tid >> 1) & 1) * plane)[tid & 1] =
+        make_int4(0, 0, 0, 0);
   __syncthreads();
   for (int x = tid; x < N; x += kHistThreads) {
     // the window's rows, eight independent loads at a time
@@ -180,21 +193,18 @@ __global__ void __launch_bounds__(kHistThreads, 1)
   };
   fetch(y0 + 1);
   unsigned long long sumsq = 0;
+  __syncthreads();  // V of row y0 complete (columns are initialised by other warps)
 
-  for (int y = y0; y < y0 + ychunk; ++y) {
-    if (y > y0) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int x = tid + k * kHistThreads;
-        const int bo = nxt_out[k] - g0, bi = nxt_in[k] - g0;
-        if (x < N && static_cast<unsigned>(bo) < static_cast<unsigned>(G)) V[x * kVRow + bo] -= 1;
-        if (x < N && static_cast<unsigned>(bi) < static_cast<unsigned>(G)) V[x * kVRow + bi] += 1;
-      }
-      if (y + 1 < y0 + ychunk) fetch(y + 1);
-    }
-    __syncthreads();
+  // Pipelined over rows with S double-buffered: iteration y scans row y (V
+  // holds its window) while writing the counts of row y - 1 from the other S
+  // buffer; after the barrier the scan's range offsets are applied, S of row y
+  // is stored and V moves on to row y + 1.  Two barriers per row.
+  for (int y = y0; y <= y0 + ychunk; ++y) {
+    const bool scan_row = y < y0 + ychunk;
+    int* Sc = S + ((y - y0) & 1) * sbuf;        // S of row y
+    const int* Sp = S + ((y - y0 + 1) & 1) * sbuf;  // S of row y - 1
     int vals[kMaxBlocks][G];
-    if (warp < scan_warps) {
+    if (scan_row && warp < scan_warps) {
       int carry[G];
 #pragma unroll
       for (int b = 0; b < G; ++b) carry[b] = 0;
@@ -237,96 +247,118 @@ __global__ void __launch_bounds__(kHistThreads, 1)
         for (int b = 0; b < G; ++b) WT[warp * G + b] = carry[b];
       }
     }
-    __syncthreads();
-    if (warp < scan_warps) {
-      // offset of this warp's range: lanes 0..15 sum one bin each over the earlier warps
-      int my = 0;
-      if (lane < G)
-        for (int k = 0; k < warp; ++k) my += WT[k * G + lane];
-      int off[G];
+    if (y > y0) {
+      // counts of every footprint of row y - 1, eight bins per item; the lanes
+      // of a warp take consecutive x, so their 16-byte prefix reads (80-byte
+      // rows) fall on distinct banks
+      const long long row8 = ((static_cast<long long>(l) * N + (y - 1)) * N * B2) >> 3;
+      for (int e = tid; e < 2 * N; e += kHistThreads) {
+        const int h = e & 1, x = e >> 1;  // lane pairs write 32 contiguous bytes
+        const int st = (x - a) & m, en = st + w;
+        const int* Sh = Sp + h * plane;
+        const int4* lo4 = reinterpret_cast<const int4*>(Sh + st * kSRow);
+        int c[8];
+        {
+          const int4 l0 = lo4[0], l1 = lo4[1];
+          int4 h0, h1;
+          if (en <= N) {
+            const int4* hi4 = reinterpret_cast<const int4*>(Sh + en * kSRow);
+            h0 = hi4[0];
+            h1 = hi4[1];
+          } else {  // window wraps: S[N] - S[st] + S[en - N]
+            const int4* tp = reinterpret_cast<const int4*>(Sh + N * kSRow);
+            const int4* wr = reinterpret_cast<const int4*>(Sh + (en - N) * kSRow);
+            const int4 t0 = tp[0], t1 = tp[1], w0 = wr[0], w1 = wr[1];
+            h0 = make_int4(t0.x + w0.x, t0.y + w0.y, t0.z + w0.z, t0.w + w0.w);
+            h1 = make_int4(t1.x + w1.x, t1.y + w1.y, t1.z + w1.z, t1.w + w1.w);
+          }
+          c[0] = h0.x - l0.x; c[1] = h0.y - l0.y; c[2] = h0.z - l0.z; c[3] = h0.w - l0.w;
+          c[4] = h1.x - l1.x; c[5] = h1.y - l1.y; c[6] = h1.z - l1.z; c[7] = h1.w - l1.w;
+        }
+        const long long i8 = row8 + ((static_cast<long long>(x) * B2 + g0) >> 3) + h;
+        if (o.h) {
+          reinterpret_cast<int4*>(o.h)[2 * i8] = make_int4(c[0], c[1], c[2], c[3]);
+          reinterpret_cast<int4*>(o.h)[2 * i8 + 1] = make_int4(c[4], c[5], c[6], c[7]);
+        }
+        // c * scale, exactly: 2^23 + c as a float (c < 2^23), times the
+        // power-of-two scale, minus 2^23 * scale, in one rounding
+        float f[8];
 #pragma unroll
-      for (int b = 0; b < G; ++b) off[b] = __shfl_sync(0xffffffffu, my, b);
-      const int xbeg = warp * xr;
+        for (int k = 0; k < 8; ++k) f[k] = fmaf(__int_as_float(c[k] | 0x4B000000), sc, nb);
+        const uint32_t d = weyl_dither(static_cast<unsigned long long>(i8) * 8);
+        if (o.f32) {
+          if (o.tf32 && l >= 6) {  // counts <= 4^5 are exact on the TF32 grid
 #pragma unroll
-      for (int blk = 0; blk < kMaxBlocks; ++blk) {
-        if (blk < nblk && blk * 32 + lane < xr) {
-          int4* dst = reinterpret_cast<int4*>(S + (xbeg + blk * 32 + lane + 1) * kSRow);
+            for (int k = 0; k < 8; ++k) f[k] = tf32_dither(f[k], d + k * kWeyl);
+          }
+          reinterpret_cast<float4*>(o.f32)[2 * i8] = make_float4(f[0], f[1], f[2], f[3]);
+          reinterpret_cast<float4*>(o.f32)[2 * i8 + 1] = make_float4(f[4], f[5], f[6], f[7]);
+        }
+        if (o.bf16 && l <= 4) {  // counts <= 256: exact in BF16
+          uint4 p;
+          p.x = __byte_perm(__float_as_uint(f[0]), __float_as_uint(f[1]), 0x7632);
+          p.y = __byte_perm(__float_as_uint(f[2]), __float_as_uint(f[3]), 0x7632);
+          p.z = __byte_perm(__float_as_uint(f[4]), __float_as_uint(f[5]), 0x7632);
+          p.w = __byte_perm(__float_as_uint(f[6]), __float_as_uint(f[7]), 0x7632);
+          reinterpret_cast<uint4*>(o.bf16)[i8] = p;
+        } else if (o.bf16) {
+          uint4 p;
+          p.x = bf16_pair_dither(f[0], d, f[1], d + kWeyl);
+          p.y = bf16_pair_dither(f[2], d + 2 * kWeyl, f[3], d + 3 * kWeyl);
+          p.z = bf16_pair_dither(f[4], d + 4 * kWeyl, f[5], d + 5 * kWeyl);
+          p.w = bf16_pair_dither(f[6], d + 6 * kWeyl, f[7], d + 7 * kWeyl);
+          reinterpret_cast<uint4*>(o.bf16)[i8] = p;
+        }
+        if (o.sumsq) {
+          if (l <= 7) {  // counts <= 4^7: eight squares fit in 32 bits
+            uint32_t q = 0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            dst[q] = make_int4(vals[blk][4 * q] + off[4 * q], vals[blk][4 * q + 1] + off[4 * q + 1],
+            for (int k = 0; k < 8; ++k) q += static_cast<uint32_t>(c[k]) * static_cast<uint32_t>(c[k]);
+            sumsq += q;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              sumsq += static_cast<unsigned long long>(static_cast<uint32_t>(c[k])) * static_cast<uint32_t>(c[k]);
+          }
+        }
+      }
+    }
+    __syncthreads();  // range totals WT complete; V and S of row y - 1 no longer read
+    if (scan_row) {
+      if (warp < scan_warps) {
+        // offset of this warp's range: lanes 0..15 sum one bin each over the earlier warps
+        int my = 0;
+        if (lane < G)
+          for (int k = 0; k < warp; ++k) my += WT[k * G + lane];
+        int off[G];
+#pragma unroll
+        for (int b = 0; b < G; ++b) off[b] = __shfl_sync(0xffffffffu, my, b);
+        const int xbeg = warp * xr;
+#pragma unroll
+        for (int blk = 0; blk < kMaxBlocks; ++blk) {
+          if (blk < nblk && blk * 32 + lane < xr) {
+            const int xs = xbeg + blk * 32 + lane + 1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              int4* dst = reinterpret_cast<int4*>(Sc + (q >> 1) * plane + xs * kSRow) + (q & 1);
+              *dst = make_int4(vals[blk][4 * q] + off[4 * q], vals[blk][4 * q + 1] + off[4 * q + 1],
                                vals[blk][4 * q + 2] + off[4 * q + 2], vals[blk][4 * q + 3] + off[4 * q + 3]);
+            }
+          }
         }
+      }
+      if (y + 1 < y0 + ychunk) {  // V: window of row y + 1
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int x = tid + k * kHistThreads;
+          const int bo = nxt_out[k] - g0, bi = nxt_in[k] - g0;
+          if (x < N && static_cast<unsigned>(bo) < static_cast<unsigned>(G)) V[x * kVRow + bo] -= 1;
+          if (x < N && static_cast<unsigned>(bi) < static_cast<unsigned>(G)) V[x * kVRow + bi] += 1;
+        }
+        if (y + 2 < y0 + ychunk) fetch(y + 2);
       }
     }
-    __syncthreads();
-    // counts of every footprint of row y, eight bins per item; the lanes of a
-    // warp take consecutive x, so their 16-byte prefix reads (80-byte rows)
-    // fall on distinct banks
-    const long long row8 = ((static_cast<long long>(l) * N + y) * N * B2) >> 3;
-    for (int e = tid; e < 2 * N; e += kHistThreads) {
-      const int h = e >> logN, x = e & m;
-      const int st = (x - a) & m, en = st + w;
-      const int4* lo4 = reinterpret_cast<const int4*>(S + st * kSRow + 8 * h);
-      int c[8];
-      {
-        const int4 l0 = lo4[0], l1 = lo4[1];
-        int4 h0, h1;
-        if (en <= N) {
-          const int4* hi4 = reinterpret_cast<const int4*>(S + en * kSRow + 8 * h);
-          h0 = hi4[0];
-          h1 = hi4[1];
-        } else {  // window wraps: S[N] - S[st] + S[en - N]
-          const int4* tp = reinterpret_cast<const int4*>(S + N * kSRow + 8 * h);
-          const int4* wr = reinterpret_cast<const int4*>(S + (en - N) * kSRow + 8 * h);
-          const int4 t0 = tp[0], t1 = tp[1], w0 = wr[0], w1 = wr[1];
-          h0 = make_int4(t0.x + w0.x, t0.y + w0.y, t0.z + w0.z, t0.w + w0.w);
-          h1 = make_int4(t1.x + w1.x, t1.y + w1.y, t1.z + w1.z, t1.w + w1.w);
-        }
-        c[0] = h0.x - l0.x; c[1] = h0.y - l0.y; c[2] = h0.z - l0.z; c[3] = h0.w - l0.w;
-        c[4] = h1.x - l1.x; c[5] = h1.y - l1.y; c[6] = h1.z - l1.z; c[7] = h1.w - l1.w;
-      }
-      const long long i8 = row8 + ((static_cast<long long>(x) * B2 + g0) >> 3) + h;
-      if (o.h) {
-        reinterpret_cast<int4*>(o.h)[2 * i8] = make_int4(c[0], c[1], c[2], c[3]);
-        reinterpret_cast<int4*>(o.h)[2 * i8 + 1] = make_int4(c[4], c[5], c[6], c[7]);
-      }
-      // c * scale, exactly: 2^23 + c as a float (c < 2^23), times the
-      // power-of-two scale, minus 2^23 * scale, in one rounding
-      float f[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) f[k] = fmaf(__int_as_float(c[k] | 0x4B000000), sc, nb);
-      const uint32_t d = weyl_dither(static_cast<unsigned long long>(i8) * 8);
-      if (o.f32) {
-        if (o.tf32) {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) f[k] = tf32_dither(f[k], d + k * kWeyl);
-        }
-        reinterpret_cast<float4*>(o.f32)[2 * i8] = make_float4(f[0], f[1], f[2], f[3]);
-        reinterpret_cast<float4*>(o.f32)[2 * i8 + 1] = make_float4(f[4], f[5], f[6], f[7]);
-      }
-      if (o.bf16) {
-        uint4 p;
-        p.x = bf16_pair_dither(f[0], d, f[1], d + kWeyl);
-        p.y = bf16_pair_dither(f[2], d + 2 * kWeyl, f[3], d + 3 * kWeyl);
-        p.z = bf16_pair_dither(f[4], d + 4 * kWeyl, f[5], d + 5 * kWeyl);
-        p.w = bf16_pair_dither(f[6], d + 6 * kWeyl, f[7], d + 7 * kWeyl);
-        reinterpret_cast<uint4*>(o.bf16)[i8] = p;
-      }
-      if (o.sumsq) {
-        if (l <= 7) {  // counts <= 4^7: eight squares fit in 32 bits
-          uint32_t q = 0;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) q += static_cast<uint32_t>(c[k]) * static_cast<uint32_t>(c[k]);
-          sumsq += q;
-        } else {
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            sumsq += static_cast<unsigned long long>(static_cast<uint32_t>(c[k])) * static_cast<uint32_t>(c[k]);
-        }
-      }
-    }
-    // the next row's updates touch V only; the barrier after them orders this
-    // row's reads of S before the next row's writes
+    __syncthreads();  // S of row y and V of row y + 1 complete; WT read
   }
   if (o.sumsq) {
     for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
@@ -363,7 +395,7 @@ int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins, uin
 
 size_t box_hist_smem(int N) {
   return static_cast<size_t>(N) * kVRow * sizeof(uint16_t) +
-         static_cast<size_t>(N + 1) * kSRow * sizeof(int);
+         4 * static_cast<size_t>(s_plane_ints(N)) * sizeof(int);
 }
 
 int launch_box_hist(const uint16_t* d_bins, int N, int levels, int bins, const HistOut& o,

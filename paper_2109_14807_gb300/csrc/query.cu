@@ -244,7 +244,33 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
 }
 
 // ----------------------------------------------------------- adjoint --
-template <int LANES>
+// VEC consecutive floats of a global table row (8 / 4-byte aligned).
+template <int VEC>
+__device__ __forceinline__ void ldg_vec(const float* __restrict__ p, float* v) {
+  if constexpr (VEC == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = a.x; v[1] = a.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+
+// Atomic add of VEC consecutive floats as one vector reduction.
+template <int VEC>
+__device__ __forceinline__ void red_add(float* p, const float* v) {
+  if constexpr (VEC == 2) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v[0]), "f"(v[1]) : "memory");
+  } else {
+    atomicAdd(p, v[0]);
+  }
+}
+
+// LANES lanes per query; lane j handles the VEC consecutive ranks
+// j*VEC + k*LANES*VEC .. + VEC-1, so that its fx / fy gradient updates are
+// vector reductions.  The per-CTA shared-memory tables store rank r of a row
+// at column (r mod VEC) * R/VEC + r / VEC, so that the lanes' atomics for one
+// v = r mod VEC hit consecutive words (no bank conflicts); the flush undoes it.
+template <int LANES, int VEC>
 __global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__ MatParams mp,
                                                          const __grid_constant__ GradParams gp,
                                                          const gsp_query* __restrict__ q,
@@ -296,39 +322,51 @@ __global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__
       sg.dft = G.dft;
     }
     const float g0 = 1.0f - t.f;
-    for (int r = j; r < R; r += LANES) {
-      float a0 = __ldg(flw + t.l0 * R + r), a1 = __ldg(flw + t.l1 * R + r);
-      float lv = fmaf(t.f, a1, g0 * a0);
-      float S = sat_mean(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
-      float T = sat_mean(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
-      float xv = __ldg(M.fx + t.x * R + r), yv = __ldg(M.fy + t.y * R + r);
-      float xy = xv * yv;
-      float st = S * T;
-      atomicAdd(G.dfx + t.x * R + r, g * yv * lv * st);
-      atomicAdd(G.dfy + t.y * R + r, g * xv * lv * st);
-      atomicAdd(sg.dflw + t.l0 * R + r, g * g0 * xy * st);
-      if (t.f != 0.0f) atomicAdd(sg.dflw + t.l1 * R + r, g * t.f * xy * st);
-      // Sbar = (F(s1) - F(s0)) / w with F(s) = P[floor s] + frac(s) fs[floor s]
-      float cs = g * xy * lv * T;
-      if (t.inv_ws > 0.0f) {
-        float a = cs * t.inv_ws;
-        atomicAdd(sg.dps + t.is1 * R + r, a);
-        atomicAdd(sg.dps + t.is0 * R + r, -a);
-        if (t.fs1 != 0.0f) atomicAdd(sg.dfs + t.is1 * R + r, a * t.fs1);
-        if (t.fs0 != 0.0f) atomicAdd(sg.dfs + t.is0 * R + r, -a * t.fs0);
-      } else {
-        atomicAdd(sg.dfs + t.isz * R + r, cs);
+    for (int rv = j * VEC; rv < R; rv += LANES * VEC) {
+      float a0v[VEC], a1v[VEC], xvv[VEC], yvv[VEC], dx[VEC], dy[VEC];
+      ldg_vec<VEC>(flw + t.l0 * R + rv, a0v);
+      ldg_vec<VEC>(flw + t.l1 * R + rv, a1v);
+      ldg_vec<VEC>(M.fx + t.x * R + rv, xvv);
+      ldg_vec<VEC>(M.fy + t.y * R + rv, yvv);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const int r0 = rv + v;
+        // column of rank r0 in this CTA's shared-memory tables (global: r0)
+        const int r = gp.use_smem ? v * (R / VEC) + rv / VEC : r0;
+        float lv = fmaf(t.f, a1v[v], g0 * a0v[v]);
+        float S = sat_mean(sats, R, r0, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
+        float T = sat_mean(satt, R, r0, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
+        float xv = xvv[v], yv = yvv[v];
+        float xy = xv * yv;
+        float st = S * T;
+        dx[v] = g * yv * lv * st;
+        dy[v] = g * xv * lv * st;
+        atomicAdd(sg.dflw + t.l0 * R + r, g * g0 * xy * st);
+        if (t.f != 0.0f) atomicAdd(sg.dflw + t.l1 * R + r, g * t.f * xy * st);
+        // Sbar = (F(s1) - F(s0)) / w with F(s) = P[floor s] + frac(s) fs[floor s]
+        float cs = g * xy * lv * T;
+        if (t.inv_ws > 0.0f) {
+          float a = cs * t.inv_ws;
+          atomicAdd(sg.dps + t.is1 * R + r, a);
+          atomicAdd(sg.dps + t.is0 * R + r, -a);
+          if (t.fs1 != 0.0f) atomicAdd(sg.dfs + t.is1 * R + r, a * t.fs1);
+          if (t.fs0 != 0.0f) atomicAdd(sg.dfs + t.is0 * R + r, -a * t.fs0);
+        } else {
+          atomicAdd(sg.dfs + t.isz * R + r, cs);
+        }
+        float ct = g * xy * lv * S;
+        if (t.inv_wt > 0.0f) {
+          float a = ct * t.inv_wt;
+          atomicAdd(sg.dpt + t.it1 * R + r, a);
+          atomicAdd(sg.dpt + t.it0 * R + r, -a);
+          if (t.ft1 != 0.0f) atomicAdd(sg.dft + t.it1 * R + r, a * t.ft1);
+          if (t.ft0 != 0.0f) atomicAdd(sg.dft + t.it0 * R + r, -a * t.ft0);
+        } else {
+          atomicAdd(sg.dft + t.itz * R + r, ct);
+        }
       }
-      float ct = g * xy * lv * S;
-      if (t.inv_wt > 0.0f) {
-        float a = ct * t.inv_wt;
-        atomicAdd(sg.dpt + t.it1 * R + r, a);
-        atomicAdd(sg.dpt + t.it0 * R + r, -a);
-        if (t.ft1 != 0.0f) atomicAdd(sg.dft + t.it1 * R + r, a * t.ft1);
-        if (t.ft0 != 0.0f) atomicAdd(sg.dft + t.it0 * R + r, -a * t.ft0);
-      } else {
-        atomicAdd(sg.dft + t.itz * R + r, ct);
-      }
+      red_add<VEC>(G.dfx + t.x * R + rv, dx);
+      red_add<VEC>(G.dfy + t.y * R + rv, dy);
     }
   }
   if (gp.use_smem) {
@@ -338,15 +376,18 @@ __global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__
       const int R = M.rank, L = M.levels, B = M.bins;
       const SmallGrad sg = small_tables(sacc + gp.soff[m], M);
       const gsp_material_grad& G = gp.g[m];
+      const int RV = R / VEC;
+      // shared column c holds rank (c mod R/VEC) * VEC + c / (R/VEC)
+      auto gidx = [&](int e) { const int c = e % R; return e - c + (c % RV) * VEC + c / RV; };
       for (int e = threadIdx.x; e < L * R; e += blockDim.x)
-        if (sg.dflw[e] != 0.0f) atomicAdd(G.dflw + e, sg.dflw[e]);
+        if (sg.dflw[e] != 0.0f) atomicAdd(G.dflw + gidx(e), sg.dflw[e]);
       for (int e = threadIdx.x; e < (B + 1) * R; e += blockDim.x) {
-        if (sg.dps[e] != 0.0f) atomicAdd(gp.dps[m] + e, sg.dps[e]);
-        if (sg.dpt[e] != 0.0f) atomicAdd(gp.dpt[m] + e, sg.dpt[e]);
+        if (sg.dps[e] != 0.0f) atomicAdd(gp.dps[m] + gidx(e), sg.dps[e]);
+        if (sg.dpt[e] != 0.0f) atomicAdd(gp.dpt[m] + gidx(e), sg.dpt[e]);
       }
       for (int e = threadIdx.x; e < B * R; e += blockDim.x) {
-        if (sg.dfs[e] != 0.0f) atomicAdd(G.dfs + e, sg.dfs[e]);
-        if (sg.dft[e] != 0.0f) atomicAdd(G.dft + e, sg.dft[e]);
+        if (sg.dfs[e] != 0.0f) atomicAdd(G.dfs + gidx(e), sg.dfs[e]);
+        if (sg.dft[e] != 0.0f) atomicAdd(G.dft + gidx(e), sg.dft[e]);
       }
     }
   }
@@ -390,6 +431,35 @@ int pick_lanes(const gsp_material* mats, int n_mats, const gsp_query_tuning* tn)
   int lanes = 4;
   while (lanes < rmax && lanes < 32) lanes *= 2;
   return lanes;
+}
+
+template <int LANES, int VEC>
+int launch_bwd_t(long long blocks, int threads, size_t dyn, cudaStream_t s, const MatParams& mp,
+                 const GradParams& gp, const gsp_query* d_q, long long n, const float* d_gout,
+                 uint32_t* d_status) {
+  GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<LANES, VEC>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+  k_range_query_bwd<LANES, VEC><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
+  return GSP_OK;
+}
+
+template <int VEC>
+int launch_bwd_v(int lanes, long long blocks, int threads, size_t dyn, cudaStream_t s,
+                 const MatParams& mp, const GradParams& gp, const gsp_query* d_q, long long n,
+                 const float* d_gout, uint32_t* d_status) {
+  switch (lanes) {
+    case 4: return launch_bwd_t<4, VEC>(blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
+    case 8: return launch_bwd_t<8, VEC>(blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
+    case 16: return launch_bwd_t<16, VEC>(blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
+    default: return launch_bwd_t<32, VEC>(blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
+  }
+}
+
+int launch_bwd(int lanes, int vec, long long blocks, int threads, size_t dyn, cudaStream_t s,
+               const MatParams& mp, const GradParams& gp, const gsp_query* d_q, long long n,
+               const float* d_gout, uint32_t* d_status) {
+  if (vec == 2) return launch_bwd_v<2>(lanes, blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
+  return launch_bwd_v<1>(lanes, blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
 }
 
 }  // namespace
@@ -515,7 +585,24 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
   cudaStream_t s = to_stream(stream);
   GSP_CUDA(cudaMemsetAsync(d_ws, 0, need, s));
   if (n > 0) {
-    int lanes = pick_lanes(h_mats, n_mats, nullptr);
+    // VEC: 2 when it divides every rank (with at least four vectors per rank
+    // row) and keeps the factor rows and gradients aligned, else 1.  (Four
+    // ranks per lane needed 128 registers and cost a third of the occupancy.)
+    int vec = 2;
+    for (int i = 0; i < n_mats; ++i) {
+      const gsp_material& m = h_mats[i];
+      const gsp_material_grad& g = h_grads[i];
+      auto aligned = [&](int v) {
+        const uintptr_t mask = static_cast<uintptr_t>(4 * v - 1);
+        return ((reinterpret_cast<uintptr_t>(m.fx) | reinterpret_cast<uintptr_t>(m.fy) |
+                 reinterpret_cast<uintptr_t>(g.dfx) | reinterpret_cast<uintptr_t>(g.dfy)) & mask) == 0;
+      };
+      while (vec > 1 && (m.rank % vec != 0 || m.rank / vec < 4 || !aligned(vec))) vec >>= 1;
+    }
+    int rmax = 1;
+    for (int i = 0; i < n_mats; ++i) rmax = rmax > h_mats[i].rank ? rmax : h_mats[i].rank;
+    int lanes = 4;
+    while (lanes * vec < rmax && lanes < 32) lanes *= 2;
     const int threads = 256;
     const size_t dyn = gp.use_smem ? smem : 0;
     long long warps = (n + (32 / lanes) - 1) / (32 / lanes);
@@ -527,24 +614,7 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
     long long cap = static_cast<long long>(sm_count()) * per_sm;
     if (blocks > cap) blocks = cap;
     prof_begin(PROF_QUERY_BWD, s);
-    switch (lanes) {
-      case 4:
-        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-        k_range_query_bwd<4><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
-        break;
-      case 8:
-        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-        k_range_query_bwd<8><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
-        break;
-      case 16:
-        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-        k_range_query_bwd<16><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
-        break;
-      default:
-        GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-        k_range_query_bwd<32><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
-        break;
-    }
+    GSP_TRY(launch_bwd(lanes, vec, blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status));
     prof_end(PROF_QUERY_BWD, s);
     GSP_CHECK_LAUNCH();
   }
