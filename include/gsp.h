@@ -103,7 +103,8 @@ int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int levels, int bi
 
 typedef enum gsp_precision {
   GSP_PREC_FP32 = 0,    /* MTTKRP with FP32 FFMA on CUDA cores (the plain path)      */
-  GSP_PREC_TF32 = 1,    /* tcgen05, TF32 operands, FP32 accumulate                   */
+  GSP_PREC_TF32 = 1,    /* tcgen05, TF32 operands, FP32 accumulate; the NDF tensor is
+                           one TF32 value, the factor operands TF32 hi + lo pairs     */
   GSP_PREC_BF16 = 2,    /* tcgen05, BF16 operands, FP32 accumulate; the NDF tensor is
                            one BF16 value, the Khatri-Rao operand a BF16 hi + lo pair
                            (two MMAs per K slice, Henry, Tang & Heinecke 2019)      */
@@ -114,8 +115,9 @@ typedef enum gsp_precision {
  * element's index in [l][y][x][s][t], phi = the golden ratio, 32-bit fixed point)
  * is below its relative distance from the lower one, so representable values,
  * e.g. every count up to 256 (2048), are exact.  Tensor-memory accumulators
- * restart every 16 K steps (64 MMAs per operand part) and their partial sums
- * are added with round-to-nearest FP32 adds. */
+ * restart every 16 K steps of the xy pass and every map row of the (l, s, t)
+ * pass, and their partial sums are added with round-to-nearest FP32 operations.
+ * BF16 needs N >= 64 and TF32 N >= 32 (a K step stays within one map row). */
 
 /* Five factor matrices and the CP weights, device pointers, FP32:
  * fx [N][R], fy [N][R], fl [levels][R], fs [B][R], ft [B][R], lambda [R].

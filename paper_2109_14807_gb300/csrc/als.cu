@@ -26,7 +26,7 @@ constexpr int kMaxCpRank = 64;
 constexpr int kJacobiMaxRank = 64;
 
 struct CpLayout {
-  size_t T, bins, Yp, Zp, Zpart, KR, M, G, W, lam, fit, sumsq, norm2, flags, total;
+  size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, W, lam, fit, sumsq, norm2, flags, total;
 };
 
 size_t esize(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1X ? 2 : 4; }
@@ -49,7 +49,8 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   const size_t simt_part = L * static_cast<size_t>(lst_chunks(d, GSP_PREC_FP32)) * B2 * R;
   const size_t tc_part = static_cast<size_t>(kLstMaxRanges) * 2 * B2 * R;
   o.Zpart = take((prec == GSP_PREC_FP32 ? simt_part : tc_part) * sizeof(float));
-  o.KR = take(R * L * B2 * sizeof(float));
+  o.KR = take(2 * R * L * B2 * sizeof(float));  // FP32 rows, or a hi + lo operand pair
+  o.FX = take(2 * R * static_cast<size_t>(d.N) * sizeof(float));  // Z' fx operand
   size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
   o.M = take(imax * R * sizeof(double));
   o.G = take(5 * R * R * sizeof(double));
@@ -86,9 +87,8 @@ __global__ void k_kr_rows(const float* __restrict__ fl, const float* __restrict_
 }
 
 // KRt[r][l*B2 + s*B + t] in the operand type (the K-major B operand of the
-// tensor-core pass).  BF16 with `split`: rows R..2R-1 hold the remainder
-// v - bf16(v) of rows 0..R-1.  FP32 storage with `split`: values rounded to
-// the nearest TF32.
+// tensor-core pass): BF16, or FP32 rounded to the nearest TF32; with `split`
+// rows R..2R-1 hold the remainder v - hi of rows 0..R-1, rounded the same way.
 template <typename OutT>
 __global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict__ fs,
                           const float* __restrict__ ft, int L, int B, int R, int split,
@@ -107,7 +107,9 @@ __global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict_
     out[i] = hi;
     if (split) out[i + K * R] = __float2bfloat16_rn(v - __bfloat162float(hi));
   } else {
-    out[i] = split ? round_tf32(v) : v;  // split = 1 marks the TF32 operand here
+    const float hi = round_tf32(v);
+    out[i] = hi;
+    if (split) out[i + K * R] = round_tf32(v - hi);
   }
 }
 
@@ -602,8 +604,8 @@ int run_xy(const Ctx& c, const float* fl, const float* fs, const float* ft) {
 int run_lst(const Ctx& c, const float* fx, const float* fy) {
   const MttkrpDims& d = c.d;
   if (c.prec != GSP_PREC_FP32)
-    return tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.at<float>(c.lay.Zpart), c.at<float>(c.lay.Zp),
-                         d, c.prec, c.at<uint32_t>(c.lay.flags), c.s);
+    return tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.ws + c.lay.FX, c.at<float>(c.lay.Zpart),
+                         c.at<float>(c.lay.Zp), d, c.prec, c.at<uint32_t>(c.lay.flags), c.s);
   const int C = lst_chunks(d, c.prec);
   GSP_TRY(simt_mttkrp_lst(c.at<float>(c.lay.T), fx, fy, c.at<float>(c.lay.Zpart), d, C, c.s));
   long long per_level = static_cast<long long>(d.B2()) * d.R;

@@ -35,10 +35,11 @@ int simt_mttkrp_lst(const float* T, const float* fx, const float* fy, float* Zpa
 // inside the kernel gave up.
 int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d, int precision,
                  uint32_t* err, cudaStream_t s);
-// Z' pass: writes per-CTA partial slices to Zpart (at most kLstMaxRanges * 2 *
-// B2 * R floats) and reduces them into Zp [L][B2][R].
-int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart, float* Zp,
-                  const MttkrpDims& d, int precision, uint32_t* err, cudaStream_t s);
+// Z' pass: builds the fx operand in FXt (2 * R * N operand elements at most),
+// writes per-CTA partial slices to Zpart (at most kLstMaxRanges * 2 * B2 * R
+// floats) and reduces them into Zp [L][B2][R].
+int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, float* Zpart,
+                  float* Zp, const MttkrpDims& d, int precision, uint32_t* err, cudaStream_t s);
 bool tc_supported(const MttkrpDims& d, int precision);
 constexpr int kLstMaxRanges = 256;
 

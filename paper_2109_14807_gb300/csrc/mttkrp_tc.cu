@@ -8,26 +8,25 @@
 //  Y' pass  D[xy][r] = sum_{l, st} T[l][xy][st] * KRt[r][l*B2 + st]
 //           one 128-row xy tile per accumulator, K = L * B2; T is the K-major A
 //           operand, KRt (fl*fs*ft, built per sweep) the K-major B operand.
-//  Z' pass  D[st][r] = sum_{xy in chunk} T[l][xy][st] * fx[x][r] fy[y][r]
-//           per (level, xy chunk, st group): one accumulator per 128-wide st
-//           block; the same T tiles are now the MN-major A operand; the B
-//           operand (fx (.) fy over the chunk's xy rows) is computed in shared
-//           memory by the epilogue warps while they are otherwise idle.
+//  Z' pass  D[st][r] = sum_y fy[y][r] sum_x T[l][y][x][st] * fx[x][r]
+//           per (level, map row, st group); the same T tiles are now the
+//           MN-major A operand and FXt (fx, built per sweep) the K-major B
+//           operand; fy scales each map row's sums in the epilogue.
 //
 // Accumulation is chunked: the tensor core's FP32 accumulation does not round
 // to nearest, and over a chain of thousands of MMAs into one accumulator the
 // sums drift low by a few parts in 10^5 (measured: ~5e-8 relative per
-// accumulating MMA).  So every chunk of kChunk K steps starts a fresh TMEM
-// accumulator, and the epilogue adds the chunk sums with round-to-nearest FP32
-// adds in a fixed order: for Y' into registers, from double-buffered chunk
-// accumulators; for Z' into a running-sum region of tensor memory beside the
-// one chunk accumulator (the MMAs wait for that add, once per kChunkZ steps).
+// accumulating MMA).  So every chunk (kChunk K steps for Y', one map row for
+// Z') starts a fresh TMEM accumulator and the epilogue adds the chunk sums
+// with round-to-nearest FP32 operations in a fixed order: for Y' into
+// registers, from double-buffered chunk accumulators; for Z' into a
+// running-sum region of tensor memory beside the chunk accumulator.
 //
-// CTA = 6 warps: warps 0-3 epilogue (TMEM lanes 0-127) and, in the Z' pass,
-// B-operand producers; warp 4 issues TMA; warp 5 owns TMEM and issues MMAs
-// (one thread).  Every mbarrier wait is bounded by a clock budget: on expiry
-// the CTA raises GSP_DEV_TIMEOUT, waits for its own copies and MMAs in flight
-// (again bounded), frees its tensor memory and returns.
+// CTA = 6 warps: warps 0-3 epilogue (TMEM lanes 0-127); warp 4 issues TMA;
+// warp 5 owns TMEM and issues MMAs (one thread).  Every mbarrier wait is
+// bounded by a clock budget: on expiry the CTA raises GSP_DEV_TIMEOUT, waits
+// for its own copies and MMAs in flight (again bounded), frees its tensor
+// memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -43,8 +42,7 @@ constexpr int kMaxRankTc = 64;  // CP ranks served by the tensor-core passes
 constexpr int kThreads = 192;
 constexpr long long kTimeoutCycles = 4000000000LL;  // about 2 s at GB300 clocks
 constexpr int kTileBytes = 128 * 128;                // 128 rows x 128 bytes
-constexpr int kChunk = 16;   // Y' K steps (4 MMAs each) per tensor-memory accumulator chunk
-constexpr int kChunkZ = 64;  // Z' K steps per chunk
+constexpr int kChunk = 16;  // Y' K steps (4 MMAs each) per tensor-memory accumulator chunk
 
 // ------------------------------------------------------------- PTX glue --
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -76,9 +74,10 @@ __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
 }
 
 // Wait for the phase of parity `parity` to complete.  Returns false when the
-// CTA's abort flag is (or becomes) set or the clock budget runs out.
-__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
-  if (mbar_test(a, parity)) return true;
+// CTA's abort flag is (or becomes) set or the clock budget runs out.  The
+// first test is inlined: the single TMA / MMA issuing threads are on the
+// critical path and most of their waits are already satisfied.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t a, uint32_t parity, volatile int* abort) {
   const long long t0 = clock64();
   for (;;) {
     if (mbar_test(a, parity)) return true;
@@ -88,6 +87,10 @@ __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int
       return false;
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
+  return mbar_test(a, parity) || mbar_wait_slow(a, parity, abort);
 }
 
 // Bounded wait that ignores the abort flag (used to drain work in flight).
@@ -105,23 +108,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "%3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
       : "memory");
-}
-
-// The same load with an L2 eviction-priority hint (the streamed operand tensor
-// is read once per pass and should not push reused data out of L2).
-__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int c0,
-                                                 int c1, uint32_t mbar, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-      "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar), "l"(policy)
-      : "memory");
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
 }
 
 // tcgen05 shared-memory matrix descriptor, base offset 0.  layout: 2 = 128-byte
@@ -232,10 +218,6 @@ __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -264,8 +246,8 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 
 // ------------------------------------------------------------ Y' pass --
 // ELEM: 2 (BF16) or 4 (TF32/FP32 storage).  E128 = elements per 128 bytes.
-// SPLIT: the B operand holds 2R rows, a BF16 hi part and its remainder; each
-// K slice then issues two MMAs into the same accumulator.
+// SPLIT: the B operand holds 2R rows, a hi part and its remainder (BF16 or
+// TF32); each K slice then issues two MMAs into the same accumulator.
 template <int ELEM, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_xy_tc(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapKR,
@@ -310,17 +292,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_parity[kMaxStages];
       bool issued[kMaxStages];
       for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
-      const uint64_t stream_policy = policy_evict_first();
       for (int tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
-        const long long xy0 = static_cast<long long>(tile) * 128;
+        // T row of level l: l * N^2 + tile * 128; K column of the KR operand: l * B2 + kc * E128
+        int trow = tile * 128, kcol = 0, kc = 0;
         for (int it = 0; it < kiters; ++it) {
           if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
-          const int l = it / kpl, kc = it % kpl;
           const uint32_t sa = smem_u32(smem + s * stage_bytes);
           const uint32_t fb = smem_u32(&bar.full[s]);
           mbar_expect_tx(fb, stage_bytes);
-          tma_load_2d_hint(sa, &mapT, kc * E128, static_cast<int>(l * N2 + xy0), fb, stream_policy);
-          tma_load_2d(sa + kTileBytes, &mapKR, l * B2 + kc * E128, 0, fb);
+          tma_load_2d(sa, &mapT, kc * E128, trow, fb);
+          tma_load_2d(sa + kTileBytes, &mapKR, kcol, 0, fb);
+          kcol += E128;
+          if (++kc == kpl) {
+            kc = 0;
+            trow += static_cast<int>(N2);
+          }
           issued[s] = true;
           issued_parity[s] = ph;
           if (++s == kStages) {
@@ -341,36 +327,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t ph = 0, aph = 0;
       bool any = false;
       for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        uint32_t d = tmem;
-        for (int it = 0; it < kiters; ++it) {
-          const int c = it % kChunk;
-          if (c == 0) {  // a fresh accumulator for each chunk of K steps
-            if (!mbar_wait(smem_u32(&bar.acc_empty[acc]), aph ^ 1u, abort)) goto mma_done;
-            tc_fence_after();
-            d = tmem + static_cast<uint32_t>(acc * R);
-          }
-          if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
+        for (int it0 = 0; it0 < kiters; it0 += kChunk) {  // a fresh accumulator per chunk
+          if (!mbar_wait(smem_u32(&bar.acc_empty[acc]), aph ^ 1u, abort)) goto mma_done;
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * stage_bytes);
-          const uint32_t sb = sa + kTileBytes;
+          const uint32_t d = tmem + static_cast<uint32_t>(acc * R);
+          const int it1 = it0 + kChunk < kiters ? it0 + kChunk : kiters;
+          for (int it = it0; it < it1; ++it) {
+            if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * stage_bytes);
+            // descriptor address fields are in 16-byte units: slice j adds 2 j
+            const uint64_t a0 = sdesc(sa, 16, 1024), b0 = sdesc(sa + kTileBytes, 16, 1024);
+            const uint64_t blo = static_cast<uint64_t>(R * 128 / 16);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {  // four K slices of 32 bytes per 128-byte row
-            const uint64_t a = sdesc(sa + j * 32, 16, 1024);
-            umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (c > 0 || j > 0) ? 1u : 0u);
-            if constexpr (SPLIT) umma<ELEM>(d, a, sdesc(sb + R * 128 + j * 32, 16, 1024), id, 1u);
-          }
-          any = true;
-          umma_commit(smem_u32(&bar.empty[s]));
-          if (++s == kStages) {
-            s = 0;
-            ph ^= 1u;
-          }
-          if (c == kChunk - 1 || it == kiters - 1) {
-            umma_commit(smem_u32(&bar.acc_full[acc]));
-            if (++acc == 2) {
-              acc = 0;
-              aph ^= 1u;
+            for (int j = 0; j < 4; ++j) {  // four K slices of 32 bytes per 128-byte row
+              umma<ELEM>(d, a0 + 2 * j, b0 + 2 * j, id, (it > it0 || j > 0) ? 1u : 0u);
+              if constexpr (SPLIT) umma<ELEM>(d, a0 + 2 * j, b0 + blo + 2 * j, id, 1u);
             }
+            any = true;
+            umma_commit(smem_u32(&bar.empty[s]));
+            if (++s == kStages) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+          umma_commit(smem_u32(&bar.acc_full[acc]));
+          if (++acc == 2) {
+            acc = 0;
+            aph ^= 1u;
           }
         }
       }
@@ -427,15 +411,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------ Z' pass --
-// The K steps (E128 xy rows each) of all levels form one sequence of
-// L * N^2 / E128 steps; CTA p of st group g takes the contiguous range
-// [p K / P, (p+1) K / P).  A range is shorter than a level, so it holds at most
+// Z'[l][st][r] = sum_y fy[y][r] U_{l,y}[st][r],  U_{l,y}[st][r] = sum_x T[l][y][x][st] fx[x][r].
+//
+// The K steps (E128 x values of one map row each; N >= E128) of all levels
+// form one sequence of L N (N / E128) steps; CTA p of st group g takes the
+// contiguous range [p K / P, (p+1) K / P).  With P >= L a range holds at most
 // two segments (the part in its first level and the part in the next); each
-// segment's accumulators go to partial slice 2p + seg of the group's st rows
-// and a fixed-order reduce adds the slices of each level.  Within a K step the
-// producer loads, for every st block m of the group, the [E128 rows x 128 st]
-// tile as 128/E128 TMA boxes (MN-major atoms, LBO = box bytes); the epilogue
-// warps write KRxy[r][k] = fx[x_k][r] fy[y_k][r] (K-major, 128-byte rows).
+// segment's sums go to partial slice 2p + seg of the group's st rows and a
+// fixed-order reduce adds the slices of each level.
+//
+// Per step the producer loads the B tile (the step's E128 rows of fx as the
+// K-major operand FXt, a BF16 hi + lo pair for the split precision) and, for
+// every st block m of the group, the [E128 x rows x 128 st] T tile as 128/E128
+// MN-major TMA boxes (LBO = box bytes).  The accumulators collect U of one map
+// row (a chunk of N / E128 steps); at the row's end the epilogue warps add
+// fy[y][r] times the chunk to the running sums in TMEM columns [MB R, 2 MB R)
+// with FP32 round-to-nearest FMAs, or, for the segment's last row, write the
+// result to the partial slice.  fy is applied in FP32 and never rounded to the
+// operand type.
 struct LstRange {
   long long k0, k1;     // this CTA's steps
   long long mid;        // end of the first segment
@@ -454,7 +447,7 @@ __device__ __forceinline__ LstRange lst_range(int p, int P, long long K, long lo
 
 template <int ELEM, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_lst_tc(const __grid_constant__ CUtensorMap mapT, const float* __restrict__ fx,
+    k_lst_tc(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapFX,
              const float* __restrict__ fy, float* __restrict__ Zpart, int P, int logN, int L,
              int B2, int R, int MB, int G, int kStages, uint32_t* err) {
   constexpr int E128 = 128 / ELEM;
@@ -468,15 +461,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ Barriers bar;
   uint8_t* smem = align1024(smem_raw);
   uint8_t* bslots = smem + kStages * kTileBytes;
-  const int b_bytes = R * 128 * (SPLIT ? 2 : 1);
+  const int b_rows = R * (SPLIT ? 2 : 1);
+  const int b_bytes = b_rows * 128;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = 1 << logN;
   const long long N2 = static_cast<long long>(N) * N;
+  const int spr = N / E128;               // steps per map row (one chunk)
   const long long spl = N2 / E128;        // steps per level
   const long long K = spl * L;
   const int g = blockIdx.x % G, p = blockIdx.x / G;
   const LstRange rg = lst_range(p, P, K, spl);
-  const uint32_t ncols = tmem_cols_for(2 * MB * R);  // chunk accumulator + running sums
+  const uint32_t ncols = tmem_cols_for(2 * MB * R);  // chunk accumulators + running sums
   volatile int* abort = &bar.abort;
 
   if (threadIdx.x == 0) {
@@ -487,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(smem_u32(&bar.acc_full[0]), 1);
     mbar_init(smem_u32(&bar.acc_empty[0]), 128);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&bar.b_full[b]), 128);
+      mbar_init(smem_u32(&bar.b_full[b]), 1);
       mbar_init(smem_u32(&bar.b_empty[b]), 1);
     }
     mbar_init(smem_u32(&bar.drain), 1);
@@ -501,23 +496,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = bar.tmem_base;
 
   if (warp == 4) {
-    if (lane == 0) {  // ---- TMA producer
-      int s = 0;
-      uint32_t ph = 0;
-      uint32_t issued_parity[kMaxStages];
-      bool issued[kMaxStages];
+    if (lane == 0) {  // ---- TMA producer: per step the B tile, then MB T tiles
+      int s = 0, bs = 0;
+      uint32_t ph = 0, bph = 0;
+      uint32_t issued_parity[kMaxStages], b_parity[2];
+      bool issued[kMaxStages], b_issued[2] = {false, false};
       for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
-      const uint64_t stream_policy = policy_evict_first();
-      for (long long k = rg.k0; k < rg.k1 && !*abort; ++k) {
+      int xb = static_cast<int>(rg.k0 % spr);  // x block of step k
+      for (long long k = rg.k0; k < rg.k1 && !*abort; ++k, xb = xb + 1 == spr ? 0 : xb + 1) {
+        if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto producer_done;
+        {
+          const uint32_t bb = smem_u32(&bar.b_full[bs]);
+          mbar_expect_tx(bb, static_cast<uint32_t>(b_bytes));
+          tma_load_2d(smem_u32(bslots + bs * b_bytes), &mapFX, xb * E128, 0, bb);
+          b_issued[bs] = true;
+          b_parity[bs] = bph;
+          if (++bs == 2) {
+            bs = 0;
+            bph ^= 1u;
+          }
+        }
         for (int m = 0; m < MB; ++m) {
           if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
           const uint32_t sa = smem_u32(smem + s * kTileBytes);
           const uint32_t fb = smem_u32(&bar.full[s]);
           mbar_expect_tx(fb, kTileBytes);
           const int st0 = (g * MB + m) * 128;
+          const int trow = static_cast<int>(k * E128);
+#pragma unroll
           for (int b = 0; b < BOXES; ++b)
-            tma_load_2d_hint(sa + b * BOX_BYTES, &mapT, st0 + b * E128, static_cast<int>(k * E128),
-                             fb, stream_policy);
+            tma_load_2d(sa + b * BOX_BYTES, &mapT, st0 + b * E128, trow, fb);
           issued[s] = true;
           issued_parity[s] = ph;
           if (++s == kStages) {
@@ -527,9 +535,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     producer_done:
-      if (*abort)
+      if (*abort) {  // wait for this CTA's own copies still in flight
         for (int i = 0; i < kStages; ++i)
           if (issued[i]) mbar_drain(smem_u32(&bar.full[i]), issued_parity[i]);
+        for (int i = 0; i < 2; ++i)
+          if (b_issued[i]) mbar_drain(smem_u32(&bar.b_full[i]), b_parity[i]);
+      }
     }
   } else if (warp == 5) {
     if (lane == 0) {  // ---- MMA issuer
@@ -539,44 +550,45 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool any = false;
       for (int seg = 0; seg < 2; ++seg) {
         const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
-        if (kb >= ke) continue;
-        for (long long k = kb; k < ke; ++k) {
-          const int c = static_cast<int>((k - kb) % kChunkZ);
-          if (c == 0) {  // a fresh accumulator for each chunk of K steps
-            if (!mbar_wait(smem_u32(&bar.acc_empty[0]), uph ^ 1u, abort)) goto mma_done;
-            tc_fence_after();
-          }
-          if (!mbar_wait(smem_u32(&bar.b_full[bs]), bph, abort)) goto mma_done;
+        for (long long c0 = kb; c0 < ke;) {  // one chunk (accumulator) per map row
+          const long long row_end = (c0 / spr + 1) * spr;
+          const long long c1 = row_end < ke ? row_end : ke;
+          if (!mbar_wait(smem_u32(&bar.acc_empty[0]), uph ^ 1u, abort)) goto mma_done;
           tc_fence_after();
-          const uint32_t sb = smem_u32(bslots + bs * b_bytes);
-          for (int m = 0; m < MB; ++m) {
-            if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
+          for (long long k = c0; k < c1; ++k) {
+            if (!mbar_wait(smem_u32(&bar.b_full[bs]), bph, abort)) goto mma_done;
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * kTileBytes);
-            const uint32_t d = tmem + static_cast<uint32_t>(m * R);
+            const uint64_t b0 = sdesc(smem_u32(bslots + bs * b_bytes), 16, 1024);
+            const uint64_t blo = static_cast<uint64_t>(R * 128 / 16);
+            for (int m = 0; m < MB; ++m) {
+              if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + s * kTileBytes);
+              const uint32_t d = tmem + static_cast<uint32_t>(m * R);
+              // descriptor address fields are in 16-byte units
+              const uint64_t a0 = sdesc(sa, BOX_BYTES, A_SBO, A_LAYOUT);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const uint64_t a = sdesc(sa + j * MMA_K_ROWS * 128, BOX_BYTES, A_SBO, A_LAYOUT);
-              umma<ELEM>(d, a, sdesc(sb + j * 32, 16, 1024), id, (c > 0 || j > 0) ? 1u : 0u);
-              if constexpr (SPLIT)
-                umma<ELEM>(d, a, sdesc(sb + R * 128 + j * 32, 16, 1024), id, 1u);
+              for (int j = 0; j < 4; ++j) {
+                const uint64_t a = a0 + static_cast<uint64_t>(j * MMA_K_ROWS * 128 / 16);
+                umma<ELEM>(d, a, b0 + 2 * j, id, (k > c0 || j > 0) ? 1u : 0u);
+                if constexpr (SPLIT) umma<ELEM>(d, a, b0 + blo + 2 * j, id, 1u);
+              }
+              any = true;
+              umma_commit(smem_u32(&bar.empty[s]));
+              if (++s == kStages) {
+                s = 0;
+                ph ^= 1u;
+              }
             }
-            any = true;
-            umma_commit(smem_u32(&bar.empty[s]));
-            if (++s == kStages) {
-              s = 0;
-              ph ^= 1u;
+            umma_commit(smem_u32(&bar.b_empty[bs]));
+            if (++bs == 2) {
+              bs = 0;
+              bph ^= 1u;
             }
           }
-          umma_commit(smem_u32(&bar.b_empty[bs]));
-          if (++bs == 2) {
-            bs = 0;
-            bph ^= 1u;
-          }
-          if (c == kChunkZ - 1 || k == ke - 1) {
-            umma_commit(smem_u32(&bar.acc_full[0]));
-            uph ^= 1u;
-          }
+          umma_commit(smem_u32(&bar.acc_full[0]));
+          uph ^= 1u;
+          c0 = c1;
         }
       }
     mma_done:
@@ -585,125 +597,61 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_drain(smem_u32(&bar.drain), 0);
       }
     }
-  } else {  // ---- warps 0-3: B operand producer, then epilogue per segment
-    // thread t fills xy row k = t / TPR of the tile, ranks [r0, r0 + R/TPR),
-    // all its fx and fy loads issued before any product is formed
-    constexpr int TPR = 128 / E128;  // threads per xy row
-    constexpr int MAXV = kMaxRankTc / 4 / TPR;  // float4 per operand row part
-    const int t = threadIdx.x;       // 0..127
-    const int kk = t / TPR;
-    const int rpart = R / TPR;
-    const int r0 = (t % TPR) * rpart;
-    const int byte_in_row = kk * ELEM;
-    const int chunk = byte_in_row >> 4, within = byte_in_row & 15;
-    int bs = 0;
-    uint32_t bph = 0, uph = 0;
+  } else {  // ---- warps 0-3: per map row, running sums += fy[y] * chunk
+    uint32_t uph = 0;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     const uint32_t sum_col = static_cast<uint32_t>(MB * R);
-    // Add chunk j of the accumulators (TMEM columns [0, MB R)) to the running
-    // sums (columns [MB R, 2 MB R)); the last chunk of a segment goes to
-    // partial slice 2p + seg instead.  32 columns per tensor-memory round trip.
-    auto drain = [&](long long j, bool last, int seg) -> bool {
-      if (!mbar_wait(smem_u32(&bar.acc_full[0]), uph, abort)) return false;
-      tc_fence_after();
-      float* part = Zpart + (static_cast<size_t>(p) * 2 + seg) * B2 * R;
-      for (int m = 0; m < MB; ++m) {
-        float* row = part + (static_cast<size_t>((g * MB + m) * 128) + warp * 32 + lane) * R;
-        for (int c = 0; c < R; c += 32) {
-          const uint32_t col = static_cast<uint32_t>(m * R + c);
-          const bool two = c + 16 < R;  // R = 16 has one 16-column group
-          uint32_t a[32], b[32];
-#pragma unroll
-          for (int i = 0; i < 32; ++i) b[i] = 0u;
-          tmem_ld16_nowait(lane_base + col, a);
-          if (two) tmem_ld16_nowait(lane_base + col + 16, a + 16);
-          if (j > 0) {
-            tmem_ld16_nowait(lane_base + sum_col + col, b);
-            if (two) tmem_ld16_nowait(lane_base + sum_col + col + 16, b + 16);
-          }
-          tmem_ld_wait();
-          float v[32];
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            v[i] = j > 0 ? __uint_as_float(b[i]) + __uint_as_float(a[i]) : __uint_as_float(a[i]);
-          if (last) {
-            float4* dst = reinterpret_cast<float4*>(row + c);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            if (two) {
-#pragma unroll
-              for (int i = 4; i < 8; ++i)
-                dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            }
-          } else {
-            tmem_st16(lane_base + sum_col + col, v);
-            if (two) tmem_st16(lane_base + sum_col + col + 16, v + 16);
-          }
-        }
-      }
-      if (!last) tmem_st_wait();
-      tc_fence_before();
-      mbar_arrive(smem_u32(&bar.acc_empty[0]));
-      uph ^= 1u;
-      return true;
-    };
     for (int seg = 0; seg < 2; ++seg) {
       const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
       if (kb >= ke) continue;
-      const int l = rg.level0 + seg;
-      const long long nch = (ke - kb + kChunkZ - 1) / kChunkZ;
-      long long drained = 0;
-      for (long long k = kb; k < ke; ++k) {
-        if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto epi_done;
-        const long long xy = k * E128 + kk - l * N2;
-        const int x = static_cast<int>(xy & (N - 1)), y = static_cast<int>(xy >> logN);
-        const float4* fx4 = reinterpret_cast<const float4*>(fx + static_cast<size_t>(x) * R + r0);
-        const float4* fy4 = reinterpret_cast<const float4*>(fy + static_cast<size_t>(y) * R + r0);
-        float4 av[MAXV], bv[MAXV];
+      const long long row0 = kb / spr, row1 = (ke - 1) / spr;  // map rows (l N + y)
+      float* part = Zpart + (static_cast<size_t>(p) * 2 + seg) * B2 * R;
+      for (long long row = row0; row <= row1; ++row) {
+        const bool first = row == row0, last = row == row1;
+        // the row's fy values, loaded while the MMAs still run
+        const float4* fyr = reinterpret_cast<const float4*>(fy + static_cast<size_t>(row & (N - 1)) * R);
+        float f[kMaxRankTc];
 #pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-          if (i < rpart / 4) {
-            av[i] = __ldg(fx4 + i);
-            bv[i] = __ldg(fy4 + i);
+        for (int i = 0; i < kMaxRankTc / 4; ++i) {
+          if (4 * i < R) {
+            const float4 q = __ldg(fyr + i);
+            f[4 * i] = q.x; f[4 * i + 1] = q.y; f[4 * i + 2] = q.z; f[4 * i + 3] = q.w;
           }
-        uint8_t* tile = bslots + bs * b_bytes;
+        }
+        if (!mbar_wait(smem_u32(&bar.acc_full[0]), uph, abort)) goto epi_done;
+        tc_fence_after();
+        for (int m = 0; m < MB; ++m) {
+          float* out = part + (static_cast<size_t>((g * MB + m) * 128) + warp * 32 + lane) * R;
 #pragma unroll
-        for (int i = 0; i < MAXV; ++i) {
-          if (i < rpart / 4) {
-            const float v[4] = {av[i].x * bv[i].x, av[i].y * bv[i].y, av[i].z * bv[i].z,
-                                av[i].w * bv[i].w};
+          for (int cb = 0; cb < kMaxRankTc / 16; ++cb) {
+            if (cb * 16 < R) {
+              const uint32_t col = static_cast<uint32_t>(m * R + cb * 16);
+              uint32_t a[16], b[16];
+              tmem_ld16_nowait(lane_base + col, a);
+              if (!first) tmem_ld16_nowait(lane_base + sum_col + col, b);
+              tmem_ld_wait();
+              float v[16];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int r = r0 + 4 * i + e;
-              uint8_t* dst = tile + r * 128 + ((((chunk ^ (r & 7)) << 4)) | within);
-              if constexpr (ELEM == 2) {
-                const __nv_bfloat16 hi = __float2bfloat16_rn(v[e]);
-                *reinterpret_cast<__nv_bfloat16*>(dst) = hi;
-                if constexpr (SPLIT)  // row R + r: same swizzle phase since R % 8 == 0
-                  *reinterpret_cast<__nv_bfloat16*>(dst + R * 128) =
-                      __float2bfloat16_rn(v[e] - __bfloat162float(hi));
+              for (int i = 0; i < 16; ++i)
+                v[i] = first ? f[cb * 16 + i] * __uint_as_float(a[i])
+                             : fmaf(f[cb * 16 + i], __uint_as_float(a[i]), __uint_as_float(b[i]));
+              if (last) {
+                float4* dst = reinterpret_cast<float4*>(out + cb * 16);
+                dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+                dst[3] = make_float4(v[12], v[13], v[14], v[15]);
               } else {
-                *reinterpret_cast<float*>(dst) = round_tf32(v[e]);
+                tmem_st16(lane_base + sum_col + col, v);
               }
             }
           }
         }
-        fence_async_smem();
-        mbar_arrive(smem_u32(&bar.b_full[bs]));
-        if (++bs == 2) {
-          bs = 0;
-          bph ^= 1u;
-        }
-        // chunk j is added once the B operand of the next chunk's first step
-        // is ready, so the MMAs resume as soon as the accumulator is free
-        if (drained < nch - 1 && k >= kb + (drained + 1) * kChunkZ) {
-          if (!drain(drained, false, seg)) goto epi_done;
-          ++drained;
-        }
+        if (!last) tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bar.acc_empty[0]));
+        uph ^= 1u;
       }
-      for (; drained < nch; ++drained)
-        if (!drain(drained, drained == nch - 1, seg)) goto epi_done;
     }
   epi_done:;
   }
@@ -713,6 +661,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 5) {
     tc_fence_after();
     tmem_dealloc(tmem, ncols);
+  }
+}
+
+// FXt[r][x] = fx[x][r] in the operand type (K-major B operand of the Z' pass):
+// BF16, or FP32 rounded to the nearest TF32; with `split` rows R..2R-1 hold
+// the remainder fx - hi rounded the same way.
+template <typename OutT>
+__global__ void k_fx_cols(const float* __restrict__ fx, int N, int R, int split,
+                          OutT* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * R) return;
+  const int r = i / N, x = i - r * N;
+  const float v = fx[static_cast<size_t>(x) * R + r];
+  if constexpr (sizeof(OutT) == 2) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    out[i] = hi;
+    if (split) out[static_cast<size_t>(R) * N + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  } else {
+    const float hi = round_tf32(v);
+    out[i] = hi;
+    if (split) out[static_cast<size_t>(R) * N + i] = round_tf32(v - hi);
   }
 }
 
@@ -812,9 +781,9 @@ bool tc_supported(const MttkrpDims& d, int precision) {
   if (precision != GSP_PREC_BF16 && precision != GSP_PREC_BF16_1X && precision != GSP_PREC_TF32)
     return false;
   if (!(d.R == 16 || d.R == 32 || d.R == 64)) return false;
-  if (d.B < 16 || d.N < 16) return false;
+  if (d.B < 16 || d.N < 128 / (precision == GSP_PREC_TF32 ? 4 : 2)) return false;  // Z' steps stay in one map row
   if (d.L * d.N2() >= (1LL << 31)) return false;  // TMA row coordinate is int32
-  const bool split = precision == GSP_PREC_BF16;
+  const bool split = precision != GSP_PREC_BF16_1X;  // BF16 and TF32 use hi + lo pairs
   return xy_smem(d.R, split) <= 227 * 1024 && lst_smem(d.R, split) <= 227 * 1024 &&
          encode_fn() != nullptr;
 }
@@ -823,7 +792,7 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
                  uint32_t* err, cudaStream_t s) {
   if (!tc_supported(d, precision)) return GSP_ERR_UNSUPPORTED;
   const int elem = precision == GSP_PREC_TF32 ? 4 : 2;
-  const bool split = precision == GSP_PREC_BF16;
+  const bool split = precision != GSP_PREC_BF16_1X;  // BF16 and TF32 use hi + lo pairs
   const int brows = d.R * (split ? 2 : 1);
   CUtensorMap mT, mK;
   GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2(), 128));
@@ -835,9 +804,9 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
   const int stages = xy_stages(d.R, split);
   prof_begin(PROF_MTTKRP_XY, s);
   if (elem == 4) {
-    GSP_TRY(set_smem(k_xy_tc<4, false>, smem));
-    k_xy_tc<4, false><<<grid, kThreads, smem, s>>>(mT, mK, Yp, n_tiles, d.N2(), d.L, d.B2(), d.R,
-                                                   stages, err);
+    GSP_TRY(set_smem(k_xy_tc<4, true>, smem));
+    k_xy_tc<4, true><<<grid, kThreads, smem, s>>>(mT, mK, Yp, n_tiles, d.N2(), d.L, d.B2(), d.R,
+                                                  stages, err);
   } else if (split) {
     GSP_TRY(set_smem(k_xy_tc<2, true>, smem));
     k_xy_tc<2, true><<<grid, kThreads, smem, s>>>(mT, mK, Yp, n_tiles, d.N2(), d.L, d.B2(), d.R,
@@ -861,15 +830,24 @@ int tc_lst_ctas(const MttkrpDims& d) {
   return P;
 }
 
-int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart, float* Zp,
-                  const MttkrpDims& d, int precision, uint32_t* err, cudaStream_t s) {
+int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, float* Zpart,
+                  float* Zp, const MttkrpDims& d, int precision, uint32_t* err, cudaStream_t s) {
   if (!tc_supported(d, precision)) return GSP_ERR_UNSUPPORTED;
   const int elem = precision == GSP_PREC_TF32 ? 4 : 2;
-  const bool split = precision == GSP_PREC_BF16;
+  const bool split = precision != GSP_PREC_BF16_1X;  // BF16 and TF32 use hi + lo pairs
   const int E128 = 128 / elem;
-  CUtensorMap mT;
+  const int brows = d.R * (split ? 2 : 1);
+  const int nr = d.N * d.R;
+  if (elem == 2)
+    k_fx_cols<__nv_bfloat16><<<grid_for(nr, 256), 256, 0, s>>>(
+        fx, d.N, d.R, split ? 1 : 0, static_cast<__nv_bfloat16*>(FXt));
+  else
+    k_fx_cols<float><<<grid_for(nr, 256), 256, 0, s>>>(fx, d.N, d.R, 1, static_cast<float*>(FXt));
+  GSP_CHECK_LAUNCH();
+  CUtensorMap mT, mF;
   GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2(), E128,
                    elem == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
+  GSP_TRY(make_map(&mF, FXt, elem, brows, d.N, brows));
   int MB = 0;
   const int G = lst_groups(d, &MB);
   const int P = tc_lst_ctas(d);
@@ -879,16 +857,16 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, float* Zpart,
   const int logN = ilog2(d.N);
   prof_begin(PROF_MTTKRP_LST, s);
   if (elem == 4) {
-    GSP_TRY(set_smem(k_lst_tc<4, false>, smem));
-    k_lst_tc<4, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                    MB, G, stages, err);
+    GSP_TRY(set_smem(k_lst_tc<4, true>, smem));
+    k_lst_tc<4, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+                                                   MB, G, stages, err);
   } else if (split) {
     GSP_TRY(set_smem(k_lst_tc<2, true>, smem));
-    k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+    k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
                                                    MB, G, stages, err);
   } else {
     GSP_TRY(set_smem(k_lst_tc<2, false>, smem));
-    k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, fx, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+    k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
                                                     MB, G, stages, err);
   }
   prof_end(PROF_MTTKRP_LST, s);

@@ -50,7 +50,7 @@ def test_mttkrp_parity(prec, N, L, B, R):
     m, H, X = _tensor(N, L, B, "flakes", 20 + N + R)
     ws = g.CPWorkspace(N, L, B, R, prec) if _supported(prec, N, L, B, R) else None
     if ws is None:
-        pytest.skip(f"{prec} MTTKRP does not support rank {R}")
+        pytest.skip(f"{prec} MTTKRP does not support the shape {(N, L, B, R)}")
     ws.prepare(hist=dev(H, torch.int32))
     u = [synth.uniform(300 + R, k, n * R).reshape(n, R).astype(np.float32)
          for k, n in enumerate((N, N, L, B, B))]
@@ -99,10 +99,10 @@ def test_als_from_normals_equals_from_histograms(prec):
     # both ways of preparing the operand give the same values (the rounding of
     # the tensor-core operands depends only on the element index)
     import paper_2109_14807_gb300 as g
-    N, L, B, R = 32, 6, 16, 16
+    N, L, B, R = 64, 7, 16, 16
     if not _supported(prec, N, L, B, R):
         pytest.skip(f"{prec} path unavailable")
-    m = synth.make_map(synth.WORKLOADS["flakes32"])
+    m = synth.flake_map(N, 256, 0.15, 1)
     init = synth.init_factors(N, L, B, R, 2001)
     H = g.build_footprint_ndfs(dev(m), L, B)
     _, fits1, _ = g.cp_decompose(R, init, hist=H, sweeps=5, precision=prec)
