@@ -4,7 +4,10 @@
 //
 // Every level is computed from the 2-byte bin map alone (it stays in L2) by
 // box sums of per-bin indicators staged in shared memory, so the only HBM
-// traffic is the output itself; all arithmetic is integer, hence bit-exact.
+// traffic is the output itself.  Every value is an integer count, exact in
+// the types it passes through (FP16 <= 2^11, FP32 < 2^24), hence bit-exact.
+#include <cuda_fp16.h>
+
 #include "ndf_build.cuh"
 
 namespace gsp {
@@ -90,12 +93,15 @@ __device__ __forceinline__ void sink_sumsq(const LevelSink& o, int4 v, bool acti
 // removes one texel and adds one per column.  For each row the histograms of
 // all N footprints are window sums of V along x, read from the prefix sum S
 // over x: two look-ups per count, three across the wrap.
-//  - updates: thread t owns the columns x = t, t + 512, ... (no atomics);
-//  - prefix: warp w scans its contiguous x range in blocks of 32 columns, one
-//    column per lane, on pairs of 16-bit counts packed in 32-bit words (a sum
-//    over 32 columns is at most 32 w <= 2^15), carries between blocks in 32
-//    bits, and stores S once the offsets of the earlier ranges are known;
-//  - rows of V (48 B) are padded so that 16-byte accesses of consecutive
+//  - updates: thread t owns the columns x = t, t + 512, ... (no atomics); V
+//    holds FP16 counts (<= 2^10, exact), updated by exact +-1 adds;
+//  - prefix: warp w covers a contiguous x range in blocks of 32 columns; the
+//    inclusive prefix of a block is a lower-triangular ones matrix times the
+//    block's [32 x 16] counts, six warp MMAs (m16n8k16, FP16 in, FP32 out,
+//    exact since every sum is an integer below 2^24); block totals carry in
+//    FP32, and S is stored (as int) once the offsets of the earlier ranges
+//    are known;
+//  - rows of V (48 B) are padded so that the ldmatrix row reads of consecutive
 //    columns fall on distinct banks; S is kept as two planes of 8 bins (32-byte
 //    rows) whose offsets differ by 16 mod 128 bytes, so the output's reads
 //    (lane pairs per column, one plane each) fall on distinct banks;
@@ -114,15 +120,41 @@ __host__ __device__ constexpr int s_plane_ints(int N) {
   return (N + 1) * kSRow + (((4 - (N + 1) * kSRow) % 32) + 32) % 32;
 }
 
+// Four 8x8 b16 matrices from shared memory, transposed into the B-fragment
+// layout of mma.m16n8k16 (lanes 8i..8i+7 give the row addresses of matrix i).
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+
+// D = A B + C, A 16x16 and B 16x8 FP16, C and D FP32 (warp-level MMA).
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                          uint32_t b1, const float (&c)[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%10, %11, %12, %13};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]),
+        "f"(c[2]), "f"(c[3]));
+}
+
+// An exact non-negative integer below 2^23 held in a float, as an int.
+__device__ __forceinline__ int float_to_int_exact(float v) {
+  return __float_as_int(v + 8388608.0f) - 0x4B000000;
+}
+
 __global__ void __launch_bounds__(kHistThreads, 1)
     k_box_hist(const uint16_t* __restrict__ bins_map, int logN, int B2, int ychunk,
                const __grid_constant__ HistOut o) {
   constexpr int G = kHistG;
   extern __shared__ __align__(16) uint8_t smem_b[];
-  __shared__ __align__(16) int WT[kHistWarps * G];
+  __shared__ __align__(16) float WT[kHistWarps * G];
   const int N = 1 << logN, m = N - 1;
-  uint16_t* V = reinterpret_cast<uint16_t*>(smem_b);                         // [N][24]
-  int* S = reinterpret_cast<int*>(smem_b + N * kVRow * sizeof(uint16_t));    // [2][2][N + 1][8]
+  const int vrows = N < 32 ? 32 : N;                                          // whole 32-column blocks
+  __half* V = reinterpret_cast<__half*>(smem_b);                              // [vrows][24]
+  int* S = reinterpret_cast<int*>(smem_b + vrows * kVRow * sizeof(__half));  // [2][2][N + 1][8]
   const int plane = s_plane_ints(N), sbuf = 2 * plane;
   const int g0 = blockIdx.x * G;
   const int y0 = blockIdx.y * ychunk;
@@ -156,8 +188,27 @@ __global__ void __launch_bounds__(kHistThreads, 1)
   const int scan_warps = N >= 32 * kHistWarps ? kHistWarps : (N >= 32 ? N >> 5 : 1);
   const int xr = N / scan_warps;               // columns per scanning warp
   const int nblk = xr >= 32 ? xr >> 5 : 1;     // 32-column blocks per warp
+  // Prefix over a 32-column block by warp MMA: S_block = [Tri; Ones Tri] V_block
+  // with Tri the 16x16 lower-triangular ones.  Counts (<= 2^10) are exact in
+  // FP16 and every sum (< 2^24) in FP32, whatever the accumulation order.
+  const int fr = lane >> 2, fc = 2 * (lane & 3);  // fragment row / column pair of this lane
+  uint32_t aTri[4], aOne[4];
+  {
+    auto tri = [](int mm, int kk) -> uint32_t { return kk <= mm ? 0x3C00u : 0u; };
+    aTri[0] = tri(fr, fc) | (tri(fr, fc + 1) << 16);
+    aTri[1] = tri(fr + 8, fc) | (tri(fr + 8, fc + 1) << 16);
+    aTri[2] = tri(fr, fc + 8) | (tri(fr, fc + 9) << 16);
+    aTri[3] = tri(fr + 8, fc + 8) | (tri(fr + 8, fc + 9) << 16);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) aOne[i] = 0x3C003C00u;
+  }
+  // ldmatrix row address of this lane: matrix q = lane / 8 covers k rows
+  // (q & 1) * 8 .. + 7 and bins (q >> 1) * 8 .. + 7 of a 16-column half block
+  const uint32_t v_lane = static_cast<uint32_t>(__cvta_generic_to_shared(V)) +
+                          static_cast<uint32_t>((((lane >> 3) & 1) * 8 + (lane & 7)) * kVRow +
+                                                (lane >> 4) * 8) * 2u;
 
-  for (int i = tid; i < N * kVRow / 8; i += kHistThreads)
+  for (int i = tid; i < vrows * kVRow / 8; i += kHistThreads)
     reinterpret_cast<uint4*>(V)[i] = make_uint4(0, 0, 0, 0);
   if (tid < 8)  // S[0] = 0 in both planes of both buffers
     reinterpret_cast<int4*>(S + (tid >> 2) * sbuf + ((tid >> 1) & 1) * plane)[tid & 1] =
@@ -173,7 +224,8 @@ __global__ void __launch_bounds__(kHistThreads, 1)
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int b = static_cast<int>(code[u]) - g0;
-        if (j0 + u < w && static_cast<unsigned>(b) < static_cast<unsigned>(G)) V[x * kVRow + b] += 1;
+        if (j0 + u < w && static_cast<unsigned>(b) < static_cast<unsigned>(G))
+          V[x * kVRow + b] = __hadd(V[x * kVRow + b], __float2half(1.0f));
       }
     }
   }
@@ -203,48 +255,44 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     const bool scan_row = y < y0 + ychunk;
     int* Sc = S + ((y - y0) & 1) * sbuf;        // S of row y
     const int* Sp = S + ((y - y0 + 1) & 1) * sbuf;  // S of row y - 1
-    int vals[kMaxBlocks][G];
+    // inclusive prefix of each block, per lane: [block][nt][row group][2 bins]
+    float pre[kMaxBlocks][2][4][2];
     if (scan_row && warp < scan_warps) {
-      int carry[G];
-#pragma unroll
-      for (int b = 0; b < G; ++b) carry[b] = 0;
+      float carry[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
       const int xbeg = warp * xr;
 #pragma unroll
       for (int blk = 0; blk < kMaxBlocks; ++blk) {
         if (blk < nblk) {
-          const int x = xbeg + blk * 32 + lane;
-          const bool in = blk * 32 + lane < xr;
-          uint32_t wd[8];
-          if (in) {
-            const uint4 p0 = *reinterpret_cast<const uint4*>(V + x * kVRow);
-            const uint4 p1 = *reinterpret_cast<const uint4*>(V + x * kVRow + 8);
-            wd[0] = p0.x; wd[1] = p0.y; wd[2] = p0.z; wd[3] = p0.w;
-            wd[4] = p1.x; wd[5] = p1.y; wd[6] = p1.z; wd[7] = p1.w;
-          } else {
+          const int xb = xbeg + blk * 32;
+          uint32_t bk0[4], bk1[4];  // B fragments of columns xb..xb+15 and xb+16..xb+31
+          ldsm_x4_trans(v_lane + static_cast<uint32_t>(xb * kVRow * 2), bk0);
+          ldsm_x4_trans(v_lane + static_cast<uint32_t>((xb + 16) * kVRow * 2), bk1);
+          const float zero[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) wd[k] = 0u;
+          for (int nt = 0; nt < 2; ++nt) {
+            float top[4], bot[4];
+            mma_16816(top, aTri, bk0[2 * nt], bk0[2 * nt + 1], zero);
+            mma_16816(bot, aOne, bk0[2 * nt], bk0[2 * nt + 1], zero);
+            mma_16816(bot, aTri, bk1[2 * nt], bk1[2 * nt + 1], bot);
+            pre[blk][nt][0][0] = top[0] + carry[nt][0];
+            pre[blk][nt][0][1] = top[1] + carry[nt][1];
+            pre[blk][nt][1][0] = top[2] + carry[nt][0];
+            pre[blk][nt][1][1] = top[3] + carry[nt][1];
+            pre[blk][nt][2][0] = bot[0] + carry[nt][0];
+            pre[blk][nt][2][1] = bot[1] + carry[nt][1];
+            pre[blk][nt][3][0] = bot[2] + carry[nt][0];
+            pre[blk][nt][3][1] = bot[3] + carry[nt][1];
+            // block total: row 31 (lanes 28..31 hold it for their bin pairs)
+            carry[nt][0] = __shfl_sync(0xffffffffu, pre[blk][nt][3][0], 28 + (lane & 3));
+            carry[nt][1] = __shfl_sync(0xffffffffu, pre[blk][nt][3][1], 28 + (lane & 3));
           }
-#pragma unroll
-          for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const uint32_t u = __shfl_up_sync(0xffffffffu, wd[k], off);
-              if (lane >= off) wd[k] += u;  // two 16-bit lanes, no carry across
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            vals[blk][2 * k] = static_cast<int>(wd[k] & 0xFFFFu) + carry[2 * k];
-            vals[blk][2 * k + 1] = static_cast<int>(wd[k] >> 16) + carry[2 * k + 1];
-          }
-          const int last = (xr - blk * 32 < 32 ? xr - blk * 32 : 32) - 1;
-#pragma unroll
-          for (int b = 0; b < G; ++b) carry[b] = __shfl_sync(0xffffffffu, vals[blk][b], last);
         }
       }
-      if (lane == 0) {
-#pragma unroll
-        for (int b = 0; b < G; ++b) WT[warp * G + b] = carry[b];
+      if (lane < 4) {  // range totals of bins fc, fc + 1 (plane 0) and fc + 8, fc + 9
+        WT[warp * G + fc] = carry[0][0];
+        WT[warp * G + fc + 1] = carry[0][1];
+        WT[warp * G + 8 + fc] = carry[1][0];
+        WT[warp * G + 8 + fc + 1] = carry[1][1];
       }
     }
     if (y > y0) {
@@ -327,22 +375,29 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     if (scan_row) {
       if (warp < scan_warps) {
         // offset of this warp's range: lanes 0..15 sum one bin each over the earlier warps
-        int my = 0;
+        float my = 0.f;
         if (lane < G)
           for (int k = 0; k < warp; ++k) my += WT[k * G + lane];
-        int off[G];
-#pragma unroll
-        for (int b = 0; b < G; ++b) off[b] = __shfl_sync(0xffffffffu, my, b);
+        float off[2][2];
+        off[0][0] = __shfl_sync(0xffffffffu, my, fc);
+        off[0][1] = __shfl_sync(0xffffffffu, my, fc + 1);
+        off[1][0] = __shfl_sync(0xffffffffu, my, fc + 8);
+        off[1][1] = __shfl_sync(0xffffffffu, my, fc + 9);
         const int xbeg = warp * xr;
 #pragma unroll
         for (int blk = 0; blk < kMaxBlocks; ++blk) {
-          if (blk < nblk && blk * 32 + lane < xr) {
-            const int xs = xbeg + blk * 32 + lane + 1;
+          if (blk < nblk) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              int4* dst = reinterpret_cast<int4*>(Sc + (q >> 1) * plane + xs * kSRow) + (q & 1);
-              *dst = make_int4(vals[blk][4 * q] + off[4 * q], vals[blk][4 * q + 1] + off[4 * q + 1],
-                               vals[blk][4 * q + 2] + off[4 * q + 2], vals[blk][4 * q + 3] + off[4 * q + 3]);
+            for (int rg = 0; rg < 4; ++rg) {
+              const int x = xbeg + blk * 32 + rg * 8 + fr;  // rows fr, fr+8, 16+fr, 24+fr
+              if (x < N) {
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                  int2* dst = reinterpret_cast<int2*>(Sc + nt * plane + (x + 1) * kSRow + fc);
+                  *dst = make_int2(float_to_int_exact(pre[blk][nt][rg][0] + off[nt][0]),
+                                   float_to_int_exact(pre[blk][nt][rg][1] + off[nt][1]));
+                }
+              }
             }
           }
         }
@@ -352,8 +407,10 @@ __global__ void __launch_bounds__(kHistThreads, 1)
         for (int k = 0; k < 2; ++k) {
           const int x = tid + k * kHistThreads;
           const int bo = nxt_out[k] - g0, bi = nxt_in[k] - g0;
-          if (x < N && static_cast<unsigned>(bo) < static_cast<unsigned>(G)) V[x * kVRow + bo] -= 1;
-          if (x < N && static_cast<unsigned>(bi) < static_cast<unsigned>(G)) V[x * kVRow + bi] += 1;
+          if (x < N && static_cast<unsigned>(bo) < static_cast<unsigned>(G))
+            V[x * kVRow + bo] = __hsub(V[x * kVRow + bo], __float2half(1.0f));
+          if (x < N && static_cast<unsigned>(bi) < static_cast<unsigned>(G))
+            V[x * kVRow + bi] = __hadd(V[x * kVRow + bi], __float2half(1.0f));
         }
         if (y + 2 < y0 + ychunk) fetch(y + 2);
       }
@@ -394,7 +451,7 @@ int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins, uin
 }
 
 size_t box_hist_smem(int N) {
-  return static_cast<size_t>(N) * kVRow * sizeof(uint16_t) +
+  return static_cast<size_t>(N < 32 ? 32 : N) * kVRow * sizeof(__half) +
          4 * static_cast<size_t>(s_plane_ints(N)) * sizeof(int);
 }
 
