@@ -214,18 +214,29 @@ __global__ void __launch_bounds__(kHistThreads, 1)
     reinterpret_cast<int4*>(S + (tid >> 2) * sbuf + ((tid >> 1) & 1) * plane)[tid & 1] =
         make_int4(0, 0, 0, 0);
   __syncthreads();
-  for (int x = tid; x < N; x += kHistThreads) {
-    // the window's rows, eight independent loads at a time
-    for (int j0 = 0; j0 < w; j0 += 8) {
-      uint16_t code[8];
+  {
+    // the window's rows for this thread's columns x = tid, tid + 512:
+    // 16 rows x 2 columns of independent loads in flight (N <= 2 * kHistThreads)
+    constexpr int kRows = 16;
+    for (int j0 = 0; j0 < w; j0 += kRows) {
+      uint16_t code[2][kRows];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        code[u] = j0 + u < w ? bins_map[(((y0 - a + j0 + u) & m) << logN) + x] : 0xFFFFu;
+      for (int k = 0; k < 2; ++k) {
+        const int x = tid + k * kHistThreads;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int b = static_cast<int>(code[u]) - g0;
-        if (j0 + u < w && static_cast<unsigned>(b) < static_cast<unsigned>(G))
-          V[x * kVRow + b] = __hadd(V[x * kVRow + b], __float2half(1.0f));
+        for (int u = 0; u < kRows; ++u)
+          code[k][u] = (x < N && j0 + u < w) ? bins_map[(((y0 - a + j0 + u) & m) << logN) + x]
+                                              : static_cast<uint16_t>(0xFFFFu);
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int x = tid + k * kHistThreads;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+          const int b = static_cast<int>(code[k][u]) - g0;
+          if (static_cast<unsigned>(b) < static_cast<unsigned>(G))
+            V[x * kVRow + b] = __hadd(V[x * kVRow + b], __float2half(1.0f));
+        }
       }
     }
   }
@@ -376,8 +387,11 @@ __global__ void __launch_bounds__(kHistThreads, 1)
       if (warp < scan_warps) {
         // offset of this warp's range: lanes 0..15 sum one bin each over the earlier warps
         float my = 0.f;
-        if (lane < G)
-          for (int k = 0; k < warp; ++k) my += WT[k * G + lane];
+        if (lane < G) {
+#pragma unroll
+          for (int k = 0; k < kHistWarps; ++k)  // independent loads, then the sum
+            if (k < warp) my += WT[k * G + lane];
+        }
         float off[2][2];
         off[0][0] = __shfl_sync(0xffffffffu, my, fc);
         off[0][1] = __shfl_sync(0xffffffffu, my, fc + 1);
