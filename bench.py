@@ -58,6 +58,10 @@ def parse_args():
                         "autotuner's choice")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--precision-report", action="store_true",
+                   help="instead of the step: CP-ALS fit error vs the FP64 oracle and sweep time "
+                        "per MTTKRP precision on the 512^2 precision workload, and the sweep time "
+                        "per precision on the benchmark workload")
     return p.parse_args()
 
 
@@ -498,8 +502,58 @@ def run_e2e(args, g, dev, m_np, q_np, normals, qd, out, step, barrier, world):
             "d2h_bytes_per_step": int(h_out.numel() * 4)}
 
 
+# ------------------------------------------------------ precision report --
+GOLDEN_FITS = os.path.join(ROOT, "tests", "golden", "brushed512_als_fits.txt")
+
+
+def precision_report(args):
+    """CP-ALS per MTTKRP precision: fit error after each of 20 sweeps against
+    the FP64 oracle's fits from the same seeded init (stored by
+    tests/golden/make_brushed512_fits.py), and the time of one sweep
+    (CUDA events), on the 512^2 brushed map and on the benchmark map."""
+    import numpy as np
+    import torch
+    import paper_2109_14807_gb300 as g
+    torch.cuda.set_device(0)
+    ref = np.loadtxt(GOLDEN_FITS, comments="#")[:, 1]
+    out = {"metric": "CP-ALS fit error vs FP64 oracle and sweep time per MTTKRP precision",
+           "data": "synthetic", "variants": {}}
+    for wname in ("brushed512", "flakes1024"):
+        w = synth.WORKLOADS[wname]
+        N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
+        m = torch.from_numpy(synth.make_map(w)).cuda()
+        init = synth.init_factors(N, L, B, R, 2000 + w["seed"])
+        for prec in ("fp32", "tf32", "bf16", "bf16_1x"):
+            ws = g.CPWorkspace(N, L, B, R, prec)
+            ws.prepare(normal_xy=m)
+            rec = out["variants"].setdefault(prec, {})
+            if wname == "brushed512":
+                f = g.init_factors_to_device(init)
+                fits, _ = ws.sweeps(f, w["sweeps"])
+                rel = np.abs(np.array(fits) - ref[: len(fits)]) / np.abs(ref[: len(fits)])
+                rec[wname] = {"max_rel_fit_error": float(rel.max()), "final_fit": fits[-1]}
+            else:
+                rec[wname] = {}
+            # sweep time: one untimed sweep, then 5 sweeps in one call (no host sync)
+            f = g.init_factors_to_device(init)
+            ws.sweeps(f, 1, report=False)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ws.sweeps(f, 5, report=False)
+            b.record()
+            torch.cuda.synchronize()
+            rec[wname]["sweep_ms"] = round(a.elapsed_time(b) / 5, 3)
+            del ws
+            torch.cuda.empty_cache()
+    out["oracle_final_fit_brushed512"] = float(ref[-1])
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.precision_report:
+        precision_report(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
