@@ -182,27 +182,36 @@ __global__ void __launch_bounds__(256) k_contract(CParams p) {
   }
 }
 
-// M[i][r] = sum_j W[(i + j*w1)][r] * A1[j][r] for consecutive i (wi = 1): each
-// CTA owns 256/R consecutive rows i, so every step over j reads one
-// contiguous run of W; one output per thread, fixed summation order.
+// M[i][r] = sum_j W[(i + j*w1)][r] * A1[j][r] for rows i of stride 1: one CTA
+// per row i, its 256 threads = 256/R groups of j (j = g, g + G, ...) x R
+// ranks, 8 loads in flight per thread; the group sums are combined in shared
+// memory in a fixed order.
 __global__ void __launch_bounds__(256) k_contract_rows(const float* __restrict__ W, long long w1,
                                                        int J, const float* __restrict__ A1,
                                                        int R, double* __restrict__ M,
                                                        float* __restrict__ Mf) {
-  const int per = blockDim.x / R;
-  const int i = blockIdx.x * per + threadIdx.x / R;
-  const int r = threadIdx.x % R;
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // 8 loads in flight
-  int j = 0;
-  for (; j + 8 <= J; j += 8) {
+  __shared__ float part[256];
+  const int G = blockDim.x / R;
+  const int i = blockIdx.x;
+  const int gj = threadIdx.x / R, r = threadIdx.x % R;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int j = gj;
+  for (; j + 7 * G < J; j += 8 * G) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      acc[u] = fmaf(W[(i + (j + u) * w1) * R + r], A1[(j + u) * R + r], acc[u]);
+    for (int u = 0; u < 8; ++u) {
+      const long long jj = j + u * G;
+      acc[u] = fmaf(W[(i + jj * w1) * R + r], A1[jj * R + r], acc[u]);
+    }
   }
-  for (; j < J; ++j) acc[0] = fmaf(W[(i + j * w1) * R + r], A1[j * R + r], acc[0]);
-  const float t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-  if (M) M[i * R + r] = static_cast<double>(t);
-  if (Mf) Mf[i * R + r] = t;
+  for (; j < J; j += G) acc[0] = fmaf(W[(i + static_cast<long long>(j) * w1) * R + r], A1[j * R + r], acc[0]);
+  part[threadIdx.x] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  __syncthreads();
+  if (gj == 0) {
+    float t = part[r];
+    for (int k = 1; k < G; ++k) t += part[k * R + r];
+    if (M) M[i * R + r] = static_cast<double>(t);
+    if (Mf) Mf[i * R + r] = t;
+  }
 }
 
 // G[r1][r2] = sum_i A[i][r1] A[i][r2], FP64; 256/R row slices per output row,
@@ -234,12 +243,13 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int I
 }
 
 // Hadamard product of the four Gram matrices other than `skip`.
-__device__ void hadamard_v(const double* __restrict__ G, int R, int skip, double* V) {
+// V (row stride ld) = Hadamard product of the Gram matrices of all modes but `skip`.
+__device__ void hadamard_v(const double* __restrict__ G, int R, int skip, double* V, int ld) {
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     double v = 1.0;
     for (int m = 0; m < 5; ++m)
       if (m != skip) v *= G[m * R * R + e];
-    V[e] = v;
+    V[(e / R) * ld + e % R] = v;
   }
 }
 
@@ -312,42 +322,53 @@ __device__ void jacobi_eigen(double* V, double* Q, int R) {
 
 // Right-looking Cholesky of V in shared memory (lower triangle, row-major).
 // Returns false when a pivot is not above thresh; block-uniform result.
-__device__ bool cholesky_inplace(double* V, int R, double thresh, double* invd) {
-  __shared__ int fail;
-  if (threadIdx.x == 0) fail = 0;
+// In place on V (row stride ld = R + 1, so that the column reads of the
+// trailing update fall on distinct banks).
+__device__ bool cholesky_inplace(double* V, int R, int ld, double thresh, double* invd) {
+  // Right-looking, columns left unscaled until the end: step j subtracts
+  // A_ij A_kj / A_jj from the trailing lower triangle, which only reads column
+  // j and the pivot, so one barrier per column suffices; L_ij = A_ij / sqrt(A_jj)
+  // is formed for all columns at the end.  Thread 0 owns element (j+1, j+1)
+  // of step j's update, so it forms the next pivot's reciprocal right after
+  // updating it, before the barrier (double-buffered: step j reads slot j & 1
+  // while thread 0 fills slot (j + 1) & 1).
+  __shared__ double piv_inv[2];
+  const int ti = threadIdx.x >> 4, tk = threadIdx.x & 15;  // 16 x 16 grid (blockDim.x == 256)
+  if (threadIdx.x == 0 && V[0] > thresh) {
+    piv_inv[0] = 1.0 / V[0];
+    invd[0] = 1.0 / sqrt(V[0]);
+  }
   __syncthreads();
   for (int j = 0; j < R; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = V[j * R + j];
-      if (!(d > thresh)) {
-        fail = 1;
-      } else {
-        const double s = sqrt(d);
-        V[j * R + j] = s;
-        invd[j] = 1.0 / s;
+    const double d = V[j * ld + j];  // final: written by step j - 1 before its barrier
+    if (!(d > thresh)) return false;  // every thread reads the same pivot
+    const double inv = piv_inv[j & 1];
+    for (int i = j + 1 + ti; i < R; i += 16) {
+      const double aij = V[i * ld + j] * inv;
+      for (int k = j + 1 + tk; k <= i; k += 16) V[i * ld + k] -= aij * V[k * ld + j];
+    }
+    if (threadIdx.x == 0 && j + 1 < R) {
+      const double dn = V[(j + 1) * ld + j + 1];
+      if (dn > thresh) {
+        piv_inv[(j + 1) & 1] = 1.0 / dn;
+        invd[j + 1] = 1.0 / sqrt(dn);
       }
     }
     __syncthreads();
-    if (fail) return false;
-    const double ij = invd[j];
-    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) V[i * R + j] *= ij;
-    __syncthreads();
-    // trailing lower triangle on a 16 x 16 thread grid (blockDim.x == 256)
-    const int ti = threadIdx.x >> 4, tk = threadIdx.x & 15;
-    for (int i = j + 1 + ti; i < R; i += 16) {
-      const double lij = V[i * R + j];
-      for (int k = j + 1 + tk; k <= i; k += 16) V[i * R + k] -= lij * V[k * R + j];
-    }
-    __syncthreads();
   }
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, j = e % R;
+    if (j <= i) V[i * ld + j] *= invd[j];
+  }
+  __syncthreads();
   return true;
 }
 
-__device__ double max_diag(const double* V, int R) {
+__device__ double max_diag(const double* V, int R, int ld) {
   __shared__ double mx;
   if (threadIdx.x == 0) {
     double m = 0.0;
-    for (int a = 0; a < R; ++a) m = fmax(m, fabs(V[a * R + a]));
+    for (int a = 0; a < R; ++a) m = fmax(m, fabs(V[a * ld + a]));
     mx = m;
   }
   __syncthreads();
@@ -378,24 +399,25 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
                                               double* __restrict__ out, uint32_t* flags) {
   extern __shared__ double smem[];
   __shared__ double invd_s[kMaxCpRank];
-  double* V = smem;          // [R][R]
-  double* Q = smem + R * R;  // [R][R] (eigenvectors, R <= 64 only)
+  const int ld = R + 1;
+  double* V = smem;               // [R][R + 1] for the Cholesky, [R][R] for the fallback
+  double* Q = smem + R * ld;      // [R][R] (eigenvectors, R <= 64 only)
   const SolveScratch ss = solve_scratch(out, R);
   double* L = ss.L;
   double* invd = ss.invd;
   int* mode = ss.mode;
   const double eps = 2.220446049250313e-16;
-  hadamard_v(G, R, skip, V);
+  hadamard_v(G, R, skip, V, ld);
   __syncthreads();
-  const double mx = max_diag(V, R);
-  bool ok = cholesky_inplace(V, R, R * eps * mx, invd_s);
+  const double mx = max_diag(V, R, ld);
+  bool ok = cholesky_inplace(V, R, ld, R * eps * mx, invd_s);
   if (!ok) {
     if (threadIdx.x == 0 && flags) atomicOr(flags, GSP_DEV_NUMERIC);
     if (R <= kJacobiMaxRank) {
-      hadamard_v(G, R, skip, V);
+      hadamard_v(G, R, skip, V, R);
       __syncthreads();
       jacobi_eigen(V, Q, R);
-      const double lmax = max_diag(V, R);
+      const double lmax = max_diag(V, R, R);
       const double cutoff = R * eps * lmax;
       for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         const int a = e / R, b = e % R;
@@ -411,12 +433,12 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
     }
     const double deltas[3] = {1e-12, 1e-9, 1e-6};
     for (int t = 0; t < 3 && !ok; ++t) {
-      hadamard_v(G, R, skip, V);
+      hadamard_v(G, R, skip, V, ld);
       __syncthreads();
       if (threadIdx.x == 0)
-        for (int k = 0; k < R; ++k) V[k * R + k] += deltas[t] * mx;
+        for (int k = 0; k < R; ++k) V[k * ld + k] += deltas[t] * mx;
       __syncthreads();
-      ok = cholesky_inplace(V, R, R * eps * mx, invd_s);
+      ok = cholesky_inplace(V, R, ld, R * eps * mx, invd_s);
     }
     if (!ok) {  // give up on this update: A = 0, lambda = 0 for the mode
       for (int e = threadIdx.x; e < R * R; e += blockDim.x) ss.W[e] = 0.0;
@@ -426,7 +448,7 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
   }
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     const int i = e / R, k = e % R;
-    L[e] = k <= i ? V[e] : 0.0;
+    L[e] = k <= i ? V[i * ld + k] : 0.0;
   }
   for (int k = threadIdx.x; k < R; k += blockDim.x) invd[k] = invd_s[k];
   if (threadIdx.x == 0) *mode = 0;
@@ -573,9 +595,9 @@ int ensure_smem_attr() {
   int dev = 0;
   GSP_CUDA(cudaGetDevice(&dev));
   if (done_dev != dev) {
-    // k_chol: V (R*R doubles) plus eigenvectors for R <= 64: at most 128 KB
+    // k_chol: V (R*(R+1) doubles) plus eigenvectors for R <= 64
     GSP_CUDA(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  2 * kMaxCpRank * kMaxCpRank * static_cast<int>(sizeof(double))));
+                                  (2 * kMaxCpRank + 1) * kMaxCpRank * static_cast<int>(sizeof(double))));
     done_dev = dev;
   }
   return GSP_OK;
@@ -647,11 +669,8 @@ int contract(const Ctx& c, int mode, const gsp_cp_factors& f, double* M, float* 
       break;
   }
   prof_begin(PROF_ALS_SMALL, c.s);
-  if (mode == 0) {
-    int per = 256 / d.R;
-    if (per > I) per = I;  // both powers of two: per divides I
-    k_contract_rows<<<I / per, per * d.R, 0, c.s>>>(p.W, p.w1, p.J1, p.A1, d.R, M, Mf);
-  }
+  if (mode == 0)
+    k_contract_rows<<<I, 256, 0, c.s>>>(p.W, p.w1, p.J1, p.A1, d.R, M, Mf);
   else
     k_contract<<<I, 256, 0, c.s>>>(p);
   prof_end(PROF_ALS_SMALL, c.s);
@@ -684,7 +703,8 @@ int gram(const Ctx& c, const gsp_cp_factors& f, int mode) {
 int update(const Ctx& c, const gsp_cp_factors& f, int mode) {
   const int R = c.d.R;
   const int I = mode_rows(c.d, mode);
-  size_t smem = static_cast<size_t>(R) * R * sizeof(double) * (R <= kJacobiMaxRank ? 2 : 1);
+  size_t smem = static_cast<size_t>(R) * (R + 1) * sizeof(double) +
+                (R <= kJacobiMaxRank ? static_cast<size_t>(R) * R * sizeof(double) : 0);
   prof_begin(PROF_ALS_SMALL, c.s);
   k_chol<<<1, 256, smem, c.s>>>(c.at<double>(c.lay.G), R, mode, c.at<double>(c.lay.W),
                                 c.at<uint32_t>(c.lay.flags));
