@@ -256,6 +256,23 @@ __global__ void __launch_bounds__(kHistThreads, 1)
   };
   fetch(y0 + 1);
   unsigned long long sumsq = 0;
+  // The output items of this thread (x = e / 2, plane h = e % 2 for
+  // e = tid + k * 512, k < 2N / 512) are the same in every row: their prefix
+  // offsets within an S buffer (ints), the wrap term and the column part of
+  // the output index are computed once.  S[N] + S[en - N] replaces S[en] for
+  // a window that wraps (wr >= 0).
+  constexpr int kMaxItems = 4;  // 2N / kHistThreads for N <= 1024
+  int it_lo[kMaxItems], it_hi[kMaxItems], it_wr[kMaxItems], it_col[kMaxItems];
+#pragma unroll
+  for (int k = 0; k < kMaxItems; ++k) {
+    const int e = tid + k * kHistThreads;
+    const int h = e & 1, x = e >> 1;
+    const int st = (x - a) & m, en = st + w;
+    it_lo[k] = h * plane + st * kSRow;
+    it_hi[k] = h * plane + (en <= N ? en : N) * kSRow;
+    it_wr[k] = en <= N ? -1 : h * plane + (en - N) * kSRow;
+    it_col[k] = ((x * B2 + g0) >> 3) + h;
+  }
   __syncthreads();  // V of row y0 complete (columns are initialised by other warps)
 
   // Pipelined over rows with S double-buffered: iteration y scans row y (V
@@ -311,30 +328,25 @@ __global__ void __launch_bounds__(kHistThreads, 1)
       // of a warp take consecutive x, so their 16-byte prefix reads (80-byte
       // rows) fall on distinct banks
       const long long row8 = ((static_cast<long long>(l) * N + (y - 1)) * N * B2) >> 3;
-      for (int e = tid; e < 2 * N; e += kHistThreads) {
-        const int h = e & 1, x = e >> 1;  // lane pairs write 32 contiguous bytes
-        const int st = (x - a) & m, en = st + w;
-        const int* Sh = Sp + h * plane;
-        const int4* lo4 = reinterpret_cast<const int4*>(Sh + st * kSRow);
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) {
+        if (tid + k * kHistThreads >= 2 * N) break;  // lane pairs write 32 contiguous bytes
+        const int4* lo4 = reinterpret_cast<const int4*>(Sp + it_lo[k]);
+        const int4* hi4 = reinterpret_cast<const int4*>(Sp + it_hi[k]);
         int c[8];
         {
           const int4 l0 = lo4[0], l1 = lo4[1];
-          int4 h0, h1;
-          if (en <= N) {
-            const int4* hi4 = reinterpret_cast<const int4*>(Sh + en * kSRow);
-            h0 = hi4[0];
-            h1 = hi4[1];
-          } else {  // window wraps: S[N] - S[st] + S[en - N]
-            const int4* tp = reinterpret_cast<const int4*>(Sh + N * kSRow);
-            const int4* wr = reinterpret_cast<const int4*>(Sh + (en - N) * kSRow);
-            const int4 t0 = tp[0], t1 = tp[1], w0 = wr[0], w1 = wr[1];
-            h0 = make_int4(t0.x + w0.x, t0.y + w0.y, t0.z + w0.z, t0.w + w0.w);
-            h1 = make_int4(t1.x + w1.x, t1.y + w1.y, t1.z + w1.z, t1.w + w1.w);
+          int4 h0 = hi4[0], h1 = hi4[1];
+          if (it_wr[k] >= 0) {  // window wraps: S[N] - S[st] + S[en - N]
+            const int4* wr = reinterpret_cast<const int4*>(Sp + it_wr[k]);
+            const int4 w0 = wr[0], w1 = wr[1];
+            h0 = make_int4(h0.x + w0.x, h0.y + w0.y, h0.z + w0.z, h0.w + w0.w);
+            h1 = make_int4(h1.x + w1.x, h1.y + w1.y, h1.z + w1.z, h1.w + w1.w);
           }
           c[0] = h0.x - l0.x; c[1] = h0.y - l0.y; c[2] = h0.z - l0.z; c[3] = h0.w - l0.w;
           c[4] = h1.x - l1.x; c[5] = h1.y - l1.y; c[6] = h1.z - l1.z; c[7] = h1.w - l1.w;
         }
-        const long long i8 = row8 + ((static_cast<long long>(x) * B2 + g0) >> 3) + h;
+        const long long i8 = row8 + it_col[k];
         if (o.h) {
           reinterpret_cast<int4*>(o.h)[2 * i8] = make_int4(c[0], c[1], c[2], c[3]);
           reinterpret_cast<int4*>(o.h)[2 * i8 + 1] = make_int4(c[4], c[5], c[6], c[7]);
