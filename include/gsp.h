@@ -321,6 +321,15 @@ const char* gsp_profile_name(int id);
 /* Kernel launches issued by this library since the process started. */
 uint64_t gsp_kernel_launches(void);
 
+/* Failure-path self-test of the bounded device waits (no fault, no hang).
+ * Launches one CTA that waits on an mbarrier nothing ever arrives at, through
+ * the same bounded wait the tensor-core kernels use for their TMA / MMA
+ * pipelines.  The wait gives up after its clock budget (4e9 SM cycles, about
+ * 2 s at GB300 clocks), the CTA ORs GSP_DEV_TIMEOUT into *d_err (device
+ * word, required) and returns, leaving the context usable.  Returns GSP_OK
+ * once launched; the status bit arrives asynchronously on `stream`. */
+int gsp_selftest_wait_timeout(uint32_t* d_err, gsp_stream stream);
+
 const char* gsp_strerror(int status);
 /* cudaError_t value of the last failing CUDA call in this thread (0 if none). */
 int gsp_last_cuda_error(void);

@@ -95,6 +95,7 @@ _SIGS = {
     "gsp_strerror": (c_char_p, [c_int]),
     "gsp_last_cuda_error": (c_int, []),
     "gsp_version": (c_int, []),
+    "gsp_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
 }
 
 _LIB = None

@@ -297,3 +297,15 @@ class RangeQueryFn(torch.autograd.Function):
 
 def range_query_autograd(queries, fx, fy, flw, fs, ft):
     return RangeQueryFn.apply(queries, fx, fy, flw, fs, ft)
+
+
+def selftest_wait_timeout(status: torch.Tensor | None = None) -> torch.Tensor:
+    """Run the failure-path self-test of the bounded device waits: one CTA waits
+    on an mbarrier nothing arrives at until the wait's clock budget (about 2 s)
+    runs out, then raises GSP_DEV_TIMEOUT in `status` (a new zeroed device word
+    when None).  Returns the status tensor (read it after synchronising)."""
+    lib = load()
+    if status is None:
+        status = new_status()
+    check("gsp_selftest_wait_timeout", lib.gsp_selftest_wait_timeout(_ptr(status), _stream()))
+    return status

@@ -664,6 +664,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// One CTA waits for a phase of an mbarrier that nothing arrives at: the
+// bounded wait gives up after kTimeoutCycles and the status path runs.
+__global__ void k_selftest_timeout(uint32_t* err) {
+  __shared__ uint64_t mb;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&mb), 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&mb), 0u, &abort_flag)) atomicOr(err, GSP_DEV_TIMEOUT);
+}
+
 // FXt[r][x] = fx[x][r] in the operand type (K-major B operand of the Z' pass):
 // BF16, or FP32 rounded to the nearest TF32; with `split` rows R..2R-1 hold
 // the remainder fx - hi rounded the same way.
@@ -890,3 +904,11 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
 
 
 }  // namespace gsp
+
+extern "C" int gsp_selftest_wait_timeout(uint32_t* d_err, gsp_stream stream) {
+  if (!d_err) return GSP_ERR_INVALID_ARG;
+  gsp::k_selftest_timeout<<<1, 32, 0, gsp::to_stream(stream)>>>(d_err);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
