@@ -66,6 +66,9 @@ def parse_args():
                    help="instead of the step: 8 materials (maps 128-1024, ranks 16-64, bins "
                         "16-64) queried together by 5e7 camera-sweep queries through the "
                         "autotuned, graph-captured query kernel")
+    p.add_argument("--sampling-report", action="store_true",
+                   help="instead of the step: hierarchical NDF importance sampling (Sec. 5.2) of "
+                        "1e7 footprints of the 1024^2, rank-64, 32^2-bin material")
     return p.parse_args()
 
 
@@ -614,8 +617,49 @@ def batching_report(args):
                       "data": "synthetic (seeded random factors, camera-sweep queries)"}), flush=True)
 
 
+def sampling_report(args):
+    """Samples/s of gsp_sample_ndf: 10^7 footprints (x, y, fractional level)
+    of one 1024^2 material with 11 levels, 32^2 bins and rank 64 (seeded
+    random non-negative factors), each descending log2(32) = 5 quad levels
+    with four range queries per level."""
+    import numpy as np
+    import torch
+    import paper_2109_14807_gb300 as g
+    torch.cuda.set_device(0)
+    N, L, B, R = 1024, 11, 32, 64
+    fac = {}
+    for j, (k, n) in enumerate((("fx", N), ("fy", N), ("fl", L), ("fs", B), ("ft", B))):
+        fac[k] = torch.from_numpy(synth.uniform(950, j, n * R).reshape(n, R).astype(np.float32)).cuda()
+    fac["lambda"] = torch.ones(R, dtype=torch.float32, device="cuda")
+    mat = g.QueryMaterial.from_factors(fac)
+    g.build_query_tables(mat)
+    n = 10_000_000
+    sd = g.samples_to_device(synth.sample_footprints(N, L, n, 951))
+    ud = torch.from_numpy(synth.sample_uniforms(952, n)).cuda()
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        g.sample_ndf(mat, sd, ud, out=out)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, args.steps // 3)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        g.sample_ndf(mat, sd, ud, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    print(json.dumps({"metric": "hierarchical NDF importance samples/s (Sec. 5.2)",
+                      "value": n / (ms / 1e3), "unit": "samples/s", "ms_per_launch": ms,
+                      "samples": n, "range_queries_per_sample": 4 * 5,
+                      "config": {"N": N, "levels": L, "bins": B, "rank": R},
+                      "data": "synthetic (seeded random factors, uniform footprints)"}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.sampling_report:
+        sampling_report(args)
+        return
     if args.batching_report:
         batching_report(args)
         return

@@ -247,6 +247,45 @@ int gsp_range_query(const gsp_material* h_mats, int n_mats, const gsp_query* d_q
                     void* d_ws, size_t ws_bytes, gsp_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* f1 -- hierarchical NDF importance sampling from range queries (Sec. 5.2)  */
+/* ------------------------------------------------------------------------ */
+
+/* A footprint to sample: texel (x, y) taken mod N, level clamped to
+ * [0, levels-1] and blended between floor(level) and floor(level) + 1 as in
+ * gsp_query, material: index into the materials array.  16 bytes. */
+typedef struct gsp_sample_query {
+  int32_t x, y;
+  float level;
+  uint32_t material;
+} gsp_sample_query;
+
+/* Uniform random numbers in [0, 1) each sample consumes: u[k] chooses the
+ * quad at subdivision step k (k < log2 B <= 6), u[6] and u[7] place the sample
+ * inside the final bin. */
+#define GSP_SAMPLE_UNIFORMS 8
+
+/* Hierarchical importance sampling of the NDF image of each footprint (Sec.
+ * 5.2, Fig. sampling): start from the whole B x B image; split the current
+ * square into four quads at its midpoints, take their average NDF values by
+ * four range queries (Sec. 4.3), clamp negative averages (possible for a CP
+ * approximation) to 0 and choose one quad with probability proportional to
+ * its average (quads in the order (s low, t low), (s low, t high), (s high, t
+ * low), (s high, t high): the first k with u * total < cumulative sum); if all
+ * four are 0 the choice is uniform.  After log2 B steps the square is one bin;
+ * the sample is placed uniformly inside it.  Output per sample, d_out [n][4]:
+ *   s, t        the sampled direction in bin units, in [0, B)
+ *   pmf         probability of the chosen bin (product of the step probabilities;
+ *               for a non-negative tensor the bin's value / the image sum)
+ *   value       the range average of the chosen bin, i.e. its NDF value.
+ * Requires every material's bin count to be a power of two <= 64
+ * (GSP_ERR_UNSUPPORTED otherwise) and built tables.  d_u: [n][GSP_SAMPLE_UNIFORMS]
+ * floats.  A malformed sample (bad material or non-finite level) writes NaN
+ * and sets GSP_DEV_BAD_QUERY.  Capturable in a CUDA graph. */
+int gsp_sample_ndf(const gsp_material* h_mats, int n_mats, const gsp_sample_query* d_q,
+                   int64_t n, const float* d_u, float* d_out, uint32_t* d_status,
+                   gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* a7 -- adjoint of the range query and the refinement step                  */
 /* ------------------------------------------------------------------------ */
 

@@ -237,6 +237,35 @@ def range_query(materials, queries: torch.Tensor, out=None, status=None, tuning=
     return out
 
 
+SAMPLE_WORDS = 4     # a sample descriptor is 16 bytes = 4 int32 words
+SAMPLE_UNIFORMS = 8  # uniforms one sample consumes
+
+
+def samples_to_device(s: np.ndarray, device="cuda") -> torch.Tensor:
+    """numpy array of 16-byte sample descriptors (x, y, level, material) ->
+    int32 tensor [n][4] on the device."""
+    words = np.frombuffer(np.ascontiguousarray(s).tobytes(), dtype=np.int32).reshape(-1, SAMPLE_WORDS)
+    return torch.from_numpy(words.copy()).to(device)
+
+
+def sample_ndf(materials, samples: torch.Tensor, uniforms: torch.Tensor, out=None,
+               status=None) -> torch.Tensor:
+    """Hierarchical NDF importance sampling (Sec. 5.2): one sample per
+    descriptor, consuming uniforms[i] (float32 [n][8] in [0, 1)).  Returns
+    float32 [n][4]: s, t (bin units), pmf of the chosen bin, its NDF value."""
+    lib = load()
+    arr, nm = _mats(materials)
+    n = samples.shape[0]
+    if uniforms.shape != (n, SAMPLE_UNIFORMS):
+        raise ValueError(f"uniforms must be [n][{SAMPLE_UNIFORMS}]")
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.float32, device=samples.device)
+    check("gsp_sample_ndf", lib.gsp_sample_ndf(
+        arr, nm, _ptr(samples, torch.int32, "samples"), n, _ptr(uniforms, torch.float32, "uniforms"),
+        _ptr(out, torch.float32, "out"), _ptr(status), _stream()))
+    return out
+
+
 def backward_workspace_bytes(materials) -> int:
     arr, nm = _mats(materials)
     return load().gsp_backward_workspace_bytes(arr, nm)

@@ -424,6 +424,150 @@ bool valid_material(const gsp_material& m) {
          m.tables && (reinterpret_cast<uintptr_t>(m.tables) & 15) == 0;
 }
 
+// -------------------------------------------------------------- sampling --
+// Hierarchical NDF importance sampling (Sec. 5.2).  LANES lanes per sample;
+// lane j holds ranks j and j + LANES (LANES >= R / 2) with their
+// constant factor c_r = fx[x,r] fy[y,r] flw(level)[r] and the summed-area-table
+// prefix sums at the current square's edges.  A step loads the prefix sums at
+// the two midpoints, forms the four quad averages per rank, sums them over
+// the lanes by an xor butterfly and takes the same choice on every lane.  The
+// step count is the maximum over the warp's samples, so the shuffles of a
+// warp stay in step whatever the materials.
+constexpr int kSampleMaxRank = 64;
+
+template <int LANES>
+__global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatParams mp,
+                                                    const gsp_sample_query* __restrict__ q,
+                                                    long long n, const float* __restrict__ u,
+                                                    float* __restrict__ out, uint32_t* status) {
+  constexpr int QPW = 32 / LANES;
+  constexpr int NC = 2;  // rank slots per lane
+  const int lane = threadIdx.x & 31, sub = lane / LANES, j = lane % LANES;
+  const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+  const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  for (long long base = warp_id * QPW; base < n; base += n_warps * QPW) {  // warp-uniform
+    const long long qi = base + sub;
+    const bool active = qi < n;
+    int4 dq = make_int4(0, 0, 0, 0);
+    if (active) dq = __ldg(reinterpret_cast<const int4*>(q) + qi);
+    const float level = __int_as_float(dq.z);
+    const uint32_t mi = static_cast<uint32_t>(dq.w);
+    const bool bad = active && (mi >= static_cast<uint32_t>(mp.n) || !isfinite(level));
+    const bool live = active && !bad;
+    const gsp_material& M = mp.m[live ? mi : 0];
+    const int R = M.rank, B = M.bins, N = M.N, L = M.levels;
+    const int x = dq.x & (N - 1), y = dq.y & (N - 1);
+    const float lev = live ? fminf(fmaxf(level, 0.0f), static_cast<float>(L - 1)) : 0.0f;
+    const int l0 = static_cast<int>(floorf(lev)), l1 = min(l0 + 1, L - 1);
+    const float f = lev - static_cast<float>(l0), g0 = 1.0f - f;
+    const float* flw = M.tables;
+    const float4* sats = reinterpret_cast<const float4*>(M.tables + flw_floats(L, R));
+    const float4* satt = sats + static_cast<size_t>(B + 1) * R;
+    // per rank slot: c_r and the prefix sums (hi, lo) at the square's edges
+    float c[NC], s0h[NC], s0l[NC], s1h[NC], s1l[NC], t0h[NC], t0l[NC], t1h[NC], t1l[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const int r = j + k * LANES;
+      c[k] = 0.f;
+      s0h[k] = s0l[k] = s1h[k] = s1l[k] = t0h[k] = t0l[k] = t1h[k] = t1l[k] = 0.f;
+      if (live && r < R) {
+        c[k] = __ldg(M.fx + static_cast<size_t>(x) * R + r) * __ldg(M.fy + static_cast<size_t>(y) * R + r) *
+               fmaf(f, __ldg(flw + l1 * R + r), g0 * __ldg(flw + l0 * R + r));
+        const float4 a = __ldg(sats + r), b = __ldg(sats + static_cast<size_t>(B) * R + r);
+        const float4 ct = __ldg(satt + r), dt = __ldg(satt + static_cast<size_t>(B) * R + r);
+        s0h[k] = a.x; s0l[k] = a.y; s1h[k] = b.x; s1l[k] = b.y;
+        t0h[k] = ct.x; t0l[k] = ct.y; t1h[k] = dt.x; t1l[k] = dt.y;
+      }
+    }
+    const float* uq = u + (live ? qi : 0) * GSP_SAMPLE_UNIFORMS;  // this sample's uniforms
+    const int my_steps = live ? 31 - __clz(B) : 0;  // B is a power of two
+    int steps = my_steps;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, o));
+    int s0 = 0, t0 = 0, sz = B;
+    float pmf = 1.0f, value = 0.0f;
+    for (int st = 0; st < steps; ++st) {
+      const bool go = st < my_steps;
+      const int half = sz >> 1, sm = s0 + half, tm = t0 + half;
+      const float inv = go ? 1.0f / static_cast<float>(half) : 0.0f;
+      float q4[4] = {0.f, 0.f, 0.f, 0.f};
+      float smh[NC], sml[NC], tmh[NC], tml[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const int r = j + k * LANES;
+        smh[k] = sml[k] = tmh[k] = tml[k] = 0.f;
+        if (go && r < R) {
+          const float4 ps = __ldg(sats + static_cast<size_t>(sm) * R + r);
+          const float4 pt = __ldg(satt + static_cast<size_t>(tm) * R + r);
+          smh[k] = ps.x; sml[k] = ps.y; tmh[k] = pt.x; tml[k] = pt.y;
+          const float sa = ((smh[k] - s0h[k]) + (sml[k] - s0l[k])) * inv;
+          const float sb = ((s1h[k] - smh[k]) + (s1l[k] - sml[k])) * inv;
+          const float ta = ((tmh[k] - t0h[k]) + (tml[k] - t0l[k])) * inv;
+          const float tb = ((t1h[k] - tmh[k]) + (t1l[k] - tml[k])) * inv;
+          const float ca = c[k] * sa, cb = c[k] * sb;
+          q4[0] = fmaf(ca, ta, q4[0]);
+          q4[1] = fmaf(ca, tb, q4[1]);
+          q4[2] = fmaf(cb, ta, q4[2]);
+          q4[3] = fmaf(cb, tb, q4[3]);
+        }
+      }
+#pragma unroll
+      for (int o = LANES / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q4[i] += __shfl_xor_sync(0xffffffffu, q4[i], o);
+      }
+      if (go) {
+        float p[4], tot = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          p[i] = fmaxf(q4[i], 0.0f);
+          tot += p[i];
+        }
+        int ch;
+        const float ust = __ldg(uq + st);
+        if (tot > 0.0f) {
+          const float target = ust * tot;
+          float cum = p[0];
+          ch = 0;
+          if (!(target < cum)) { cum += p[1]; ch = 1; }
+          if (ch == 1 && !(target < cum)) { cum += p[2]; ch = 2; }
+          if (ch == 2 && !(target < cum)) ch = 3;
+          if (p[ch] <= 0.0f) {  // rounding put the target past a zero quad: last positive one
+            ch = p[3] > 0.f ? 3 : p[2] > 0.f ? 2 : p[1] > 0.f ? 1 : 0;
+          }
+          pmf *= p[ch] / tot;
+        } else {
+          ch = min(3, static_cast<int>(ust * 4.0f));
+          pmf *= 0.25f;
+        }
+        value = q4[ch];
+        const bool s_hi = ch >= 2, t_hi = ch & 1;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          if (s_hi) { s0h[k] = smh[k]; s0l[k] = sml[k]; } else { s1h[k] = smh[k]; s1l[k] = sml[k]; }
+          if (t_hi) { t0h[k] = tmh[k]; t0l[k] = tml[k]; } else { t1h[k] = tmh[k]; t1l[k] = tml[k]; }
+        }
+        if (s_hi) s0 = sm;
+        if (t_hi) t0 = tm;
+        sz = half;
+      }
+    }
+    if (active && j == 0) {
+      float4 o;
+      if (bad) {
+        o = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                        __int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+        set_status(status, GSP_DEV_BAD_QUERY);
+      } else {
+        // rounded down, so that bin + u stays inside the bin for u < 1
+        o = make_float4(__fadd_rd(static_cast<float>(s0), __ldg(uq + 6)),
+                        __fadd_rd(static_cast<float>(t0), __ldg(uq + 7)), pmf, value);
+      }
+      reinterpret_cast<float4*>(out)[qi] = o;
+    }
+  }
+}
+
 int pick_lanes(const gsp_material* mats, int n_mats, const gsp_query_tuning* tn) {
   if (tn && tn->lanes_per_query) return tn->lanes_per_query;
   int rmax = 1;
@@ -625,6 +769,43 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
     k_suffix<<<grid_for(R, 64), 64, 0, s>>>(gp.dpt[i], h_grads[i].dft, h_mats[i].bins, R);
     GSP_CHECK_LAUNCH();
   }
+  return GSP_OK;
+}
+
+extern "C" int gsp_sample_ndf(const gsp_material* h_mats, int n_mats, const gsp_sample_query* d_q,
+                              int64_t n, const float* d_u, float* d_out, uint32_t* d_status,
+                              gsp_stream stream) {
+  if (!h_mats || n_mats < 1 || n_mats > GSP_MAX_MATERIALS || n < 0) return GSP_ERR_INVALID_ARG;
+  if (n > 0 && (!d_q || !d_u || !d_out || (reinterpret_cast<uintptr_t>(d_q) & 15) ||
+                (reinterpret_cast<uintptr_t>(d_u) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 15)))
+    return GSP_ERR_INVALID_ARG;
+  MatParams mp;
+  mp.n = n_mats;
+  int rmax = 1;
+  for (int i = 0; i < n_mats; ++i) {
+    const gsp_material& m = h_mats[i];
+    if (!valid_material(m)) return GSP_ERR_INVALID_ARG;
+    if (!is_pow2(m.bins) || m.bins < 2 || m.bins > 64 || m.rank > kSampleMaxRank)
+      return GSP_ERR_UNSUPPORTED;
+    mp.m[i] = m;
+    rmax = rmax > m.rank ? rmax : m.rank;
+  }
+  if (n == 0) return GSP_OK;
+  int lanes = 4;
+  while (lanes * 2 < rmax) lanes *= 2;  // two rank slots per lane (rmax <= 64)
+  const int threads = 256;
+  const long long per_cta = threads / 32 * (32 / lanes);
+  long long blocks = (n + per_cta - 1) / per_cta;
+  const long long cap = static_cast<long long>(sm_count()) * 8;
+  if (blocks > cap) blocks = cap;
+  cudaStream_t s = to_stream(stream);
+  switch (lanes) {
+    case 4: k_sample_ndf<4><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+    case 8: k_sample_ndf<8><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+    case 16: k_sample_ndf<16><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+    default: k_sample_ndf<32><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+  }
+  GSP_CHECK_LAUNCH();
   return GSP_OK;
 }
 

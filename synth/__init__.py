@@ -23,7 +23,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "QUERY_DTYPE", "splitmix64", "uniform", "normal", "flake_map", "brushed_map",
+    "QUERY_DTYPE", "SAMPLE_DTYPE", "splitmix64", "uniform", "normal", "flake_map", "brushed_map",
+    "sample_footprints", "sample_uniforms",
     "init_factors", "queries_integer", "queries_fractional", "queries_camera",
     "WORKLOADS",
 ]
@@ -39,6 +40,10 @@ QUERY_DTYPE = np.dtype([
     ("material", "<u4"),
 ])
 assert QUERY_DTYPE.itemsize == 32
+
+# Footprint of a hierarchical NDF sample: texel, level, material (16 bytes).
+SAMPLE_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("level", "<f4"), ("material", "<u4")])
+assert SAMPLE_DTYPE.itemsize == 16
 
 
 def splitmix64(z: np.ndarray) -> np.ndarray:
@@ -262,3 +267,21 @@ def make_map(w: dict) -> np.ndarray:
     if w["map"] == "flakes":
         return flake_map(w["N"], w["cells"], w["alpha"], w["seed"])
     return brushed_map(w["N"], w["sigma_x"], w["sigma_y"], w["scratches"], w["seed"])
+
+
+def sample_footprints(N: int, levels: int, n: int, seed: int, material: int = 0) -> np.ndarray:
+    """Footprints to sample: x, y ~ U{0..N-1}, level ~ U[0, levels-1]."""
+    u = uniform(seed, 15, 3 * n).reshape(n, 3)
+    s = np.zeros(n, dtype=SAMPLE_DTYPE)
+    s["x"] = np.minimum((u[:, 0] * N).astype(np.int64), N - 1)
+    s["y"] = np.minimum((u[:, 1] * N).astype(np.int64), N - 1)
+    s["level"] = (u[:, 2] * (levels - 1)).astype(np.float32)
+    s["material"] = material
+    return s
+
+
+def sample_uniforms(seed: int, n: int, k: int = 8) -> np.ndarray:
+    """[n][k] float32 uniforms in [0, 1) for the samplers (float64 draws rounded
+    to float32 and kept below 1)."""
+    u = uniform(seed, 16, n * k).astype(np.float32)
+    return np.minimum(u, np.float32(1.0 - 2.0 ** -24)).reshape(n, k)
