@@ -285,6 +285,26 @@ int gsp_sample_ndf(const gsp_material* h_mats, int n_mats, const gsp_sample_quer
                    int64_t n, const float* d_u, float* d_out, uint32_t* d_status,
                    gsp_stream stream);
 
+/* A range query at a fractional texel position: x, y in texel units (|x|,
+ * |y| < 2^30), the other fields as in gsp_query.  32 bytes. */
+typedef struct gsp_query_f {
+  float x, y;
+  float level, s0, s1, t0, t1;
+  uint32_t material;
+} gsp_query_f;
+
+/* gsp_range_query at fractional positions (Sec. 4.1: the NDF of an arbitrary
+ * footprint by interpolation between neighbouring footprint samples): the
+ * bilinear blend over the texels floor(x) + {0, 1}, floor(y) + {0, 1} (mod N)
+ * of their range queries, computed as one query with the fx and fy rows
+ * interpolated (the CP tensor is multilinear).  At integer positions the
+ * result equals gsp_range_query's.  A non-finite or too large x or y counts
+ * as a malformed query. */
+int gsp_range_query_interp(const gsp_material* h_mats, int n_mats, const gsp_query_f* d_q,
+                           int64_t n, float* d_out, uint32_t* d_status,
+                           const gsp_query_tuning* tuning, void* d_ws, size_t ws_bytes,
+                           gsp_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* a7 -- adjoint of the range query and the refinement step                  */
 /* ------------------------------------------------------------------------ */

@@ -214,3 +214,27 @@ def cp_range_query_adjoint(materials, q: np.ndarray, g: np.ndarray):
             G["fs"] += gi * np.outer(ws, fx[x] * fy[y] * L * T)
             G["ft"] += gi * np.outer(wt, fx[x] * fy[y] * L * S)
     return grads[0] if single else grads
+
+
+def cp_range_query_interp(materials, q: np.ndarray) -> np.ndarray:
+    """Range queries at fractional texel positions (Sec. 4.1: interpolation
+    between neighbouring footprint samples), by definition the bilinear blend
+    sum_{i,j in {0,1}} w_i(x) w_j(y) Q(floor(x) + i, floor(y) + j) of the
+    integer-position range queries (positions mod N)."""
+    x = q["x"].astype(np.float64)
+    y = q["y"].astype(np.float64)
+    x0, y0 = np.floor(x), np.floor(y)
+    wx, wy = x - x0, y - y0
+    out = np.zeros(len(q))
+    for i in (0, 1):
+        for j in (0, 1):
+            qi = np.zeros(len(q), dtype=[(k, q.dtype[k] if k not in ("x", "y") else "<i4")
+                                         for k in q.dtype.names])
+            for k in q.dtype.names:
+                if k not in ("x", "y"):
+                    qi[k] = q[k]
+            qi["x"] = (x0 + i).astype(np.int64)
+            qi["y"] = (y0 + j).astype(np.int64)
+            w = (wx if i else 1.0 - wx) * (wy if j else 1.0 - wy)
+            out += w * cp_range_query(materials, qi)
+    return out

@@ -8,13 +8,15 @@ package is its Python binding.  Build it with ``paper_2109_14807_gb300.build.bui
 from .api import (CPWorkspace, QueryMaterial, RangeQueryFn, adam_step, backward_workspace_bytes,
                   bin_normals, build_footprint_ndfs, build_query_tables, cp_decompose,
                   init_factors_to_device, new_status, queries_to_device, range_query,
-                  range_query_autograd, range_query_backward, sample_ndf, samples_to_device,
+                  range_query_autograd, range_query_backward, range_query_interp, sample_ndf,
+                  samples_to_device,
                   selftest_wait_timeout, status_bits)
 
 __all__ = [
     "CPWorkspace", "QueryMaterial", "RangeQueryFn", "adam_step", "backward_workspace_bytes",
     "bin_normals", "build_footprint_ndfs", "build_query_tables", "cp_decompose",
     "init_factors_to_device", "new_status", "queries_to_device", "range_query",
-    "range_query_autograd", "range_query_backward", "sample_ndf", "samples_to_device",
+    "range_query_autograd", "range_query_backward", "range_query_interp", "sample_ndf",
+    "samples_to_device",
     "selftest_wait_timeout", "status_bits",
 ]

@@ -266,6 +266,26 @@ def sample_ndf(materials, samples: torch.Tensor, uniforms: torch.Tensor, out=Non
     return out
 
 
+def range_query_interp(materials, queries: torch.Tensor, out=None, status=None, tuning=None,
+                       workspace=None) -> torch.Tensor:
+    """Range queries at fractional texel positions (descriptors with float x, y,
+    int32 [n][8] words): the bilinear blend of the four neighbouring
+    footprints' range queries."""
+    lib = load()
+    arr, nm = _mats(materials)
+    n = queries.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=queries.device)
+    if workspace is None:
+        workspace = torch.empty(16, dtype=torch.uint8, device=queries.device)
+    tn = QueryTuning(*tuning) if tuning is not None else None
+    check("gsp_range_query_interp", lib.gsp_range_query_interp(
+        arr, nm, _ptr(queries, torch.int32, "queries"), n, _ptr(out, torch.float32, "out"),
+        _ptr(status), ctypes.byref(tn) if tn is not None else None, _ptr(workspace),
+        workspace.numel(), _stream()))
+    return out
+
+
 def backward_workspace_bytes(materials) -> int:
     arr, nm = _mats(materials)
     return load().gsp_backward_workspace_bytes(arr, nm)

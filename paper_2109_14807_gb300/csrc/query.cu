@@ -157,7 +157,11 @@ __device__ __forceinline__ float sat_mean(const float4* __restrict__ sat, int R,
 // combined in the order of a 32-lane xor butterfly.  Lane j of a group of
 // LANES holds the conceptual lanes j + k*LANES (k < 32/LANES) in registers and
 // performs the butterfly steps of offset >= LANES locally, the rest by shuffle.
-template <int LANES>
+// FXY: the descriptor's x, y are floats (gsp_query_f) and the fx, fy rows are
+// interpolated linearly between floor(x) and floor(x) + 1 (mod N): since the
+// CP tensor is multilinear this is the bilinear blend of the four
+// neighbouring footprints' range queries (Sec. 4.1 spatial interpolation).
+template <int LANES, bool FXY>
 __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ MatParams mp,
                                                      const gsp_query* __restrict__ q,
                                                      long long n, float* __restrict__ out,
@@ -204,6 +208,21 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           const float4* satt = sats + static_cast<size_t>(M.bins + 1) * R;
           const float* __restrict__ fxr = M.fx + static_cast<size_t>(t.x) * R;
           const float* __restrict__ fyr = M.fy + static_cast<size_t>(t.y) * R;
+          const float* __restrict__ fxr1 = fxr;
+          const float* __restrict__ fyr1 = fyr;
+          float wx = 0.f, wy = 0.f;
+          if constexpr (FXY) {
+            const float xf = __int_as_float(d.x), yf = __int_as_float(d.y);
+            if (!(fabsf(xf) < 1073741824.0f) || !(fabsf(yf) < 1073741824.0f)) bad = true;
+            const float x0 = bad ? 0.f : floorf(xf), y0 = bad ? 0.f : floorf(yf);
+            wx = bad ? 0.f : xf - x0;
+            wy = bad ? 0.f : yf - y0;
+            const int N = M.N, ix = static_cast<int>(x0), iy = static_cast<int>(y0);
+            fxr = M.fx + static_cast<size_t>(ix & (N - 1)) * R;
+            fxr1 = M.fx + static_cast<size_t>((ix + 1) & (N - 1)) * R;
+            fyr = M.fy + static_cast<size_t>(iy & (N - 1)) * R;
+            fyr1 = M.fy + static_cast<size_t>((iy + 1) & (N - 1)) * R;
+          }
           const float* __restrict__ fl0 = flw + static_cast<size_t>(t.l0) * R;
           const float* __restrict__ fl1 = flw + static_cast<size_t>(t.l1) * R;
           const float g0 = 1.0f - t.f;
@@ -215,7 +234,12 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
                 const float lv = fmaf(t.f, __ldg(fl1 + r), g0 * __ldg(fl0 + r));
                 const float S = sat_mean(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
                 const float T = sat_mean(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
-                acc[k] = fmaf(__ldg(fxr + r) * __ldg(fyr + r), lv * S * T, acc[k]);
+                float xv = __ldg(fxr + r), yv = __ldg(fyr + r);
+                if constexpr (FXY) {
+                  xv = fmaf(wx, __ldg(fxr1 + r) - xv, xv);
+                  yv = fmaf(wy, __ldg(fyr1 + r) - yv, yv);
+                }
+                acc[k] = fmaf(xv * yv, lv * S * T, acc[k]);
               }
             }
           }
@@ -629,10 +653,12 @@ extern "C" int gsp_build_query_tables(const gsp_material* h_mat, gsp_stream stre
   return GSP_OK;
 }
 
-extern "C" int gsp_range_query(const gsp_material* h_mats, int n_mats, const gsp_query* d_q,
-                               int64_t n, float* d_out, uint32_t* d_status,
-                               const gsp_query_tuning* tuning, void* d_ws, size_t ws_bytes,
-                               gsp_stream stream) {
+namespace gsp {
+namespace {
+template <bool FXY>
+int range_query_launch(const gsp_material* h_mats, int n_mats, const gsp_query* d_q, int64_t n,
+                       float* d_out, uint32_t* d_status, const gsp_query_tuning* tuning,
+                       void* d_ws, size_t ws_bytes, gsp_stream stream) {
   if (!h_mats || n_mats < 1 || n_mats > GSP_MAX_MATERIALS || n < 0) return GSP_ERR_INVALID_ARG;
   if (n > 0 && (!d_q || !d_out || (reinterpret_cast<uintptr_t>(d_q) & 15))) return GSP_ERR_INVALID_ARG;
   MatParams mp;
@@ -664,16 +690,16 @@ extern "C" int gsp_range_query(const gsp_material* h_mats, int n_mats, const gsp
   prof_begin(PROF_QUERY, s);
   switch (lanes) {
     case 4:
-      k_range_query<4><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      k_range_query<4, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
       break;
     case 8:
-      k_range_query<8><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      k_range_query<8, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
       break;
     case 16:
-      k_range_query<16><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      k_range_query<16, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
       break;
     case 32:
-      k_range_query<32><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      k_range_query<32, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
       break;
     default:
       return GSP_ERR_INVALID_ARG;
@@ -681,6 +707,25 @@ extern "C" int gsp_range_query(const gsp_material* h_mats, int n_mats, const gsp
   prof_end(PROF_QUERY, s);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
+}
+}  // namespace
+}  // namespace gsp
+
+extern "C" int gsp_range_query(const gsp_material* h_mats, int n_mats, const gsp_query* d_q,
+                               int64_t n, float* d_out, uint32_t* d_status,
+                               const gsp_query_tuning* tuning, void* d_ws, size_t ws_bytes,
+                               gsp_stream stream) {
+  return range_query_launch<false>(h_mats, n_mats, d_q, n, d_out, d_status, tuning, d_ws,
+                                   ws_bytes, stream);
+}
+
+extern "C" int gsp_range_query_interp(const gsp_material* h_mats, int n_mats,
+                                      const gsp_query_f* d_q, int64_t n, float* d_out,
+                                      uint32_t* d_status, const gsp_query_tuning* tuning,
+                                      void* d_ws, size_t ws_bytes, gsp_stream stream) {
+  // same 32-byte layout; the kernel reads words 0 and 1 as floats
+  return range_query_launch<true>(h_mats, n_mats, reinterpret_cast<const gsp_query*>(d_q), n,
+                                  d_out, d_status, tuning, d_ws, ws_bytes, stream);
 }
 
 extern "C" size_t gsp_backward_workspace_bytes(const gsp_material* h_mats, int n_mats) {

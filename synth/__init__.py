@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "QUERY_DTYPE", "SAMPLE_DTYPE", "splitmix64", "uniform", "normal", "flake_map", "brushed_map",
-    "sample_footprints", "sample_uniforms",
+    "sample_footprints", "sample_uniforms", "QUERY_F_DTYPE", "queries_fractional_xy",
     "init_factors", "queries_integer", "queries_fractional", "queries_camera",
     "WORKLOADS",
 ]
@@ -40,6 +40,14 @@ QUERY_DTYPE = np.dtype([
     ("material", "<u4"),
 ])
 assert QUERY_DTYPE.itemsize == 32
+
+# A range query at a fractional texel position (same layout, float x, y).
+QUERY_F_DTYPE = np.dtype([
+    ("x", "<f4"), ("y", "<f4"), ("level", "<f4"),
+    ("s0", "<f4"), ("s1", "<f4"), ("t0", "<f4"), ("t1", "<f4"),
+    ("material", "<u4"),
+])
+assert QUERY_F_DTYPE.itemsize == 32
 
 # Footprint of a hierarchical NDF sample: texel, level, material (16 bytes).
 SAMPLE_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("level", "<f4"), ("material", "<u4")])
@@ -285,3 +293,18 @@ def sample_uniforms(seed: int, n: int, k: int = 8) -> np.ndarray:
     to float32 and kept below 1)."""
     u = uniform(seed, 16, n * k).astype(np.float32)
     return np.minimum(u, np.float32(1.0 - 2.0 ** -24)).reshape(n, k)
+
+
+def queries_fractional_xy(N: int, levels: int, bins: int, n: int, seed: int,
+                          material: int = 0) -> np.ndarray:
+    """Queries at fractional texel positions: x, y ~ U[-N, 2N) (exercising the
+    wrap), fractional levels and fractional bin rectangles as in
+    queries_fractional."""
+    base = queries_fractional(N, levels, bins, n, seed, frac_level=True, material=material)
+    u = uniform(seed, 17, 2 * n).reshape(n, 2)
+    q = np.zeros(n, dtype=QUERY_F_DTYPE)
+    for k in ("level", "s0", "s1", "t0", "t1", "material"):
+        q[k] = base[k]
+    q["x"] = (u[:, 0] * 3 * N - N).astype(np.float32)
+    q["y"] = (u[:, 1] * 3 * N - N).astype(np.float32)
+    return q
