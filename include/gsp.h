@@ -306,6 +306,45 @@ int gsp_range_query_interp(const gsp_material* h_mats, int n_mats, const gsp_que
                            gsp_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* f4 -- environment-lighting prefiltering queries (Sec. 5.4)                */
+/* ------------------------------------------------------------------------ */
+
+/* A spherical Gaussian lobe of the environment light (Sec. 5.4):
+ * G(v) = amplitude * exp(sharpness * (dot(v, axis) - 1)), axis a unit vector. */
+typedef struct gsp_sg {
+  float axis[3];
+  float amplitude;
+  float sharpness;
+  float pad[3];
+} gsp_sg; /* 32 bytes */
+
+/* One shading record: footprint (x, y, level, material as in gsp_query), the
+ * unit outgoing direction wo, and the index of the SG lobe the light sampling
+ * chose.  32 bytes. */
+typedef struct gsp_env_record {
+  int32_t x, y;
+  float level;
+  float wo[3];
+  uint32_t sg;
+  uint32_t material;
+} gsp_env_record;
+
+/* Range-query descriptors for environment-light prefiltering (Sec. 5.4), one
+ * per record, written to d_q (then answered by gsp_range_query):
+ *   theta = arccos((ln eps - ln A) / lambda + 1)       (compact-eps support of the lobe;
+ *           theta = pi when the argument is below -1, theta = 0 when A <= eps)
+ *   Q     = B * theta / pi                             (side of the square in bins; the
+ *                                                      paper's 256-pixel images -> B bins)
+ *   h     = normalize(wo + axis), centre (s, t) = ((h.x + 1) B / 2, (h.y + 1) B / 2)
+ *   range [s - Q/2, s + Q/2] x [t - Q/2, t + Q/2]   (clamped by the query itself).
+ * B is the bin count of the record's material (h_mats as for gsp_range_query).
+ * A record whose SG index or material is out of range, or with wo = -axis,
+ * gets level = NaN (the query then reports GSP_DEV_BAD_QUERY). */
+int gsp_env_queries(const gsp_material* h_mats, int n_mats, const gsp_sg* d_sgs, int n_sgs,
+                    const gsp_env_record* d_rec, int64_t n, float eps, gsp_query* d_q,
+                    gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* a7 -- adjoint of the range query and the refinement step                  */
 /* ------------------------------------------------------------------------ */
 

@@ -238,3 +238,36 @@ def cp_range_query_interp(materials, q: np.ndarray) -> np.ndarray:
             w = (wx if i else 1.0 - wx) * (wy if j else 1.0 - wy)
             out += w * cp_range_query(materials, qi)
     return out
+
+
+def sg_support_angle(amplitude: np.ndarray, sharpness: np.ndarray, eps: float = 0.3) -> np.ndarray:
+    """Compact-eps support of a spherical Gaussian A exp(lambda (cos v - 1))
+    (Sec. 5.4): the angle theta inside which the lobe exceeds eps,
+    theta = arccos((ln eps - ln A) / lambda + 1); pi when the argument is below
+    -1 (the whole sphere), 0 when A <= eps (nowhere)."""
+    A = np.asarray(amplitude, dtype=np.float64)
+    lam = np.asarray(sharpness, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = (np.log(eps) - np.log(A)) / lam + 1.0
+    theta = np.arccos(np.clip(c, -1.0, 1.0))
+    return np.where(A > eps, theta, 0.0)
+
+
+def env_queries(sgs: np.ndarray, records: np.ndarray, bins, eps: float = 0.3) -> np.ndarray:
+    """Range-query descriptors of Sec. 5.4 for shading records: the square of
+    side Q = B theta / pi (the paper's 256-pixel image -> B bins) centred on
+    the bin of the half vector h = normalize(wo + axis).  `bins[m]` is the bin
+    count of material m.  Returns a structured array of queries (FP64 ends)."""
+    bins = np.asarray(bins)
+    g = sgs[records["sg"]]
+    B = bins[records["material"]].astype(np.float64)
+    h = records["wo"].astype(np.float64) + g["axis"].astype(np.float64)
+    h = h / np.linalg.norm(h, axis=1)[:, None]
+    theta = sg_support_angle(g["amplitude"], g["sharpness"], eps)
+    side = B * theta / np.pi
+    sc, tc = (h[:, 0] + 1.0) * B / 2, (h[:, 1] + 1.0) * B / 2
+    q = np.zeros(len(records), dtype=[("x", "<i8"), ("y", "<i8"), ("level", "<f8"), ("s0", "<f8"),
+                                      ("s1", "<f8"), ("t0", "<f8"), ("t1", "<f8"), ("material", "<u4")])
+    q["x"], q["y"], q["level"], q["material"] = records["x"], records["y"], records["level"], records["material"]
+    q["s0"], q["s1"], q["t0"], q["t1"] = sc - side / 2, sc + side / 2, tc - side / 2, tc + side / 2
+    return q

@@ -80,6 +80,8 @@ _SIGS = {
                                 POINTER(QueryTuning), c_void_p, c_size_t, c_void_p]),
     "gsp_sample_ndf": (c_int, [POINTER(Material), c_int, c_void_p, c_int64, c_void_p, c_void_p,
                                c_void_p, c_void_p]),
+    "gsp_env_queries": (c_int, [POINTER(Material), c_int, c_void_p, c_int, c_void_p, c_int64,
+                                c_float, c_void_p, c_void_p]),
     "gsp_range_query_interp": (c_int, [POINTER(Material), c_int, c_void_p, c_int64, c_void_p,
                                        c_void_p, POINTER(QueryTuning), c_void_p, c_size_t,
                                        c_void_p]),

@@ -286,6 +286,23 @@ def range_query_interp(materials, queries: torch.Tensor, out=None, status=None, 
     return out
 
 
+def env_queries(materials, sgs: torch.Tensor, records: torch.Tensor, eps: float = 0.3,
+                out=None) -> torch.Tensor:
+    """Range-query descriptors for environment-light prefiltering (Sec. 5.4):
+    `sgs` float32 [n_sg][8] (axis x, y, z, amplitude, sharpness, 3 pad),
+    `records` int32 [n][8] words of gsp_env_record; returns int32 [n][8]
+    query descriptors for range_query."""
+    lib = load()
+    arr, nm = _mats(materials)
+    n = records.shape[0]
+    if out is None:
+        out = torch.empty((n, QUERY_WORDS), dtype=torch.int32, device=records.device)
+    check("gsp_env_queries", lib.gsp_env_queries(
+        arr, nm, _ptr(sgs, torch.float32, "sgs"), sgs.shape[0], _ptr(records, torch.int32, "records"),
+        n, float(eps), _ptr(out, torch.int32, "out"), _stream()))
+    return out
+
+
 def backward_workspace_bytes(materials) -> int:
     arr, nm = _mats(materials)
     return load().gsp_backward_workspace_bytes(arr, nm)

@@ -854,6 +854,65 @@ extern "C" int gsp_sample_ndf(const gsp_material* h_mats, int n_mats, const gsp_
   return GSP_OK;
 }
 
+// ------------------------------------------------------- env queries --
+// Sec. 5.4: the compact-eps support angle of the chosen SG lobe gives the
+// side of a square angular range centred on the half vector's bin.
+struct EnvParams {
+  int bins[GSP_MAX_MATERIALS];
+  int n_mats;
+};
+
+__global__ void k_env_queries(const EnvParams ep, const gsp_sg* __restrict__ sgs, int n_sgs,
+                              const gsp_env_record* __restrict__ rec, long long n, float eps,
+                              gsp_query* __restrict__ q) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const gsp_env_record r = rec[i];
+  gsp_query d;
+  d.x = r.x;
+  d.y = r.y;
+  d.level = r.level;
+  d.material = r.material;
+  const bool ok_idx = r.sg < static_cast<uint32_t>(n_sgs) && r.material < static_cast<uint32_t>(ep.n_mats);
+  const gsp_sg g = sgs[ok_idx ? r.sg : 0];
+  const float B = static_cast<float>(ep.bins[ok_idx ? r.material : 0]);
+  const float hx = r.wo[0] + g.axis[0], hy = r.wo[1] + g.axis[1], hz = r.wo[2] + g.axis[2];
+  const float hn = sqrtf(hx * hx + hy * hy + hz * hz);
+  float theta;
+  if (!(g.amplitude > eps)) {
+    theta = 0.0f;  // the lobe never exceeds eps: a point query
+  } else {
+    const float c = (logf(eps) - logf(g.amplitude)) / g.sharpness + 1.0f;
+    theta = c <= -1.0f ? 3.14159265358979f : acosf(fminf(c, 1.0f));
+  }
+  const float side = B * theta / 3.14159265358979f;
+  const float sc = (hx / hn + 1.0f) * 0.5f * B, tc = (hy / hn + 1.0f) * 0.5f * B;
+  d.s0 = sc - 0.5f * side;
+  d.s1 = sc + 0.5f * side;
+  d.t0 = tc - 0.5f * side;
+  d.t1 = tc + 0.5f * side;
+  if (!ok_idx || !(hn > 0.0f)) d.level = __int_as_float(0x7fc00000);
+  q[i] = d;
+}
+
+extern "C" int gsp_env_queries(const gsp_material* h_mats, int n_mats, const gsp_sg* d_sgs,
+                               int n_sgs, const gsp_env_record* d_rec, int64_t n, float eps,
+                               gsp_query* d_q, gsp_stream stream) {
+  if (!h_mats || n_mats < 1 || n_mats > GSP_MAX_MATERIALS || n < 0 || n_sgs < 1 || !(eps > 0.0f))
+    return GSP_ERR_INVALID_ARG;
+  if (n > 0 && (!d_sgs || !d_rec || !d_q)) return GSP_ERR_INVALID_ARG;
+  EnvParams ep;
+  ep.n_mats = n_mats;
+  for (int i = 0; i < n_mats; ++i) {
+    if (h_mats[i].bins < 1) return GSP_ERR_INVALID_ARG;
+    ep.bins[i] = h_mats[i].bins;
+  }
+  if (n == 0) return GSP_OK;
+  k_env_queries<<<grid_for(n, 256), 256, 0, to_stream(stream)>>>(ep, d_sgs, n_sgs, d_rec, n, eps, d_q);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
 // ------------------------------------------------ no-allocation backward --
 // Fixed device scratch for gsp_range_query_backward_noalloc: the prefix-sum
 // gradient tables of the adjoint, for callers that cannot allocate.  Every

@@ -25,6 +25,7 @@ import numpy as np
 __all__ = [
     "QUERY_DTYPE", "SAMPLE_DTYPE", "splitmix64", "uniform", "normal", "flake_map", "brushed_map",
     "sample_footprints", "sample_uniforms", "QUERY_F_DTYPE", "queries_fractional_xy",
+    "SG_DTYPE", "ENV_RECORD_DTYPE", "env_lobes", "env_records",
     "init_factors", "queries_integer", "queries_fractional", "queries_camera",
     "WORKLOADS",
 ]
@@ -48,6 +49,14 @@ QUERY_F_DTYPE = np.dtype([
     ("material", "<u4"),
 ])
 assert QUERY_F_DTYPE.itemsize == 32
+
+# A spherical Gaussian lobe of an environment light and a shading record
+# choosing one (32 bytes each).
+SG_DTYPE = np.dtype([("axis", "<f4", (3,)), ("amplitude", "<f4"), ("sharpness", "<f4"),
+                     ("pad", "<f4", (3,))])
+ENV_RECORD_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("level", "<f4"), ("wo", "<f4", (3,)),
+                             ("sg", "<u4"), ("material", "<u4")])
+assert SG_DTYPE.itemsize == 32 and ENV_RECORD_DTYPE.itemsize == 32
 
 # Footprint of a hierarchical NDF sample: texel, level, material (16 bytes).
 SAMPLE_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("level", "<f4"), ("material", "<u4")])
@@ -308,3 +317,40 @@ def queries_fractional_xy(N: int, levels: int, bins: int, n: int, seed: int,
     q["x"] = (u[:, 0] * 3 * N - N).astype(np.float32)
     q["y"] = (u[:, 1] * 3 * N - N).astype(np.float32)
     return q
+
+
+def _hemisphere(u1, u2):
+    """Unit vectors uniform on the upper hemisphere (z >= 0)."""
+    z = u1
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = 2.0 * math.pi * u2
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def env_lobes(n: int, seed: int) -> np.ndarray:
+    """SG lobes of an environment light: axes uniform on the upper hemisphere,
+    amplitude log-uniform in [0.1, 10], sharpness log-uniform in [1, 1000]."""
+    u = uniform(seed, 18, 4 * n).reshape(n, 4)
+    g = np.zeros(n, dtype=SG_DTYPE)
+    g["axis"] = _hemisphere(u[:, 0], u[:, 1]).astype(np.float32)
+    g["amplitude"] = np.exp(math.log(0.1) + u[:, 2] * math.log(100.0)).astype(np.float32)
+    g["sharpness"] = np.exp(u[:, 3] * math.log(1000.0)).astype(np.float32)
+    return g
+
+
+def env_records(materials: list, n: int, n_sg: int, seed: int) -> np.ndarray:
+    """Shading records over several materials ((N, levels, bins) tuples):
+    uniform footprints with fractional levels, outgoing directions uniform on
+    the upper hemisphere, SG lobe indices uniform."""
+    u = uniform(seed, 19, 7 * n).reshape(n, 7)
+    r = np.zeros(n, dtype=ENV_RECORD_DTYPE)
+    m = np.minimum((u[:, 0] * len(materials)).astype(np.int64), len(materials) - 1)
+    Ns = np.array([mt[0] for mt in materials])[m]
+    Ls = np.array([mt[1] for mt in materials])[m]
+    r["x"] = np.minimum((u[:, 1] * Ns).astype(np.int64), Ns - 1)
+    r["y"] = np.minimum((u[:, 2] * Ns).astype(np.int64), Ns - 1)
+    r["level"] = (u[:, 3] * (Ls - 1)).astype(np.float32)
+    r["wo"] = _hemisphere(u[:, 4], u[:, 5]).astype(np.float32)
+    r["sg"] = np.minimum((u[:, 6] * n_sg).astype(np.int64), n_sg - 1)
+    r["material"] = m
+    return r
