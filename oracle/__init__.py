@@ -12,7 +12,10 @@ Decomposition, arXiv 2109.14807):
 
 * ``ndf``   -- normal binning and exhaustive multi-level footprint histograms
                (Sec. 4.1), the normalised NDF tensor;
-* ``cp``    -- CP decomposition by alternating least squares (Sec. 4.2, Eq. 3);
+* ``cp``    -- CP decomposition by alternating least squares (Sec. 4.2, Eq. 3),
+               with the MTTKRP on the dense tensor, streamed level by level,
+               or in the structured form that moves the footprint window onto
+               the spatial factors (exact, O(N^2 L R));
 * ``query`` -- point query (Sec. 4.3, Eq. 4), range query through 1D summed-area
                tables (Sec. 4.4, Eq. 5 and the Appendix proposition), the dense
                brute-force range average it must equal, and the adjoint of the

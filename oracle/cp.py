@@ -82,7 +82,8 @@ def fit_gram(normX2: float, lam: np.ndarray, factors, M_last: np.ndarray) -> flo
 
 
 def cp_als(X, rank: int, init, sweeps: int, tol: float = 0.0, fit_method: str = "explicit"):
-    """CP-ALS on a dense numpy tensor or on a FootprintTensor.  `init` is a list
+    """CP-ALS on a dense numpy tensor, a FootprintTensor or a
+    StructuredFootprint.  `init` is a list
     of one [I_m][rank] matrix per mode.  Returns (lambda, factors, fits), one fit
     per sweep done; fit_method "gram" uses fit_gram instead of the residual."""
     dense = isinstance(X, np.ndarray)
@@ -158,6 +159,97 @@ class FootprintTensor:
     def dense_logical(self) -> np.ndarray:
         T = np.stack([self.slice(l) for l in range(self.levels)])
         return np.transpose(T, (2, 1, 0, 3, 4))
+
+
+class StructuredFootprint:
+    """The normalised footprint tensor of FootprintTensor (logical modes x, y,
+    l, s, t; T = H_l * c_l with c_l = B^2/(4*4^l), or 1 for raw counts) held
+    only through its bin map s, t [y][x], never as counts.
+
+    Sec. 4.1 builds every level slice as a box sum of the texel -> bin one-hot
+    E: H_l[y, x, s, t] counts the texels u of the window W_l(x, y) with bin
+    (s, t).  Texel u lies in the window of column x exactly when x = u + a_l - i
+    (mod N) for some i < 2^l, so a contraction of T with a spatial factor moves
+    the window from the tensor onto the factor:
+        alpha_l(u, r) = sum_{i < 2^l} fx[(u + a_l - i) mod N, r]   (beta_l: fy).
+    With h(u, r) = fs[s_u, r] ft[t_u, r] the five MTTKRPs are
+        M_x[x, r] = sum_l c_l fl[l, r] sum_{i < 2^l} rho_l((x - a_l + i) mod N, r),
+                    rho_l(u_x, r) = sum_{u_y} h(u, r) beta_l(u_y, r);
+        M_y        the same with x and y exchanged (sigma_l from alpha_l);
+        M_l[l, r] = c_l sum_u h(u, r) alpha_l(u_x, r) beta_l(u_y, r);
+        M_s[s, r] = sum_{u: s_u = s} ft[t_u, r] P(u, r),
+                    P(u, r) = sum_l c_l fl[l, r] alpha_l(u_x, r) beta_l(u_y, r);
+        M_t[t, r] = sum_{u: t_u = t} fs[s_u, r] P(u, r).
+    These are the sums of FootprintTensor.mttkrp taken in another order, at
+    O(N^2 L R) operations instead of O(N^2 L B^2 R).  ||T||^2 comes from the
+    exact integer sums of squares of ndf.level_sumsq (or is passed in)."""
+
+    def __init__(self, s: np.ndarray, t: np.ndarray, levels: int, bins: int,
+                 raw_counts: bool = False, norm2: float | None = None):
+        self.s = np.asarray(s, dtype=np.int64)
+        self.t = np.asarray(t, dtype=np.int64)
+        self.N = self.s.shape[0]
+        self.levels = levels
+        self.bins = bins
+        self.scale = [1.0 if raw_counts else bins * bins / (4.0 * float(4 ** l)) for l in range(levels)]
+        self.shape = (self.N, self.N, levels, bins, bins)
+        self._norm2 = norm2
+
+    def window_adjoint(self, f: np.ndarray, l: int) -> np.ndarray:
+        """alpha_l [N][R] of a spatial factor f [N][R]."""
+        N, w = self.N, 1 << l
+        a = w // 2
+        u = np.arange(N)
+        out = np.zeros_like(f)
+        for i in range(w):
+            out += f[(u + a - i) % N]
+        return out
+
+    def window(self, g: np.ndarray, l: int) -> np.ndarray:
+        """sum_{i < 2^l} g[(x - a_l + i) mod N] for every x: the footprint window."""
+        N, w = self.N, 1 << l
+        a = w // 2
+        x = np.arange(N)
+        out = np.zeros_like(g)
+        for i in range(w):
+            out += g[(x - a + i) % N]
+        return out
+
+    def norm2(self) -> float:
+        if self._norm2 is None:
+            from . import ndf
+            self._norm2 = float(sum(ndf.level_sumsq(self.s, self.t, l, self.bins) * self.scale[l] ** 2
+                                    for l in range(self.levels)))
+        return self._norm2
+
+    def mttkrp(self, A, n: int) -> np.ndarray:
+        fx, fy, fl, fs, ft = A
+        L = self.levels
+        h = fs[self.s] * ft[self.t]  # [y][x][R]
+        if n in (0, 1, 2):
+            alpha = [self.window_adjoint(fx, l) for l in range(L)]
+            beta = [self.window_adjoint(fy, l) for l in range(L)]
+        if n == 0:
+            return sum(self.scale[l] * fl[l] * self.window(np.einsum("yxr,yr->xr", h, beta[l]), l)
+                       for l in range(L))
+        if n == 1:
+            return sum(self.scale[l] * fl[l] * self.window(np.einsum("yxr,xr->yr", h, alpha[l]), l)
+                       for l in range(L))
+        if n == 2:
+            return np.stack([self.scale[l] * np.einsum("yxr,xr,yr->r", h, alpha[l], beta[l])
+                             for l in range(L)])
+        P = np.zeros(h.shape)
+        for l in range(L):
+            al = self.window_adjoint(fx, l)
+            be = self.window_adjoint(fy, l)
+            P += self.scale[l] * fl[l] * al[None, :, :] * be[:, None, :]
+        key, other = (self.s, ft[self.t]) if n == 3 else (self.t, fs[self.s])
+        M = np.zeros((self.bins, P.shape[2]))
+        np.add.at(M, key.ravel(), (other * P).reshape(-1, P.shape[2]))
+        return M
+
+    def fit(self, lam: np.ndarray, A) -> float:
+        raise ValueError("StructuredFootprint has no explicit residual: use fit_method='gram'")
 
 
 def to_material(lam: np.ndarray, factors) -> dict:

@@ -82,6 +82,23 @@ def level_histograms(s: np.ndarray, t: np.ndarray, level: int, bins: int) -> np.
     return _cyclic_window_sum(_cyclic_window_sum(onehot, 1, w, a), 0, w, a)
 
 
+def level_sumsq(s: np.ndarray, t: np.ndarray, level: int, bins: int, chunk: int = 32) -> int:
+    """Sum over every footprint (x, y) and bin of H_l[y][x][s][t]^2, exact.  The
+    same separable window sums as level_histograms, taken over a few occupied
+    bins at a time (a bin holding no texel has zero counts everywhere), so that
+    the largest maps fit in host memory."""
+    flat = s.astype(np.int64) * bins + t
+    occupied = np.unique(flat)
+    w, a = 1 << level, window_offset(level)
+    total = 0
+    for i in range(0, len(occupied), chunk):
+        ids = occupied[i:i + chunk]
+        onehot = (flat[:, :, None] == ids[None, None, :]).astype(np.int64)
+        H = _cyclic_window_sum(_cyclic_window_sum(onehot, 1, w, a), 0, w, a)
+        total += int(np.sum(H * H))
+    return total
+
+
 def footprint_histograms(s: np.ndarray, t: np.ndarray, levels: int, bins: int) -> np.ndarray:
     """All levels, int64 array [levels][y][x][s][t]."""
     N = s.shape[0]
