@@ -58,6 +58,10 @@ def parse_args():
                         "autotuner's choice")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--report-precisions", default="fp32,tf32,bf16,bf16_1x,structured",
+                   help="precisions the precision report covers (comma-separated)")
+    p.add_argument("--report-workloads", default="brushed512,flakes1024",
+                   help="workloads the precision report covers (comma-separated)")
     p.add_argument("--precision-report", action="store_true",
                    help="instead of the step: CP-ALS fit error vs the FP64 oracle and sweep time "
                         "per MTTKRP precision on the 512^2 precision workload, and the sweep time "
@@ -380,7 +384,7 @@ def run_gsp(args, rank, world):
               for i, name in enumerate(["ndf_build_ms", "als_sweep_ms", "tables_ms",
                                         "range_query_ms", "adjoint_adam_ms"])}
     prof = {}
-    for pid in range(11):
+    for pid in range(15):
         n_l = _lib.c_int64()
         ms = _lib.c_double()
         _lib.check("gsp_profile_read", lib.gsp_profile_read(pid, n_l, ms))
@@ -526,15 +530,20 @@ def precision_report(args):
     ref = np.loadtxt(GOLDEN_FITS, comments="#")[:, 1]
     out = {"metric": "CP-ALS fit error vs FP64 oracle and sweep time per MTTKRP precision",
            "data": "synthetic", "variants": {}}
-    for wname in ("brushed512", "flakes1024"):
+    for wname in args.report_workloads.split(","):
         w = synth.WORKLOADS[wname]
         N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
         m = torch.from_numpy(synth.make_map(w)).cuda()
         init = synth.init_factors(N, L, B, R, 2000 + w["seed"])
-        for prec in ("fp32", "tf32", "bf16", "bf16_1x"):
+        for prec in args.report_precisions.split(","):
             ws = g.CPWorkspace(N, L, B, R, prec)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
             ws.prepare(normal_xy=m)
+            b.record()
+            torch.cuda.synchronize()
             rec = out["variants"].setdefault(prec, {})
+            prep_ms = a.elapsed_time(b)
             if wname == "brushed512":
                 f = g.init_factors_to_device(init)
                 fits, _ = ws.sweeps(f, w["sweeps"])
@@ -551,10 +560,46 @@ def precision_report(args):
             b.record()
             torch.cuda.synchronize()
             rec[wname]["sweep_ms"] = round(a.elapsed_time(b) / 5, 3)
+            rec[wname]["prepare_ms"] = round(prep_ms, 3)
+            rec[wname]["workspace_mb"] = round(ws.buf.numel() / 2 ** 20, 1)
+            if prec == "structured":
+                rec[wname]["kernels"] = structured_kernels(ws, f, w)
             del ws
             torch.cuda.empty_cache()
     out["oracle_final_fit_brushed512"] = float(ref[-1])
     print(json.dumps(out), flush=True)
+
+
+def structured_kernels(ws, f, w):
+    """Per-sweep device time of the structured passes (library event pairs over
+    5 sweeps) and their FP32 rate against the CUDA-core FMA peak: 152 SMs x 128
+    FP32 lanes x 2 flops x the maximum SM clock.  Algorithmic flops per texel
+    and rank: side pass 1 + 2L (h = fs * ft, then L FMAs), bin pass 2L + 2
+    (L FMAs for P, one FMA into the bin table)."""
+    from paper_2109_14807_gb300 import _lib
+    lib = _lib.load()
+    peaks, _ = load_peaks()
+    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    N, L, R = w["N"], w["levels"], w["rank"]
+    lib.gsp_profile_reset()
+    lib.gsp_profile_enable(1)
+    ws.sweeps(f, 5, report=False)
+    lib.gsp_profile_enable(0)
+    flops = {"struct_side": N * N * R * (2 * L + 1), "struct_bins": N * N * R * (2 * L + 2)}
+    out = {}
+    for pid in range(15):
+        n_l, ms = _lib.c_int64(), _lib.c_double()
+        _lib.check("gsp_profile_read", lib.gsp_profile_read(pid, n_l, ms))
+        name = lib.gsp_profile_name(pid).decode()
+        if not n_l.value:
+            continue
+        rec = {"launches_per_sweep": n_l.value / 5, "ms_per_sweep": round(ms.value / 5, 4)}
+        if name in flops:
+            tf = flops[name] / (ms.value / n_l.value * 1e-3) / 1e12
+            rec.update({"tflops": round(tf, 2), "alu_peak_tflops": round(alu_peak, 1),
+                        "frac_of_alu_peak": round(tf / alu_peak, 3)})
+        out[name] = rec
+    return out
 
 
 # ------------------------------------------------------- batching report --

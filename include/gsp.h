@@ -108,7 +108,15 @@ typedef enum gsp_precision {
   GSP_PREC_BF16 = 2,    /* tcgen05, BF16 operands, FP32 accumulate; the NDF tensor is
                            one BF16 value, the Khatri-Rao operand a BF16 hi + lo pair
                            (two MMAs per K slice, Henry, Tang & Heinecke 2019)      */
-  GSP_PREC_BF16_1X = 3  /* tcgen05, both operands rounded once to BF16             */
+  GSP_PREC_BF16_1X = 3, /* tcgen05, both operands rounded once to BF16             */
+  GSP_PREC_STRUCTURED = 4 /* exact structured MTTKRP: the tensor is never built.  Each
+                           level slice is a box sum of the texel -> bin one-hot
+                           (Sec. 4.1), so the footprint window moves onto the spatial
+                           factors (its adjoint: alpha_l(u) = sum_{i < 2^l}
+                           fx[(u + a - i) mod N]) and every MTTKRP is a pass over the
+                           N x N bin map: O(N^2 levels R) FP32 multiply-adds per mode,
+                           FP64 for the long sums, instead of the O(N^2 levels B^2 R)
+                           contraction; levels <= 11, any N >= 8 of the map limits */
 } gsp_precision;
 /* Tensor-core precisions round the NDF tensor without bias: a value between two
  * BF16 (TF32) neighbours goes to the upper one when frac(i * phi) (i = the
@@ -149,7 +157,8 @@ typedef struct gsp_als_report {
   double fit[GSP_MAX_SWEEPS];
 } gsp_als_report;
 
-/* Workspace bytes for gsp_cp_prepare / gsp_cp_sweeps / gsp_cp_mttkrp. */
+/* Workspace bytes for gsp_cp_prepare / gsp_cp_sweeps / gsp_cp_mttkrp (for
+ * GSP_PREC_STRUCTURED tens of MB instead of the tensor). */
 size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precision);
 
 /* Build the MTTKRP operand (the NDF tensor in the precision's input type,
@@ -158,7 +167,11 @@ size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precisi
  * d_ws) and ||T||^2 inside the workspace.  Exactly one of d_hist
  * (int32 histograms from gsp_build_footprint_ndfs) and d_normal_xy (the normal
  * map: the histograms are then produced level by level straight into the
- * operand, never stored as int32) must be non-NULL. */
+ * operand, never stored as int32) must be non-NULL.  GSP_PREC_STRUCTURED builds
+ * no operand: it keeps the bin map (binned from d_normal_xy, or read from the
+ * level-0 slice of d_hist, which holds a single count of 1 per texel; a slice
+ * that does not sets GSP_DEV_BAD_QUERY in d_status and that texel's bin to 0)
+ * and ||T||^2 (from the histogram counts' sums of squares). */
 int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, int N, int levels,
                    int bins, int rank, const gsp_als_opts* opts, void* d_ws,
                    size_t ws_bytes, uint32_t* d_status, gsp_stream stream);
@@ -168,7 +181,12 @@ int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, int N, int l
  * per sweep: x, y, l, s, t; each update is the exact least-squares solution
  * A_n = M_n V^-1 with V the Hadamard product of the other modes' FP64 Gram
  * matrices (Cholesky; pseudo-inverse fallback), then 2-norm column
- * normalisation into lambda. */
+ * normalisation into lambda.  V does not depend on the mode's MTTKRP, so its
+ * factorisation and inverse run on a side stream the call creates, concurrently
+ * with that MTTKRP; the side stream starts after the work already queued on
+ * `stream`, and everything the call queues joins back into `stream`.  While
+ * `stream` is being captured into a CUDA graph everything stays on `stream`
+ * (capture then needs h_report == NULL and tol == 0: no host reads). */
 int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_als_opts* opts,
                   const gsp_cp_factors* f, gsp_als_report* h_report, void* d_ws,
                   size_t ws_bytes, gsp_stream stream);
@@ -410,8 +428,11 @@ int gsp_adam_step(float* d_param, const float* d_grad, float* d_m, float* d_v, i
  * the launch count and summed device time since the last reset.  Off by
  * default; keep it off while capturing CUDA graphs.
  *   0 bins, 1 (unused), 2 box_hist, 3 cast, 4 mttkrp_xy, 5 mttkrp_lst,
- *   6 als_small, 7 tables, 8 range_query, 9 range_query_backward, 10 adam */
-#define GSP_PROFILE_SLOTS 11
+ *   6 als_small, 7 tables, 8 range_query, 9 range_query_backward, 10 adam,
+ *   11 struct_tables, 12 struct_side, 13 struct_bins (GSP_PREC_STRUCTURED),
+ *   14 solve (Cholesky and inverse of the ALS Gram system, on the side stream
+ *   gsp_cp_sweeps runs it on, concurrently with the mode's MTTKRP) */
+#define GSP_PROFILE_SLOTS 15
 int gsp_profile_enable(int on);
 void gsp_profile_reset(void);
 int gsp_profile_read(int id, int64_t* h_launches, double* h_total_ms);
@@ -427,6 +448,12 @@ uint64_t gsp_kernel_launches(void);
  * word, required) and returns, leaving the context usable.  Returns GSP_OK
  * once launched; the status bit arrives asynchronously on `stream`. */
 int gsp_selftest_wait_timeout(uint32_t* d_err, gsp_stream stream);
+
+/* Self-test of the FP64 reciprocal on the Cholesky pivot chain of the CP-ALS
+ * solve (Newton-Raphson from the FP32 reciprocal): d_out[i] = that reciprocal
+ * of d_in[i], FP64 device arrays of n elements (n >= 0), so that it can be
+ * checked against the correctly rounded 1/d. */
+int gsp_selftest_recip(const double* d_in, int64_t n, double* d_out, gsp_stream stream);
 
 const char* gsp_strerror(int status);
 /* cudaError_t value of the last failing CUDA call in this thread (0 if none). */

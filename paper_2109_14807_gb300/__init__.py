@@ -10,7 +10,7 @@ from .api import (CPWorkspace, QueryMaterial, RangeQueryFn, adam_step, backward_
                   init_factors_to_device, new_status, queries_to_device, range_query,
                   range_query_autograd, range_query_backward, range_query_interp, sample_ndf,
                   samples_to_device,
-                  selftest_wait_timeout, status_bits)
+                  selftest_recip, selftest_wait_timeout, status_bits)
 
 __all__ = [
     "CPWorkspace", "QueryMaterial", "RangeQueryFn", "adam_step", "backward_workspace_bytes",
@@ -18,5 +18,5 @@ __all__ = [
     "init_factors_to_device", "new_status", "queries_to_device", "range_query",
     "range_query_autograd", "range_query_backward", "range_query_interp", "sample_ndf",
     "samples_to_device",
-    "selftest_wait_timeout", "status_bits",
+    "selftest_recip", "selftest_wait_timeout", "status_bits",
 ]

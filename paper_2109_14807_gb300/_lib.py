@@ -25,7 +25,7 @@ DEV_NUMERIC = 0x4
 DEV_TIMEOUT = 0x8
 MAX_MATERIALS = 16
 MAX_SWEEPS = 512
-PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16_1x": 3}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16_1x": 3, "structured": 4}
 
 
 class Material(Structure):
@@ -103,6 +103,7 @@ _SIGS = {
     "gsp_last_cuda_error": (c_int, []),
     "gsp_version": (c_int, []),
     "gsp_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
+    "gsp_selftest_recip": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
 }
 
 _LIB = None

@@ -375,3 +375,13 @@ def selftest_wait_timeout(status: torch.Tensor | None = None) -> torch.Tensor:
         status = new_status()
     check("gsp_selftest_wait_timeout", lib.gsp_selftest_wait_timeout(_ptr(status), _stream()))
     return status
+
+
+def selftest_recip(d: torch.Tensor) -> torch.Tensor:
+    """The CP-ALS solve's FP64 reciprocal of every element of `d` (device FP64)."""
+    lib = load()
+    d = d.contiguous()
+    out = torch.empty_like(d)
+    check("gsp_selftest_recip", lib.gsp_selftest_recip(_ptr(d, torch.float64, "d"), d.numel(),
+                                                      _ptr(out, torch.float64), _stream()))
+    return out

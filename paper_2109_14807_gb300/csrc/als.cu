@@ -24,9 +24,12 @@ namespace {
 
 constexpr int kMaxCpRank = 64;
 constexpr int kJacobiMaxRank = 64;
+constexpr int kGramRows = 64;  // rows of a factor per partial Gram matrix
 
 struct CpLayout {
-  size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, W, lam, fit, sumsq, norm2, flags, total;
+  size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, Gpart, W, lam, fit, sumsq, norm2, flags, total;
+  // GSP_PREC_STRUCTURED only (zero-sized otherwise)
+  size_t binsT, AL, BE, part, pre, sig, sig64, segtot, off, stpart, lscale;
 };
 
 size_t esize(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1X ? 2 : 4; }
@@ -42,18 +45,33 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   };
   const size_t N2 = static_cast<size_t>(d.N2()), B2 = static_cast<size_t>(d.B2());
   const size_t L = d.L, R = d.R;
-  o.T = take(N2 * L * B2 * esize(prec));
+  const bool st = prec == GSP_PREC_STRUCTURED;
+  const size_t dense = st ? 0 : 1;  // the structured path builds no tensor
+  o.T = take(dense * N2 * L * B2 * esize(prec));
   o.bins = take(N2 * sizeof(uint16_t) + kGroupBytes);
-  o.Yp = take(N2 * R * sizeof(float));
-  o.Zp = take(L * B2 * R * sizeof(float));
+  o.Yp = take(dense * N2 * R * sizeof(float));
+  o.Zp = take(dense * L * B2 * R * sizeof(float));
   const size_t simt_part = L * static_cast<size_t>(lst_chunks(d, GSP_PREC_FP32)) * B2 * R;
   const size_t tc_part = static_cast<size_t>(kLstMaxRanges) * 2 * B2 * R;
-  o.Zpart = take((prec == GSP_PREC_FP32 ? simt_part : tc_part) * sizeof(float));
-  o.KR = take(2 * R * L * B2 * sizeof(float));  // FP32 rows, or a hi + lo operand pair
-  o.FX = take(2 * R * static_cast<size_t>(d.N) * sizeof(float));  // Z' fx operand
+  o.Zpart = take(dense * (prec == GSP_PREC_FP32 ? simt_part : tc_part) * sizeof(float));
+  o.KR = take(dense * 2 * R * L * B2 * sizeof(float));  // FP32 rows, or a hi + lo operand pair
+  o.FX = take(dense * 2 * R * static_cast<size_t>(d.N) * sizeof(float));  // Z' fx operand
+  const StructSizes z = st ? struct_sizes(d) : StructSizes{0, 0, 0, 0, 0};
+  o.binsT = take(st ? N2 * sizeof(uint16_t) : 0);
+  o.AL = take(z.table_floats * sizeof(float));
+  o.BE = take(z.table_floats * sizeof(float));
+  o.part = take(z.part_floats * sizeof(float));
+  o.pre = take(z.pre_doubles * sizeof(double));
+  o.sig = take(z.table_floats * sizeof(float));
+  o.sig64 = take(z.table_floats * sizeof(double));
+  o.segtot = take(z.seg_doubles * sizeof(double));
+  o.off = take(z.seg_doubles * sizeof(double));
+  o.stpart = take(z.stpart_floats * sizeof(float));
+  o.lscale = take(st ? L * sizeof(double) : 0);
   size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
   o.M = take(imax * R * sizeof(double));
   o.G = take(5 * R * R * sizeof(double));
+  o.Gpart = take((imax + kGramRows - 1) / kGramRows * R * R * sizeof(double));
   o.W = take((3 * R * R + R) * sizeof(double) + 16);  // L, Z^T, 1/diag(L), mode, then W
   o.lam = take(R * sizeof(double));
   o.fit = take(GSP_MAX_SWEEPS * sizeof(double));
@@ -66,7 +84,7 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
 
 bool valid_cp(int N, int L, int B, int R, int prec) {
   return valid_map(N, L, B) && N >= 8 && B >= 8 && is_pow2(R) && R >= 8 && R <= kMaxCpRank &&
-         prec >= GSP_PREC_FP32 && prec <= GSP_PREC_BF16_1X;
+         prec >= GSP_PREC_FP32 && prec <= GSP_PREC_STRUCTURED;
 }
 
 // --------------------------------------------------------------- kernels --
@@ -216,30 +234,39 @@ __global__ void __launch_bounds__(256) k_contract_rows(const float* __restrict__
 
 // G[r1][r2] = sum_i A[i][r1] A[i][r2], FP64; 256/R row slices per output row,
 // combined in a fixed order
-__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int I, int R,
-                                              double* __restrict__ G) {
-  __shared__ double part[256];
-  const int r1 = blockIdx.x, r2 = threadIdx.x % R, p = threadIdx.x / R;
-  const int P = blockDim.x / R;
-  double acc = 0.0;
-  float chunk = 0.0f;
-  int cnt = 0;
-  for (int i = p; i < I; i += P) {  // FP32 dot products over 32 rows, summed in FP64
-    chunk = fmaf(A[i * R + r1], A[i * R + r2], chunk);
-    if (++cnt == 32) {
-      acc += static_cast<double>(chunk);
-      chunk = 0.0f;
-      cnt = 0;
-    }
-  }
-  acc += static_cast<double>(chunk);
-  part[threadIdx.x] = acc;
+
+// Gpart[chunk][r1][r2] = sum over the chunk's rows of A[i][r1] A[i][r2]: FP32
+// dot products over 32 rows, added in FP64.  One CTA per 64-row chunk, the
+// chunk staged in shared memory.
+__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A, int I, int R,
+                                                   double* __restrict__ Gpart) {
+  __shared__ float As[kGramRows * kMaxCpRank];
+  const int i0 = blockIdx.x * kGramRows;
+  const int rows = min(kGramRows, I - i0);
+  for (int e = threadIdx.x; e < rows * R; e += blockDim.x) As[e] = A[static_cast<size_t>(i0) * R + e];
   __syncthreads();
-  if (p == 0) {
-    double t = part[r2];
-    for (int k = 1; k < P; ++k) t += part[k * R + r2];
-    G[r1 * R + r2] = t;
+  double* out = Gpart + static_cast<size_t>(blockIdx.x) * R * R;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int r1 = e / R, r2 = e % R;
+    double acc = 0.0;
+    for (int c0 = 0; c0 < rows; c0 += 32) {
+      float chunk = 0.0f;
+      const int c1 = min(rows, c0 + 32);
+      for (int i = c0; i < c1; ++i) chunk = fmaf(As[i * R + r1], As[i * R + r2], chunk);
+      acc += static_cast<double>(chunk);
+    }
+    out[e] = acc;
   }
+}
+
+// G[e] = sum_chunk Gpart[chunk][e], FP64 in chunk order.
+__global__ void k_gram_sum(const double* __restrict__ Gpart, int chunks, int R2,
+                           double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= R2) return;
+  double acc = 0.0;
+  for (int c = 0; c < chunks; ++c) acc += Gpart[static_cast<size_t>(c) * R2 + e];
+  G[e] = acc;
 }
 
 // Hadamard product of the four Gram matrices other than `skip`.
@@ -324,6 +351,20 @@ __device__ void jacobi_eigen(double* V, double* Q, int R) {
 // Returns false when a pivot is not above thresh; block-uniform result.
 // In place on V (row stride ld = R + 1, so that the column reads of the
 // trailing update fall on distinct banks).
+// 1/d for d > 0 by the Newton-Raphson iteration x <- x + x (1 - d x), whose
+// relative error squares every step: from the FP32 reciprocal (error below
+// 2^-23) two steps reach FP64 precision.  Four dependent FMAs instead of a full
+// FP64 division on the Cholesky's sequential pivot chain.  Outside the FP32
+// range of d it falls back to the division.
+__device__ __forceinline__ double recip_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double x = static_cast<double>(__frcp_rn(static_cast<float>(d)));
+  double e = fma(-d, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-d, x, 1.0);
+  return fma(x, e, x);
+}
+
 __device__ bool cholesky_inplace(double* V, int R, int ld, double thresh, double* invd) {
   // Right-looking, columns left unscaled until the end: step j subtracts
   // A_ij A_kj / A_jj from the trailing lower triangle, which only reads column
@@ -331,13 +372,12 @@ __device__ bool cholesky_inplace(double* V, int R, int ld, double thresh, double
   // is formed for all columns at the end.  Thread 0 owns element (j+1, j+1)
   // of step j's update, so it forms the next pivot's reciprocal right after
   // updating it, before the barrier (double-buffered: step j reads slot j & 1
-  // while thread 0 fills slot (j + 1) & 1).
+  // while thread 0 fills slot (j + 1) & 1).  The reciprocal square roots of
+  // the pivots are taken at the end, in parallel.
   __shared__ double piv_inv[2];
+  __shared__ double piv[kMaxCpRank];
   const int ti = threadIdx.x >> 4, tk = threadIdx.x & 15;  // 16 x 16 grid (blockDim.x == 256)
-  if (threadIdx.x == 0 && V[0] > thresh) {
-    piv_inv[0] = 1.0 / V[0];
-    invd[0] = 1.0 / sqrt(V[0]);
-  }
+  if (threadIdx.x == 0 && V[0] > thresh) piv_inv[0] = recip_newton(V[0]);
   __syncthreads();
   for (int j = 0; j < R; ++j) {
     const double d = V[j * ld + j];  // final: written by step j - 1 before its barrier
@@ -347,15 +387,17 @@ __device__ bool cholesky_inplace(double* V, int R, int ld, double thresh, double
       const double aij = V[i * ld + j] * inv;
       for (int k = j + 1 + tk; k <= i; k += 16) V[i * ld + k] -= aij * V[k * ld + j];
     }
-    if (threadIdx.x == 0 && j + 1 < R) {
-      const double dn = V[(j + 1) * ld + j + 1];
-      if (dn > thresh) {
-        piv_inv[(j + 1) & 1] = 1.0 / dn;
-        invd[j + 1] = 1.0 / sqrt(dn);
+    if (threadIdx.x == 0) {
+      piv[j] = d;
+      if (j + 1 < R) {
+        const double dn = V[(j + 1) * ld + j + 1];
+        if (dn > thresh) piv_inv[(j + 1) & 1] = recip_newton(dn);
       }
     }
     __syncthreads();
   }
+  for (int j = threadIdx.x; j < R; j += blockDim.x) invd[j] = 1.0 / sqrt(piv[j]);
+  __syncthreads();
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     const int i = e / R, j = e % R;
     if (j <= i) V[i * ld + j] *= invd[j];
@@ -454,27 +496,27 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
   if (threadIdx.x == 0) *mode = 0;
 }
 
-// Column c of Z = L^-1, one CTA of 64 threads per column: forward substitution
-// z_k = -(sum_{c<=j<k} L[k][j] z_j) / L[k][k], each sum a fixed-order block
-// reduction; writes Z^T[c][:].  Skipped in mode 1.
-__global__ void __launch_bounds__(64) k_inv_cols(double* __restrict__ fac, int R) {
+// Column c of Z = L^-1 by forward substitution in column (axpy) form, one warp
+// per column: lane q holds b_k for rows k = c + q and c + q + 32; for j = c ..
+// R - 1, z_j = b_j / L_jj is broadcast from its owner and every later row does
+// b_k -= L_kj z_j.  No block barriers on the sequential chain.  Writes Z^T[c][:].
+// Skipped in mode 1.
+__global__ void __launch_bounds__(128) k_inv_cols(double* __restrict__ fac, int R) {
   const SolveScratch ss = solve_scratch(fac, R);
   if (*ss.mode != 0) return;
-  __shared__ double z[kMaxCpRank];
-  __shared__ double wsum[2];
-  const int c = blockIdx.x, t = threadIdx.x;
-  if (t < R) z[t] = (t == c) ? ss.invd[c] : 0.0;
-  __syncthreads();
-  for (int k = c + 1; k < R; ++k) {
-    double part = (t >= c && t < k) ? ss.L[k * R + t] * z[t] : 0.0;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    if ((t & 31) == 0) wsum[t >> 5] = part;
-    __syncthreads();
-    if (t == 0) z[k] = -(wsum[0] + wsum[1]) * ss.invd[k];
-    __syncthreads();
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (c >= R) return;
+  const int k0 = c + lane, k1 = k0 + 32;
+  double b0 = lane == 0 ? 1.0 : 0.0, b1 = 0.0;
+  for (int j = c; j < R; ++j) {
+    const int q = j - c;
+    const double bj = __shfl_sync(0xffffffffu, q >= 32 ? b1 : b0, q & 31);
+    const double z = bj * ss.invd[j];
+    if (lane == 0) ss.Zt[c * R + j] = z;
+    if (k0 > j && k0 < R) b0 = fma(-ss.L[k0 * R + j], z, b0);
+    if (k1 > j && k1 < R) b1 = fma(-ss.L[k1 * R + j], z, b1);
   }
-  if (t < R) ss.Zt[c * R + t] = z[t];
+  for (int j = lane; j < c; j += 32) ss.Zt[c * R + j] = 0.0;
 }
 
 // W = Z^T Z = V^-1: W[a][b] = sum_{k >= max(a, b)} Z^T[a][k] Z^T[b][k]; one CTA
@@ -586,8 +628,35 @@ struct Ctx {
   CpLayout lay;
   char* ws;
   cudaStream_t s;
+  // Side stream for the part of a mode update that does not need the mode's
+  // MTTKRP (null: everything runs on s).
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   template <typename T>
   T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+
+// Owns the side stream and the fork / join events of one gsp_cp_sweeps call.
+struct SideStream {
+  Ctx& c;
+  explicit SideStream(Ctx& ctx) : c(ctx) {}
+  int open() {
+    // while c.s is being captured into a graph everything stays on c.s
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GSP_CUDA(cudaStreamIsCapturing(c.s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return GSP_OK;
+    GSP_CUDA(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
+    GSP_CUDA(cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming));
+    GSP_CUDA(cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming));
+    return GSP_OK;
+  }
+  ~SideStream() {
+    if (c.join_ev) cudaEventDestroy(c.join_ev);
+    if (c.fork_ev) cudaEventDestroy(c.fork_ev);
+    if (c.side) cudaStreamDestroy(c.side);  // deferred until its work completes
+    c.side = nullptr;
+    c.fork_ev = c.join_ev = nullptr;
+  }
 };
 
 int ensure_smem_attr() {
@@ -694,29 +763,48 @@ int mode_rows(const MttkrpDims& d, int mode) {
 
 int gram(const Ctx& c, const gsp_cp_factors& f, int mode) {
   const int R = c.d.R;
-  k_gram<<<R, 256, 0, c.s>>>(factor_ptr(f, mode), mode_rows(c.d, mode), R,
-                           c.at<double>(c.lay.G) + static_cast<size_t>(mode) * R * R);
+  const int I = mode_rows(c.d, mode);
+  const int chunks = (I + kGramRows - 1) / kGramRows;
+  double* G = c.at<double>(c.lay.G) + static_cast<size_t>(mode) * R * R;
+  double* Gpart = c.at<double>(c.lay.Gpart);
+  k_gram_part<<<chunks, 256, 0, c.s>>>(factor_ptr(f, mode), I, R, chunks > 1 ? Gpart : G);
   GSP_CHECK_LAUNCH();
+  if (chunks > 1) {
+    k_gram_sum<<<grid_for(R * R, 256), 256, 0, c.s>>>(Gpart, chunks, R * R, G);
+    GSP_CHECK_LAUNCH();
+  }
   return GSP_OK;
 }
 
-int update(const Ctx& c, const gsp_cp_factors& f, int mode) {
+// First half of a mode update, independent of the mode's MTTKRP: factor V (the
+// Hadamard product of the other modes' Grams) and form W = V^-1 (or V^+), on
+// stream st.
+int solve_factor(const Ctx& c, int mode, cudaStream_t st) {
   const int R = c.d.R;
-  const int I = mode_rows(c.d, mode);
   size_t smem = static_cast<size_t>(R) * (R + 1) * sizeof(double) +
                 (R <= kJacobiMaxRank ? static_cast<size_t>(R) * R * sizeof(double) : 0);
-  prof_begin(PROF_ALS_SMALL, c.s);
-  k_chol<<<1, 256, smem, c.s>>>(c.at<double>(c.lay.G), R, mode, c.at<double>(c.lay.W),
-                                c.at<uint32_t>(c.lay.flags));
-  GSP_CHECK_LAUNCH();
-  float* A = factor_ptr(f, mode);
   double* fac = c.at<double>(c.lay.W);
-  k_inv_cols<<<R, 64, 0, c.s>>>(fac, R);
+  prof_begin(PROF_SOLVE, st);
+  k_chol<<<1, 256, smem, st>>>(c.at<double>(c.lay.G), R, mode, fac, c.at<uint32_t>(c.lay.flags));
   GSP_CHECK_LAUNCH();
-  k_gram_inv<<<R, kMaxCpRank, 0, c.s>>>(fac, R);
+  k_inv_cols<<<(R + 3) / 4, 128, 0, st>>>(fac, R);
   GSP_CHECK_LAUNCH();
+  k_gram_inv<<<R, kMaxCpRank, 0, st>>>(fac, R);
+  GSP_CHECK_LAUNCH();
+  prof_end(PROF_SOLVE, st);
+  return GSP_OK;
+}
+
+// Second half, on the main stream once M_n is there: A_n = M_n W, column norms
+// into lambda, the new Gram matrix of the mode.
+int solve_apply(const Ctx& c, const gsp_cp_factors& f, int mode) {
+  const int R = c.d.R;
+  const int I = mode_rows(c.d, mode);
+  float* A = factor_ptr(f, mode);
+  prof_begin(PROF_ALS_SMALL, c.s);
   k_apply<<<grid_for(static_cast<long long>(I) * R, 256), 256, 0, c.s>>>(c.at<double>(c.lay.M),
-                                                                         fac, I, R, A);
+                                                                         c.at<double>(c.lay.W), I,
+                                                                         R, A);
   GSP_CHECK_LAUNCH();
   k_colnorm<<<R, 256, 0, c.s>>>(A, I, R, c.at<double>(c.lay.lam), f.lambda);
   GSP_CHECK_LAUNCH();
@@ -725,12 +813,39 @@ int update(const Ctx& c, const gsp_cp_factors& f, int mode) {
   return GSP_OK;
 }
 
+// Start the first half of mode `mode`'s update: on the side stream after
+// everything already queued on the main stream, or inline without one.  Call
+// it before the mode's MTTKRP so the two run concurrently.
+int fork_solve(const Ctx& c, int mode) {
+  if (!c.side) return GSP_OK;
+  GSP_CUDA(cudaEventRecord(c.fork_ev, c.s));
+  GSP_CUDA(cudaStreamWaitEvent(c.side, c.fork_ev, 0));
+  GSP_TRY(solve_factor(c, mode, c.side));
+  GSP_CUDA(cudaEventRecord(c.join_ev, c.side));
+  return GSP_OK;
+}
+
+// Finish mode `mode`'s update once its MTTKRP (in c.lay.M) is queued.
+int join_solve(const Ctx& c, const gsp_cp_factors& f, int mode) {
+  if (c.side)
+    GSP_CUDA(cudaStreamWaitEvent(c.s, c.join_ev, 0));
+  else
+    GSP_TRY(solve_factor(c, mode, c.s));
+  return solve_apply(c, f, mode);
+}
+
+bool path_supported(const MttkrpDims& d, int prec) {
+  if (prec == GSP_PREC_FP32) return true;
+  if (prec == GSP_PREC_STRUCTURED) return struct_supported(d);
+  return tc_supported(d, prec);
+}
+
 int make_ctx(int N, int L, int B, int R, int prec, void* d_ws, size_t ws_bytes, gsp_stream st,
              Ctx& c) {
   if (!valid_cp(N, L, B, R, prec)) return GSP_ERR_INVALID_ARG;
   c.d = MttkrpDims{N, L, B, R};
   c.prec = prec;
-  if (prec != GSP_PREC_FP32 && !tc_supported(c.d, prec)) return GSP_ERR_UNSUPPORTED;
+  if (!path_supported(c.d, prec)) return GSP_ERR_UNSUPPORTED;
   c.lay = cp_layout(c.d, prec);
   if (!d_ws || ws_bytes < c.lay.total) return GSP_ERR_WORKSPACE;
   c.ws = static_cast<char*>(d_ws);
@@ -742,15 +857,121 @@ bool valid_factors(const gsp_cp_factors* f) {
   return f && f->fx && f->fy && f->fl && f->fs && f->ft && f->lambda;
 }
 
+// One sweep over the prepared operand: the xy pass, modes x and y, the (l, s, t)
+// pass, modes l, s and t.
+int dense_sweep(const Ctx& c, const gsp_cp_factors& f) {
+  double* M = c.at<double>(c.lay.M);
+  GSP_TRY(fork_solve(c, 0));
+  GSP_TRY(run_xy(c, f.fl, f.fs, f.ft));
+  GSP_TRY(contract(c, 0, f, M, nullptr));
+  GSP_TRY(join_solve(c, f, 0));
+  GSP_TRY(fork_solve(c, 1));
+  GSP_TRY(contract(c, 1, f, M, nullptr));
+  GSP_TRY(join_solve(c, f, 1));
+  GSP_TRY(fork_solve(c, 2));
+  GSP_TRY(run_lst(c, f.fx, f.fy));
+  for (int m = 2; m < 5; ++m) {
+    if (m > 2) GSP_TRY(fork_solve(c, m));
+    GSP_TRY(contract(c, m, f, M, nullptr));
+    GSP_TRY(join_solve(c, f, m));
+  }
+  return GSP_OK;
+}
+
+StructWs struct_ws(const Ctx& c) {
+  StructWs w;
+  w.part = c.at<float>(c.lay.part);
+  w.pre = c.at<double>(c.lay.pre);
+  w.sig = c.at<float>(c.lay.sig);
+  w.sig64 = c.at<double>(c.lay.sig64);
+  w.segtot = c.at<double>(c.lay.segtot);
+  w.off = c.at<double>(c.lay.off);
+  w.stpart = c.at<float>(c.lay.stpart);
+  w.lscale = c.at<double>(c.lay.lscale);
+  return w;
+}
+
+// Structured operand: the bin map (and its transpose), the level scales and
+// ||T||^2; no tensor.
+int prepare_structured(const int32_t* d_hist, const float* d_normal_xy, int raw,
+                       uint32_t* d_status, const Ctx& c) {
+  const MttkrpDims& d = c.d;
+  uint16_t* bm = c.at<uint16_t>(c.lay.bins);
+  uint32_t* groups = reinterpret_cast<uint32_t*>(c.ws + c.lay.bins + d.N2() * sizeof(uint16_t));
+  unsigned long long* sumsq = c.at<unsigned long long>(c.lay.sumsq);
+  if (d_hist) {
+    const long long slice = d.N2() * d.B2();
+    GSP_TRY(struct_bins_from_level0(d_hist, d.N, d.B, bm, d_status, c.s));
+    for (int l = 0; l < d.L; ++l) {
+      LevelSink o{nullptr, nullptr, nullptr, 1.0f, sumsq + l, 0, 0};
+      GSP_TRY(launch_cast(d_hist + slice * l, d.N, d.B, o, c.s));
+    }
+  } else {
+    GSP_TRY(launch_bins(d_normal_xy, d.N, d.B, bm, d_status, groups, c.s));
+    HistOut o{};
+    o.sumsq = sumsq;
+    o.groups = groups;
+    GSP_TRY(launch_box_hist(bm, d.N, d.L, d.B, o, c.s));
+  }
+  GSP_TRY(struct_transpose_bins(bm, c.at<uint16_t>(c.lay.binsT), d.N, c.s));
+  return struct_level_scales(d.L, d.B, raw, c.at<double>(c.lay.lscale), c.s);
+}
+
+// One structured sweep, modes x, y, l, s, t.  BE holds beta of f.fy on entry
+// and on exit; AL holds alpha of f.fx on exit.
+int structured_sweep(const Ctx& c, const gsp_cp_factors& f) {
+  const MttkrpDims& d = c.d;
+  const StructWs w = struct_ws(c);
+  const uint16_t* bm = c.at<uint16_t>(c.lay.bins);
+  const uint16_t* bt = c.at<uint16_t>(c.lay.binsT);
+  float* al = c.at<float>(c.lay.AL);
+  float* be = c.at<float>(c.lay.BE);
+  double* M = c.at<double>(c.lay.M);
+  GSP_TRY(fork_solve(c, 0));
+  GSP_TRY(struct_side(bm, be, f.fs, f.ft, f.fl, w, d, M, nullptr, c.s));
+  GSP_TRY(join_solve(c, f, 0));
+  GSP_TRY(fork_solve(c, 1));
+  GSP_TRY(struct_window_tables(f.fx, al, d, c.s));
+  GSP_TRY(struct_side(bt, al, f.fs, f.ft, f.fl, w, d, M, nullptr, c.s));
+  GSP_TRY(join_solve(c, f, 1));
+  GSP_TRY(fork_solve(c, 2));
+  GSP_TRY(struct_window_tables(f.fy, be, d, c.s));
+  GSP_TRY(struct_level(be, w, d, M, nullptr, c.s));
+  GSP_TRY(join_solve(c, f, 2));
+  GSP_TRY(fork_solve(c, 3));
+  GSP_TRY(struct_bins(bm, al, be, f.fl, f.ft, 0, w, d, M, nullptr, c.s));
+  GSP_TRY(join_solve(c, f, 3));
+  GSP_TRY(fork_solve(c, 4));
+  GSP_TRY(struct_bins(bm, al, be, f.fl, f.fs, 1, w, d, M, nullptr, c.s));
+  return join_solve(c, f, 4);
+}
+
 }  // namespace
 }  // namespace gsp
 
 using namespace gsp;
 
+namespace gsp {
+namespace {
+__global__ void k_selftest_recip(const double* __restrict__ in, long long n, double* __restrict__ out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i < n) out[i] = recip_newton(in[i]);
+}
+}  // namespace
+}  // namespace gsp
+
+extern "C" int gsp_selftest_recip(const double* d_in, int64_t n, double* d_out, gsp_stream stream) {
+  if (n < 0 || (n > 0 && (!d_in || !d_out))) return GSP_ERR_INVALID_ARG;
+  if (n == 0) return GSP_OK;
+  k_selftest_recip<<<grid_for(n, 256), 256, 0, to_stream(stream)>>>(d_in, n, d_out);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
 extern "C" size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precision) {
   if (!valid_cp(N, levels, bins, rank, precision)) return 0;
   MttkrpDims d{N, levels, bins, rank};
-  if (precision != GSP_PREC_FP32 && !tc_supported(d, precision)) return 0;
+  if (!path_supported(d, precision)) return 0;
   return cp_layout(d, precision).total;
 }
 
@@ -765,7 +986,9 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
   unsigned long long* sumsq = c.at<unsigned long long>(c.lay.sumsq);
   GSP_CUDA(cudaMemsetAsync(sumsq, 0, sizeof(unsigned long long) * levels, c.s));
   GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
-  if (d_hist) {
+  if (c.prec == GSP_PREC_STRUCTURED) {
+    GSP_TRY(prepare_structured(d_hist, d_normal_xy, opts->raw_counts, d_status, c));
+  } else if (d_hist) {
     for (int l = 0; l < levels; ++l) {
       LevelSink o{nullptr, nullptr, nullptr, 1.0f, sumsq + l, c.prec == GSP_PREC_TF32, slice * l};
       o.scale = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
@@ -804,23 +1027,18 @@ extern "C" int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_al
     return GSP_ERR_INVALID_ARG;
   Ctx c;
   GSP_TRY(make_ctx(N, levels, bins, rank, opts->precision, d_ws, ws_bytes, stream, c));
+  SideStream side(c);
+  GSP_TRY(side.open());
   double* M = c.at<double>(c.lay.M);
   double* fits = c.at<double>(c.lay.fit);
   GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
   for (int m = 0; m < 5; ++m) GSP_TRY(gram(c, *f, m));
+  const bool st = c.prec == GSP_PREC_STRUCTURED;
+  if (st) GSP_TRY(struct_window_tables(f->fy, c.at<float>(c.lay.BE), c.d, c.s));
   int done = 0;
   double prev = 0.0;
   for (int sweep = 0; sweep < opts->sweeps; ++sweep) {
-    GSP_TRY(run_xy(c, f->fl, f->fs, f->ft));
-    GSP_TRY(contract(c, 0, *f, M, nullptr));
-    GSP_TRY(update(c, *f, 0));
-    GSP_TRY(contract(c, 1, *f, M, nullptr));
-    GSP_TRY(update(c, *f, 1));
-    GSP_TRY(run_lst(c, f->fx, f->fy));
-    for (int m = 2; m < 5; ++m) {
-      GSP_TRY(contract(c, m, *f, M, nullptr));
-      GSP_TRY(update(c, *f, m));
-    }
+    GSP_TRY(st ? structured_sweep(c, *f) : dense_sweep(c, *f));
     k_fit<<<1, 256, 0, c.s>>>(M, f->ft, c.at<double>(c.lay.lam), c.at<double>(c.lay.G), bins,
                               rank, c.at<double>(c.lay.norm2), fits + sweep);
     GSP_CHECK_LAUNCH();
@@ -862,6 +1080,20 @@ extern "C" int gsp_cp_mttkrp(int N, int levels, int bins, int rank, int precisio
     if (!d_m[m]) return GSP_ERR_INVALID_ARG;
   Ctx c;
   GSP_TRY(make_ctx(N, levels, bins, rank, precision, d_ws, ws_bytes, stream, c));
+  if (precision == GSP_PREC_STRUCTURED) {
+    const StructWs w = struct_ws(c);
+    const uint16_t* bm = c.at<uint16_t>(c.lay.bins);
+    float* al = c.at<float>(c.lay.AL);
+    float* be = c.at<float>(c.lay.BE);
+    double* M = c.at<double>(c.lay.M);
+    GSP_TRY(struct_window_tables(f->fx, al, c.d, c.s));
+    GSP_TRY(struct_window_tables(f->fy, be, c.d, c.s));
+    GSP_TRY(struct_side(bm, be, f->fs, f->ft, f->fl, w, c.d, M, d_m[0], c.s));
+    GSP_TRY(struct_side(c.at<uint16_t>(c.lay.binsT), al, f->fs, f->ft, f->fl, w, c.d, M, d_m[1], c.s));
+    GSP_TRY(struct_level(be, w, c.d, M, d_m[2], c.s));
+    GSP_TRY(struct_bins(bm, al, be, f->fl, f->ft, 0, w, c.d, M, d_m[3], c.s));
+    return struct_bins(bm, al, be, f->fl, f->fs, 1, w, c.d, M, d_m[4], c.s);
+  }
   GSP_TRY(run_xy(c, f->fl, f->fs, f->ft));
   GSP_TRY(contract(c, 0, *f, nullptr, d_m[0]));
   GSP_TRY(contract(c, 1, *f, nullptr, d_m[1]));

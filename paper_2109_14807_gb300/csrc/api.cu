@@ -30,7 +30,8 @@ cudaEvent_t take_event() {
 }
 const char* kProfNames[PROF_COUNT] = {"bins", "level0", "box_hist", "cast", "mttkrp_xy",
                                       "mttkrp_lst", "als_small", "tables", "range_query",
-                                      "range_query_backward", "adam"};
+                                      "range_query_backward", "adam", "struct_tables",
+                                      "struct_side", "struct_bins", "solve"};
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

@@ -34,7 +34,8 @@ void count_launch();
 
 enum ProfId {
   PROF_BINS = 0, PROF_LEVEL0, PROF_DOUBLE, PROF_CAST, PROF_MTTKRP_XY, PROF_MTTKRP_LST,
-  PROF_ALS_SMALL, PROF_TABLES, PROF_QUERY, PROF_QUERY_BWD, PROF_ADAM, PROF_COUNT
+  PROF_ALS_SMALL, PROF_TABLES, PROF_QUERY, PROF_QUERY_BWD, PROF_ADAM, PROF_STRUCT_TABLES,
+  PROF_STRUCT_SIDE, PROF_STRUCT_BINS, PROF_SOLVE, PROF_COUNT
 };
 // Event pair around one launch (no-ops unless profiling is enabled).
 void prof_begin(int id, cudaStream_t s);

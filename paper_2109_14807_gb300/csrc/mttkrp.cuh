@@ -43,4 +43,42 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
 bool tc_supported(const MttkrpDims& d, int precision);
 constexpr int kLstMaxRanges = 256;
 
+// Structured path (structured.cu): exact MTTKRPs from the bin map, the footprint
+// windows moved onto the spatial factors.  Buffers, all device, caller-owned:
+struct StructWs {
+  float* part;    // [splits][N][L][R]  side-pass partials
+  double* pre;    // [L][N + 1][R]      FP64 prefix along the pass's columns
+  float* sig;     // [N][L][R]          the pass's reduced sums (sigma for mode l)
+  double* sig64;  // [N][L][R]          the same in FP64
+  double* segtot; // [L][N / 32][R]     prefix segment totals
+  double* off;    // [L][N / 32][R]     prefix segment offsets
+  float* stpart;  // [ctas][B][R]       bin-pass partials
+  const double* lscale;  // [L]         c_l: counts -> tensor values
+};
+struct StructSizes {
+  size_t table_floats, part_floats, pre_doubles, seg_doubles, stpart_floats;
+};
+bool struct_supported(const MttkrpDims& d);
+StructSizes struct_sizes(const MttkrpDims& d);
+// out[u][l][r] = sum_{i < 2^l} f[(u + a_l - i) mod N][r]  (the window's adjoint)
+int struct_window_tables(const float* f, float* out, const MttkrpDims& d, cudaStream_t s);
+// Side pass over bm [rows][cols] (rows = the reduction index, win its window
+// table) into w.pre; with M non-null also M[col][r] of the mode (FP64, and FP32
+// into Mf when non-null).
+int struct_side(const uint16_t* bm, const float* win, const float* fs, const float* ft,
+                const float* fl, const StructWs& w, const MttkrpDims& d, double* M, float* Mf,
+                cudaStream_t s);
+// M_l from w.sig of the y side pass and the beta table.
+int struct_level(const float* be, const StructWs& w, const MttkrpDims& d, double* M, float* Mf,
+                 cudaStream_t s);
+// Bin pass: mode s (mode_t 0, tab = ft) or t (mode_t 1, tab = fs).
+int struct_bins(const uint16_t* bm, const float* al, const float* be, const float* fl,
+                const float* tab, int mode_t, const StructWs& w, const MttkrpDims& d, double* M,
+                float* Mf, cudaStream_t s);
+// lscale[l] = B^2 / (4 * 4^l), or 1 with raw counts
+int struct_level_scales(int L, int B, int raw, double* lscale, cudaStream_t s);
+int struct_transpose_bins(const uint16_t* in, uint16_t* out, int N, cudaStream_t s);
+int struct_bins_from_level0(const int32_t* h0, int N, int B, uint16_t* bins, uint32_t* status,
+                            cudaStream_t s);
+
 }  // namespace gsp

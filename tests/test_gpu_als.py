@@ -205,3 +205,18 @@ def test_als_brushed512_full_size_vs_fp64_oracle(prec, tol):
     rel = np.abs(np.array(fits) - ref) / np.abs(ref)
     assert np.max(rel) <= tol, (prec, np.max(rel), fits[-1], ref[-1])
     torch.cuda.empty_cache()
+
+
+def test_solve_reciprocal_is_within_one_ulp():
+    # the Cholesky pivot reciprocal (Newton-Raphson from the FP32 reciprocal)
+    # against the correctly rounded 1/d, over a log-uniform range and the edges
+    # of its fast path
+    import paper_2109_14807_gb300 as g
+    u = synth.uniform(17, 0, 200_000)
+    d = 10.0 ** (60 * u - 30)
+    d = np.concatenate([d, [1.0, 2.0, 0.5, 3.0, 1e-30, 1.0000001e-30, 9.999e29, 1e30, 1e-300, 1e300,
+                            np.nextafter(1.0, 2.0), np.nextafter(1.0, 0.0)]])
+    got = g.selftest_recip(dev(d, torch.float64)).cpu().numpy()
+    ref = 1.0 / d
+    assert np.all(np.abs(got - ref) <= np.spacing(ref)), np.max(np.abs(got - ref) / np.spacing(ref))
+    assert g.selftest_recip(dev(d[:0], torch.float64)).numel() == 0
