@@ -182,35 +182,62 @@ class StructuredFootprint:
         M_t[t, r] = sum_{u: t_u = t} fs[s_u, r] P(u, r).
     These are the sums of FootprintTensor.mttkrp taken in another order, at
     O(N^2 L R) operations instead of O(N^2 L B^2 R).  ||T||^2 comes from the
-    exact integer sums of squares of ndf.level_sumsq (or is passed in)."""
+    exact integer sums of squares of ndf.level_sumsq (or is passed in).
+
+    footprint="gaussian" takes Eq. geom's Gaussian pixel footprint instead of
+    the box (ndf.gaussian_weights: separable, normalised, sigma_l = 1.5 2^l /
+    sqrt(12)): the same sums with the footprint weights g_l(u - x) in place of
+    the box indicator, T = B^2/4 times the weight sum, and ||T||^2 from the
+    same-bin autocorrelation (ndf.gaussian_sumsq)."""
 
     def __init__(self, s: np.ndarray, t: np.ndarray, levels: int, bins: int,
-                 raw_counts: bool = False, norm2: float | None = None):
+                 raw_counts: bool = False, norm2: float | None = None, footprint: str = "box"):
         self.s = np.asarray(s, dtype=np.int64)
         self.t = np.asarray(t, dtype=np.int64)
         self.N = self.s.shape[0]
         self.levels = levels
         self.bins = bins
-        self.scale = [1.0 if raw_counts else bins * bins / (4.0 * float(4 ** l)) for l in range(levels)]
+        self.footprint = footprint
+        assert footprint in ("box", "gaussian")
+        # box: counts -> density B^2 / (4 * 4^l); Gaussian: the weights already sum
+        # to 1 per footprint, so density B^2 / 4
+        den = (lambda l: 4.0 * float(4 ** l)) if footprint == "box" else (lambda l: 4.0)
+        self.scale = [1.0 if raw_counts else bins * bins / den(l) for l in range(levels)]
         self.shape = (self.N, self.N, levels, bins, bins)
         self._norm2 = norm2
 
     def window_adjoint(self, f: np.ndarray, l: int) -> np.ndarray:
-        """alpha_l [N][R] of a spatial factor f [N][R]."""
-        N, w = self.N, 1 << l
-        a = w // 2
+        """alpha_l [N][R] of a spatial factor f [N][R]: the weight-sum of f over
+        the footprints that contain texel u."""
+        N = self.N
         u = np.arange(N)
         out = np.zeros_like(f)
+        if self.footprint == "gaussian":
+            from . import ndf
+            g, rho = ndf.gaussian_weights(l, N), ndf.gaussian_radius(l, N)
+            for d in range(-rho, rho + 1):  # texel u sits at offset d from centre u - d
+                out += g[d % N] * f[(u - d) % N]
+            return out
+        w = 1 << l
+        a = w // 2
         for i in range(w):
             out += f[(u + a - i) % N]
         return out
 
     def window(self, g: np.ndarray, l: int) -> np.ndarray:
-        """sum_{i < 2^l} g[(x - a_l + i) mod N] for every x: the footprint window."""
-        N, w = self.N, 1 << l
-        a = w // 2
+        """The footprint of every x applied to g: sum_{i < 2^l} g[(x - a_l + i) mod N]
+        (box), or sum_d g_l(d) g[(x + d) mod N] (Gaussian)."""
+        N = self.N
         x = np.arange(N)
         out = np.zeros_like(g)
+        if self.footprint == "gaussian":
+            from . import ndf
+            wts, rho = ndf.gaussian_weights(l, N), ndf.gaussian_radius(l, N)
+            for d in range(-rho, rho + 1):
+                out += wts[d % N] * g[(x + d) % N]
+            return out
+        w = 1 << l
+        a = w // 2
         for i in range(w):
             out += g[(x - a + i) % N]
         return out
@@ -218,8 +245,13 @@ class StructuredFootprint:
     def norm2(self) -> float:
         if self._norm2 is None:
             from . import ndf
-            self._norm2 = float(sum(ndf.level_sumsq(self.s, self.t, l, self.bins) * self.scale[l] ** 2
-                                    for l in range(self.levels)))
+            if self.footprint == "gaussian":
+                A = ndf.match_autocorrelation(self.s, self.t, self.bins)
+                self._norm2 = float(sum(ndf.gaussian_sumsq(A, l) * self.scale[l] ** 2
+                                        for l in range(self.levels)))
+            else:
+                self._norm2 = float(sum(ndf.level_sumsq(self.s, self.t, l, self.bins) * self.scale[l] ** 2
+                                        for l in range(self.levels)))
         return self._norm2
 
     def mttkrp(self, A, n: int) -> np.ndarray:

@@ -119,6 +119,69 @@ def window_histogram(s: np.ndarray, t: np.ndarray, bins: int, x: int, y: int, le
     return np.bincount(flat, minlength=bins * bins).reshape(bins, bins)
 
 
+def gaussian_sigma(level: int) -> float:
+    """sigma_l = 1.5 * 2^l / sqrt(12): Sec. 4.1 sizes a footprint as a Gaussian of
+    standard deviation 1.5 s / sqrt(12) for the sampling stride s; the box of
+    level l (width 2^l) plays the stride here."""
+    return 1.5 * float(1 << level) / np.sqrt(12.0)
+
+
+def gaussian_radius(level: int, N: int) -> int:
+    """Support half-width: ceil(3 sigma_l), at most floor((N - 1) / 2) so that
+    the support never overlaps itself on the N-periodic map."""
+    return int(min(np.ceil(3.0 * gaussian_sigma(level)), (N - 1) // 2))
+
+
+def gaussian_weights(level: int, N: int) -> np.ndarray:
+    """g_l[d mod N], d = -rho .. rho: exp(-d^2 / (2 sigma_l^2)) normalised to sum
+    1 (Eq. geom's G_p, separable, truncated to the support); 0 elsewhere."""
+    sig, rho = gaussian_sigma(level), gaussian_radius(level, N)
+    d = np.arange(-rho, rho + 1)
+    w = np.exp(-(d.astype(np.float64) ** 2) / (2.0 * sig * sig))
+    g = np.zeros(N)
+    g[d % N] = w / w.sum()
+    return g
+
+
+def gaussian_histograms(s: np.ndarray, t: np.ndarray, level: int, bins: int) -> np.ndarray:
+    """Gaussian-footprint NDF weights of one level, [y][x][s][t] (FP64): the
+    footprint of (x, y) weighs texel u by g_l(u_x - x) g_l(u_y - y).  Written
+    out texel by texel: tiny maps only."""
+    N = s.shape[0]
+    g = gaussian_weights(level, N)
+    H = np.zeros((N, N, bins, bins))
+    for uy in range(N):
+        for ux in range(N):
+            wx = g[(ux - np.arange(N)) % N]  # over footprint centres x
+            wy = g[(uy - np.arange(N)) % N]
+            H[:, :, s[uy, ux], t[uy, ux]] += np.outer(wy, wx)
+    return H
+
+
+def match_autocorrelation(s: np.ndarray, t: np.ndarray, bins: int) -> np.ndarray:
+    """A[e_y][e_x] = number of texels u whose bin equals the bin of u + e
+    (cyclic), counted shift by shift."""
+    b = s.astype(np.int64) * bins + t
+    N = b.shape[0]
+    A = np.zeros((N, N), dtype=np.int64)
+    for ey in range(N):
+        by = np.roll(b, -ey, axis=0)
+        for ex in range(N):
+            A[ey, ex] = int(np.count_nonzero(b == np.roll(by, -ex, axis=1)))
+    return A
+
+
+def gaussian_sumsq(A: np.ndarray, level: int) -> float:
+    """Sum over footprints and bins of the squared Gaussian weights of one level,
+    from the same-bin autocorrelation A: the sum over texel pairs (u, v) in a
+    common bin of K(u_x - v_x) K(u_y - v_y), K(e) = sum_d g(d) g(d + e) being
+    the number of ways a footprint weighs both (separable Gaussian)."""
+    N = A.shape[0]
+    g = gaussian_weights(level, N)
+    K = np.array([np.dot(g, np.roll(g, -e)) for e in range(N)])
+    return float(K @ A @ K)
+
+
 def density_scale(level: int, bins: int) -> float:
     """Counts -> NDF values.  Eq. 2 normalises the footprint weight, so an NDF
     image is a density; over [-1,1]^2 with bin area (2/B)^2 the density of a bin
