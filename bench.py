@@ -58,7 +58,7 @@ def parse_args():
                         "autotuner's choice")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--report-precisions", default="fp32,tf32,bf16,bf16_1x,structured",
+    p.add_argument("--report-precisions", default="fp32,tf32,bf16,bf16_1x,structured,structured_gaussian",
                    help="precisions the precision report covers (comma-separated)")
     p.add_argument("--report-workloads", default="brushed512,flakes1024",
                    help="workloads the precision report covers (comma-separated)")
@@ -544,7 +544,12 @@ def precision_report(args):
             torch.cuda.synchronize()
             rec = out["variants"].setdefault(prec, {})
             prep_ms = a.elapsed_time(b)
-            if wname == "brushed512":
+            if wname == "brushed512" and prec == "structured_gaussian":
+                # the Gaussian-footprint tensor is another tensor: its fit only
+                f = g.init_factors_to_device(init)
+                fits, _ = ws.sweeps(f, w["sweeps"])
+                rec[wname] = {"final_fit": fits[-1], "footprint": "gaussian"}
+            elif wname == "brushed512":
                 f = g.init_factors_to_device(init)
                 fits, _ = ws.sweeps(f, w["sweeps"])
                 rel = np.abs(np.array(fits) - ref[: len(fits)]) / np.abs(ref[: len(fits)])
@@ -562,7 +567,7 @@ def precision_report(args):
             rec[wname]["sweep_ms"] = round(a.elapsed_time(b) / 5, 3)
             rec[wname]["prepare_ms"] = round(prep_ms, 3)
             rec[wname]["workspace_mb"] = round(ws.buf.numel() / 2 ** 20, 1)
-            if prec == "structured":
+            if prec.startswith("structured"):
                 rec[wname]["kernels"] = structured_kernels(ws, f, w)
             del ws
             torch.cuda.empty_cache()

@@ -109,7 +109,7 @@ typedef enum gsp_precision {
                            one BF16 value, the Khatri-Rao operand a BF16 hi + lo pair
                            (two MMAs per K slice, Henry, Tang & Heinecke 2019)      */
   GSP_PREC_BF16_1X = 3, /* tcgen05, both operands rounded once to BF16             */
-  GSP_PREC_STRUCTURED = 4 /* exact structured MTTKRP: the tensor is never built.  Each
+  GSP_PREC_STRUCTURED = 4, /* exact structured MTTKRP: the tensor is never built.  Each
                            level slice is a box sum of the texel -> bin one-hot
                            (Sec. 4.1), so the footprint window moves onto the spatial
                            factors (its adjoint: alpha_l(u) = sum_{i < 2^l}
@@ -117,6 +117,16 @@ typedef enum gsp_precision {
                            N x N bin map: O(N^2 levels R) FP32 multiply-adds per mode,
                            FP64 for the long sums, instead of the O(N^2 levels B^2 R)
                            contraction; levels <= 11, any N >= 8 of the map limits */
+  GSP_PREC_STRUCTURED_GAUSSIAN = 5 /* the same structured MTTKRP for the Gaussian
+                           pixel footprint of Eq. geom instead of the box: level l
+                           weighs texel u of the footprint at x by g_l(u_x - x)
+                           g_l(u_y - y), g_l(d) proportional to exp(-d^2 / (2 s_l^2)),
+                           s_l = 1.5 * 2^l / sqrt(12), for |d| <= min(ceil(3 s_l),
+                           (N - 1) / 2), normalised to sum 1; T = B^2/4 times the
+                           footprint's weight per bin (1 with raw_counts).  Built from
+                           d_normal_xy only; ||T||^2 from the exact same-bin
+                           autocorrelation of the bin map (O(N^4) integer compares
+                           in gsp_cp_prepare: ~0.1 s at N = 1024) */
 } gsp_precision;
 /* Tensor-core precisions round the NDF tensor without bias: a value between two
  * BF16 (TF32) neighbours goes to the upper one when frac(i * phi) (i = the

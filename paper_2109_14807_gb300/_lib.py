@@ -25,7 +25,8 @@ DEV_NUMERIC = 0x4
 DEV_TIMEOUT = 0x8
 MAX_MATERIALS = 16
 MAX_SWEEPS = 512
-PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16_1x": 3, "structured": 4}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16_1x": 3, "structured": 4,
+        "structured_gaussian": 5}
 
 
 class Material(Structure):

@@ -30,10 +30,15 @@ struct CpLayout {
   size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, Gpart, W, lam, fit, sumsq, norm2, flags, total;
   // GSP_PREC_STRUCTURED only (zero-sized otherwise)
   size_t binsT, AL, BE, part, pre, sig, sig64, segtot, off, stpart, lscale;
+  // GSP_PREC_STRUCTURED_GAUSSIAN only
+  size_t gw, gw64, K, conv, A, normpart;
 };
 
 size_t esize(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1X ? 2 : 4; }
 bool is_bf16(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1X; }
+bool is_structured(int prec) {
+  return prec == GSP_PREC_STRUCTURED || prec == GSP_PREC_STRUCTURED_GAUSSIAN;
+}
 
 CpLayout cp_layout(const MttkrpDims& d, int prec) {
   CpLayout o;
@@ -45,7 +50,8 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   };
   const size_t N2 = static_cast<size_t>(d.N2()), B2 = static_cast<size_t>(d.B2());
   const size_t L = d.L, R = d.R;
-  const bool st = prec == GSP_PREC_STRUCTURED;
+  const bool st = prec == GSP_PREC_STRUCTURED || prec == GSP_PREC_STRUCTURED_GAUSSIAN;
+  const bool ga = prec == GSP_PREC_STRUCTURED_GAUSSIAN;
   const size_t dense = st ? 0 : 1;  // the structured path builds no tensor
   o.T = take(dense * N2 * L * B2 * esize(prec));
   o.bins = take(N2 * sizeof(uint16_t) + kGroupBytes);
@@ -56,7 +62,7 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   o.Zpart = take(dense * (prec == GSP_PREC_FP32 ? simt_part : tc_part) * sizeof(float));
   o.KR = take(dense * 2 * R * L * B2 * sizeof(float));  // FP32 rows, or a hi + lo operand pair
   o.FX = take(dense * 2 * R * static_cast<size_t>(d.N) * sizeof(float));  // Z' fx operand
-  const StructSizes z = st ? struct_sizes(d) : StructSizes{0, 0, 0, 0, 0};
+  const StructSizes z = st ? struct_sizes(d) : StructSizes{0, 0, 0, 0, 0, 0, 0, 0};
   o.binsT = take(st ? N2 * sizeof(uint16_t) : 0);
   o.AL = take(z.table_floats * sizeof(float));
   o.BE = take(z.table_floats * sizeof(float));
@@ -68,6 +74,12 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   o.off = take(z.seg_doubles * sizeof(double));
   o.stpart = take(z.stpart_floats * sizeof(float));
   o.lscale = take(st ? L * sizeof(double) : 0);
+  o.gw = take(ga ? z.gauss_floats * sizeof(float) : 0);
+  o.gw64 = take(ga ? z.gauss_floats * sizeof(double) : 0);
+  o.K = take(ga ? z.gauss_floats * sizeof(double) : 0);
+  o.conv = take(ga ? z.table_floats * sizeof(float) : 0);
+  o.A = take(ga ? z.autocorr_ints * sizeof(int32_t) : 0);
+  o.normpart = take(ga ? z.normpart_doubles * sizeof(double) : 0);
   size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
   o.M = take(imax * R * sizeof(double));
   o.G = take(5 * R * R * sizeof(double));
@@ -84,7 +96,7 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
 
 bool valid_cp(int N, int L, int B, int R, int prec) {
   return valid_map(N, L, B) && N >= 8 && B >= 8 && is_pow2(R) && R >= 8 && R <= kMaxCpRank &&
-         prec >= GSP_PREC_FP32 && prec <= GSP_PREC_STRUCTURED;
+         prec >= GSP_PREC_FP32 && prec <= GSP_PREC_STRUCTURED_GAUSSIAN;
 }
 
 // --------------------------------------------------------------- kernels --
@@ -836,7 +848,7 @@ int join_solve(const Ctx& c, const gsp_cp_factors& f, int mode) {
 
 bool path_supported(const MttkrpDims& d, int prec) {
   if (prec == GSP_PREC_FP32) return true;
-  if (prec == GSP_PREC_STRUCTURED) return struct_supported(d);
+  if (is_structured(prec)) return struct_supported(d);
   return tc_supported(d, prec);
 }
 
@@ -888,6 +900,10 @@ StructWs struct_ws(const Ctx& c) {
   w.off = c.at<double>(c.lay.off);
   w.stpart = c.at<float>(c.lay.stpart);
   w.lscale = c.at<double>(c.lay.lscale);
+  if (c.prec == GSP_PREC_STRUCTURED_GAUSSIAN) {
+    w.gw = c.at<float>(c.lay.gw);
+    w.conv = c.at<float>(c.lay.conv);
+  }
   return w;
 }
 
@@ -896,9 +912,12 @@ StructWs struct_ws(const Ctx& c) {
 int prepare_structured(const int32_t* d_hist, const float* d_normal_xy, int raw,
                        uint32_t* d_status, const Ctx& c) {
   const MttkrpDims& d = c.d;
+  const bool gauss = c.prec == GSP_PREC_STRUCTURED_GAUSSIAN;
+  if (gauss && d_hist) return GSP_ERR_INVALID_ARG;  // box histograms hold no Gaussian weights
   uint16_t* bm = c.at<uint16_t>(c.lay.bins);
   uint32_t* groups = reinterpret_cast<uint32_t*>(c.ws + c.lay.bins + d.N2() * sizeof(uint16_t));
   unsigned long long* sumsq = c.at<unsigned long long>(c.lay.sumsq);
+  GSP_TRY(struct_level_scales(d.L, d.B, raw, gauss ? 1 : 0, c.at<double>(c.lay.lscale), c.s));
   if (d_hist) {
     const long long slice = d.N2() * d.B2();
     GSP_TRY(struct_bins_from_level0(d_hist, d.N, d.B, bm, d_status, c.s));
@@ -908,13 +927,21 @@ int prepare_structured(const int32_t* d_hist, const float* d_normal_xy, int raw,
     }
   } else {
     GSP_TRY(launch_bins(d_normal_xy, d.N, d.B, bm, d_status, groups, c.s));
-    HistOut o{};
-    o.sumsq = sumsq;
-    o.groups = groups;
-    GSP_TRY(launch_box_hist(bm, d.N, d.L, d.B, o, c.s));
+    if (!gauss) {
+      HistOut o{};
+      o.sumsq = sumsq;
+      o.groups = groups;
+      GSP_TRY(launch_box_hist(bm, d.N, d.L, d.B, o, c.s));
+    }
   }
   GSP_TRY(struct_transpose_bins(bm, c.at<uint16_t>(c.lay.binsT), d.N, c.s));
-  return struct_level_scales(d.L, d.B, raw, c.at<double>(c.lay.lscale), c.s);
+  if (gauss)
+    return struct_gauss_prepare(bm, struct_ws(c), d, c.at<double>(c.lay.gw64), c.at<double>(c.lay.K),
+                                c.at<int32_t>(c.lay.A), c.at<double>(c.lay.normpart),
+                                c.at<double>(c.lay.norm2), c.s);
+  k_norm2<<<1, 32, 0, c.s>>>(sumsq, d.L, d.B, raw, c.at<double>(c.lay.norm2));
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
 }
 
 // One structured sweep, modes x, y, l, s, t.  BE holds beta of f.fy on entry
@@ -931,11 +958,11 @@ int structured_sweep(const Ctx& c, const gsp_cp_factors& f) {
   GSP_TRY(struct_side(bm, be, f.fs, f.ft, f.fl, w, d, M, nullptr, c.s));
   GSP_TRY(join_solve(c, f, 0));
   GSP_TRY(fork_solve(c, 1));
-  GSP_TRY(struct_window_tables(f.fx, al, d, c.s));
+  GSP_TRY(struct_window_tables(f.fx, al, w, d, c.s));
   GSP_TRY(struct_side(bt, al, f.fs, f.ft, f.fl, w, d, M, nullptr, c.s));
   GSP_TRY(join_solve(c, f, 1));
   GSP_TRY(fork_solve(c, 2));
-  GSP_TRY(struct_window_tables(f.fy, be, d, c.s));
+  GSP_TRY(struct_window_tables(f.fy, be, w, d, c.s));
   GSP_TRY(struct_level(be, w, d, M, nullptr, c.s));
   GSP_TRY(join_solve(c, f, 2));
   GSP_TRY(fork_solve(c, 3));
@@ -986,9 +1013,8 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
   unsigned long long* sumsq = c.at<unsigned long long>(c.lay.sumsq);
   GSP_CUDA(cudaMemsetAsync(sumsq, 0, sizeof(unsigned long long) * levels, c.s));
   GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
-  if (c.prec == GSP_PREC_STRUCTURED) {
-    GSP_TRY(prepare_structured(d_hist, d_normal_xy, opts->raw_counts, d_status, c));
-  } else if (d_hist) {
+  if (is_structured(c.prec)) return prepare_structured(d_hist, d_normal_xy, opts->raw_counts, d_status, c);
+  if (d_hist) {
     for (int l = 0; l < levels; ++l) {
       LevelSink o{nullptr, nullptr, nullptr, 1.0f, sumsq + l, c.prec == GSP_PREC_TF32, slice * l};
       o.scale = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
@@ -1033,8 +1059,8 @@ extern "C" int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_al
   double* fits = c.at<double>(c.lay.fit);
   GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
   for (int m = 0; m < 5; ++m) GSP_TRY(gram(c, *f, m));
-  const bool st = c.prec == GSP_PREC_STRUCTURED;
-  if (st) GSP_TRY(struct_window_tables(f->fy, c.at<float>(c.lay.BE), c.d, c.s));
+  const bool st = is_structured(c.prec);
+  if (st) GSP_TRY(struct_window_tables(f->fy, c.at<float>(c.lay.BE), struct_ws(c), c.d, c.s));
   int done = 0;
   double prev = 0.0;
   for (int sweep = 0; sweep < opts->sweeps; ++sweep) {
@@ -1080,14 +1106,14 @@ extern "C" int gsp_cp_mttkrp(int N, int levels, int bins, int rank, int precisio
     if (!d_m[m]) return GSP_ERR_INVALID_ARG;
   Ctx c;
   GSP_TRY(make_ctx(N, levels, bins, rank, precision, d_ws, ws_bytes, stream, c));
-  if (precision == GSP_PREC_STRUCTURED) {
+  if (is_structured(precision)) {
     const StructWs w = struct_ws(c);
     const uint16_t* bm = c.at<uint16_t>(c.lay.bins);
     float* al = c.at<float>(c.lay.AL);
     float* be = c.at<float>(c.lay.BE);
     double* M = c.at<double>(c.lay.M);
-    GSP_TRY(struct_window_tables(f->fx, al, c.d, c.s));
-    GSP_TRY(struct_window_tables(f->fy, be, c.d, c.s));
+    GSP_TRY(struct_window_tables(f->fx, al, w, c.d, c.s));
+    GSP_TRY(struct_window_tables(f->fy, be, w, c.d, c.s));
     GSP_TRY(struct_side(bm, be, f->fs, f->ft, f->fl, w, c.d, M, d_m[0], c.s));
     GSP_TRY(struct_side(c.at<uint16_t>(c.lay.binsT), al, f->fs, f->ft, f->fl, w, c.d, M, d_m[1], c.s));
     GSP_TRY(struct_level(be, w, c.d, M, d_m[2], c.s));

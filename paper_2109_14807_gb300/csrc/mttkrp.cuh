@@ -54,14 +54,18 @@ struct StructWs {
   double* off;    // [L][N / 32][R]     prefix segment offsets
   float* stpart;  // [ctas][B][R]       bin-pass partials
   const double* lscale;  // [L]         c_l: counts -> tensor values
+  float* gw = nullptr;   // [L][N]      Gaussian footprint weights (null: box footprints)
+  float* conv = nullptr; // [N][L][R]   Gaussian-weighted sums of the side pass
 };
 struct StructSizes {
   size_t table_floats, part_floats, pre_doubles, seg_doubles, stpart_floats;
+  size_t gauss_floats, autocorr_ints, normpart_doubles;
 };
 bool struct_supported(const MttkrpDims& d);
 StructSizes struct_sizes(const MttkrpDims& d);
 // out[u][l][r] = sum_{i < 2^l} f[(u + a_l - i) mod N][r]  (the window's adjoint)
-int struct_window_tables(const float* f, float* out, const MttkrpDims& d, cudaStream_t s);
+int struct_window_tables(const float* f, float* out, const StructWs& w, const MttkrpDims& d,
+                         cudaStream_t s);
 // Side pass over bm [rows][cols] (rows = the reduction index, win its window
 // table) into w.pre; with M non-null also M[col][r] of the mode (FP64, and FP32
 // into Mf when non-null).
@@ -76,7 +80,13 @@ int struct_bins(const uint16_t* bm, const float* al, const float* be, const floa
                 const float* tab, int mode_t, const StructWs& w, const MttkrpDims& d, double* M,
                 float* Mf, cudaStream_t s);
 // lscale[l] = B^2 / (4 * 4^l), or 1 with raw counts
-int struct_level_scales(int L, int B, int raw, double* lscale, cudaStream_t s);
+int struct_level_scales(int L, int B, int raw, int gauss, double* lscale, cudaStream_t s);
+// Gaussian footprints: the weights (w.gw, and FP64 in gw64 [L][N]) and ||T||^2
+// into *norm2 from the same-bin autocorrelation A [N][N] of the bin map and the
+// weights' autocorrelation K [L][N]; normpart [N][L] scratch.  Needs w.lscale.
+int struct_gauss_prepare(const uint16_t* bins, const StructWs& w, const MttkrpDims& d,
+                         double* gw64, double* K, int32_t* A, double* normpart, double* norm2,
+                         cudaStream_t s);
 int struct_transpose_bins(const uint16_t* in, uint16_t* out, int N, cudaStream_t s);
 int struct_bins_from_level0(const int32_t* h0, int N, int B, uint16_t* bins, uint32_t* status,
                             cudaStream_t s);

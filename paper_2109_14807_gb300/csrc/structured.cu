@@ -481,9 +481,11 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const float* __restrict__ st
 
 // lscale[l] = B^2 / (4 * 4^l), the counts -> NDF density factor of level l
 // (Eq. 2 normalises the footprint; a bin covers (2/B)^2), or 1 for raw counts
-__global__ void k_level_scales(int L, int B, int raw, double* __restrict__ lscale) {
+// (box counts; a Gaussian footprint's weights already sum to 1: B^2 / 4)
+__global__ void k_level_scales(int L, int B, int raw, int gauss, double* __restrict__ lscale) {
   const int l = threadIdx.x;
-  if (l < L) lscale[l] = raw ? 1.0 : static_cast<double>(B) * B / (4.0 * ldexp(1.0, 2 * l));
+  if (l < L)
+    lscale[l] = raw ? 1.0 : static_cast<double>(B) * B / (4.0 * (gauss ? 1.0 : ldexp(1.0, 2 * l)));
 }
 
 // bins_t[x][y] = bins[y][x]
@@ -529,6 +531,264 @@ __global__ void k_bins_from_level0(const int32_t* __restrict__ h0, int N, int B2
     bins[u] = static_cast<uint16_t>(bad ? 0 : b);
     if (bad) set_status(status, GSP_DEV_BAD_QUERY);
   }
+}
+
+// ------------------------------------------------ Gaussian footprints --
+// Eq. geom weighs the footprint's texels by a Gaussian G_p instead of a box.
+// Level l here: a separable Gaussian of sigma_l = 1.5 * 2^l / sqrt(12) (the
+// paper's 1.5 s / sqrt(12) with the box width 2^l as the stride s), truncated
+// to |d| <= rho_l = min(ceil(3 sigma_l), (N - 1) / 2) (never overlapping itself
+// on the periodic map) and normalised to sum 1.  The structured MTTKRPs keep
+// their form with the weights g_l(u - x) in place of the box indicator: the
+// window tables and the mode-x / mode-y window step become Gaussian-weighted
+// sums over the support (k_gauss_conv), and T = B^2/4 times the weight sums.
+
+__host__ __device__ inline double gauss_sigma(int l) { return 1.5 * ldexp(1.0, l) / sqrt(12.0); }
+__host__ __device__ inline int gauss_radius(int l, int N) {
+  const int r = static_cast<int>(ceil(3.0 * gauss_sigma(l)));
+  const int m = (N - 1) / 2;
+  return r < m ? r : m;
+}
+
+// gw[l][d mod N] (FP32) and gw64 (FP64): one CTA per level, the normalising sum
+// in a fixed order.
+__global__ void __launch_bounds__(256) k_gauss_weights(int N, float* __restrict__ gw,
+                                                       double* __restrict__ gw64) {
+  __shared__ double red[256];
+  const int l = blockIdx.x;
+  const double sig = gauss_sigma(l);
+  const int rho = gauss_radius(l, N);
+  double part = 0.0;
+  for (int d = -rho + static_cast<int>(threadIdx.x); d <= rho; d += blockDim.x)
+    part += exp(-static_cast<double>(d) * d / (2.0 * sig * sig));
+  red[threadIdx.x] = part;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double z = red[0];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int d = i <= N / 2 ? i : i - N;  // the cyclic offset of slot i
+    const double v = (d >= -rho && d <= rho) ? exp(-static_cast<double>(d) * d / (2.0 * sig * sig)) / z : 0.0;
+    gw64[static_cast<size_t>(l) * N + i] = v;
+    gw[static_cast<size_t>(l) * N + i] = static_cast<float>(v);
+  }
+}
+
+// out[u][l][r] = sum_{|d| <= rho_l} g_l(d) src[(u - d) mod N] (level l's slice of
+// src when lstride = 1, else the level-independent src [N][R]), compensated
+// FP32.  CTA: 64 outputs u x (up to) 32 ranks of one level; the 64 + 2 rho rows
+// it reads and the weights staged in shared memory.
+constexpr int kConvRows = 64;
+__global__ void __launch_bounds__(256) k_gauss_conv(const float* __restrict__ src, int lstride,
+                                                    const float* __restrict__ gw, int N, int L,
+                                                    int R, float* __restrict__ out) {
+  extern __shared__ float cs[];  // weights [2 rho + 1], rows [kConvRows + 2 rho][RL]
+  const int l = blockIdx.y;
+  const int RL = rank_lanes(R);
+  const int rbase = blockIdx.z * RL;
+  const int rho = gauss_radius(l, N);
+  const int u0 = blockIdx.x * kConvRows;
+  const int nw = 2 * rho + 1;
+  const int nrows = kConvRows + 2 * rho;
+  float* wts = cs;
+  float* rows = cs + ((nw + 3) & ~3);
+  for (int i = threadIdx.x; i < nw; i += blockDim.x)
+    wts[i] = gw[static_cast<size_t>(l) * N + ((i - rho + N) % N)];
+  const size_t rs = lstride ? static_cast<size_t>(L) * R : static_cast<size_t>(R);
+  const size_t lo = lstride ? static_cast<size_t>(l) * R : 0;
+  for (int i = threadIdx.x; i < nrows * RL; i += blockDim.x) {
+    const int j = i / RL, k = i - j * RL;
+    const int u = ((u0 - rho + j) % N + N) % N;
+    rows[i] = src[u * rs + lo + rbase + k];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kConvRows * RL; i += blockDim.x) {
+    const int iu = i / RL, k = i - iu * RL;
+    if (u0 + iu >= N) continue;
+    float hi = 0.0f, lo2 = 0.0f;
+    // output u0 + iu reads rows j = iu + rho - d, d = -rho .. rho
+    for (int t = 0; t < nw; ++t) sum2_add(hi, lo2, wts[t] * rows[(iu + 2 * rho - t) * RL + k]);
+    out[(static_cast<size_t>(u0 + iu) * L + l) * R + rbase + k] = hi + lo2;
+  }
+}
+
+// M[x][r] = sum_l c_l fl[l][r] conv[x][l][r], FP64.
+__global__ void k_level_combine(const float* __restrict__ conv, const float* __restrict__ fl, int N,
+                                int L, int R, const double* __restrict__ lscale,
+                                double* __restrict__ M, float* __restrict__ Mf) {
+  const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (e >= static_cast<long long>(N) * R) return;
+  const int x = static_cast<int>(e / R), r = static_cast<int>(e % R);
+  double acc = 0.0;
+  for (int l = 0; l < L; ++l)
+    acc += lscale[l] * static_cast<double>(fl[l * R + r]) *
+           static_cast<double>(conv[(static_cast<size_t>(x) * L + l) * R + r]);
+  M[e] = acc;
+  if (Mf) Mf[e] = static_cast<float>(acc);
+}
+
+// A[ey][ex] = #{u : bin(u) = bin(u + (ex, ey))} (cyclic): the same-bin
+// autocorrelation of the map.  The sum of squared Gaussian footprint weights of
+// a level is sum_e K(ex) K(ey) A[ey][ex] with K the weights' autocorrelation
+// (the texel pairs of a bin weighed by how much a footprint covers both).  One
+// CTA per ey; warp w takes rows y = w, w + 8, ...: the row y + ey is staged
+// twice (as is and shifted by one bin) so that every lane reads its two
+// neighbouring shifts ex = 2j, 2j + 1 as one aligned 32-bit word and compares
+// both with one SIMD 16-bit compare; matches are counted in 16-bit halves and
+// flushed to 32 bits every 32 rows.
+constexpr int kAcWarps = 8;
+constexpr int kAcPairs = 16;  // 32-bit words (bin pairs) per lane: N <= 1024
+__global__ void __launch_bounds__(kAcWarps * 32) k_match_autocorr(const uint16_t* __restrict__ bm,
+                                                                  int N, int32_t* __restrict__ A) {
+  extern __shared__ uint16_t acs[];  // per warp: row y [N], shifted rows R0, R1 [N + 64]; then red
+  const int ey = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P = (N + 63) / 64;  // words per lane
+  const int span = N + 64 * P;  // a lane reads up to element ux + 2 (32 P - 1) + 1
+  uint16_t* ry = acs + warp * (N + 2 * span);
+  uint16_t* r0 = ry + N;
+  uint16_t* r1 = r0 + span;
+  uint32_t packed[kAcPairs];
+  uint32_t cnt[2 * kAcPairs];
+#pragma unroll
+  for (int k = 0; k < kAcPairs; ++k) packed[k] = 0u;
+#pragma unroll
+  for (int k = 0; k < 2 * kAcPairs; ++k) cnt[k] = 0u;
+  int rows_since = 0;
+  for (int y = warp; y < N; y += kAcWarps) {
+    const int ys = (y + ey) & (N - 1);
+    for (int i = lane; i < N; i += 32) ry[i] = bm[static_cast<size_t>(y) * N + i];
+    for (int i = lane; i < span; i += 32) {
+      r0[i] = bm[static_cast<size_t>(ys) * N + (i & (N - 1))];
+      r1[i] = bm[static_cast<size_t>(ys) * N + ((i + 1) & (N - 1))];
+    }
+    __syncwarp();
+    const uint32_t* w0 = reinterpret_cast<const uint32_t*>(r0);
+    const uint32_t* w1 = reinterpret_cast<const uint32_t*>(r1);
+    for (int ux = 0; ux < N; ++ux) {
+      const uint32_t a = ry[ux] * 0x00010001u;
+      const uint32_t* wsrc = (ux & 1) ? w1 : w0;
+      const int base = ux >> 1;
+#pragma unroll
+      for (int k = 0; k < kAcPairs; ++k) {
+        if (k < P) {
+          const int j = lane + 32 * k;  // shifts ex = 2j, 2j + 1
+          const uint32_t m = __vcmpeq2(wsrc[base + j], a);
+          packed[k] += m & 0x00010001u;
+        }
+      }
+    }
+    __syncwarp();
+    if (++rows_since == 32) {  // at most 32 * N <= 32768 per 16-bit half
+#pragma unroll
+      for (int k = 0; k < kAcPairs; ++k) {
+        cnt[2 * k] += packed[k] & 0xffffu;
+        cnt[2 * k + 1] += packed[k] >> 16;
+        packed[k] = 0u;
+      }
+      rows_since = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kAcPairs; ++k) {
+    cnt[2 * k] += packed[k] & 0xffffu;
+    cnt[2 * k + 1] += packed[k] >> 16;
+  }
+  __syncthreads();
+  int32_t* red = reinterpret_cast<int32_t*>(acs);  // [kAcWarps][N]
+#pragma unroll
+  for (int k = 0; k < kAcPairs; ++k) {
+    const int ex = 2 * (lane + 32 * k);
+    if (k < P && ex < N) {
+      red[warp * N + ex] = static_cast<int32_t>(cnt[2 * k]);
+      if (ex + 1 < N) red[warp * N + ex + 1] = static_cast<int32_t>(cnt[2 * k + 1]);
+    }
+  }
+  __syncthreads();
+  for (int ex = threadIdx.x; ex < N; ex += blockDim.x) {
+    int32_t t = 0;
+    for (int w = 0; w < kAcWarps; ++w) t += red[w * N + ex];
+    A[static_cast<size_t>(ey) * N + ex] = t;
+  }
+}
+
+// K[l][e] = sum_d g_l(d) g_l((d + e) mod N), FP64.
+__global__ void k_gauss_autocorr(const double* __restrict__ gw64, int N, int L, double* __restrict__ K) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<long long>(N) * L) return;
+  const int l = static_cast<int>(i / N), e = static_cast<int>(i % N);
+  const int rho = gauss_radius(l, N);
+  const double* g = gw64 + static_cast<size_t>(l) * N;
+  double acc = 0.0;
+  for (int d = -rho; d <= rho; ++d) acc += g[(d + N) % N] * g[((d + e) % N + N) % N];
+  K[i] = acc;
+}
+
+// part[ey][l] = K_l[ey] sum_ex K_l[ex] A[ey][ex]; one CTA per ey, fixed order.
+__global__ void __launch_bounds__(256) k_gauss_norm_rows(const int32_t* __restrict__ A,
+                                                         const double* __restrict__ K, int N, int L,
+                                                         double* __restrict__ part) {
+  __shared__ double red[256];
+  const int ey = blockIdx.x;
+  for (int l = 0; l < L; ++l) {
+    const double* Kl = K + static_cast<size_t>(l) * N;
+    double acc = 0.0;
+    for (int ex = threadIdx.x; ex < N; ex += blockDim.x)
+      acc += Kl[ex] * static_cast<double>(A[static_cast<size_t>(ey) * N + ex]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[static_cast<size_t>(ey) * L + l] = Kl[ey] * red[0];
+    __syncthreads();
+  }
+}
+
+// norm2 = sum_l lscale[l]^2 sum_ey part[ey][l], fixed order.
+__global__ void __launch_bounds__(256) k_gauss_norm_final(const double* __restrict__ part, int N,
+                                                          int L, const double* __restrict__ lscale,
+                                                          double* __restrict__ norm2) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < N * L; i += blockDim.x) {
+    const double c = lscale[i % L];
+    acc += c * c * part[i];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *norm2 = red[0];
+}
+
+size_t conv_smem(int l, int N, int RL) {
+  const int rho = gauss_radius(l, N);
+  return (static_cast<size_t>((2 * rho + 1 + 3) & ~3) + static_cast<size_t>(kConvRows + 2 * rho) * RL) *
+         sizeof(float);
+}
+
+size_t autocorr_smem(int N) {
+  const size_t span = static_cast<size_t>(N) + 64 * ((N + 63) / 64);
+  const size_t rows = static_cast<size_t>(kAcWarps) * (N + 2 * span) * sizeof(uint16_t);
+  const size_t red = static_cast<size_t>(kAcWarps) * N * sizeof(int32_t);
+  return rows > red ? rows : red;
+}
+
+int launch_gauss_conv(const float* src, int lstride, const float* gw, const MttkrpDims& d, float* out,
+                      cudaStream_t s) {
+  const int RL = rank_lanes(d.R);
+  size_t smem = 0;
+  for (int l = 0; l < d.L; ++l) smem = std::max(smem, conv_smem(l, d.N, RL));
+  k_gauss_conv<<<dim3((d.N + kConvRows - 1) / kConvRows, d.L, d.R / RL), 256, smem, s>>>(
+      src, lstride, gw, d.N, d.L, d.R, out);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
 }
 
 // Row splits of a side or bin pass: about kSideTargetCtas CTAs, at least 16 rows each.
@@ -579,6 +839,10 @@ int ensure_struct_attrs(const MttkrpDims& d) {
 #undef GSP_SET_ATTR
   GSP_CUDA(cudaFuncSetAttribute(k_window_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (1024 + 1) * kWinRanks * static_cast<int>(sizeof(double))));
+  GSP_CUDA(cudaFuncSetAttribute(k_gauss_conv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(conv_smem(kMaxLevels - 1, 1024, 32))));
+  GSP_CUDA(cudaFuncSetAttribute(k_match_autocorr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(autocorr_smem(1024))));
   (void)d;
   done_dev = dev;
   return GSP_OK;
@@ -598,12 +862,21 @@ StructSizes struct_sizes(const MttkrpDims& d) {
   z.pre_doubles = static_cast<size_t>(d.L) * (d.N + 1) * d.R;
   z.seg_doubles = static_cast<size_t>(d.L) * seg_count(d.N) * d.R;
   z.stpart_floats = static_cast<size_t>(g.x) * g.y * d.B * d.R;
+  z.gauss_floats = static_cast<size_t>(d.L) * d.N;  // weights; FP64 copy and K alike
+  z.autocorr_ints = static_cast<size_t>(d.N) * d.N;
+  z.normpart_doubles = static_cast<size_t>(d.N) * d.L;
   return z;
 }
 
-int struct_window_tables(const float* f, float* out, const MttkrpDims& d, cudaStream_t s) {
+int struct_window_tables(const float* f, float* out, const StructWs& w, const MttkrpDims& d,
+                         cudaStream_t s) {
   GSP_TRY(ensure_struct_attrs(d));
   prof_begin(PROF_STRUCT_TABLES, s);
+  if (w.gw) {
+    GSP_TRY(launch_gauss_conv(f, 0, w.gw, d, out, s));
+    prof_end(PROF_STRUCT_TABLES, s);
+    return GSP_OK;
+  }
   k_window_tables<<<dim3(d.R / kWinRanks, d.L), 256, (d.N + 1) * kWinRanks * sizeof(double), s>>>(
       f, d.N, d.L, d.R, out);
   prof_end(PROF_STRUCT_TABLES, s);
@@ -635,6 +908,16 @@ int struct_side(const uint16_t* bm, const float* win, const float* fs, const flo
   const long long nel = static_cast<long long>(d.N) * d.L * d.R;
   k_side_reduce<<<grid_for(nel, 256), 256, 0, s>>>(w.part, S, nel, w.sig, w.sig64);
   GSP_CHECK_LAUNCH();
+  if (w.gw) {  // Gaussian footprints: weighted sums of sigma, no prefix
+    if (M) {
+      GSP_TRY(launch_gauss_conv(w.sig, 1, w.gw, d, w.conv, s));
+      k_level_combine<<<grid_for(static_cast<long long>(d.N) * d.R, 256), 256, 0, s>>>(
+          w.conv, fl, d.N, d.L, d.R, w.lscale, M, Mf);
+      GSP_CHECK_LAUNCH();
+    }
+    prof_end(PROF_STRUCT_SIDE, s);
+    return GSP_OK;
+  }
   k_side_segments<<<grid_for(static_cast<long long>(nseg) * d.L * chunks * 32, 256), 256, 0, s>>>(
       w.sig64, d.N, d.L, d.R, w.pre, w.segtot);
   GSP_CHECK_LAUNCH();
@@ -687,8 +970,26 @@ int struct_bins(const uint16_t* bm, const float* al, const float* be, const floa
   return GSP_OK;
 }
 
-int struct_level_scales(int L, int B, int raw, double* lscale, cudaStream_t s) {
-  k_level_scales<<<1, 32, 0, s>>>(L, B, raw, lscale);
+int struct_level_scales(int L, int B, int raw, int gauss, double* lscale, cudaStream_t s) {
+  k_level_scales<<<1, 32, 0, s>>>(L, B, raw, gauss, lscale);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+int struct_gauss_prepare(const uint16_t* bins, const StructWs& w, const MttkrpDims& d,
+                         double* gw64, double* K, int32_t* A, double* normpart, double* norm2,
+                         cudaStream_t s) {
+  GSP_TRY(ensure_struct_attrs(d));
+  if (d.N > 1024 || !is_pow2(d.N)) return GSP_ERR_UNSUPPORTED;
+  k_gauss_weights<<<d.L, 256, 0, s>>>(d.N, w.gw, gw64);
+  GSP_CHECK_LAUNCH();
+  k_match_autocorr<<<d.N, kAcWarps * 32, autocorr_smem(d.N), s>>>(bins, d.N, A);
+  GSP_CHECK_LAUNCH();
+  k_gauss_autocorr<<<grid_for(static_cast<long long>(d.N) * d.L, 256), 256, 0, s>>>(gw64, d.N, d.L, K);
+  GSP_CHECK_LAUNCH();
+  k_gauss_norm_rows<<<d.N, 256, 0, s>>>(A, K, d.N, d.L, normpart);
+  GSP_CHECK_LAUNCH();
+  k_gauss_norm_final<<<1, 256, 0, s>>>(normpart, d.N, d.L, w.lscale, norm2);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
 }
