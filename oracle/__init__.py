@@ -21,7 +21,12 @@ Decomposition, arXiv 2109.14807):
                brute-force range average it must equal, and the adjoint of the
                range query.
 
+* ``clustered`` -- the clustered compression layout of Sec. 4.2 (t x t angular
+               blocks, 8 x 8-texel regions, blank blocks dropped, a 3-mode CP
+               per group) and its block-splitting range query (Sec. 4.4);
+* ``sampling`` -- hierarchical NDF importance sampling (Sec. 5.2).
+
 Parity pins (what fixes each function to something other than itself) live in
 ``tests/test_oracle_*.py``.  No function here is "parity unpinned".
 """
-from . import ndf, cp, query  # noqa: F401
+from . import ndf, cp, query, clustered, sampling  # noqa: F401
