@@ -373,6 +373,81 @@ int gsp_env_queries(const gsp_material* h_mats, int n_mats, const gsp_sg* d_sgs,
                     gsp_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* f2 -- the clustered compression layout of Sec. 4.2                        */
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.2 compresses groups of angular blocks instead of one global tensor.
+ * Every footprint histogram (B x B bins, from gsp_build_footprint_ndfs) is
+ * split into t x t blocks, t = 16 (bins a multiple of 16, B >= 16).  The
+ * blocks at one block position (bs, bt) of the footprints centred in one
+ * 8 x 8-texel region (cx, cy) (N >= 8) form group
+ *   j = ((cy * (N / 8) + cx) * nb + bs) * nb + bt,   nb = bins / 16.
+ * A group keeps its non-blank blocks (some count > 0) in the order level, then
+ * y, then x; z numbers them; completely blank blocks are dropped.  Group j's
+ * tensor D_j[s'][t'][z] = c_l * H_l[y][x][16 bs + s'][16 bt + t'] (c_l the
+ * density scale B^2/(4*4^l), or 1 with raw counts) is decomposed by its own
+ * CP-ALS: D_j ~ sum_r lambda_r X_r o Y_r o Z_r (Eq. 3), modes X (s'), Y (t'),
+ * Z (z), in that order per sweep. */
+
+/* Number of groups (N / 8)^2 * (bins / 16)^2 (0 if the shape is unsupported)
+ * and the scratch bytes gsp_cluster_layout needs. */
+int gsp_cluster_groups(int N, int levels, int bins);
+size_t gsp_cluster_layout_bytes(int N, int levels, int bins);
+
+/* Build the layout from int32 histograms d_hist [levels][N][N][B][B].
+ *  d_offsets [groups + 1]: group j's members are rows offsets[j] ..
+ *            offsets[j + 1] - 1 (written);
+ *  d_members [levels * N * N * nb * nb] capacity: packed member (level << 20 |
+ *            y << 10 | x) of every row (written);
+ *  d_zmap    [levels][N][N][nb * nb]: z of the footprint's block in its group,
+ *            -1 if blank (written);
+ *  h_stats   [2] host: total members, largest group (the call synchronises).
+ * Deterministic; bit-exact. */
+int gsp_cluster_layout(const int32_t* d_hist, int N, int levels, int bins, int32_t* d_offsets,
+                       int32_t* d_members, int32_t* d_zmap, int64_t* h_stats, void* d_ws,
+                       size_t ws_bytes, gsp_stream stream);
+
+/* Shared memory per group CTA of gsp_cluster_als (0 if unsupported); the call
+ * needs at most 227 KB. */
+size_t gsp_cluster_als_smem(int rank, int max_members);
+
+/* Batched CP-ALS of every group, one CTA per group (rank 8, 16 or 32).
+ *  d_X, d_Y [groups][16][rank], d_Z [total members][rank]: initial factors
+ *  in, result out (unit 2-norm columns); d_lambda [groups][rank] out.
+ *  Every group runs until |fit_k - fit_(k-1)| < tol (Sec. 4.2: 1e-4; 0: never)
+ *  or max_sweeps; d_sweeps [groups] (int32) and d_fit [groups] (FP64, 1 -
+ *  ||D - D_hat|| / ||D||) receive what each group did; empty groups report 0.
+ *  FP32 MTTKRP products with compensated sums, FP64 Gram / Cholesky / inverse /
+ *  apply / normalisation; a Gram system that is not positive definite is
+ *  retried with a growing ridge and flags GSP_DEV_NUMERIC in d_status.
+ *  d_ws: at least levels * 8 bytes. */
+int gsp_cluster_als(const int32_t* d_hist, int N, int levels, int bins, int rank,
+                    const int32_t* d_offsets, const int32_t* d_members, int max_members,
+                    float* d_X, float* d_Y, float* d_Z, float* d_lambda, int max_sweeps,
+                    double tol, int raw_counts, int32_t* d_sweeps, double* d_fit,
+                    uint32_t* d_status, void* d_ws, size_t ws_bytes, gsp_stream stream);
+
+/* Query tables of the decomposed groups (Sec. 4.4): d_xsat, d_ysat
+ * [groups][17][rank][4] floats {hi, lo, f[i], f[i-1]} with hi + lo =
+ * sum_{k < i} f[k] (FP64 sums split into two FP32); d_zw [total members][rank]
+ * = lambda * Z. */
+int gsp_cluster_tables(int N, int levels, int bins, int rank, const int32_t* d_offsets,
+                       const float* d_X, const float* d_Y, const float* d_Z,
+                       const float* d_lambda, float* d_xsat, float* d_ysat, float* d_zw,
+                       gsp_stream stream);
+
+/* Range query against the clustered layout: gsp_query descriptors (material
+ * ignored), semantics of gsp_range_query (x, y wrap; level clamped and blended
+ * linearly; bin ends clamped to [0, B] and ordered; zero width = the point
+ * value of the bin holding the end).  A range that crosses block borders is
+ * split at them (Sec. 4.4) and the parts weighted by their share of the
+ * range; a blank block reads 0.  d_out [n] FP32; malformed -> NaN and
+ * GSP_DEV_BAD_QUERY. */
+int gsp_cluster_range_query(int N, int levels, int bins, int rank, const int32_t* d_offsets,
+                            const int32_t* d_zmap, const float* d_xsat, const float* d_ysat,
+                            const float* d_zw, const gsp_query* d_q, int64_t n, float* d_out,
+                            uint32_t* d_status, gsp_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* a7 -- adjoint of the range query and the refinement step                  */
 /* ------------------------------------------------------------------------ */
 

@@ -81,6 +81,19 @@ _SIGS = {
                                 POINTER(QueryTuning), c_void_p, c_size_t, c_void_p]),
     "gsp_sample_ndf": (c_int, [POINTER(Material), c_int, c_void_p, c_int64, c_void_p, c_void_p,
                                c_void_p, c_void_p]),
+    "gsp_cluster_groups": (c_int, [c_int, c_int, c_int]),
+    "gsp_cluster_layout_bytes": (c_size_t, [c_int, c_int, c_int]),
+    "gsp_cluster_layout": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                   POINTER(c_int64), c_void_p, c_size_t, c_void_p]),
+    "gsp_cluster_als_smem": (c_size_t, [c_int, c_int]),
+    "gsp_cluster_als": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_int,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gsp_cluster_tables": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gsp_cluster_range_query": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
+                                        c_void_p]),
     "gsp_env_queries": (c_int, [POINTER(Material), c_int, c_void_p, c_int, c_void_p, c_int64,
                                 c_float, c_void_p, c_void_p]),
     "gsp_range_query_interp": (c_int, [POINTER(Material), c_int, c_void_p, c_int64, c_void_p,

@@ -303,6 +303,89 @@ def env_queries(materials, sgs: torch.Tensor, records: torch.Tensor, eps: float 
     return out
 
 
+# ------------------------------------------------------------------- f2 --
+
+CLUSTER_BLOCK = 16
+
+
+def cluster_layout(hist: torch.Tensor) -> dict:
+    """The clustered layout (Sec. 4.2) of int32 histograms [L][N][N][B][B]:
+    offsets [G+1], members, zmap [L][N][N][nb*nb], total and largest group."""
+    lib = load()
+    L, N, _, B, _ = hist.shape
+    G = lib.gsp_cluster_groups(N, L, B)
+    if G == 0:
+        raise ValueError("unsupported clustered shape")
+    nb = B // CLUSTER_BLOCK
+    dev = hist.device
+    offsets = torch.empty(G + 1, dtype=torch.int32, device=dev)
+    members = torch.empty(L * N * N * nb * nb, dtype=torch.int32, device=dev)
+    zmap = torch.empty((L, N, N, nb * nb), dtype=torch.int32, device=dev)
+    ws = torch.empty(lib.gsp_cluster_layout_bytes(N, L, B), dtype=torch.uint8, device=dev)
+    stats = (ctypes.c_int64 * 2)()
+    check("gsp_cluster_layout", lib.gsp_cluster_layout(
+        _ptr(hist, torch.int32, "hist"), N, L, B, _ptr(offsets), _ptr(members), _ptr(zmap), stats,
+        _ptr(ws), ws.numel(), _stream()))
+    total, mmax = int(stats[0]), int(stats[1])
+    return dict(N=N, L=L, B=B, nb=nb, G=G, offsets=offsets, members=members[:total], zmap=zmap,
+                total=total, max_members=mmax)
+
+
+def cluster_decompose(hist: torch.Tensor, lay: dict, rank: int, init, max_sweeps=500, tol=1e-4,
+                      raw_counts=False, status=None) -> dict:
+    """Batched CP-ALS of every group (one CTA per group).  `init` = (X0 [G][16][R],
+    Y0 [G][16][R], Z0 [total][R]) (numpy or device tensors); returns the factors,
+    lambda [G][R], sweeps [G] and fit [G]."""
+    lib = load()
+    dev = hist.device
+
+    def _dev(a):
+        t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+        return t.to(dev, torch.float32).contiguous().clone()
+
+    X, Y, Z = (_dev(a) for a in init)
+    G, L = lay["G"], lay["L"]
+    lam = torch.empty((G, rank), dtype=torch.float32, device=dev)
+    sweeps = torch.empty(G, dtype=torch.int32, device=dev)
+    fit = torch.empty(G, dtype=torch.float64, device=dev)
+    ws = torch.empty(max(8 * L, 256), dtype=torch.uint8, device=dev)
+    check("gsp_cluster_als", lib.gsp_cluster_als(
+        _ptr(hist, torch.int32, "hist"), lay["N"], L, lay["B"], rank, _ptr(lay["offsets"]),
+        _ptr(lay["members"]) if lay["total"] else _ptr(lay["offsets"]), lay["max_members"],
+        _ptr(X), _ptr(Y), _ptr(Z) if lay["total"] else _ptr(X), _ptr(lam), int(max_sweeps), float(tol),
+        int(bool(raw_counts)), _ptr(sweeps), _ptr(fit), _ptr(status), _ptr(ws), ws.numel(), _stream()))
+    return dict(X=X, Y=Y, Z=Z, lam=lam, sweeps=sweeps, fit=fit, rank=rank)
+
+
+def cluster_tables(lay: dict, fac: dict) -> dict:
+    """SATs of X and Y per group and lambda-weighted Z rows (Sec. 4.4)."""
+    lib = load()
+    G, R = lay["G"], fac["rank"]
+    dev = fac["X"].device
+    xsat = torch.empty((G, CLUSTER_BLOCK + 1, R, 4), dtype=torch.float32, device=dev)
+    ysat = torch.empty_like(xsat)
+    zw = torch.empty((max(lay["total"], 1), R), dtype=torch.float32, device=dev)
+    check("gsp_cluster_tables", lib.gsp_cluster_tables(
+        lay["N"], lay["L"], lay["B"], R, _ptr(lay["offsets"]), _ptr(fac["X"]), _ptr(fac["Y"]),
+        _ptr(fac["Z"]), _ptr(fac["lam"]), _ptr(xsat), _ptr(ysat), _ptr(zw), _stream()))
+    return dict(xsat=xsat, ysat=ysat, zw=zw, rank=R)
+
+
+def cluster_range_query(lay: dict, tables: dict, queries: torch.Tensor, out=None,
+                        status=None) -> torch.Tensor:
+    """Range queries (gsp_query descriptors, int32 [n][8]) against the clustered layout."""
+    lib = load()
+    n = queries.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=queries.device)
+    check("gsp_cluster_range_query", lib.gsp_cluster_range_query(
+        lay["N"], lay["L"], lay["B"], tables["rank"], _ptr(lay["offsets"]), _ptr(lay["zmap"]),
+        _ptr(tables["xsat"]), _ptr(tables["ysat"]), _ptr(tables["zw"]),
+        _ptr(queries, torch.int32, "queries"), n, _ptr(out, torch.float32, "out"), _ptr(status),
+        _stream()))
+    return out
+
+
 def backward_workspace_bytes(materials) -> int:
     arr, nm = _mats(materials)
     return load().gsp_backward_workspace_bytes(arr, nm)

@@ -28,6 +28,7 @@ __all__ = [
     "SG_DTYPE", "ENV_RECORD_DTYPE", "env_lobes", "env_records",
     "init_factors", "queries_integer", "queries_fractional", "queries_camera",
     "WORKLOADS",
+    "cluster_init",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -171,6 +172,25 @@ def init_factors(N: int, levels: int, bins: int, rank: int, seed: int) -> dict:
         out[name] = u[off:off + n * rank].reshape(n, rank).copy()
         off += n * rank
     return out
+
+
+def cluster_init(G: int, offsets: np.ndarray, rank: int, seed: int, block: int = 16):
+    """Seeded U[0,1) initial factors of every group of a clustered layout:
+    X0, Y0 [G][block][rank] and Z0 [total][rank] (float64; the GPU gets exact
+    FP32 roundings).  Group j's rows are drawn from its own stream, so they do
+    not depend on the other groups."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    X0 = np.empty((G, block, rank))
+    Y0 = np.empty((G, block, rank))
+    Z0 = np.empty((int(offsets[-1]), rank))
+    for j in range(G):
+        m = int(offsets[j + 1] - offsets[j])
+        u = uniform(seed, 1_000_000 + j, (2 * block + m) * rank)
+        X0[j] = u[:block * rank].reshape(block, rank)
+        Y0[j] = u[block * rank:2 * block * rank].reshape(block, rank)
+        Z0[offsets[j]:offsets[j + 1]] = u[2 * block * rank:].reshape(m, rank)
+    return (X0.astype(np.float32).astype(np.float64), Y0.astype(np.float32).astype(np.float64),
+            Z0.astype(np.float32).astype(np.float64))
 
 
 def _empty_queries(n: int) -> np.ndarray:
