@@ -71,7 +71,7 @@ __global__ void k_tables(const float* __restrict__ fl, const float* __restrict__
       float hi = static_cast<float>(P);
       float lo = static_cast<float>(P - static_cast<double>(hi));
       float fi = i < B ? f[i * R + r] : 0.0f;
-      t[static_cast<size_t>(i) * R + r] = make_float4(hi, lo, fi, 0.0f);
+      t[static_cast<size_t>(i) * R + r] = make_float4(hi, lo, fi, i > 0 ? f[(i - 1) * R + r] : 0.0f);
       if (i < B) P += static_cast<double>(fi);
     }
   }
@@ -139,15 +139,23 @@ __device__ __forceinline__ QTerms query_terms(const gsp_query& d, const gsp_mate
   return t;
 }
 
-// Range average of one rank from two SAT rows (hi/lo split prefix sums).
+// Range average of one rank from two SAT rows {hi, lo, f[i], f[i-1]} (hi + lo =
+// sum_{k < i} f[k]).  The partial end bins are weighted directly and only the
+// whole bins between them come from the prefix difference, so each part is
+// rounded relative to its own size: a range that starts just before the end
+// of a large bin followed by zeros keeps its small integral instead of
+// cancelling two large prefix values.  A range inside one bin is that bin's
+// value.
 __device__ __forceinline__ float sat_mean(const float4* __restrict__ sat, int R, int r, int i0,
                                           int i1, float f0, float f1, float inv_w, int iz) {
   if (inv_w > 0.0f) {
-    float4 p0 = __ldg(sat + static_cast<size_t>(i0) * R + r);
-    float4 p1 = __ldg(sat + static_cast<size_t>(i1) * R + r);
-    float dh = p1.x - p0.x;
-    float dl = fmaf(f1, p1.z, p1.y) - fmaf(f0, p0.z, p0.y);
-    return (dh + dl) * inv_w;
+    if (i0 == i1) return __ldg(reinterpret_cast<const float*>(sat + static_cast<size_t>(i0) * R + r) + 2);
+    const float4 a = __ldg(sat + static_cast<size_t>(i0 + 1) * R + r);  // prefix(i0 + 1), f[i0]
+    const float4 b = __ldg(sat + static_cast<size_t>(i1) * R + r);      // prefix(i1), f[i1]
+    const float mid = (b.x - a.x) + (b.y - a.y);
+    const float head = (1.0f - f0) * a.w;
+    const float tail = f1 * b.z;
+    return ((head + mid) + tail) * inv_w;
   }
   return __ldg(reinterpret_cast<const float*>(sat + static_cast<size_t>(iz) * R + r) + 2);
 }

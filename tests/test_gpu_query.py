@@ -49,6 +49,7 @@ def test_tables_layout():
         assert np.all(np.abs(hi + lo - P) <= 1e-14 * np.maximum(1, np.abs(P)))
         assert np.array_equal(sat[side, :B, :, 2], f[fk])
         assert np.all(sat[side, B, :, 2] == 0)
+        assert np.array_equal(sat[side, 1:, :, 3], f[fk]) and np.all(sat[side, 0, :, 3] == 0)
 
 
 def test_golden_rank2_hand_worked():
@@ -84,6 +85,31 @@ def test_fractional_queries_fractional_levels():
     assert st == 0
     err, _ = query_error(got, oracle_material(f), q)
     assert err <= QUERY_TOL
+
+
+def test_ranges_ending_in_blank_bins():
+    # a CP material whose angular factors are large in some bins and exactly 0
+    # in others (blank regions of the NDF images): ranges that start just
+    # before the end of a large bin and run into zeros have a tiny integral;
+    # it must not be the difference of two large prefix sums
+    f = random_factors(32, 6, 32, 16, 17, signed=True)
+    for k in ("fs", "ft"):
+        f[k][6:20] = 0.0
+        f[k][5] *= 40.0
+        f[k][20] *= 40.0
+    u = synth.uniform(91, 1, 5 * 4000).reshape(4000, 5)
+    q = np.zeros(4000, dtype=synth.QUERY_DTYPE)
+    q["x"] = (u[:, 0] * 32).astype(np.int32)
+    q["y"] = (u[:, 1] * 32).astype(np.int32)
+    q["level"] = (u[:, 2] * 5).astype(np.float32)
+    q["s0"] = (6.0 - 10.0 ** (-1.0 - 4.0 * u[:, 3])).astype(np.float32)  # just before 6
+    q["s1"] = (6.0 + 13.0 * u[:, 4]).astype(np.float32)
+    q["t0"] = (20.0 - 14.0 * u[:, 3]).astype(np.float32)
+    q["t1"] = (20.0 + 10.0 ** (-1.0 - 4.0 * u[:, 4])).astype(np.float32)  # just past 20
+    got, st = _run(_material(f), q)
+    assert st == 0
+    err, _ = query_error(got, oracle_material(f), q)
+    assert err <= QUERY_TOL, err
 
 
 def test_scale_shape_ten_million_queries_sampled():
