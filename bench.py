@@ -62,6 +62,10 @@ def parse_args():
                    help="precisions the precision report covers (comma-separated)")
     p.add_argument("--report-workloads", default="brushed512,flakes1024",
                    help="workloads the precision report covers (comma-separated)")
+    p.add_argument("--clustered-report", action="store_true",
+                   help="instead of the step: the clustered compression layout of Sec. 4.2 on a "
+                        "256^2 flake map with 64^2 bins (layout, per-group CP-ALS, compression, "
+                        "block-splitting range queries)")
     p.add_argument("--precision-report", action="store_true",
                    help="instead of the step: CP-ALS fit error vs the FP64 oracle and sweep time "
                         "per MTTKRP precision on the 512^2 precision workload, and the sweep time "
@@ -705,8 +709,91 @@ def sampling_report(args):
                       "data": "synthetic (seeded random factors, uniform footprints)"}), flush=True)
 
 
+def clustered_report(args):
+    """The clustered compression layout of Sec. 4.2 (row f2) on a 256^2 flake
+    map with 9 levels and 64^2 bins (16 angular blocks of 16^2 per image),
+    rank 16: layout, batched per-group CP-ALS to |delta fit| < 1e-4 (at most
+    500 sweeps, Sec. 4.2), compression ratio, and 10^6 fractional range queries
+    through the block-splitting query kernel, with its HBM roofline."""
+    import numpy as np
+    import torch
+    import paper_2109_14807_gb300 as g
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS["clustered256"]
+    N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    m = torch.from_numpy(synth.make_map(w)).cuda()
+    H = g.build_footprint_ndfs(m, L, B)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    lay = g.cluster_layout(H)
+    b.record()
+    torch.cuda.synchronize()
+    layout_ms = a.elapsed_time(b)
+    off = lay["offsets"].cpu().numpy()
+    init = synth.cluster_init(lay["G"], off, R, 6006)
+    st = g.new_status()
+    a, b = ev(), ev()
+    a.record()
+    fac = g.cluster_decompose(H, lay, R, init, max_sweeps=500, tol=1e-4, status=st)
+    b.record()
+    torch.cuda.synchronize()
+    als_ms = a.elapsed_time(b)
+    sweeps = fac["sweeps"].cpu().numpy()
+    fits = fac["fit"].cpu().numpy()
+    nonempty = np.diff(off) > 0
+    t = g.CLUSTER_BLOCK
+    stored = int(sum(R * (2 * t + int(mj) + 1) + 2 * R * (t + 1) for mj in np.diff(off) if mj))
+    ratio = stored / float(L * N * N * B * B)
+    tab = g.cluster_tables(lay, fac)
+    q = synth.queries_fractional(N, L, B, w["queries"], 6007, frac_level=True)
+    qd = g.queries_to_device(q)
+    out = torch.empty(len(q), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        g.cluster_range_query(lay, tab, qd, out=out)
+    times = []
+    for _ in range(max(3, args.steps // 3)):
+        flush.zero_()  # L2 flush between timed launches
+        a, b = ev(), ev()
+        a.record()
+        g.cluster_range_query(lay, tab, qd, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    qms = float(np.median(times))
+    # algorithmic bytes per query: the descriptor, then for each of the two
+    # blended levels one z-map word, the group offset and, per rank, two SAT
+    # rows of each in-block factor and one Z row entry (blocks crossed: 1 for
+    # almost every range of the mix)
+    per_q = 32 + 2 * (8 + R * (2 * 16 + 2 * 16 + 4))
+    peaks, src = load_peaks()
+    peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    achieved = per_q * len(q) / (qms / 1e3) / 1e9
+    print(json.dumps({
+        "metric": "clustered layout (Sec. 4.2): per-group CP-ALS and block-splitting range queries",
+        "config": {"workload": "clustered256", "N": N, "levels": L, "bins": B, "block": t, "region": 8,
+                   "rank": R, "groups": lay["G"], "queries": len(q)},
+        "layout_ms": layout_ms, "members": lay["total"], "largest_group": lay["max_members"],
+        "nonempty_groups": int(nonempty.sum()),
+        "blank_blocks_dropped": 1.0 - lay["total"] / float(L * N * N * (B // t) ** 2),
+        "als_ms": als_ms, "als_sweeps_mean": float(sweeps[nonempty].mean()),
+        "als_sweeps_max": int(sweeps.max()), "fit_min": float(fits[nonempty].min()),
+        "fit_median": float(np.median(fits[nonempty])), "status": g.status_bits(st),
+        "compression_ratio": ratio,
+        "query_ms": qms, "queries_per_s": len(q) / (qms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "bytes_per_query": per_q,
+                     "peak_source": src},
+        "data": "synthetic (seeded flake map, seeded initial factors)"}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.clustered_report:
+        clustered_report(args)
+        return
     if args.sampling_report:
         sampling_report(args)
         return

@@ -293,6 +293,8 @@ WORKLOADS = {
                        sigma_x=0.05, sigma_y=0.3, scratches=200, sweeps=20),
     "flakes1024": dict(N=1024, levels=11, bins=32, rank=64, seed=3, map="flakes",
                        cells=16384, alpha=0.1, queries=10_000_000, qkind="fractional"),
+    "clustered256": dict(N=256, levels=9, bins=64, rank=16, seed=6, map="flakes",
+                         cells=1024, alpha=0.15, queries=1_000_000, qkind="fractional"),
     "flakes256": dict(N=256, levels=9, bins=32, rank=16, seed=5, map="flakes",
                       cells=1024, alpha=0.15, sweeps=20, queries=1_000_000,
                       qkind="fractional"),
