@@ -149,13 +149,11 @@ __device__ __forceinline__ QTerms query_terms(const gsp_query& d, const gsp_mate
 __device__ __forceinline__ float sat_mean(const float4* __restrict__ sat, int R, int r, int i0,
                                           int i1, float f0, float f1, float inv_w, int iz) {
   if (inv_w > 0.0f) {
-    if (i0 == i1) return __ldg(reinterpret_cast<const float*>(sat + static_cast<size_t>(i0) * R + r) + 2);
     const float4 a = __ldg(sat + static_cast<size_t>(i0 + 1) * R + r);  // prefix(i0 + 1), f[i0]
     const float4 b = __ldg(sat + static_cast<size_t>(i1) * R + r);      // prefix(i1), f[i1]
     const float mid = (b.x - a.x) + (b.y - a.y);
-    const float head = (1.0f - f0) * a.w;
-    const float tail = f1 * b.z;
-    return ((head + mid) + tail) * inv_w;
+    const float v = fmaf(f1, b.z, fmaf(1.0f - f0, a.w, mid)) * inv_w;
+    return i0 == i1 ? a.w : v;  // inside one bin: the bin's value
   }
   return __ldg(reinterpret_cast<const float*>(sat + static_cast<size_t>(iz) * R + r) + 2);
 }
@@ -303,7 +301,7 @@ __device__ __forceinline__ void red_add(float* p, const float* v) {
 // at column (r mod VEC) * R/VEC + r / VEC, so that the lanes' atomics for one
 // v = r mod VEC hit consecutive words (no bank conflicts); the flush undoes it.
 template <int LANES, int VEC>
-__global__ void __launch_bounds__(256) k_range_query_bwd(const __grid_constant__ MatParams mp,
+__global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constant__ MatParams mp,
                                                          const __grid_constant__ GradParams gp,
                                                          const gsp_query* __restrict__ q,
                                                          long long n,
