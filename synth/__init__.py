@@ -295,6 +295,8 @@ WORKLOADS = {
                        cells=16384, alpha=0.1, queries=10_000_000, qkind="fractional"),
     "clustered256": dict(N=256, levels=9, bins=64, rank=16, seed=6, map="flakes",
                          cells=1024, alpha=0.15, queries=1_000_000, qkind="fractional"),
+    "clustered64": dict(N=64, levels=7, bins=64, rank=16, seed=7, map="flakes",
+                        cells=64, alpha=0.15, queries=100_000, qkind="fractional"),
     "flakes256": dict(N=256, levels=9, bins=32, rank=16, seed=5, map="flakes",
                       cells=1024, alpha=0.15, sweeps=20, queries=1_000_000,
                       qkind="fractional"),
