@@ -158,25 +158,33 @@ def load_peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
-def _src_hash(name):
-    path = os.path.join(ROOT, "paper_2109_14807_gb300", "csrc", name)
+def _src_hash(names):
+    """sha256 prefix of the concatenated sources `names` (csrc file names)."""
+    h = hashlib.sha256()
     try:
-        return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
+        for name in names:
+            h.update(open(os.path.join(ROOT, "paper_2109_14807_gb300", "csrc", name), "rb").read())
     except OSError:
         return None
+    return h.hexdigest()[:12]
 
 
-KERNEL_SOURCE = {"box_hist": "binning.cu", "cast": "binning.cu",
-                 "mttkrp_xy": "mttkrp_tc.cu", "mttkrp_lst": "mttkrp_tc.cu",
-                 "range_query": "query.cu", "range_query_backward": "query.cu"}
+# The source files that fix a kernel's DRAM traffic: its own, plus, for the
+# operand kernels, the operand layout (columns kept, tile shapes).
+_OPERAND = ("als.cu", "mttkrp.cuh")
+KERNEL_SOURCE = {"box_hist": ("binning.cu",) + _OPERAND, "cast": ("als.cu", "mttkrp.cuh"),
+                 "mttkrp_xy": ("mttkrp_tc.cu",) + _OPERAND, "mttkrp_lst": ("mttkrp_tc.cu",) + _OPERAND,
+                 "range_query": ("query.cu",), "range_query_backward": ("query.cu",)}
 
 
 def ncu_traffic(kernel, precision):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
-    when absent or when the kernel's source changed since the capture."""
+    when absent or when the kernel's sources changed since the capture."""
     src = KERNEL_SOURCE.get(kernel)
+    if src is None:
+        return None
     if precision == "fp32" and kernel.startswith("mttkrp"):
-        src = "mttkrp_simt.cu"
+        src = ("mttkrp_simt.cu",) + _OPERAND
     try:
         lines = open(TRAFFIC_FILE).read().splitlines()
     except OSError:
@@ -405,7 +413,8 @@ def run_gsp(args, rank, world):
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
-    roof = roofline(prof, w, prec, peaks, peak_src)
+    n_occ, cols = ws.operand_cols()
+    roof = roofline(prof, w, prec, peaks, peak_src, n_occ, cols)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -446,37 +455,60 @@ def run_gsp(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+# Per-query gather and update rows of the query kernels (fractional rectangle,
+# integer level): fx, fy, flw and the two summed-area-table rows of each end
+# of both angular ranges read; the adjoint adds one R-wide update row for every
+# row read (dfx, dfy, dflw, dP and df at both ends of both ranges).
+QUERY_ROWS = 11
 ALG_BYTES_DESC = {
-    "box_hist": "NDF tensor of all levels written once in the operand type (|X| x element bytes)",
-    "cast": "int32 histogram slice read and operand slice written",
+    "box_hist": "NDF tensor of all levels written once in the operand type (|X| x element bytes, "
+                "|X| = N^2 x levels x operand columns)",
+    "cast": "occupied int32 counts of a histogram slice read and operand slice written",
     "mttkrp_xy": "operand tensor read once (|X| x element bytes)",
     "mttkrp_lst": "operand tensor read once (|X| x element bytes)",
-    "range_query": "11 table rows x R x 4 B + 36 B per fractional query",
+    "range_query": "11 table rows x R x 4 B + 36 B per fractional query (rows are L1/L2-resident: "
+                   "DRAM sees the 36 B)",
+    "range_query_backward": "11 table rows read + 11 R-wide gradient rows updated, x R x 4 B, + 36 B "
+                            "per query (rows and gradient tables are L1/L2/shared-resident)",
 }
 
 
-def roofline(prof, w, prec, peaks, peak_src):
+def roofline(prof, w, prec, peaks, peak_src, n_occ, cols):
+    """Roofline of the dominant kernel.  The operand holds `cols` columns per
+    footprint (the n_occ bins occurring in the map, zero-padded), so
+    |X| = N^2 * L * cols."""
     N, L, B, R, nq = w["N"], w["levels"], w["bins"], w["rank"], w["queries"]
     esize = 2 if prec == "bf16" else 4
-    X = N * N * L * B * B
+    X = N * N * L * cols
     per_launch = {
-        "box_hist": X * esize, "cast": N * N * B * B * (4 + esize),
+        "box_hist": X * esize, "cast": N * N * (n_occ * 4 + cols * esize),
         "mttkrp_xy": X * esize, "mttkrp_lst": X * esize,
-        "range_query": nq * (11 * R * 4 + 36),
+        "range_query": nq * (QUERY_ROWS * R * 4 + 36),
+        "range_query_backward": nq * (2 * QUERY_ROWS * R * 4 + 36),
     }
-    cands = [(v[1], k) for k, v in prof.items() if k in per_launch]
-    if not cands:
-        return None
-    _, k = max(cands)
-    n_l, ms = prof[k]
-    avg_s = ms / n_l / 1e3
-    achieved = per_launch[k] / avg_s / 1e9
     peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
-    return {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(k, prec),
-            "algorithmic_bytes_per_launch": per_launch[k], "avg_launch_ms": avg_s * 1e3,
-            "bytes_definition": ALG_BYTES_DESC[k], "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)"
-            if peak_src == "measured" else "fallback"}
+    src = f"{peak_src} (MEASURED_PEAKS hbm_gbs)" if peak_src == "measured" else "fallback"
+
+    def entry(k):
+        n_l, ms = prof[k]
+        avg_s = ms / n_l / 1e3
+        achieved = per_launch[k] / avg_s / 1e9
+        return {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(k, prec),
+                "algorithmic_bytes_per_launch": per_launch[k], "avg_launch_ms": avg_s * 1e3,
+                "bytes_definition": ALG_BYTES_DESC[k], "peak_source": src}
+
+    # the kernel with the largest share of the step, over every profiled kernel
+    top = max(prof, key=lambda k: prof[k][1]) if prof else None
+    if top not in per_launch:
+        return None
+    out = entry(top)
+    out["occupied_bins"], out["operand_columns"] = n_occ, cols
+    out["others"] = [{k2: v for k2, v in entry(k).items() if k2 in ("kernel", "achieved", "frac", "traffic",
+                                                                    "avg_launch_ms")}
+                     for k in sorted(per_launch, key=lambda k: -prof.get(k, (1, 0.0))[1])
+                     if k in prof and k != top]
+    return out
 
 
 def query_parity(g, mat, qd, q_np, out, n_sample=100_000, tuning=None):

@@ -172,12 +172,21 @@ typedef struct gsp_als_report {
 size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precision);
 
 /* Build the MTTKRP operand (the NDF tensor in the precision's input type,
- * [l][y][x][s][t]: BF16 for GSP_PREC_BF16 / _BF16_1X, else FP32, on the TF32
- * grid for GSP_PREC_TF32; it occupies the first levels*N*N*B*B elements of
- * d_ws) and ||T||^2 inside the workspace.  Exactly one of d_hist
+ * [l][y][x][c]: BF16 for GSP_PREC_BF16 / _BF16_1X, else FP32, on the TF32
+ * grid for GSP_PREC_TF32; it occupies the first levels*N*N*C elements of
+ * d_ws) and ||T||^2 inside the workspace.  The operand keeps only the bins
+ * that occur somewhere in the map (all other bins are zero in every
+ * footprint): column c < n holds the c-th occurring bin (s*B + t, in
+ * increasing order), columns n .. C-1 are zero, C = n rounded up to a multiple
+ * of 128 (at most B*B); with B*B < 256, C = B*B and column c is bin c.  The
+ * call synchronises `stream` once to learn C (gsp_cp_operand_cols reports
+ * it).  Dropping the all-zero columns changes only the order of the FP32
+ * accumulation against the full B*B operand.  Exactly one of d_hist
  * (int32 histograms from gsp_build_footprint_ndfs) and d_normal_xy (the normal
  * map: the histograms are then produced level by level straight into the
- * operand, never stored as int32) must be non-NULL.  GSP_PREC_STRUCTURED builds
+ * operand, never stored as int32) must be non-NULL; with d_hist the occurring
+ * bins are those of its level-0 slice (one count of 1 per texel, checked as
+ * for GSP_PREC_STRUCTURED below).  GSP_PREC_STRUCTURED builds
  * no operand: it keeps the bin map (binned from d_normal_xy, or read from the
  * level-0 slice of d_hist, which holds a single count of 1 per texel; a slice
  * that does not sets GSP_DEV_BAD_QUERY in d_status and that texel's bin to 0)
@@ -185,6 +194,12 @@ size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precisi
 int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, int N, int levels,
                    int bins, int rank, const gsp_als_opts* opts, void* d_ws,
                    size_t ws_bytes, uint32_t* d_status, gsp_stream stream);
+
+/* The operand columns of a workspace prepared by gsp_cp_prepare (dense-path
+ * precisions): h_cols[0] = bins occurring in the map, h_cols[1] = columns C
+ * per footprint.  Synchronises `stream`. */
+int gsp_cp_operand_cols(int N, int levels, int bins, int rank, int precision, const void* d_ws,
+                        size_t ws_bytes, int32_t* h_cols, gsp_stream stream);
 
 /* Run ALS sweeps on the operand prepared in d_ws.  `f` holds the starting
  * factors on entry (e.g. seeded U[0,1)) and the result on exit.  Mode order
@@ -196,7 +211,9 @@ int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, int N, int l
  * with that MTTKRP; the side stream starts after the work already queued on
  * `stream`, and everything the call queues joins back into `stream`.  While
  * `stream` is being captured into a CUDA graph everything stays on `stream`
- * (capture then needs h_report == NULL and tol == 0: no host reads). */
+ * (capture then needs h_report == NULL, tol == 0 and a workspace prepared in
+ * this process, whose operand column count the library then knows without
+ * reading the device). */
 int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_als_opts* opts,
                   const gsp_cp_factors* f, gsp_als_report* h_report, void* d_ws,
                   size_t ws_bytes, gsp_stream stream);

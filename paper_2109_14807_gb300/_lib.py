@@ -81,6 +81,8 @@ _SIGS = {
                                 POINTER(QueryTuning), c_void_p, c_size_t, c_void_p]),
     "gsp_sample_ndf": (c_int, [POINTER(Material), c_int, c_void_p, c_int64, c_void_p, c_void_p,
                                c_void_p, c_void_p]),
+    "gsp_cp_operand_cols": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, c_size_t,
+                                    POINTER(c_int32), c_void_p]),
     "gsp_cluster_groups": (c_int, [c_int, c_int, c_int]),
     "gsp_cluster_layout_bytes": (c_size_t, [c_int, c_int, c_int]),
     "gsp_cluster_layout": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,

@@ -111,6 +111,16 @@ class CPWorkspace:
             self.N, self.levels, self.bins, self.rank, ctypes.byref(opts), _ptr(self.buf),
             self.buf.numel(), _ptr(status), _stream()))
 
+    def operand_cols(self):
+        """(bins occurring in the map, operand columns per footprint) of the
+        prepared operand (dense-path precisions)."""
+        lib = load()
+        h = (ctypes.c_int32 * 2)()
+        check("gsp_cp_operand_cols", lib.gsp_cp_operand_cols(
+            self.N, self.levels, self.bins, self.rank, self.precision, _ptr(self.buf),
+            self.buf.numel(), h, _stream()))
+        return int(h[0]), int(h[1])
+
     def sweeps(self, factors: dict, sweeps: int, tol=0.0, report=True):
         """Run ALS sweeps in place on `factors`; returns the list of fits (or None)."""
         lib = load()

@@ -16,6 +16,9 @@
 // FP64; the two passes over T are the MTTKRP kernels (FP32 FFMA or tcgen05).
 #include <math.h>
 
+#include <mutex>
+#include <vector>
+
 #include "mttkrp.cuh"
 #include "ndf_build.cuh"
 #include "solve.cuh"
@@ -28,7 +31,7 @@ constexpr int kJacobiMaxRank = 64;
 constexpr int kGramRows = 64;  // rows of a factor per partial Gram matrix
 
 struct CpLayout {
-  size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, Gpart, W, lam, fit, sumsq, norm2, flags, total;
+  size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, Gpart, W, lam, fit, sumsq, norm2, flags, cols, total;
   // GSP_PREC_STRUCTURED only (zero-sized otherwise)
   size_t binsT, AL, BE, part, pre, sig, sig64, segtot, off, stpart, lscale;
   // GSP_PREC_STRUCTURED_GAUSSIAN only
@@ -91,6 +94,9 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   o.sumsq = take(L * sizeof(unsigned long long));
   o.norm2 = take(sizeof(double));
   o.flags = take(16);
+  // bin compaction: {count, Bk, pad, pad}, column -> dense bin [B2], dense bin ->
+  // column [B2] (int32), occupancy bitmask [B2 / 32]
+  o.cols = take((4 + 2 * B2 + (B2 + 31) / 32) * sizeof(int32_t));
   o.total = off;
   return o;
 }
@@ -102,37 +108,42 @@ bool valid_cp(int N, int L, int B, int R, int prec) {
 
 // --------------------------------------------------------------- kernels --
 
-// KR[(l*B2 + s*B + t)][r] = fl[l][r] fs[s][r] ft[t][r]   (row layout, FP32)
+// Dense bin of operand column c: cols (column -> dense bin, -1 for padding)
+// or the identity when the operand holds all B * B bins.
+__device__ __forceinline__ int col_bin(const int32_t* cols, int c) { return cols ? cols[c] : c; }
+
+// KR[(l*K1 + c)][r] = fl[l][r] fs[s][r] ft[t][r], (s, t) the bin of column c
+// (0 for a padding column); row layout, FP32.  K1 = operand columns.
 __global__ void k_kr_rows(const float* __restrict__ fl, const float* __restrict__ fs,
-                          const float* __restrict__ ft, int L, int B, int R,
-                          float* __restrict__ out) {
+                          const float* __restrict__ ft, int L, int B, int K1, int R,
+                          const int32_t* __restrict__ cols, float* __restrict__ out) {
   long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  long long total = static_cast<long long>(L) * B * B * R;
+  long long total = static_cast<long long>(L) * K1 * R;
   if (i >= total) return;
   int r = static_cast<int>(i % R);
   long long k = i / R;
-  int t = static_cast<int>(k % B);
-  int s = static_cast<int>((k / B) % B);
-  int l = static_cast<int>(k / (static_cast<long long>(B) * B));
-  out[i] = fl[l * R + r] * fs[s * R + r] * ft[t * R + r];
+  const int cidx = static_cast<int>(k % K1);
+  const int l = static_cast<int>(k / K1);
+  const int b = col_bin(cols, cidx);
+  out[i] = b < 0 ? 0.0f : fl[l * R + r] * fs[(b / B) * R + r] * ft[(b % B) * R + r];
 }
 
-// KRt[r][l*B2 + s*B + t] in the operand type (the K-major B operand of the
+// KRt[r][l*K1 + c] in the operand type (the K-major B operand of the
 // tensor-core pass): BF16, or FP32 rounded to the nearest TF32; with `split`
 // rows R..2R-1 hold the remainder v - hi of rows 0..R-1, rounded the same way.
 template <typename OutT>
 __global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict__ fs,
-                          const float* __restrict__ ft, int L, int B, int R, int split,
-                          OutT* __restrict__ out) {
+                          const float* __restrict__ ft, int L, int B, int K1, int R, int split,
+                          const int32_t* __restrict__ cols, OutT* __restrict__ out) {
   long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  long long K = static_cast<long long>(L) * B * B;
+  long long K = static_cast<long long>(L) * K1;
   if (i >= K * R) return;
   long long k = i % K;
   int r = static_cast<int>(i / K);
-  int t = static_cast<int>(k % B);
-  int s = static_cast<int>((k / B) % B);
-  int l = static_cast<int>(k / (static_cast<long long>(B) * B));
-  float v = fl[l * R + r] * fs[s * R + r] * ft[t * R + r];
+  const int cidx = static_cast<int>(k % K1);
+  const int l = static_cast<int>(k / K1);
+  const int b = col_bin(cols, cidx);
+  float v = b < 0 ? 0.0f : fl[l * R + r] * fs[(b / B) * R + r] * ft[(b % B) * R + r];
   if constexpr (sizeof(OutT) == 2) {
     __nv_bfloat16 hi = __float2bfloat16_rn(v);
     out[i] = hi;
@@ -141,6 +152,185 @@ __global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict_
     const float hi = round_tf32(v);
     out[i] = hi;
     if (split) out[i + K * R] = round_tf32(v - hi);
+  }
+}
+
+// ------------------------------------------------------- bin compaction --
+// Bins that no texel of the map falls in are zero in every footprint of every
+// level: the dense operand's columns for them carry nothing (Sec. 4.2 drops
+// blank NDF blocks for the same reason).  The operand keeps the occupied bins
+// only, in increasing order, padded with zero columns to a multiple of 128
+// (the tensor-core tiles); the bin map is renumbered to those columns, so the
+// histogram and MTTKRP kernels just see a smaller bin axis, and only the
+// Khatri-Rao operand and the (l, s, t) contractions map a column back to its
+// (s, t).  All results are those of the dense operand.
+
+// occ bit b: bin b occurs in the map.  Lanes holding the same bin elect one
+// shared-memory OR; every CTA ORs its mask into the global one.
+__global__ void k_bin_occupancy(const uint16_t* __restrict__ bins, long long n, int B2,
+                                uint32_t* __restrict__ occ) {
+  __shared__ uint32_t m[512];  // B2 <= 16384
+  const int words = (B2 + 31) / 32;
+  for (int i = threadIdx.x; i < words; i += blockDim.x) m[i] = 0u;
+  __syncthreads();
+  for (long long u = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; u < n;
+       u += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int b = bins[u];
+    const unsigned peers = __match_any_sync(__activemask(), b);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(m + (b >> 5), 1u << (b & 31));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < words; i += blockDim.x)
+    if (m[i]) atomicOr(occ + i, m[i]);
+}
+
+// cols = {count, Bk, 0, 0, col -> bin [Bk] (-1: padding), bin -> col [B2] (-1:
+// absent)}.  Bk = B2 (identity columns) when B2 < 256, else the occupied count
+// rounded up to 128, at most B2.  One CTA of 512 threads, one word each.
+__global__ void __launch_bounds__(512) k_bin_compact(const uint32_t* __restrict__ occ, int B2,
+                                                     int32_t* __restrict__ cols) {
+  __shared__ int wbase[512];
+  const int words = (B2 + 31) / 32;
+  const int w = threadIdx.x;
+  const uint32_t bits = w < words ? occ[w] : 0u;
+  wbase[w] = __popc(bits);
+  __syncthreads();
+  for (int off = 1; off < 512; off <<= 1) {  // inclusive scan of the word counts
+    const int v = w >= off ? wbase[w - off] : 0;
+    __syncthreads();
+    wbase[w] += v;
+    __syncthreads();
+  }
+  const int count = wbase[511];
+  const bool ident = B2 < 256;
+  int Bk = ident ? B2 : ((count + 127) / 128) * 128;
+  if (Bk < 128 && !ident) Bk = 128;
+  if (Bk > B2) Bk = B2;
+  int32_t* col_bin_t = cols + 4;
+  int32_t* bin_col_t = cols + 4 + B2;
+  if (w == 0) {
+    cols[0] = ident ? B2 : count;
+    cols[1] = Bk;
+    cols[2] = cols[3] = 0;
+  }
+  if (w < words) {
+    int rank = wbase[w] - __popc(bits);
+    for (int k = 0; k < 32; ++k) {
+      const int b = w * 32 + k;
+      if (b >= B2) break;
+      if (ident) {
+        bin_col_t[b] = b;
+        col_bin_t[b] = b;
+      } else if ((bits >> k) & 1u) {
+        bin_col_t[b] = rank;
+        col_bin_t[rank] = b;
+        ++rank;
+      } else {
+        bin_col_t[b] = -1;
+      }
+    }
+  }
+  __syncthreads();
+  if (!ident)
+    for (int c = count + w; c < Bk; c += 512) col_bin_t[c] = -1;
+}
+
+// bins[u] <- column of bins[u]
+__global__ void k_bin_remap(uint16_t* __restrict__ bins, long long n, const int32_t* __restrict__ cols,
+                            int B2) {
+  const long long u = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (u < n) bins[u] = static_cast<uint16_t>(cols[4 + B2 + bins[u]]);
+}
+
+// groups bit g: column group g (16 columns) holds an occupied bin
+__global__ void k_col_groups(const int32_t* __restrict__ cols, uint32_t* __restrict__ groups) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= static_cast<int>(kGroupBytes * 8)) return;
+  const int count = cols[0];
+  if ((g & 31) == 0) {
+    uint32_t wbits = 0u;
+    for (int k = 0; k < 32; ++k)
+      if ((g + k) * 16 < count) wbits |= 1u << k;
+    groups[g >> 5] = wbits;
+  }
+}
+
+// The operand from int32 histograms [N][N][B2] of one level: column c takes
+// the count of its bin (0 for padding), times scale, rounded like the
+// histogram sink (exact FP32; TF32 / BF16 without bias, the dither indexed by
+// the element's index base + i in the operand); Sigma count^2 into *sumsq.
+template <typename OutT>
+__global__ void k_cast_cols(const int32_t* __restrict__ h, long long fps, int B2, int Bk,
+                            const int32_t* __restrict__ cols, float scale, int tf32,
+                            long long base, OutT* __restrict__ out,
+                            unsigned long long* __restrict__ sumsq) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  unsigned long long q = 0;
+  if (i < fps * Bk) {
+    const long long fp = i / Bk;
+    const int c = static_cast<int>(i % Bk);
+    const int b = cols[4 + c];
+    const int v = b < 0 ? 0 : h[fp * B2 + b];
+    q = static_cast<unsigned long long>(static_cast<long long>(v) * v);
+    const float f = static_cast<float>(v) * scale;
+    const uint32_t d = weyl_dither(static_cast<unsigned long long>(base + i));
+    if constexpr (sizeof(OutT) == 2) {
+      out[i] = __ushort_as_bfloat16(static_cast<unsigned short>(bf16_dither(f, d)));
+    } else {
+      out[i] = tf32 ? tf32_dither(f, d) : f;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
+  if ((threadIdx.x & 31) == 0 && q) atomicAdd(sumsq, q);
+}
+
+// M_l, M_s or M_t (mode 2, 3, 4) from Z' [L][K1][R] over the operand columns:
+//   l: M[l][r] = sum_c Z'[l][c][r] fs[s_c][r] ft[t_c][r]
+//   s: M[s][r] = sum_{l, c : s_c = s} Z'[l][c][r] fl[l][r] ft[t_c][r]
+//   t: M[t][r] = sum_{l, c : t_c = t} Z'[l][c][r] fl[l][r] fs[s_c][r]
+// (s_c, t_c) the bin of column c (padding columns skipped).  One CTA per output
+// row; thread (part, r) sums every 256/R-th term with compensated FP32, the
+// parts are added in FP64 in a fixed order.
+__global__ void __launch_bounds__(256) k_contract_cols(const float* __restrict__ Zp, int L, int B,
+                                                       int K1, int R, const int32_t* __restrict__ colbin,
+                                                       const float* __restrict__ fl,
+                                                       const float* __restrict__ fs,
+                                                       const float* __restrict__ ft, int mode,
+                                                       double* __restrict__ M,
+                                                       float* __restrict__ Mf) {
+  __shared__ double red[256];
+  const int i = blockIdx.x;
+  const int r = threadIdx.x % R, part = threadIdx.x / R, P = blockDim.x / R;
+  float hi = 0.0f, lo = 0.0f;
+  auto add = [&](float x) {
+    const float t = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+    hi = t;
+  };
+  if (part < P) {
+    if (mode == 2) {
+      for (int c = part; c < K1; c += P) {
+        const int b = colbin[c];
+        if (b >= 0)
+          add(Zp[(static_cast<size_t>(i) * K1 + c) * R + r] * fs[(b / B) * R + r] * ft[(b % B) * R + r]);
+      }
+    } else {
+      for (int c = part; c < K1; c += P) {
+        const int b = colbin[c];
+        if (b < 0 || (mode == 3 ? b / B : b % B) != i) continue;
+        const float o = mode == 3 ? ft[(b % B) * R + r] : fs[(b / B) * R + r];
+        for (int l = 0; l < L; ++l) add(Zp[(static_cast<size_t>(l) * K1 + c) * R + r] * fl[l * R + r] * o);
+      }
+    }
+  }
+  red[threadIdx.x] = part < P ? static_cast<double>(hi) + static_cast<double>(lo) : 0.0;
+  __syncthreads();
+  if (threadIdx.x < R) {
+    double acc = 0.0;
+    for (int q = 0; q < P; ++q) acc += red[q * R + threadIdx.x];
+    if (M) M[i * R + threadIdx.x] = acc;
+    if (Mf) Mf[i * R + threadIdx.x] = static_cast<float>(acc);
   }
 }
 
@@ -557,18 +747,20 @@ int ensure_smem_attr() {
 int run_xy(const Ctx& c, const float* fl, const float* fs, const float* ft) {
   const MttkrpDims& d = c.d;
   long long K = static_cast<long long>(d.L) * d.B2();
+  const int32_t* cb = c.at<int32_t>(c.lay.cols) + 4;
   if (c.prec == GSP_PREC_FP32) {
-    k_kr_rows<<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.R, c.at<float>(c.lay.KR));
+    k_kr_rows<<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.B2(), d.R, cb,
+                                                       c.at<float>(c.lay.KR));
     GSP_CHECK_LAUNCH();
     return simt_mttkrp_xy(c.at<float>(c.lay.T), c.at<float>(c.lay.KR), c.at<float>(c.lay.Yp), d, c.s);
   }
   if (is_bf16(c.prec))
     k_kr_cols<__nv_bfloat16><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(
-        fl, fs, ft, d.L, d.B, d.R, c.prec == GSP_PREC_BF16 ? 1 : 0,
+        fl, fs, ft, d.L, d.B, d.B2(), d.R, c.prec == GSP_PREC_BF16 ? 1 : 0, cb,
         c.at<__nv_bfloat16>(c.lay.KR));
   else
-    k_kr_cols<float><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.R, 1,
-                                                               c.at<float>(c.lay.KR));
+    k_kr_cols<float><<<grid_for(K * d.R, 256), 256, 0, c.s>>>(fl, fs, ft, d.L, d.B, d.B2(), d.R, 1,
+                                                               cb, c.at<float>(c.lay.KR));
   GSP_CHECK_LAUNCH();
   return tc_mttkrp_xy(c.ws + c.lay.T, c.ws + c.lay.KR, c.at<float>(c.lay.Yp), d, c.prec,
                       c.at<uint32_t>(c.lay.flags), c.s);
@@ -579,7 +771,12 @@ int run_lst(const Ctx& c, const float* fx, const float* fy) {
   if (c.prec != GSP_PREC_FP32)
     return tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.ws + c.lay.FX, c.at<float>(c.lay.Zpart),
                          c.at<float>(c.lay.Zp), d, c.prec, c.at<uint32_t>(c.lay.flags), c.s);
-  const int C = lst_chunks(d, c.prec);
+  // split-K chunks: within the partial buffer the layout sized for all B * B columns
+  MttkrpDims dense = d;
+  dense.Bk = 0;
+  int C = lst_chunks(d, c.prec);
+  const long long cap = static_cast<long long>(lst_chunks(dense, c.prec)) * dense.B2() / d.B2();
+  while (C > 1 && C > cap) C >>= 1;
   GSP_TRY(simt_mttkrp_lst(c.at<float>(c.lay.T), fx, fy, c.at<float>(c.lay.Zpart), d, C, c.s));
   long long per_level = static_cast<long long>(d.B2()) * d.R;
   k_zreduce<<<grid_for(per_level * d.L, 256), 256, 0, c.s>>>(c.at<float>(c.lay.Zpart),
@@ -622,8 +819,11 @@ int contract(const Ctx& c, int mode, const gsp_cp_factors& f, double* M, float* 
   prof_begin(PROF_ALS_SMALL, c.s);
   if (mode == 0)
     k_contract_rows<<<I, 256, 0, c.s>>>(p.W, p.w1, p.J1, p.A1, d.R, M, Mf);
-  else
+  else if (mode == 1)
     k_contract<<<I, 256, 0, c.s>>>(p);
+  else
+    k_contract_cols<<<I, 256, 0, c.s>>>(c.at<float>(c.lay.Zp), d.L, d.B, d.B2(), d.R,
+                                        c.at<int32_t>(c.lay.cols) + 4, f.fl, f.fs, f.ft, mode, M, Mf);
   prof_end(PROF_ALS_SMALL, c.s);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
@@ -716,6 +916,39 @@ int join_solve(const Ctx& c, const gsp_cp_factors& f, int mode) {
   return solve_apply(c, f, mode);
 }
 
+// Operand columns of prepared workspaces, kept on the host so that sweeps and
+// MTTKRPs launch without reading the device (and can be graph-captured).
+struct ColsEntry {
+  const void* ws;
+  int N, L, B, R, prec, Bk;
+};
+std::mutex g_cols_mu;
+std::vector<ColsEntry> g_cols;
+
+void remember_cols(const void* ws, const MttkrpDims& d, int prec, int Bk) {
+  std::lock_guard<std::mutex> lk(g_cols_mu);
+  for (auto& e : g_cols)
+    if (e.ws == ws) {
+      e = ColsEntry{ws, d.N, d.L, d.B, d.R, prec, Bk};
+      return;
+    }
+  if (g_cols.size() >= 256) g_cols.erase(g_cols.begin());
+  g_cols.push_back(ColsEntry{ws, d.N, d.L, d.B, d.R, prec, Bk});
+}
+
+int recall_cols(const void* ws, const MttkrpDims& d, int prec) {
+  std::lock_guard<std::mutex> lk(g_cols_mu);
+  for (const auto& e : g_cols)
+    if (e.ws == ws && e.N == d.N && e.L == d.L && e.B == d.B && e.R == d.R && e.prec == prec)
+      return e.Bk;
+  return -1;
+}
+
+bool valid_cols(const MttkrpDims& d, int Bk) {
+  const int B2 = d.B * d.B;
+  return B2 < 256 ? Bk == B2 : (Bk >= 128 && Bk <= B2 && Bk % 128 == 0);
+}
+
 bool path_supported(const MttkrpDims& d, int prec) {
   if (prec == GSP_PREC_FP32) return true;
   if (is_structured(prec)) return struct_supported(d);
@@ -733,6 +966,23 @@ int make_ctx(int N, int L, int B, int R, int prec, void* d_ws, size_t ws_bytes, 
   c.ws = static_cast<char*>(d_ws);
   c.s = to_stream(st);
   return ensure_smem_attr();
+}
+
+// The operand columns of a prepared dense-path workspace: from the host record
+// of its prepare, else read from the workspace.
+int resolve_cols(Ctx& c) {
+  if (is_structured(c.prec)) return GSP_OK;
+  int Bk = recall_cols(c.ws, c.d, c.prec);
+  if (Bk < 0) {
+    int32_t h[2] = {0, 0};
+    GSP_CUDA(cudaMemcpyAsync(h, c.ws + c.lay.cols, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+    GSP_CUDA(cudaStreamSynchronize(c.s));
+    Bk = h[1];
+    if (!valid_cols(c.d, Bk)) return GSP_ERR_INVALID_ARG;  // not a prepared workspace
+    remember_cols(c.ws, c.d, c.prec, Bk);
+  }
+  c.d.Bk = Bk;
+  return GSP_OK;
 }
 
 bool valid_factors(const gsp_cp_factors* f) {
@@ -801,7 +1051,7 @@ int prepare_structured(const int32_t* d_hist, const float* d_normal_xy, int raw,
       HistOut o{};
       o.sumsq = sumsq;
       o.groups = groups;
-      GSP_TRY(launch_box_hist(bm, d.N, d.L, d.B, o, c.s));
+      GSP_TRY(launch_box_hist(bm, d.N, d.L, d.B * d.B, o, c.s));
     }
   }
   GSP_TRY(struct_transpose_bins(bm, c.at<uint16_t>(c.lay.binsT), d.N, c.s));
@@ -879,25 +1129,52 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
   Ctx c;
   GSP_TRY(make_ctx(N, levels, bins, rank, opts->precision, d_ws, ws_bytes, stream, c));
   const MttkrpDims& d = c.d;
-  const long long slice = d.N2() * d.B2();
   unsigned long long* sumsq = c.at<unsigned long long>(c.lay.sumsq);
   GSP_CUDA(cudaMemsetAsync(sumsq, 0, sizeof(unsigned long long) * levels, c.s));
   GSP_CUDA(cudaMemsetAsync(c.ws + c.lay.flags, 0, 16, c.s));
   if (is_structured(c.prec)) return prepare_structured(d_hist, d_normal_xy, opts->raw_counts, d_status, c);
+  // bin map (dense bins), occupied bins, operand columns
+  const int B2 = bins * bins;
+  uint16_t* bm = c.at<uint16_t>(c.lay.bins);
+  uint32_t* groups = reinterpret_cast<uint32_t*>(c.ws + c.lay.bins + d.N2() * sizeof(uint16_t));
+  int32_t* cols = c.at<int32_t>(c.lay.cols);
+  uint32_t* occ = reinterpret_cast<uint32_t*>(cols + 4 + 2 * B2);
+  if (d_hist)
+    GSP_TRY(struct_bins_from_level0(d_hist, N, bins, bm, d_status, c.s));
+  else
+    GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, nullptr, c.s));
+  GSP_CUDA(cudaMemsetAsync(occ, 0, (B2 + 31) / 32 * sizeof(uint32_t), c.s));
+  k_bin_occupancy<<<sm_count() * 2, 256, 0, c.s>>>(bm, d.N2(), B2, occ);
+  GSP_CHECK_LAUNCH();
+  k_bin_compact<<<1, 512, 0, c.s>>>(occ, B2, cols);
+  GSP_CHECK_LAUNCH();
+  int32_t hc[2] = {0, 0};
+  GSP_CUDA(cudaMemcpyAsync(hc, cols, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
+  GSP_CUDA(cudaStreamSynchronize(c.s));
+  const int Bk = hc[1];
+  if (!valid_cols(d, Bk)) return GSP_ERR_INVALID_ARG;
+  remember_cols(c.ws, d, c.prec, Bk);
+  const long long slice = d.N2() * Bk;  // operand elements per level
   if (d_hist) {
     for (int l = 0; l < levels; ++l) {
-      LevelSink o{nullptr, nullptr, nullptr, 1.0f, sumsq + l, c.prec == GSP_PREC_TF32, slice * l};
-      o.scale = opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
+      const float scale =
+          opts->raw_counts ? 1.0f : static_cast<float>(bins * bins) / (4.0f * ldexpf(1.0f, 2 * l));
+      const int32_t* hl = d_hist + d.N2() * B2 * l;
       if (is_bf16(c.prec))
-        o.bf16 = c.at<__nv_bfloat16>(c.lay.T) + slice * l;
+        k_cast_cols<__nv_bfloat16><<<grid_for(slice, 256), 256, 0, c.s>>>(
+            hl, d.N2(), B2, Bk, cols, scale, 0, slice * l, c.at<__nv_bfloat16>(c.lay.T) + slice * l,
+            sumsq + l);
       else
-        o.f32 = c.at<float>(c.lay.T) + slice * l;
-      GSP_TRY(launch_cast(d_hist + slice * l, N, bins, o, c.s));
+        k_cast_cols<float><<<grid_for(slice, 256), 256, 0, c.s>>>(
+            hl, d.N2(), B2, Bk, cols, scale, c.prec == GSP_PREC_TF32, slice * l,
+            c.at<float>(c.lay.T) + slice * l, sumsq + l);
+      GSP_CHECK_LAUNCH();
     }
   } else {
-    uint16_t* bm = c.at<uint16_t>(c.lay.bins);
-    uint32_t* groups = reinterpret_cast<uint32_t*>(c.ws + c.lay.bins + d.N2() * sizeof(uint16_t));
-    GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, groups, c.s));
+    k_bin_remap<<<grid_for(d.N2(), 256), 256, 0, c.s>>>(bm, d.N2(), cols, B2);
+    GSP_CHECK_LAUNCH();
+    k_col_groups<<<grid_for(kGroupBytes * 8, 256), 256, 0, c.s>>>(cols, groups);
+    GSP_CHECK_LAUNCH();
     HistOut o{};
     o.sumsq = sumsq;
     o.groups = groups;
@@ -908,10 +1185,25 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
     else
       o.f32 = c.at<float>(c.lay.T);
     o.tf32 = c.prec == GSP_PREC_TF32;
-    GSP_TRY(launch_box_hist(bm, N, levels, bins, o, c.s));
+    GSP_TRY(launch_box_hist(bm, N, levels, Bk, o, c.s));
   }
   k_norm2<<<1, 32, 0, c.s>>>(sumsq, levels, bins, opts->raw_counts, c.at<double>(c.lay.norm2));
   GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+extern "C" int gsp_cp_operand_cols(int N, int levels, int bins, int rank, int precision,
+                                   const void* d_ws, size_t ws_bytes, int32_t* h_cols,
+                                   gsp_stream stream) {
+  if (!h_cols || is_structured(precision)) return GSP_ERR_INVALID_ARG;
+  Ctx c;
+  GSP_TRY(make_ctx(N, levels, bins, rank, precision, const_cast<void*>(d_ws), ws_bytes, stream, c));
+  int32_t h[2] = {0, 0};
+  GSP_CUDA(cudaMemcpyAsync(h, c.ws + c.lay.cols, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+  GSP_CUDA(cudaStreamSynchronize(c.s));
+  if (!valid_cols(c.d, h[1])) return GSP_ERR_INVALID_ARG;
+  h_cols[0] = h[0];
+  h_cols[1] = h[1];
   return GSP_OK;
 }
 
@@ -923,6 +1215,7 @@ extern "C" int gsp_cp_sweeps(int N, int levels, int bins, int rank, const gsp_al
     return GSP_ERR_INVALID_ARG;
   Ctx c;
   GSP_TRY(make_ctx(N, levels, bins, rank, opts->precision, d_ws, ws_bytes, stream, c));
+  GSP_TRY(resolve_cols(c));
   SideStream side(c);
   GSP_TRY(side.open());
   double* M = c.at<double>(c.lay.M);
@@ -976,6 +1269,7 @@ extern "C" int gsp_cp_mttkrp(int N, int levels, int bins, int rank, int precisio
     if (!d_m[m]) return GSP_ERR_INVALID_ARG;
   Ctx c;
   GSP_TRY(make_ctx(N, levels, bins, rank, precision, d_ws, ws_bytes, stream, c));
+  GSP_TRY(resolve_cols(c));
   if (is_structured(precision)) {
     const StructWs w = struct_ws(c);
     const uint16_t* bm = c.at<uint16_t>(c.lay.bins);

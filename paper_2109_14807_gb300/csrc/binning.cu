@@ -481,9 +481,8 @@ size_t box_hist_smem(int N) {
          4 * static_cast<size_t>(s_plane_ints(N)) * sizeof(int);
 }
 
-int launch_box_hist(const uint16_t* d_bins, int N, int levels, int bins, const HistOut& o,
+int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const HistOut& o,
                     cudaStream_t s) {
-  const int B2 = bins * bins;
   if (B2 % kHistG) return GSP_ERR_UNSUPPORTED;
   const int ychunk = N >= 256 ? 256 : N;
   const size_t smem = box_hist_smem(N);
@@ -539,5 +538,5 @@ extern "C" int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int lev
   o.h = d_hist;
   o.groups = groups;
   for (int l = 0; l < levels; ++l) o.scale[l] = 1.0f;
-  return launch_box_hist(bins_map, N, levels, bins, o, s);
+  return launch_box_hist(bins_map, N, levels, bins * bins, o, s);
 }

@@ -14,10 +14,14 @@
 
 namespace gsp {
 
+// Bk: bin columns of the operand per footprint.  0 means all B * B bins; the
+// CP-ALS prepare sets it to the occupied bins of the map (rounded up to 128),
+// the operand then holding those columns only (see als.cu, bin compaction).
 struct MttkrpDims {
   int N, L, B, R;
+  int Bk = 0;
   long long N2() const { return static_cast<long long>(N) * N; }
-  int B2() const { return B * B; }
+  int B2() const { return Bk ? Bk : B * B; }
 };
 
 // Number of split-K chunks per level used by the Z' pass (partials [L*C][B2][R]).

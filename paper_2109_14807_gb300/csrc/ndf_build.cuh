@@ -44,8 +44,9 @@ constexpr size_t kGroupBytes = 128 * 128 / 16 / 8;
 // 16-bin groups there (kGroupBytes, cleared first).
 int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins,
                 uint32_t* d_status, uint32_t* d_groups, cudaStream_t s);
-// Histograms of every footprint of every level 0..levels-1 from the bin map.
-int launch_box_hist(const uint16_t* d_bins, int N, int levels, int bins, const HistOut& o,
+// Histograms of every footprint of every level 0..levels-1 from the bin map,
+// whose codes lie in [0, B2) (B2 columns per footprint, a multiple of 16).
+int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const HistOut& o,
                     cudaStream_t s);
 // Copy / convert an existing int32 slice into a sink.
 int launch_cast(const int32_t* d_in, int N, int bins, LevelSink o, cudaStream_t s);

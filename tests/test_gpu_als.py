@@ -113,8 +113,8 @@ def test_als_from_normals_equals_from_histograms(prec):
 
 @pytest.mark.parametrize("prec,drop", [("bf16", 16), ("tf32", 13)])
 def test_operand_rounding_is_exact_or_neighbour_and_unbiased(prec, drop):
-    # The tensor-core operand (documented as the first levels*N^2*B^2 elements
-    # of the workspace) holds every exactly representable density unchanged and
+    # The tensor-core operand (documented as the first levels*N^2*columns
+    # elements of the workspace) holds every exactly representable density unchanged and
     # every other one as its lower or upper neighbour on the BF16 / TF32 grid,
     # without bias: the summed rounding error stays within six standard
     # deviations of a sum of independent zero-mean errors of at most one ulp.
@@ -125,11 +125,21 @@ def test_operand_rounding_is_exact_or_neighbour_and_unbiased(prec, drop):
     if not _supported(prec, N, L, B, R):
         pytest.skip(f"{prec} path unavailable")
     m = synth.flake_map(N, 16, 0.1, 77)
-    H = ndf.footprint_histograms(*ndf.bin_index(m, B), L, B)
-    exact = ndf.normalised_tensor(H, B).astype(np.float32).ravel()  # exact: counts * 2^k
+    s, t = ndf.bin_index(m, B)
+    H = ndf.footprint_histograms(s, t, L, B)
+    # operand columns: the bins occurring in the map, in increasing order, then
+    # zero columns up to a multiple of 128
+    occ = np.unique(s * B + t)
+    Bk = min(B * B, max(128, -(-len(occ) // 128) * 128))
+    dense = ndf.normalised_tensor(H, B).reshape(L, N, N, B * B)
+    exact = np.zeros((L, N, N, Bk), dtype=np.float32)
+    exact[..., :len(occ)] = dense[..., occ]  # exact: counts * 2^k
+    exact = exact.ravel()
+    del dense
     ws = g.CPWorkspace(N, L, B, R, prec)
     ws.prepare(normal_xy=dev(m))
     torch.cuda.synchronize()
+    assert ws.operand_cols() == (len(occ), Bk)
     n = exact.size
     if prec == "bf16":
         raw = ws.buf[: 2 * n].cpu().numpy().view(np.uint16).astype(np.uint64) << 16
