@@ -464,8 +464,8 @@ ALG_BYTES_DESC = {
     "box_hist": "NDF tensor of all levels written once in the operand type (|X| x element bytes, "
                 "|X| = N^2 x levels x operand columns)",
     "cast": "occupied int32 counts of a histogram slice read and operand slice written",
-    "mttkrp_xy": "operand tensor read once (|X| x element bytes)",
-    "mttkrp_lst": "operand tensor read once (|X| x element bytes)",
+    "mttkrp_xy": "operand tensor read once (|X| x element bytes) + Y' written (N^2 x R x 4 B)",
+    "mttkrp_lst": "operand tensor read once (|X| x element bytes) + Z' written (levels x columns x R x 4 B)",
     "range_query": "11 table rows x R x 4 B + 36 B per fractional query (rows are L1/L2-resident: "
                    "DRAM sees the 36 B)",
     "range_query_backward": "11 table rows read + 11 R-wide gradient rows updated, x R x 4 B, + 36 B "
@@ -482,7 +482,7 @@ def roofline(prof, w, prec, peaks, peak_src, n_occ, cols):
     X = N * N * L * cols
     per_launch = {
         "box_hist": X * esize, "cast": N * N * (n_occ * 4 + cols * esize),
-        "mttkrp_xy": X * esize, "mttkrp_lst": X * esize,
+        "mttkrp_xy": X * esize + N * N * R * 4, "mttkrp_lst": X * esize + L * cols * R * 4,
         "range_query": nq * (QUERY_ROWS * R * 4 + 36),
         "range_query_backward": nq * (2 * QUERY_ROWS * R * 4 + 36),
     }

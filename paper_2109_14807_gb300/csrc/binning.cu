@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kHistThreads, 1)
   const int plane = s_plane_ints(N), sbuf = 2 * plane;
   const int g0 = blockIdx.x * G;
   const int y0 = blockIdx.y * ychunk;
-  const int l = blockIdx.z;
+  const int l = gridDim.z - 1 - blockIdx.z;  // coarsest level first: its window fill is the longest
   const int w = 1 << l, a = w >> 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (o.groups && !((o.groups[blockIdx.x >> 5] >> (blockIdx.x & 31)) & 1u)) {
@@ -484,7 +484,23 @@ size_t box_hist_smem(int N) {
 int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const HistOut& o,
                     cudaStream_t s) {
   if (B2 % kHistG) return GSP_ERR_UNSUPPORTED;
-  const int ychunk = N >= 256 ? 256 : N;
+  // Rows per CTA: of 256, 128 and 64 (at most N), the largest whose grid fills
+  // the waves of one-CTA-per-SM residency to at least 90 %, else the best
+  // filling one (the window fill, at most N rows of 2-byte L2 reads, is small
+  // next to 64 rows of output).
+  const int sms = sm_count();
+  int ychunk = N >= 256 ? 256 : N;
+  double best = -1.0;
+  for (int yc = ychunk; yc >= 64; yc >>= 1) {
+    const long long ctas = static_cast<long long>(B2 / kHistG) * (N / yc) * levels;
+    const long long waves = (ctas + sms - 1) / sms;
+    const double fill = static_cast<double>(ctas) / static_cast<double>(waves * sms);
+    if (fill > best + 1e-9) {
+      best = fill;
+      ychunk = yc;
+    }
+    if (fill >= 0.9) break;
+  }
   const size_t smem = box_hist_smem(N);
   if (smem > 227 * 1024) return GSP_ERR_UNSUPPORTED;
   dim3 grid(B2 / kHistG, N / ychunk, levels);
