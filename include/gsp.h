@@ -241,11 +241,14 @@ int gsp_cp_mttkrp(int N, int levels, int bins, int rank, int precision,
  * written by gsp_build_query_tables and holds, in order:
  *   flw  [levels][R]       fl * lambda (the CP weights folded into the level factor),
  *                          padded to a multiple of 4 floats
- *   sats [B+1][R][4]       1D summed-area table of fs: {hi, lo, fs[i], fs[i-1]}
- *                          with hi + lo = sum_{k<i} fs[k] (FP64 sum split into two
+ *   sats [B+1][3][R]       1D summed-area table of fs, row i = three planes of R
+ *                          floats: hi, lo and fs[i] (0 at i = B), with
+ *                          hi + lo = sum_{k<i} fs[k] (FP64 sum split into two
  *                          FP32); a range's partial end bins are weighted from the
  *                          bin values, the whole bins between them from hi + lo
- *   satt [B+1][R][4]       the same for ft.                                       */
+ *   satt [B+1][3][R]       the same for ft.
+ * The query kernels read consecutive ranks of a plane as vector loads when
+ * every rank is a multiple of 32 and fx, fy are 16-byte aligned.              */
 typedef struct gsp_material {
   int32_t N, levels, bins, rank;
   const float* fx;

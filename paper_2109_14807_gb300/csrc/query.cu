@@ -2,9 +2,13 @@
 // spatio-angular range query (Eq. 5 over five modes, Sec. 4.3-4.4), its adjoint
 // and the Adam refinement step.
 //
-// Query mapping: a group of LANES consecutive lanes serves one query, lane j
-// handling ranks j, j + LANES, ...; the rank sum is a butterfly shuffle inside
-// the group.  Every table row a query touches is read by the group as one
+// Query mapping: a group of LANES consecutive lanes serves one query.  When
+// every rank is a multiple of 32 (and the factor rows are 16-byte aligned)
+// lane j owns the 32 / LANES consecutive ranks from j * 32 / LANES of every
+// 32-rank block and reads each table row as one vector load per plane;
+// otherwise lane j handles ranks j, j + LANES, ... with scalar loads.  The
+// rank sum is a butterfly over the group (results do not depend on the
+// mapping).  Every table row a query touches is read by the group as one
 // contiguous run (coalesced), and the small per-material tables stay resident
 // in L1/L2.  Warps claim `chunk` groups of queries at a time from a global
 // counter (persistent CTAs, dynamic balance over uneven materials).
@@ -23,9 +27,34 @@ struct MatParams {
 };
 
 // The SAT region starts after flw, padded to a multiple of 4 floats so that
-// its float4 rows are 16-byte aligned.
+// it is 16-byte aligned.
 __host__ __device__ __forceinline__ size_t flw_floats(int L, int R) {
   return (static_cast<size_t>(L) * R + 3) / 4 * 4;
+}
+
+// Summed-area table of one angular side: rows i = 0..B of three planes of R
+// floats: hi, lo (hi + lo = sum_{k<i} f[k], an FP64 sum split into two FP32)
+// and the bin value f[i] (0 at i = B).
+constexpr int kSatPlanes = 3;
+__device__ __forceinline__ const float* sat_plane(const float* sat, int R, int i, int c) {
+  return sat + (static_cast<size_t>(i) * kSatPlanes + c) * R;
+}
+
+// V consecutive floats (p aligned to min(V, 4) floats).
+template <int V>
+__device__ __forceinline__ void ldg_n(const float* __restrict__ p, float (&v)[V]) {
+  if constexpr (V % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < V; i += 4) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p + i));
+      v[i] = a.x; v[i + 1] = a.y; v[i + 2] = a.z; v[i + 3] = a.w;
+    }
+  } else if constexpr (V == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = a.x; v[1] = a.y;
+  } else {
+    v[0] = __ldg(p);
+  }
 }
 
 struct GradParams {
@@ -62,16 +91,19 @@ __global__ void k_tables(const float* __restrict__ fl, const float* __restrict__
   if (r >= R) return;
   const float lam = lambda[r];
   for (int l = 0; l < L; ++l) tables[l * R + r] = fl[l * R + r] * lam;
-  float4* sat = reinterpret_cast<float4*>(tables + flw_floats(L, R));
+  float* sat = tables + flw_floats(L, R);
   for (int side = 0; side < 2; ++side) {
     const float* f = side == 0 ? fs : ft;
-    float4* t = sat + static_cast<size_t>(side) * (B + 1) * R;
+    float* t = sat + static_cast<size_t>(side) * (B + 1) * kSatPlanes * R;
     double P = 0.0;  // running prefix sum, FP64
     for (int i = 0; i <= B; ++i) {
       float hi = static_cast<float>(P);
       float lo = static_cast<float>(P - static_cast<double>(hi));
       float fi = i < B ? f[i * R + r] : 0.0f;
-      t[static_cast<size_t>(i) * R + r] = make_float4(hi, lo, fi, i > 0 ? f[(i - 1) * R + r] : 0.0f);
+      float* row = t + static_cast<size_t>(i) * kSatPlanes * R;
+      row[r] = hi;
+      row[R + r] = lo;
+      row[2 * R + r] = fi;
       if (i < B) P += static_cast<double>(fi);
     }
   }
@@ -139,35 +171,50 @@ __device__ __forceinline__ QTerms query_terms(const gsp_query& d, const gsp_mate
   return t;
 }
 
-// Range average of one rank from two SAT rows {hi, lo, f[i], f[i-1]} (hi + lo =
-// sum_{k < i} f[k]).  The partial end bins are weighted directly and only the
-// whole bins between them come from the prefix difference, so each part is
-// rounded relative to its own size: a range that starts just before the end
-// of a large bin followed by zeros keeps its small integral instead of
-// cancelling two large prefix values.  A range inside one bin is that bin's
-// value.
-__device__ __forceinline__ float sat_mean(const float4* __restrict__ sat, int R, int r, int i0,
-                                          int i1, float f0, float f1, float inv_w, int iz) {
+// Range averages of the V consecutive ranks rb .. rb + V - 1 from the SAT of
+// one side: prefix(i0 + 1), f[i0], prefix(i1) and f[i1].  The partial end bins
+// are weighted directly and only the whole bins between them come from the
+// prefix difference, so each part is rounded relative to its own size: a
+// range that starts just before the end of a large bin followed by zeros
+// keeps its small integral instead of cancelling two large prefix values.  A
+// range inside one bin is that bin's value; a zero-width range the value of
+// bin iz.  (i0 + 1 <= B whenever the width is positive.)
+template <int V>
+__device__ __forceinline__ void sat_mean(const float* __restrict__ sat, int R, int rb, int i0,
+                                         int i1, float f0, float f1, float inv_w, int iz,
+                                         float (&out)[V]) {
   if (inv_w > 0.0f) {
-    const float4 a = __ldg(sat + static_cast<size_t>(i0 + 1) * R + r);  // prefix(i0 + 1), f[i0]
-    const float4 b = __ldg(sat + static_cast<size_t>(i1) * R + r);      // prefix(i1), f[i1]
-    const float mid = (b.x - a.x) + (b.y - a.y);
-    const float v = fmaf(f1, b.z, fmaf(1.0f - f0, a.w, mid)) * inv_w;
-    return i0 == i1 ? a.w : v;  // inside one bin: the bin's value
+    float ah[V], al[V], af[V], bh[V], bl[V], bf[V];
+    ldg_n<V>(sat_plane(sat, R, i0 + 1, 0) + rb, ah);
+    ldg_n<V>(sat_plane(sat, R, i0 + 1, 1) + rb, al);
+    ldg_n<V>(sat_plane(sat, R, i0, 2) + rb, af);
+    ldg_n<V>(sat_plane(sat, R, i1, 0) + rb, bh);
+    ldg_n<V>(sat_plane(sat, R, i1, 1) + rb, bl);
+    ldg_n<V>(sat_plane(sat, R, i1, 2) + rb, bf);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float mid = (bh[v] - ah[v]) + (bl[v] - al[v]);
+      const float m = fmaf(f1, bf[v], fmaf(1.0f - f0, af[v], mid)) * inv_w;
+      out[v] = i0 == i1 ? af[v] : m;  // inside one bin: the bin's value
+    }
+  } else {
+    ldg_n<V>(sat_plane(sat, R, iz, 2) + rb, out);
   }
-  return __ldg(reinterpret_cast<const float*>(sat + static_cast<size_t>(iz) * R + r) + 2);
 }
 
-// Rank sum, identical for every LANES: rank r belongs to "conceptual lane"
-// c = r mod 32, accumulated in increasing r; the 32 conceptual lanes are then
-// combined in the order of a 32-lane xor butterfly.  Lane j of a group of
-// LANES holds the conceptual lanes j + k*LANES (k < 32/LANES) in registers and
-// performs the butterfly steps of offset >= LANES locally, the rest by shuffle.
+// Rank sum, identical for every LANES and both mappings: rank r belongs to
+// "conceptual lane" c = r mod 32, accumulated in increasing r; the 32
+// conceptual lanes are then combined in the order of a 32-lane xor butterfly
+// (offsets 16, 8, 4, 2, 1).  Lane j of a group of LANES holds NC = 32 / LANES
+// conceptual lanes in registers: c = j + k*LANES (strided mapping; the
+// butterfly offsets >= LANES are register adds, the rest shuffles) or
+// c = j*NC + k (CONTIG mapping, consecutive ranks per lane; offsets >= NC are
+// shuffles, the rest register adds).
 // FXY: the descriptor's x, y are floats (gsp_query_f) and the fx, fy rows are
 // interpolated linearly between floor(x) and floor(x) + 1 (mod N): since the
 // CP tensor is multilinear this is the bilinear blend of the four
 // neighbouring footprints' range queries (Sec. 4.1 spatial interpolation).
-template <int LANES, bool FXY>
+template <int LANES, bool FXY, bool CONTIG>
 __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ MatParams mp,
                                                      const gsp_query* __restrict__ q,
                                                      long long n, float* __restrict__ out,
@@ -210,8 +257,8 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           bad = !t.ok;
           const int R = M.rank;
           const float* __restrict__ flw = M.tables;
-          const float4* sats = reinterpret_cast<const float4*>(M.tables + flw_floats(M.levels, R));
-          const float4* satt = sats + static_cast<size_t>(M.bins + 1) * R;
+          const float* sats = M.tables + flw_floats(M.levels, R);
+          const float* satt = sats + static_cast<size_t>(M.bins + 1) * kSatPlanes * R;
           const float* __restrict__ fxr = M.fx + static_cast<size_t>(t.x) * R;
           const float* __restrict__ fyr = M.fy + static_cast<size_t>(t.y) * R;
           const float* __restrict__ fxr1 = fxr;
@@ -232,35 +279,80 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           const float* __restrict__ fl0 = flw + static_cast<size_t>(t.l0) * R;
           const float* __restrict__ fl1 = flw + static_cast<size_t>(t.l1) * R;
           const float g0 = 1.0f - t.f;
-          for (int r0 = 0; r0 < R; r0 += 32) {
+          if constexpr (CONTIG) {  // R a multiple of 32
+            for (int r0 = 0; r0 < R; r0 += 32) {
+              const int rb = r0 + j * NC;
+              float a0[NC], a1[NC], xv[NC], yv[NC], S[NC], T[NC];
+              ldg_n<NC>(fl0 + rb, a0);
+              ldg_n<NC>(fl1 + rb, a1);
+              ldg_n<NC>(fxr + rb, xv);
+              ldg_n<NC>(fyr + rb, yv);
+              sat_mean<NC>(sats, R, rb, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
+              sat_mean<NC>(satt, R, rb, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, T);
+              if constexpr (FXY) {
+                float x1[NC], y1[NC];
+                ldg_n<NC>(fxr1 + rb, x1);
+                ldg_n<NC>(fyr1 + rb, y1);
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-              const int r = r0 + j + k * LANES;
-              if (r < R) {
-                const float lv = fmaf(t.f, __ldg(fl1 + r), g0 * __ldg(fl0 + r));
-                const float S = sat_mean(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
-                const float T = sat_mean(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
-                float xv = __ldg(fxr + r), yv = __ldg(fyr + r);
-                if constexpr (FXY) {
-                  xv = fmaf(wx, __ldg(fxr1 + r) - xv, xv);
-                  yv = fmaf(wy, __ldg(fyr1 + r) - yv, yv);
+                for (int k = 0; k < NC; ++k) {
+                  xv[k] = fmaf(wx, x1[k] - xv[k], xv[k]);
+                  yv[k] = fmaf(wy, y1[k] - yv[k], yv[k]);
                 }
-                acc[k] = fmaf(xv * yv, lv * S * T, acc[k]);
+              }
+#pragma unroll
+              for (int k = 0; k < NC; ++k) {
+                const float lv = fmaf(t.f, a1[k], g0 * a0[k]);
+                acc[k] = fmaf(xv[k] * yv[k], lv * S[k] * T[k], acc[k]);
+              }
+            }
+          } else {
+            for (int r0 = 0; r0 < R; r0 += 32) {
+#pragma unroll
+              for (int k = 0; k < NC; ++k) {
+                const int r = r0 + j + k * LANES;
+                if (r < R) {
+                  const float lv = fmaf(t.f, __ldg(fl1 + r), g0 * __ldg(fl0 + r));
+                  float S[1], T[1];
+                  sat_mean<1>(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
+                  sat_mean<1>(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, T);
+                  float xv = __ldg(fxr + r), yv = __ldg(fyr + r);
+                  if constexpr (FXY) {
+                    xv = fmaf(wx, __ldg(fxr1 + r) - xv, xv);
+                    yv = fmaf(wy, __ldg(fyr1 + r) - yv, yv);
+                  }
+                  acc[k] = fmaf(xv * yv, lv * S[0] * T[0], acc[k]);
+                }
               }
             }
           }
         }
       }
+      float v;
+      if constexpr (CONTIG) {
 #pragma unroll
-      for (int o = 16; o >= LANES; o >>= 1) {
-        const int h = o / LANES;
+        for (int o = 16; o >= NC; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < NC; ++k)
-          if (!(k & h)) acc[k] = acc[k] + acc[k | h];
+          for (int k = 0; k < NC; ++k) acc[k] = acc[k] + __shfl_xor_sync(0xffffffffu, acc[k], o / NC);
+        }
+#pragma unroll
+        for (int o = NC / 2; o > 0; o >>= 1) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k)
+            if (!(k & o)) acc[k] = acc[k] + acc[k | o];
+        }
+        v = acc[0];
+      } else {
+#pragma unroll
+        for (int o = 16; o >= LANES; o >>= 1) {
+          const int h = o / LANES;
+#pragma unroll
+          for (int k = 0; k < NC; ++k)
+            if (!(k & h)) acc[k] = acc[k] + acc[k | h];
+        }
+        v = acc[0];
+#pragma unroll
+        for (int off = LANES / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       }
-      float v = acc[0];
-#pragma unroll
-      for (int off = LANES / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if (qi < n && j == 0) {
         if (bad) {
           out[qi] = __int_as_float(0x7fc00000);
@@ -274,17 +366,6 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
 }
 
 // ----------------------------------------------------------- adjoint --
-// VEC consecutive floats of a global table row (8 / 4-byte aligned).
-template <int VEC>
-__device__ __forceinline__ void ldg_vec(const float* __restrict__ p, float* v) {
-  if constexpr (VEC == 2) {
-    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
-    v[0] = a.x; v[1] = a.y;
-  } else {
-    v[0] = __ldg(p);
-  }
-}
-
 // Atomic add of VEC consecutive floats as one vector reduction.
 template <int VEC>
 __device__ __forceinline__ void red_add(float* p, const float* v) {
@@ -338,8 +419,8 @@ __global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constan
     if (g == 0.0f) continue;
     const int R = M.rank;
     const float* flw = M.tables;
-    const float4* sats = reinterpret_cast<const float4*>(M.tables + flw_floats(M.levels, R));
-    const float4* satt = sats + static_cast<size_t>(M.bins + 1) * R;
+    const float* sats = M.tables + flw_floats(M.levels, R);
+    const float* satt = sats + static_cast<size_t>(M.bins + 1) * kSatPlanes * R;
     const gsp_material_grad& G = gp.g[m];
     SmallGrad sg;
     if (gp.use_smem) {
@@ -353,19 +434,21 @@ __global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constan
     }
     const float g0 = 1.0f - t.f;
     for (int rv = j * VEC; rv < R; rv += LANES * VEC) {
-      float a0v[VEC], a1v[VEC], xvv[VEC], yvv[VEC], dx[VEC], dy[VEC];
-      ldg_vec<VEC>(flw + t.l0 * R + rv, a0v);
-      ldg_vec<VEC>(flw + t.l1 * R + rv, a1v);
-      ldg_vec<VEC>(M.fx + t.x * R + rv, xvv);
-      ldg_vec<VEC>(M.fy + t.y * R + rv, yvv);
+      float a0v[VEC], a1v[VEC], xvv[VEC], yvv[VEC], dx[VEC], dy[VEC], Sv[VEC], Tv[VEC];
+      ldg_n<VEC>(flw + t.l0 * R + rv, a0v);
+      ldg_n<VEC>(flw + t.l1 * R + rv, a1v);
+      ldg_n<VEC>(M.fx + t.x * R + rv, xvv);
+      ldg_n<VEC>(M.fy + t.y * R + rv, yvv);
+      sat_mean<VEC>(sats, R, rv, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, Sv);
+      sat_mean<VEC>(satt, R, rv, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, Tv);
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
         const int r0 = rv + v;
         // column of rank r0 in this CTA's shared-memory tables (global: r0)
         const int r = gp.use_smem ? v * (R / VEC) + rv / VEC : r0;
         float lv = fmaf(t.f, a1v[v], g0 * a0v[v]);
-        float S = sat_mean(sats, R, r0, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz);
-        float T = sat_mean(satt, R, r0, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz);
+        float S = Sv[v];
+        float T = Tv[v];
         float xv = xvv[v], yv = yvv[v];
         float xy = xv * yv;
         float st = S * T;
@@ -491,8 +574,8 @@ __global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatP
     const int l0 = static_cast<int>(floorf(lev)), l1 = min(l0 + 1, L - 1);
     const float f = lev - static_cast<float>(l0), g0 = 1.0f - f;
     const float* flw = M.tables;
-    const float4* sats = reinterpret_cast<const float4*>(M.tables + flw_floats(L, R));
-    const float4* satt = sats + static_cast<size_t>(B + 1) * R;
+    const float* sats = M.tables + flw_floats(L, R);
+    const float* satt = sats + static_cast<size_t>(B + 1) * kSatPlanes * R;
     // per rank slot: c_r and the prefix sums (hi, lo) at the square's edges
     float c[NC], s0h[NC], s0l[NC], s1h[NC], s1l[NC], t0h[NC], t0l[NC], t1h[NC], t1l[NC];
 #pragma unroll
@@ -503,10 +586,10 @@ __global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatP
       if (live && r < R) {
         c[k] = __ldg(M.fx + static_cast<size_t>(x) * R + r) * __ldg(M.fy + static_cast<size_t>(y) * R + r) *
                fmaf(f, __ldg(flw + l1 * R + r), g0 * __ldg(flw + l0 * R + r));
-        const float4 a = __ldg(sats + r), b = __ldg(sats + static_cast<size_t>(B) * R + r);
-        const float4 ct = __ldg(satt + r), dt = __ldg(satt + static_cast<size_t>(B) * R + r);
-        s0h[k] = a.x; s0l[k] = a.y; s1h[k] = b.x; s1l[k] = b.y;
-        t0h[k] = ct.x; t0l[k] = ct.y; t1h[k] = dt.x; t1l[k] = dt.y;
+        s0h[k] = __ldg(sat_plane(sats, R, 0, 0) + r); s0l[k] = __ldg(sat_plane(sats, R, 0, 1) + r);
+        s1h[k] = __ldg(sat_plane(sats, R, B, 0) + r); s1l[k] = __ldg(sat_plane(sats, R, B, 1) + r);
+        t0h[k] = __ldg(sat_plane(satt, R, 0, 0) + r); t0l[k] = __ldg(sat_plane(satt, R, 0, 1) + r);
+        t1h[k] = __ldg(sat_plane(satt, R, B, 0) + r); t1l[k] = __ldg(sat_plane(satt, R, B, 1) + r);
       }
     }
     const float* uq = u + (live ? qi : 0) * GSP_SAMPLE_UNIFORMS;  // this sample's uniforms
@@ -527,9 +610,10 @@ __global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatP
         const int r = j + k * LANES;
         smh[k] = sml[k] = tmh[k] = tml[k] = 0.f;
         if (go && r < R) {
-          const float4 ps = __ldg(sats + static_cast<size_t>(sm) * R + r);
-          const float4 pt = __ldg(satt + static_cast<size_t>(tm) * R + r);
-          smh[k] = ps.x; sml[k] = ps.y; tmh[k] = pt.x; tml[k] = pt.y;
+          smh[k] = __ldg(sat_plane(sats, R, sm, 0) + r);
+          sml[k] = __ldg(sat_plane(sats, R, sm, 1) + r);
+          tmh[k] = __ldg(sat_plane(satt, R, tm, 0) + r);
+          tml[k] = __ldg(sat_plane(satt, R, tm, 1) + r);
           const float sa = ((smh[k] - s0h[k]) + (sml[k] - s0l[k])) * inv;
           const float sb = ((s1h[k] - smh[k]) + (s1l[k] - sml[k])) * inv;
           const float ta = ((tmh[k] - t0h[k]) + (tml[k] - t0l[k])) * inv;
@@ -643,7 +727,7 @@ using namespace gsp;
 
 extern "C" size_t gsp_query_table_floats(int levels, int bins, int rank) {
   if (levels < 1 || bins < 1 || rank < 1) return 0;
-  return flw_floats(levels, rank) + 8 * static_cast<size_t>(bins + 1) * rank;
+  return flw_floats(levels, rank) + 2 * kSatPlanes * static_cast<size_t>(bins + 1) * rank;
 }
 
 extern "C" int gsp_build_query_tables(const gsp_material* h_mat, gsp_stream stream) {
@@ -661,6 +745,26 @@ extern "C" int gsp_build_query_tables(const gsp_material* h_mat, gsp_stream stre
 
 namespace gsp {
 namespace {
+template <bool FXY, bool CONTIG>
+void launch_query_t(int lanes, long long blocks, int threads, cudaStream_t s, const MatParams& mp,
+                    const gsp_query* d_q, long long n, float* d_out, uint32_t* d_status,
+                    unsigned long long* counter, int chunk) {
+  switch (lanes) {
+    case 4:
+      k_range_query<4, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+    case 8:
+      k_range_query<8, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+    case 16:
+      k_range_query<16, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+    default:
+      k_range_query<32, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+      break;
+  }
+}
+
 template <bool FXY>
 int range_query_launch(const gsp_material* h_mats, int n_mats, const gsp_query* d_q, int64_t n,
                        float* d_out, uint32_t* d_status, const gsp_query_tuning* tuning,
@@ -693,23 +797,17 @@ int range_query_launch(const gsp_material* h_mats, int n_mats, const gsp_query* 
   long long need = (warps_needed * 32 + threads - 1) / threads;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
+  // consecutive ranks per lane (vector loads) when every material allows it
+  bool contig = true;
+  for (int i = 0; i < n_mats; ++i)
+    contig = contig && h_mats[i].rank % 32 == 0 &&
+             ((reinterpret_cast<uintptr_t>(h_mats[i].fx) | reinterpret_cast<uintptr_t>(h_mats[i].fy)) & 15) == 0;
+  if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) return GSP_ERR_INVALID_ARG;
   prof_begin(PROF_QUERY, s);
-  switch (lanes) {
-    case 4:
-      k_range_query<4, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
-    case 8:
-      k_range_query<8, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
-    case 16:
-      k_range_query<16, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
-    case 32:
-      k_range_query<32, FXY><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
-    default:
-      return GSP_ERR_INVALID_ARG;
-  }
+  if (contig)
+    launch_query_t<FXY, true>(lanes, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
+  else
+    launch_query_t<FXY, false>(lanes, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
   prof_end(PROF_QUERY, s);
   GSP_CHECK_LAUNCH();
   return GSP_OK;

@@ -44,8 +44,8 @@ def test_host_side_sizes_and_validation(lib):
     assert lib.gsp_build_workspace_bytes(32, 6, 16) >= 32 * 32 * 2
     assert lib.gsp_build_workspace_bytes(33, 6, 16) == 0          # N not a power of two
     assert lib.gsp_build_workspace_bytes(32, 7, 16) == 0          # too many levels
-    assert lib.gsp_query_table_floats(6, 16, 8) == 6 * 8 + 8 * 17 * 8
-    assert lib.gsp_query_table_floats(5, 8, 3) == 16 + 8 * 9 * 3   # flw padded to 4 floats
+    assert lib.gsp_query_table_floats(6, 16, 8) == 6 * 8 + 6 * 17 * 8
+    assert lib.gsp_query_table_floats(5, 8, 3) == 16 + 6 * 9 * 3   # flw padded to 4 floats
     assert lib.gsp_cp_workspace_bytes(32, 6, 16, 8, 0) > 32 * 32 * 6 * 256 * 4
     assert lib.gsp_cp_workspace_bytes(32, 6, 16, 12, 0) == 0      # rank not a power of two
     assert lib.gsp_cp_workspace_bytes(32, 6, 16, 8, 3) == 0       # unknown precision
