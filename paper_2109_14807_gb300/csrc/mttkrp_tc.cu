@@ -233,8 +233,8 @@ struct Barriers {
   uint64_t empty[kMaxStages];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
-  uint64_t b_full[2];
-  uint64_t b_empty[2];
+  uint64_t b_full[kMaxStages];
+  uint64_t b_empty[kMaxStages];
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
@@ -449,7 +449,7 @@ template <int ELEM, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_lst_tc(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapFX,
              const float* __restrict__ fy, float* __restrict__ Zpart, int P, int logN, int L,
-             int B2, int R, int MB, int G, int kStages, uint32_t* err) {
+             int B2, int R, int MB, int G, int kStages, int nB, uint32_t* err) {
   constexpr int E128 = 128 / ELEM;
   constexpr uint32_t FMT = ELEM == 2 ? 1u : 2u;
   constexpr int BOXES = 128 / E128;                 // TMA boxes per 128-wide st block
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(smem_u32(&bar.acc_full[0]), 1);
     mbar_init(smem_u32(&bar.acc_empty[0]), 128);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < nB; ++b) {
       mbar_init(smem_u32(&bar.b_full[b]), 1);
       mbar_init(smem_u32(&bar.b_empty[b]), 1);
     }
@@ -499,9 +499,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {  // ---- TMA producer: per step the B tile, then MB T tiles
       int s = 0, bs = 0;
       uint32_t ph = 0, bph = 0;
-      uint32_t issued_parity[kMaxStages], b_parity[2];
-      bool issued[kMaxStages], b_issued[2] = {false, false};
-      for (int i = 0; i < kMaxStages; ++i) issued[i] = false;
+      uint32_t issued_parity[kMaxStages], b_parity[kMaxStages];
+      bool issued[kMaxStages], b_issued[kMaxStages];
+      for (int i = 0; i < kMaxStages; ++i) issued[i] = b_issued[i] = false;
       int xb = static_cast<int>(rg.k0 % spr);  // x block of step k
       for (long long k = rg.k0; k < rg.k1 && !*abort; ++k, xb = xb + 1 == spr ? 0 : xb + 1) {
         if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto producer_done;
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_2d(smem_u32(bslots + bs * b_bytes), &mapFX, xb * E128, 0, bb);
           b_issued[bs] = true;
           b_parity[bs] = bph;
-          if (++bs == 2) {
+          if (++bs == nB) {
             bs = 0;
             bph ^= 1u;
           }
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (*abort) {  // wait for this CTA's own copies still in flight
         for (int i = 0; i < kStages; ++i)
           if (issued[i]) mbar_drain(smem_u32(&bar.full[i]), issued_parity[i]);
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < nB; ++i)
           if (b_issued[i]) mbar_drain(smem_u32(&bar.b_full[i]), b_parity[i]);
       }
     }
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
             umma_commit(smem_u32(&bar.b_empty[bs]));
-            if (++bs == 2) {
+            if (++bs == nB) {
               bs = 0;
               bph ^= 1u;
             }
@@ -764,12 +764,35 @@ int xy_stages(int R, bool split) { return stages_for(xy_stage_bytes(R, split), 1
 size_t xy_smem(int R, bool split) { return 1024 + xy_stages(R, split) * xy_stage_bytes(R, split); }
 
 size_t lst_b_bytes(int R, bool split) { return static_cast<size_t>(R) * 128 * (split ? 2 : 1); }
-int lst_stages(int R, bool split) { return stages_for(kTileBytes, 1024 + 2 * lst_b_bytes(R, split)); }
-// The Z' pass allocates up to all 512 TMEM columns, so it asks for enough
-// shared memory that no second CTA fits on the SM.
-size_t lst_smem(int R, bool split) {
-  size_t need = 1024 + lst_stages(R, split) * static_cast<size_t>(kTileBytes) + 2 * lst_b_bytes(R, split);
-  return need < 120 * 1024 ? 120 * 1024 : need;
+
+// Z' ring shapes: T stages of one tile and B slots of one FXt tile.  A step
+// takes one B slot and streams its MB T tiles through the T ring, so the
+// producer runs min(B slots * MB, stages) T tiles ahead of the tensor core;
+// the split of ~200 KB that maximises that lead is taken (the first one on
+// ties, so a large MB keeps two B slots and the deepest T ring).
+struct LstCfg {
+  int stages, bslots;
+  size_t smem;
+};
+LstCfg lst_cfg(int R, bool split, int MB) {
+  const size_t b = lst_b_bytes(R, split), budget = 200 * 1024 - 1024;
+  LstCfg best{3, 2, 0};
+  int lead = -1;
+  for (int nb = 2; nb <= kMaxStages && nb * b + 3 * kTileBytes <= budget; ++nb) {
+    int st = static_cast<int>((budget - nb * b) / kTileBytes);
+    if (st > kMaxStages) st = kMaxStages;
+    if (st < 3) continue;
+    const int ahead = nb * MB < st ? nb * MB : st;
+    if (ahead > lead) {
+      lead = ahead;
+      best = LstCfg{st, nb, 0};
+    }
+  }
+  // The Z' pass allocates up to all 512 TMEM columns, so it asks for enough
+  // shared memory that no second CTA fits on the SM.
+  const size_t need = 1024 + best.stages * static_cast<size_t>(kTileBytes) + best.bslots * b;
+  best.smem = need < 120 * 1024 ? 120 * 1024 : need;
+  return best;
 }
 
 template <typename K>
@@ -798,7 +821,9 @@ bool tc_supported(const MttkrpDims& d, int precision) {
   if (d.B < 16 || d.N < 128 / (precision == GSP_PREC_TF32 ? 4 : 2)) return false;  // Z' steps stay in one map row
   if (d.L * d.N2() >= (1LL << 31)) return false;  // TMA row coordinate is int32
   const bool split = precision != GSP_PREC_BF16_1X;  // BF16 and TF32 use hi + lo pairs
-  return xy_smem(d.R, split) <= 227 * 1024 && lst_smem(d.R, split) <= 227 * 1024 &&
+  int MB = 0;
+  lst_groups(d, &MB);
+  return xy_smem(d.R, split) <= 227 * 1024 && lst_cfg(d.R, split, MB).smem <= 227 * 1024 &&
          encode_fn() != nullptr;
 }
 
@@ -866,22 +891,23 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
   const int G = lst_groups(d, &MB);
   const int P = tc_lst_ctas(d);
   const int grid = P * G;
-  const size_t smem = lst_smem(d.R, split);
-  const int stages = lst_stages(d.R, split);
+  const LstCfg cfg = lst_cfg(d.R, split, MB);
+  const size_t smem = cfg.smem;
+  const int stages = cfg.stages, nB = cfg.bslots;
   const int logN = ilog2(d.N);
   prof_begin(PROF_MTTKRP_LST, s);
   if (elem == 4) {
     GSP_TRY(set_smem(k_lst_tc<4, true>, smem));
     k_lst_tc<4, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                   MB, G, stages, err);
+                                                   MB, G, stages, nB, err);
   } else if (split) {
     GSP_TRY(set_smem(k_lst_tc<2, true>, smem));
     k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                   MB, G, stages, err);
+                                                   MB, G, stages, nB, err);
   } else {
     GSP_TRY(set_smem(k_lst_tc<2, false>, smem));
     k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                    MB, G, stages, err);
+                                                    MB, G, stages, nB, err);
   }
   prof_end(PROF_MTTKRP_LST, s);
   GSP_CHECK_LAUNCH();
