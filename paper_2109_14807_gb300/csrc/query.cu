@@ -2,13 +2,12 @@
 // spatio-angular range query (Eq. 5 over five modes, Sec. 4.3-4.4), its adjoint
 // and the Adam refinement step.
 //
-// Query mapping: a group of LANES consecutive lanes serves one query.  When
-// every rank is a multiple of 32 (and the factor rows are 16-byte aligned)
-// lane j owns the 32 / LANES consecutive ranks from j * 32 / LANES of every
-// 32-rank block and reads each table row as one vector load per plane;
-// otherwise lane j handles ranks j, j + LANES, ... with scalar loads.  The
-// rank sum is a butterfly over the group (results do not depend on the
-// mapping).  Every table row a query touches is read by the group as one
+// Query mapping: a group of LANES consecutive lanes serves one query; lane j
+// owns runs of V consecutive ranks (V = 4, 2 or 1, as the ranks and the
+// alignment of the factor rows allow), j*V, j*V + V*LANES, ... of every
+// 32-rank block, and reads each run of a table row as one vector load per
+// plane.  The rank sum is a butterfly over the group (results do not depend
+// on LANES or V).  Every table row a query touches is read by the group as one
 // contiguous run (coalesced), and the small per-material tables stay resident
 // in L1/L2.  Warps claim `chunk` groups of queries at a time from a global
 // counter (persistent CTAs, dynamic balance over uneven materials).
@@ -202,19 +201,15 @@ __device__ __forceinline__ void sat_mean(const float* __restrict__ sat, int R, i
   }
 }
 
-// Rank sum, identical for every LANES and both mappings: rank r belongs to
-// "conceptual lane" c = r mod 32, accumulated in increasing r; the 32
-// conceptual lanes are then combined in the order of a 32-lane xor butterfly
-// (offsets 16, 8, 4, 2, 1).  Lane j of a group of LANES holds NC = 32 / LANES
-// conceptual lanes in registers: c = j + k*LANES (strided mapping; the
-// butterfly offsets >= LANES are register adds, the rest shuffles) or
-// c = j*NC + k (CONTIG mapping, consecutive ranks per lane; offsets >= NC are
-// shuffles, the rest register adds).
-// FXY: the descriptor's x, y are floats (gsp_query_f) and the fx, fy rows are
-// interpolated linearly between floor(x) and floor(x) + 1 (mod N): since the
-// CP tensor is multilinear this is the bilinear blend of the four
-// neighbouring footprints' range queries (Sec. 4.1 spatial interpolation).
-template <int LANES, bool FXY, bool CONTIG>
+// Rank sum, identical for every launch shape: rank r belongs to "conceptual
+// lane" c = r mod 32, accumulated in increasing r; the 32 conceptual lanes are
+// then combined in the order of a 32-lane xor butterfly (offsets 16, 8, 4, 2,
+// 1).  Lane j of a group of LANES holds NC = 32 / LANES conceptual lanes in
+// registers, c = V*j + v + k*V*LANES (v < V, k < NC / V): runs of V
+// consecutive ranks, read as one vector load per table row and plane.  The
+// butterfly offsets >= V*LANES (bits of k) are register adds, those from V to
+// V*LANES shuffles, those below V register adds again.
+template <int LANES, bool FXY, int V>
 __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ MatParams mp,
                                                      const gsp_query* __restrict__ q,
                                                      long long n, float* __restrict__ out,
@@ -279,80 +274,61 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           const float* __restrict__ fl0 = flw + static_cast<size_t>(t.l0) * R;
           const float* __restrict__ fl1 = flw + static_cast<size_t>(t.l1) * R;
           const float g0 = 1.0f - t.f;
-          if constexpr (CONTIG) {  // R a multiple of 32
-            for (int r0 = 0; r0 < R; r0 += 32) {
-              const int rb = r0 + j * NC;
-              float a0[NC], a1[NC], xv[NC], yv[NC], S[NC], T[NC];
-              ldg_n<NC>(fl0 + rb, a0);
-              ldg_n<NC>(fl1 + rb, a1);
-              ldg_n<NC>(fxr + rb, xv);
-              ldg_n<NC>(fyr + rb, yv);
-              sat_mean<NC>(sats, R, rb, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
-              sat_mean<NC>(satt, R, rb, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, T);
-              if constexpr (FXY) {
-                float x1[NC], y1[NC];
-                ldg_n<NC>(fxr1 + rb, x1);
-                ldg_n<NC>(fyr1 + rb, y1);
+          for (int r0 = 0; r0 < R; r0 += 32) {
 #pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                  xv[k] = fmaf(wx, x1[k] - xv[k], xv[k]);
-                  yv[k] = fmaf(wy, y1[k] - yv[k], yv[k]);
-                }
-              }
+            for (int k = 0; k < NC / V; ++k) {
+              const int rb = r0 + k * V * LANES + V * j;  // R % V == 0: the run is whole
+              if (rb < R) {
+                float a0[V], a1[V], xv[V], yv[V], S[V], T[V];
+                ldg_n<V>(fl0 + rb, a0);
+                ldg_n<V>(fl1 + rb, a1);
+                ldg_n<V>(fxr + rb, xv);
+                ldg_n<V>(fyr + rb, yv);
+                sat_mean<V>(sats, R, rb, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
+                sat_mean<V>(satt, R, rb, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, T);
+                if constexpr (FXY) {
+                  float x1[V], y1[V];
+                  ldg_n<V>(fxr1 + rb, x1);
+                  ldg_n<V>(fyr1 + rb, y1);
 #pragma unroll
-              for (int k = 0; k < NC; ++k) {
-                const float lv = fmaf(t.f, a1[k], g0 * a0[k]);
-                acc[k] = fmaf(xv[k] * yv[k], lv * S[k] * T[k], acc[k]);
-              }
-            }
-          } else {
-            for (int r0 = 0; r0 < R; r0 += 32) {
-#pragma unroll
-              for (int k = 0; k < NC; ++k) {
-                const int r = r0 + j + k * LANES;
-                if (r < R) {
-                  const float lv = fmaf(t.f, __ldg(fl1 + r), g0 * __ldg(fl0 + r));
-                  float S[1], T[1];
-                  sat_mean<1>(sats, R, r, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
-                  sat_mean<1>(satt, R, r, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, T);
-                  float xv = __ldg(fxr + r), yv = __ldg(fyr + r);
-                  if constexpr (FXY) {
-                    xv = fmaf(wx, __ldg(fxr1 + r) - xv, xv);
-                    yv = fmaf(wy, __ldg(fyr1 + r) - yv, yv);
+                  for (int v = 0; v < V; ++v) {
+                    xv[v] = fmaf(wx, x1[v] - xv[v], xv[v]);
+                    yv[v] = fmaf(wy, y1[v] - yv[v], yv[v]);
                   }
-                  acc[k] = fmaf(xv * yv, lv * S[0] * T[0], acc[k]);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                  const float lv = fmaf(t.f, a1[v], g0 * a0[v]);
+                  acc[k * V + v] = fmaf(xv[v] * yv[v], lv * S[v] * T[v], acc[k * V + v]);
                 }
               }
             }
           }
         }
       }
-      float v;
-      if constexpr (CONTIG) {
+      // butterfly: bits of k (registers), of j (shuffles), of v (registers)
 #pragma unroll
-        for (int o = 16; o >= NC; o >>= 1) {
+      for (int o = 16; o >= V * LANES; o >>= 1) {
+        const int h = o / (V * LANES);
 #pragma unroll
-          for (int k = 0; k < NC; ++k) acc[k] = acc[k] + __shfl_xor_sync(0xffffffffu, acc[k], o / NC);
-        }
+        for (int k = 0; k < NC / V; ++k)
+          if (!(k & h)) {
 #pragma unroll
-        for (int o = NC / 2; o > 0; o >>= 1) {
-#pragma unroll
-          for (int k = 0; k < NC; ++k)
-            if (!(k & o)) acc[k] = acc[k] + acc[k | o];
-        }
-        v = acc[0];
-      } else {
-#pragma unroll
-        for (int o = 16; o >= LANES; o >>= 1) {
-          const int h = o / LANES;
-#pragma unroll
-          for (int k = 0; k < NC; ++k)
-            if (!(k & h)) acc[k] = acc[k] + acc[k | h];
-        }
-        v = acc[0];
-#pragma unroll
-        for (int off = LANES / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            for (int v = 0; v < V; ++v) acc[k * V + v] = acc[k * V + v] + acc[(k | h) * V + v];
+          }
       }
+#pragma unroll
+      for (int o = V * LANES / 2; o >= V; o >>= 1) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = acc[v] + __shfl_xor_sync(0xffffffffu, acc[v], o / V);
+      }
+#pragma unroll
+      for (int o = V / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (!(v & o)) acc[v] = acc[v] + acc[v | o];
+      }
+      const float v = acc[0];
       if (qi < n && j == 0) {
         if (bad) {
           out[qi] = __int_as_float(0x7fc00000);
@@ -745,24 +721,53 @@ extern "C" int gsp_build_query_tables(const gsp_material* h_mat, gsp_stream stre
 
 namespace gsp {
 namespace {
-template <bool FXY, bool CONTIG>
-void launch_query_t(int lanes, long long blocks, int threads, cudaStream_t s, const MatParams& mp,
+template <bool FXY, int LANES, int V>
+void launch_query_lv(long long blocks, int threads, cudaStream_t s, const MatParams& mp,
+                     const gsp_query* d_q, long long n, float* d_out, uint32_t* d_status,
+                     unsigned long long* counter, int chunk) {
+  k_range_query<LANES, FXY, V><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
+}
+
+template <bool FXY, int LANES>
+void launch_query_l(int vec, long long blocks, int threads, cudaStream_t s, const MatParams& mp,
                     const gsp_query* d_q, long long n, float* d_out, uint32_t* d_status,
                     unsigned long long* counter, int chunk) {
+  constexpr int NC = 32 / LANES;
+  if (vec >= 4 && NC >= 4)
+    launch_query_lv<FXY, LANES, (NC >= 4 ? 4 : 1)>(blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
+  else if (vec >= 2 && NC >= 2)
+    launch_query_lv<FXY, LANES, (NC >= 2 ? 2 : 1)>(blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
+  else
+    launch_query_lv<FXY, LANES, 1>(blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
+}
+
+template <bool FXY>
+void launch_query_t(int lanes, int vec, long long blocks, int threads, cudaStream_t s,
+                    const MatParams& mp, const gsp_query* d_q, long long n, float* d_out,
+                    uint32_t* d_status, unsigned long long* counter, int chunk) {
   switch (lanes) {
-    case 4:
-      k_range_query<4, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
-    case 8:
-      k_range_query<8, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
-    case 16:
-      k_range_query<16, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
-    default:
-      k_range_query<32, FXY, CONTIG><<<blocks, threads, 0, s>>>(mp, d_q, n, d_out, d_status, counter, chunk);
-      break;
+    case 4: launch_query_l<FXY, 4>(vec, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk); break;
+    case 8: launch_query_l<FXY, 8>(vec, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk); break;
+    case 16: launch_query_l<FXY, 16>(vec, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk); break;
+    default: launch_query_l<FXY, 32>(vec, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk); break;
   }
+}
+
+// Ranks per vector run: the largest of 4, 2 (at most 32 / lanes) that divides
+// every rank, leaves no lane of the group without a run (V * lanes <= rank)
+// and keeps the fx, fy rows aligned; else 1.
+int pick_query_vec(const gsp_material* mats, int n_mats, int lanes) {
+  for (int v = 32 / lanes < 4 ? 32 / lanes : 4; v > 1; v >>= 1) {
+    bool ok = true;
+    for (int i = 0; i < n_mats; ++i) {
+      const gsp_material& m = mats[i];
+      const uintptr_t mask = static_cast<uintptr_t>(4 * v - 1);
+      ok = ok && m.rank % v == 0 && v * lanes <= m.rank &&
+           ((reinterpret_cast<uintptr_t>(m.fx) | reinterpret_cast<uintptr_t>(m.fy)) & mask) == 0;
+    }
+    if (ok) return v;
+  }
+  return 1;
 }
 
 template <bool FXY>
@@ -797,17 +802,10 @@ int range_query_launch(const gsp_material* h_mats, int n_mats, const gsp_query* 
   long long need = (warps_needed * 32 + threads - 1) / threads;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  // consecutive ranks per lane (vector loads) when every material allows it
-  bool contig = true;
-  for (int i = 0; i < n_mats; ++i)
-    contig = contig && h_mats[i].rank % 32 == 0 &&
-             ((reinterpret_cast<uintptr_t>(h_mats[i].fx) | reinterpret_cast<uintptr_t>(h_mats[i].fy)) & 15) == 0;
   if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) return GSP_ERR_INVALID_ARG;
+  const int vec = pick_query_vec(h_mats, n_mats, lanes);
   prof_begin(PROF_QUERY, s);
-  if (contig)
-    launch_query_t<FXY, true>(lanes, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
-  else
-    launch_query_t<FXY, false>(lanes, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
+  launch_query_t<FXY>(lanes, vec, blocks, threads, s, mp, d_q, n, d_out, d_status, counter, chunk);
   prof_end(PROF_QUERY, s);
   GSP_CHECK_LAUNCH();
   return GSP_OK;

@@ -223,6 +223,24 @@ def test_results_do_not_depend_on_launch_shape():
     r2 = g.range_query(m2, q2, tuning=(32, 8, 256, 4)).clone()
     for lanes in (4, 8, 16):
         assert torch.equal(g.range_query(m2, q2, tuning=(lanes, 8, 256, 4)), r2), lanes
+    # rank 16: runs of 4 (4 lanes), 2 (8 lanes) and single ranks (16, 32 lanes)
+    f3 = random_factors(64, 7, 16, 16, 25)
+    m3 = _material(f3)
+    q3 = g.queries_to_device(synth.queries_fractional(64, 7, 16, 20_000, 26, frac_level=True))
+    r3 = g.range_query(m3, q3, tuning=(32, 8, 256, 4)).clone()
+    for lanes in (4, 8, 16):
+        assert torch.equal(g.range_query(m3, q3, tuning=(lanes, 8, 256, 4)), r3), lanes
+    # fx, fy rows 4 bytes off a 16-byte boundary: single-rank loads, same bits
+    fd = to_device_factors(f3)
+    for k in ("fx", "fy"):
+        buf = torch.zeros(fd[k].numel() + 1, dtype=torch.float32, device=fd[k].device)
+        buf[1:].copy_(fd[k].reshape(-1))
+        fd[k] = buf[1:].view(fd[k].shape)
+    m4 = g.QueryMaterial.from_factors(fd)
+    g.build_query_tables(m4)
+    assert fd["fx"].data_ptr() % 16 != 0
+    for lanes in (4, 8):
+        assert torch.equal(g.range_query(m4, q3, tuning=(lanes, 8, 256, 4)), r3), lanes
 
 
 def test_graph_replay_and_autotuner():
