@@ -425,9 +425,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 // every st block m of the group, the [E128 x rows x 128 st] T tile as 128/E128
 // MN-major TMA boxes (LBO = box bytes).  The accumulators collect U of one map
 // row (a chunk of N / E128 steps); at the row's end the epilogue warps add
-// fy[y][r] times the chunk to the running sums in TMEM columns [MB R, 2 MB R)
-// with FP32 round-to-nearest FMAs, or, for the segment's last row, write the
-// result to the partial slice.  fy is applied in FP32 and never rounded to the
+// fy[y][r] times the chunk to the running sums in TMEM columns
+// [nAcc MB R, (nAcc + 1) MB R) with FP32 round-to-nearest FMAs, or, for the
+// segment's last row, write the result to the partial slice.  With nAcc = 2
+// (when 3 MB R <= 512 columns) consecutive rows alternate between two chunk
+// accumulators, so the MMAs of a row run while the epilogue drains the last.  fy is applied in FP32 and never rounded to the
 // operand type.
 struct LstRange {
   long long k0, k1;     // this CTA's steps
@@ -449,7 +451,7 @@ template <int ELEM, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_lst_tc(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapFX,
              const float* __restrict__ fy, float* __restrict__ Zpart, int P, int logN, int L,
-             int B2, int R, int MB, int G, int kStages, int nB, uint32_t* err) {
+             int B2, int R, int MB, int G, int kStages, int nB, int nAcc, uint32_t* err) {
   constexpr int E128 = 128 / ELEM;
   constexpr uint32_t FMT = ELEM == 2 ? 1u : 2u;
   constexpr int BOXES = 128 / E128;                 // TMA boxes per 128-wide st block
@@ -471,7 +473,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long K = spl * L;
   const int g = blockIdx.x % G, p = blockIdx.x / G;
   const LstRange rg = lst_range(p, P, K, spl);
-  const uint32_t ncols = tmem_cols_for(2 * MB * R);  // chunk accumulators + running sums
+  // nAcc chunk accumulators (two: the MMAs of a map row run while the epilogue
+  // drains the previous row) and the running sums
+  const uint32_t ncols = tmem_cols_for((nAcc + 1) * MB * R);
   volatile int* abort = &bar.abort;
 
   if (threadIdx.x == 0) {
@@ -479,8 +483,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&bar.full[s]), 1);
       mbar_init(smem_u32(&bar.empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar.acc_full[0]), 1);
-    mbar_init(smem_u32(&bar.acc_empty[0]), 128);
+    for (int b = 0; b < nAcc; ++b) {
+      mbar_init(smem_u32(&bar.acc_full[b]), 1);
+      mbar_init(smem_u32(&bar.acc_empty[b]), 128);
+    }
     for (int b = 0; b < nB; ++b) {
       mbar_init(smem_u32(&bar.b_full[b]), 1);
       mbar_init(smem_u32(&bar.b_empty[b]), 1);
@@ -547,13 +553,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id = idesc(FMT, 1, static_cast<uint32_t>(R));
       int s = 0, bs = 0;
       uint32_t ph = 0, bph = 0, uph = 0;
+      int ab = 0;  // chunk accumulator of the current map row
       bool any = false;
       for (int seg = 0; seg < 2; ++seg) {
         const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
         for (long long c0 = kb; c0 < ke;) {  // one chunk (accumulator) per map row
           const long long row_end = (c0 / spr + 1) * spr;
           const long long c1 = row_end < ke ? row_end : ke;
-          if (!mbar_wait(smem_u32(&bar.acc_empty[0]), uph ^ 1u, abort)) goto mma_done;
+          if (!mbar_wait(smem_u32(&bar.acc_empty[ab]), uph ^ 1u, abort)) goto mma_done;
           tc_fence_after();
           for (long long k = c0; k < c1; ++k) {
             if (!mbar_wait(smem_u32(&bar.b_full[bs]), bph, abort)) goto mma_done;
@@ -564,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
               tc_fence_after();
               const uint32_t sa = smem_u32(smem + s * kTileBytes);
-              const uint32_t d = tmem + static_cast<uint32_t>(m * R);
+              const uint32_t d = tmem + static_cast<uint32_t>((ab * MB + m) * R);
               // descriptor address fields are in 16-byte units
               const uint64_t a0 = sdesc(sa, BOX_BYTES, A_SBO, A_LAYOUT);
 #pragma unroll
@@ -586,8 +593,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               bph ^= 1u;
             }
           }
-          umma_commit(smem_u32(&bar.acc_full[0]));
-          uph ^= 1u;
+          umma_commit(smem_u32(&bar.acc_full[ab]));
+          if (++ab == nAcc) {
+            ab = 0;
+            uph ^= 1u;
+          }
           c0 = c1;
         }
       }
@@ -599,8 +609,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {  // ---- warps 0-3: per map row, running sums += fy[y] * chunk
     uint32_t uph = 0;
+    int ab = 0;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    const uint32_t sum_col = static_cast<uint32_t>(MB * R);
+    const uint32_t sum_col = static_cast<uint32_t>(nAcc * MB * R);
     for (int seg = 0; seg < 2; ++seg) {
       const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
       if (kb >= ke) continue;
@@ -618,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             f[4 * i] = q.x; f[4 * i + 1] = q.y; f[4 * i + 2] = q.z; f[4 * i + 3] = q.w;
           }
         }
-        if (!mbar_wait(smem_u32(&bar.acc_full[0]), uph, abort)) goto epi_done;
+        if (!mbar_wait(smem_u32(&bar.acc_full[ab]), uph, abort)) goto epi_done;
         tc_fence_after();
         for (int m = 0; m < MB; ++m) {
           float* out = part + (static_cast<size_t>((g * MB + m) * 128) + warp * 32 + lane) * R;
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (cb * 16 < R) {
               const uint32_t col = static_cast<uint32_t>(m * R + cb * 16);
               uint32_t a[16], b[16];
-              tmem_ld16_nowait(lane_base + col, a);
+              tmem_ld16_nowait(lane_base + static_cast<uint32_t>(ab * MB * R) + col, a);
               if (!first) tmem_ld16_nowait(lane_base + sum_col + col, b);
               tmem_ld_wait();
               float v[16];
@@ -649,8 +660,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!last) tmem_st_wait();
         tc_fence_before();
-        mbar_arrive(smem_u32(&bar.acc_empty[0]));
-        uph ^= 1u;
+        mbar_arrive(smem_u32(&bar.acc_empty[ab]));
+        if (++ab == nAcc) {
+          ab = 0;
+          uph ^= 1u;
+        }
       }
     }
   epi_done:;
@@ -894,20 +908,21 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
   const LstCfg cfg = lst_cfg(d.R, split, MB);
   const size_t smem = cfg.smem;
   const int stages = cfg.stages, nB = cfg.bslots;
+  const int nAcc = 3 * MB * d.R <= 512 ? 2 : 1;  // double-buffered chunk accumulator when it fits
   const int logN = ilog2(d.N);
   prof_begin(PROF_MTTKRP_LST, s);
   if (elem == 4) {
     GSP_TRY(set_smem(k_lst_tc<4, true>, smem));
     k_lst_tc<4, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                   MB, G, stages, nB, err);
+                                                   MB, G, stages, nB, nAcc, err);
   } else if (split) {
     GSP_TRY(set_smem(k_lst_tc<2, true>, smem));
     k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                   MB, G, stages, nB, err);
+                                                   MB, G, stages, nB, nAcc, err);
   } else {
     GSP_TRY(set_smem(k_lst_tc<2, false>, smem));
     k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                    MB, G, stages, nB, err);
+                                                    MB, G, stages, nB, nAcc, err);
   }
   prof_end(PROF_MTTKRP_LST, s);
   GSP_CHECK_LAUNCH();

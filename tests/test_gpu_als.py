@@ -65,6 +65,55 @@ def test_mttkrp_parity(prec, N, L, B, R):
         assert err <= MTTKRP_TOL[prec], (n, err)
 
 
+def _map_of_bins(N, B, bins, seed):
+    """Normal map whose texels fall in the bins `bins` (cycled over the texels
+    in a seeded random order), each normal at its bin's centre."""
+    bins = np.asarray(bins)
+    code = bins[np.arange(N * N) % len(bins)][np.argsort(synth.uniform(seed, 5, N * N))]
+    s, t = code // B, code % B
+    m = np.stack([(s + 0.5) / (B / 2) - 1.0, (t + 0.5) / (B / 2) - 1.0], axis=-1)
+    return m.reshape(N, N, 2).astype(np.float32)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("B,n_occ", [(8, 20), (16, 1), (16, 128), (16, 129), (16, 256), (32, 128),
+                                     (32, 200), (32, 1024)])
+def test_operand_columns_and_mttkrp_at_every_occupancy(prec, B, n_occ):
+    # the operand keeps the bins that occur (increasing order), padded to a
+    # multiple of 128 columns (all B^2 bins when B^2 < 256); the MTTKRPs are
+    # those of the full tensor whatever the occupancy
+    import paper_2109_14807_gb300 as g
+    N, L, R = 64, 7, 16
+    occ = np.sort(np.argsort(synth.uniform(40 + n_occ, B, B * B))[:n_occ])
+    m = _map_of_bins(N, B, occ, 7 + n_occ)
+    s, t = ndf.bin_index(m, B)
+    assert np.array_equal(np.unique(s * B + t), occ)
+    cols = B * B if B * B < 256 else min(B * B, -(-n_occ // 128) * 128)
+    if not _supported(prec, N, L, B, R):
+        pytest.skip(f"{prec} MTTKRP does not support the shape {(N, L, B, R)}")
+    ws = g.CPWorkspace(N, L, B, R, prec)
+    ws.prepare(normal_xy=dev(m))
+    assert ws.operand_cols() == ((B * B if B * B < 256 else n_occ), cols)
+    H = ndf.footprint_histograms(s, t, L, B)
+    X = ndf.logical(ndf.normalised_tensor(H, B))
+    u = [synth.uniform(500 + B, k, n * R).reshape(n, R).astype(np.float32)
+         for k, n in enumerate((N, N, L, B, B))]
+    outs = ws.mttkrp({k: dev(a) for k, a in zip(("fx", "fy", "fl", "fs", "ft"), u)})
+    torch.cuda.synchronize()
+    A = [a.astype(np.float64) for a in u]
+    for n in range(5):
+        ref = cp.mttkrp_dense(X, A, n)
+        got = outs[n].double().cpu().numpy()
+        err = np.max(np.abs(got - ref) / np.maximum(ref, 1e-30 + np.max(ref) * 1e-6))
+        assert err <= MTTKRP_TOL[prec], (n, err)
+    # the same operand from the int32 histograms
+    ws2 = g.CPWorkspace(N, L, B, R, prec)
+    ws2.prepare(hist=dev(H, torch.int32))
+    assert ws2.operand_cols() == ws.operand_cols()
+    nb = L * N * N * cols * (2 if prec == "bf16" else 4)
+    assert torch.equal(ws.buf[:nb], ws2.buf[:nb])
+
+
 def _oracle_fits(X, R, init, sweeps):
     A0 = [init[k].astype(np.float32).astype(np.float64) for k in ("fx", "fy", "fl", "fs", "ft")]
     return cp.cp_als(X, R, A0, sweeps)
