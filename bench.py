@@ -834,7 +834,8 @@ def env_report(args):
     10^7 shading records (footprint, outgoing direction, SG lobe) against 64
     spherical-Gaussian lobes into range-query descriptors of one 1024^2 material
     (11 levels, 32^2 bins, rank 64, seeded random non-negative factors), which
-    gsp_range_query answers; both launches timed with CUDA events."""
+    gsp_range_query answers (launch shape from the autotuner, or --query-tuning);
+    both launches timed with CUDA events."""
     import numpy as np
     import torch
     import paper_2109_14807_gb300 as g
@@ -851,16 +852,22 @@ def env_report(args):
     rec = torch.from_numpy(synth.env_records([(N, L, B)], n, n_sg, 962).view(np.int32).reshape(n, 8)).cuda()
     qd = torch.empty((n, 8), dtype=torch.int32, device="cuda")
     out = torch.empty(n, dtype=torch.float32, device="cuda")
+    g.env_queries(mat, sgs, rec, out=qd)
+    if args.query_tuning:
+        tuning = tuple(int(v) for v in args.query_tuning.split(","))
+    else:
+        from paper_2109_14807_gb300 import tune
+        tuning = tune.autotune_query(mat, qd, sample=2_000_000, repeats=2)
     for _ in range(max(3, args.warmup)):
         g.env_queries(mat, sgs, rec, out=qd)
-        g.range_query(mat, qd, out=out)
+        g.range_query(mat, qd, out=out, tuning=tuning)
     gen, qry = [], []
     for _ in range(max(3, args.steps // 3)):
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record()
         g.env_queries(mat, sgs, rec, out=qd)
         b.record()
-        g.range_query(mat, qd, out=out)
+        g.range_query(mat, qd, out=out, tuning=tuning)
         c.record()
         torch.cuda.synchronize()
         gen.append(a.elapsed_time(b))
@@ -874,7 +881,7 @@ def env_report(args):
     print(json.dumps({
         "metric": "environment-light prefiltering (Sec. 5.4): records/s through descriptor generation and range query",
         "value": n / ((gms + qms) / 1e3), "unit": "records/s", "records": n, "sg_lobes": n_sg,
-        "generator_ms": gms, "range_query_ms": qms,
+        "generator_ms": gms, "range_query_ms": qms, "query_tuning": list(tuning),
         "generator_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                "frac": achieved / peak, "bytes_per_record": 64, "peak_source": src},
         "config": {"N": N, "levels": L, "bins": B, "rank": R},

@@ -276,11 +276,13 @@ size_t gsp_query_table_floats(int levels, int bins, int rank);
 /* Fill h_mat->tables from its factors (1D SAT per angular factor, Sec. 4.4). */
 int gsp_build_query_tables(const gsp_material* h_mat, gsp_stream stream);
 
-/* Launch shape of the query kernels.  NULL = the library's default. */
+/* Launch shape of the range-query kernel.  NULL, or a field of 0, takes the
+ * library's default: 8 lanes per query when some rank is >= 64, else 4; 8
+ * CTAs per SM; 256 threads; 4 queries per grab.  Results do not depend on it. */
 typedef struct gsp_query_tuning {
   int32_t lanes_per_query; /* 4, 8, 16 or 32 */
   int32_t blocks_per_sm;   /* persistent CTAs per SM (1 .. 32)   */
-  int32_t threads;         /* threads per CTA (64 .. 1024, multiple of 32) */
+  int32_t threads;         /* threads per CTA (32 .. 256, multiple of 32) */
   int32_t chunk;           /* queries a warp claims per grab (1 .. 64) */
 } gsp_query_tuning;
 

@@ -658,13 +658,13 @@ __global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatP
   }
 }
 
+// Default lanes per query (the autotuner's choice replaces it): 8 from rank 64
+// up, else 4, so that each lane reads runs of up to 4 ranks.
 int pick_lanes(const gsp_material* mats, int n_mats, const gsp_query_tuning* tn) {
   if (tn && tn->lanes_per_query) return tn->lanes_per_query;
   int rmax = 1;
   for (int i = 0; i < n_mats; ++i) rmax = rmax > mats[i].rank ? rmax : mats[i].rank;
-  int lanes = 4;
-  while (lanes < rmax && lanes < 32) lanes *= 2;
-  return lanes;
+  return rmax >= 64 ? 8 : 4;
 }
 
 template <int LANES, int VEC>
