@@ -504,6 +504,11 @@ def roofline(prof, w, prec, peaks, peak_src, n_occ, cols):
     if top not in per_launch:
         return None
     out = entry(top)
+    if top.startswith("range_query"):
+        out["note"] = ("gather bytes as the query roofline defines them; the table rows are served from "
+                       "L1/L2 and DRAM sees the 32-byte descriptor and 4-byte result per query (traffic), "
+                       "so the fraction exceeds 1; the binding units are on chip: L1 wavefronts and issue "
+                       "(forward), shared-memory float atomics (adjoint)")
     out["occupied_bins"], out["operand_columns"] = n_occ, cols
     out["others"] = [{k2: v for k2, v in entry(k).items() if k2 in ("kernel", "achieved", "frac", "traffic",
                                                                     "avg_launch_ms")}
