@@ -524,14 +524,32 @@ bool valid_material(const gsp_material& m) {
 // warp stay in step whatever the materials.
 constexpr int kSampleMaxRank = 64;
 
-template <int LANES>
+// V = 2: lane j holds the rank pair 2j, 2j + 1 and reads it as one float2 per
+// table row and plane; V = 1: ranks j and j + LANES.
+template <int LANES, int V>
 __global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatParams mp,
                                                     const gsp_sample_query* __restrict__ q,
                                                     long long n, const float* __restrict__ u,
                                                     float* __restrict__ out, uint32_t* status) {
   constexpr int QPW = 32 / LANES;
   constexpr int NC = 2;  // rank slots per lane
+  static_assert(V == 1 || V == NC, "runs of 1 or 2 ranks");
   const int lane = threadIdx.x & 31, sub = lane / LANES, j = lane % LANES;
+  // rank of slot k
+  auto slot_rank = [&](int k) { return V == 2 ? 2 * j + k : j + k * LANES; };
+  // the slots' values of one table row (V consecutive floats per load; 0 for
+  // a slot past the rank, which is never read: with V = 2 the rank is even)
+  auto row2 = [&](const float* p, int R, float (&v)[NC]) {
+#pragma unroll
+    for (int k = 0; k < NC; k += V) {
+      float w[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) w[i] = 0.f;
+      if (slot_rank(k) < R) ldg_n<V>(p + slot_rank(k), w);
+#pragma unroll
+      for (int i = 0; i < V; ++i) v[k + i] = w[i];
+    }
+  };
   const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
   for (long long base = warp_id * QPW; base < n; base += n_warps * QPW) {  // warp-uniform
@@ -556,16 +574,32 @@ __global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatP
     float c[NC], s0h[NC], s0l[NC], s1h[NC], s1l[NC], t0h[NC], t0l[NC], t1h[NC], t1l[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      const int r = j + k * LANES;
       c[k] = 0.f;
       s0h[k] = s0l[k] = s1h[k] = s1l[k] = t0h[k] = t0l[k] = t1h[k] = t1l[k] = 0.f;
-      if (live && r < R) {
-        c[k] = __ldg(M.fx + static_cast<size_t>(x) * R + r) * __ldg(M.fy + static_cast<size_t>(y) * R + r) *
-               fmaf(f, __ldg(flw + l1 * R + r), g0 * __ldg(flw + l0 * R + r));
-        s0h[k] = __ldg(sat_plane(sats, R, 0, 0) + r); s0l[k] = __ldg(sat_plane(sats, R, 0, 1) + r);
-        s1h[k] = __ldg(sat_plane(sats, R, B, 0) + r); s1l[k] = __ldg(sat_plane(sats, R, B, 1) + r);
-        t0h[k] = __ldg(sat_plane(satt, R, 0, 0) + r); t0l[k] = __ldg(sat_plane(satt, R, 0, 1) + r);
-        t1h[k] = __ldg(sat_plane(satt, R, B, 0) + r); t1l[k] = __ldg(sat_plane(satt, R, B, 1) + r);
+    }
+    // R is even for V = 2, so a pair is whole or absent
+    const bool have = live && slot_rank(0) < R;
+    if (have) {
+      float xv[NC], yv[NC], a1[NC], a0[NC];
+      row2(M.fx + static_cast<size_t>(x) * R, R, xv);
+      row2(M.fy + static_cast<size_t>(y) * R, R, yv);
+      row2(flw + l1 * R, R, a1);
+      row2(flw + l0 * R, R, a0);
+      row2(sat_plane(sats, R, 0, 0), R, s0h);
+      row2(sat_plane(sats, R, 0, 1), R, s0l);
+      row2(sat_plane(sats, R, B, 0), R, s1h);
+      row2(sat_plane(sats, R, B, 1), R, s1l);
+      row2(sat_plane(satt, R, 0, 0), R, t0h);
+      row2(sat_plane(satt, R, 0, 1), R, t0l);
+      row2(sat_plane(satt, R, B, 0), R, t1h);
+      row2(sat_plane(satt, R, B, 1), R, t1l);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        if (slot_rank(k) < R) {
+          c[k] = xv[k] * yv[k] * fmaf(f, a1[k], g0 * a0[k]);
+        } else {
+          s0h[k] = s0l[k] = s1h[k] = s1l[k] = t0h[k] = t0l[k] = t1h[k] = t1l[k] = 0.f;
+        }
       }
     }
     const float* uq = u + (live ? qi : 0) * GSP_SAMPLE_UNIFORMS;  // this sample's uniforms
@@ -582,23 +616,27 @@ __global__ void __launch_bounds__(256) k_sample_ndf(const __grid_constant__ MatP
       float q4[4] = {0.f, 0.f, 0.f, 0.f};
       float smh[NC], sml[NC], tmh[NC], tml[NC];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const int r = j + k * LANES;
-        smh[k] = sml[k] = tmh[k] = tml[k] = 0.f;
-        if (go && r < R) {
-          smh[k] = __ldg(sat_plane(sats, R, sm, 0) + r);
-          sml[k] = __ldg(sat_plane(sats, R, sm, 1) + r);
-          tmh[k] = __ldg(sat_plane(satt, R, tm, 0) + r);
-          tml[k] = __ldg(sat_plane(satt, R, tm, 1) + r);
-          const float sa = ((smh[k] - s0h[k]) + (sml[k] - s0l[k])) * inv;
-          const float sb = ((s1h[k] - smh[k]) + (s1l[k] - sml[k])) * inv;
-          const float ta = ((tmh[k] - t0h[k]) + (tml[k] - t0l[k])) * inv;
-          const float tb = ((t1h[k] - tmh[k]) + (t1l[k] - tml[k])) * inv;
-          const float ca = c[k] * sa, cb = c[k] * sb;
-          q4[0] = fmaf(ca, ta, q4[0]);
-          q4[1] = fmaf(ca, tb, q4[1]);
-          q4[2] = fmaf(cb, ta, q4[2]);
-          q4[3] = fmaf(cb, tb, q4[3]);
+      for (int k = 0; k < NC; ++k) smh[k] = sml[k] = tmh[k] = tml[k] = 0.f;
+      if (go && have) {
+        row2(sat_plane(sats, R, sm, 0), R, smh);
+        row2(sat_plane(sats, R, sm, 1), R, sml);
+        row2(sat_plane(satt, R, tm, 0), R, tmh);
+        row2(sat_plane(satt, R, tm, 1), R, tml);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          if (slot_rank(k) < R) {
+            const float sa = ((smh[k] - s0h[k]) + (sml[k] - s0l[k])) * inv;
+            const float sb = ((s1h[k] - smh[k]) + (s1l[k] - sml[k])) * inv;
+            const float ta = ((tmh[k] - t0h[k]) + (tml[k] - t0l[k])) * inv;
+            const float tb = ((t1h[k] - tmh[k]) + (t1l[k] - tml[k])) * inv;
+            const float ca = c[k] * sa, cb = c[k] * sb;
+            q4[0] = fmaf(ca, ta, q4[0]);
+            q4[1] = fmaf(ca, tb, q4[1]);
+            q4[2] = fmaf(cb, ta, q4[2]);
+            q4[3] = fmaf(cb, tb, q4[3]);
+          } else {
+            smh[k] = sml[k] = tmh[k] = tml[k] = 0.f;
+          }
         }
       }
 #pragma unroll
@@ -940,17 +978,30 @@ extern "C" int gsp_sample_ndf(const gsp_material* h_mats, int n_mats, const gsp_
   if (n == 0) return GSP_OK;
   int lanes = 4;
   while (lanes * 2 < rmax) lanes *= 2;  // two rank slots per lane (rmax <= 64)
+  bool pairs = true;  // every rank even and the fx, fy rows 8-byte aligned
+  for (int i = 0; i < n_mats; ++i)
+    pairs = pairs && h_mats[i].rank % 2 == 0 &&
+            ((reinterpret_cast<uintptr_t>(h_mats[i].fx) | reinterpret_cast<uintptr_t>(h_mats[i].fy)) & 7) == 0;
   const int threads = 256;
   const long long per_cta = threads / 32 * (32 / lanes);
   long long blocks = (n + per_cta - 1) / per_cta;
   const long long cap = static_cast<long long>(sm_count()) * 8;
   if (blocks > cap) blocks = cap;
   cudaStream_t s = to_stream(stream);
-  switch (lanes) {
-    case 4: k_sample_ndf<4><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
-    case 8: k_sample_ndf<8><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
-    case 16: k_sample_ndf<16><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
-    default: k_sample_ndf<32><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+  if (pairs) {
+    switch (lanes) {
+      case 4: k_sample_ndf<4, 2><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+      case 8: k_sample_ndf<8, 2><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+      case 16: k_sample_ndf<16, 2><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+      default: k_sample_ndf<32, 2><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+    }
+  } else {
+    switch (lanes) {
+      case 4: k_sample_ndf<4, 1><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+      case 8: k_sample_ndf<8, 1><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+      case 16: k_sample_ndf<16, 1><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+      default: k_sample_ndf<32, 1><<<blocks, threads, 0, s>>>(mp, d_q, n, d_u, d_out, d_status); break;
+    }
   }
   GSP_CHECK_LAUNCH();
   return GSP_OK;
