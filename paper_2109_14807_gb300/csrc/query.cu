@@ -235,15 +235,19 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
       ++grab;
     }
     if (base >= n) break;
+    // the descriptor of the group's next query is loaded one query ahead, so
+    // its HBM latency overlaps the current query's table reads
+    gsp_query dn{};
+    if (base + sub < n) load_query(q, base + sub, dn);
     for (int c = 0; c < chunk; ++c) {
       const long long qi = base + static_cast<long long>(c) * QPW + sub;
+      const gsp_query d = dn;
+      if (c + 1 < chunk && qi + QPW < n) load_query(q, qi + QPW, dn);
       float acc[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) acc[k] = 0.0f;
       bool bad = false;
       if (qi < n) {
-        gsp_query d;
-        load_query(q, qi, d);
         if (d.material >= static_cast<uint32_t>(mp.n)) {
           bad = true;
         } else {
@@ -375,11 +379,24 @@ __global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constan
     for (int e = threadIdx.x; e < gp.soff[mp.n]; e += blockDim.x) sacc[e] = 0.0f;
     __syncthreads();
   }
+  // the next descriptor and upstream gradient of this group are loaded one
+  // query ahead, so their HBM latency overlaps the current query's work
+  gsp_query dn{};
+  float gn = 0.0f;
+  if (warp_id * QPW + sub < n) {
+    load_query(q, warp_id * QPW + sub, dn);
+    gn = __ldg(gout + warp_id * QPW + sub);
+  }
   for (long long base = warp_id * QPW; base < n; base += n_warps * QPW) {
     const long long qi = base + sub;
+    const gsp_query d = dn;
+    const float g = gn;
+    const long long qn = qi + n_warps * QPW;
+    if (qn < n) {
+      load_query(q, qn, dn);
+      gn = __ldg(gout + qn);
+    }
     if (qi >= n) continue;
-    gsp_query d;
-    load_query(q, qi, d);
     if (d.material >= static_cast<uint32_t>(mp.n)) {
       if (j == 0) set_status(status, GSP_DEV_BAD_QUERY);
       continue;
@@ -391,7 +408,6 @@ __global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constan
       if (j == 0) set_status(status, GSP_DEV_BAD_QUERY);
       continue;
     }
-    const float g = __ldg(gout + qi);
     if (g == 0.0f) continue;
     const int R = M.rank;
     const float* flw = M.tables;
