@@ -114,6 +114,33 @@ def test_operand_columns_and_mttkrp_at_every_occupancy(prec, B, n_occ):
     assert torch.equal(ws.buf[:nb], ws2.buf[:nb])
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_operand_columns_at_128_bins(prec):
+    # B = 128 (16384 bins, the largest bin grid): 300 bins occur, 384 operand
+    # columns; the MTTKRPs against the structured oracle (pinned to the dense
+    # definition), which never forms the 16384-column tensor
+    import paper_2109_14807_gb300 as g
+    N, L, B, R = 64, 7, 128, 16
+    if not _supported(prec, N, L, B, R):
+        pytest.skip(f"{prec} MTTKRP does not support the shape {(N, L, B, R)}")
+    occ = np.sort(np.argsort(synth.uniform(41, B, B * B))[:300])
+    m = _map_of_bins(N, B, occ, 9)
+    s, t = ndf.bin_index(m, B)
+    ws = g.CPWorkspace(N, L, B, R, prec)
+    ws.prepare(normal_xy=dev(m))
+    assert ws.operand_cols() == (300, 384)
+    u = [synth.uniform(700, k, n * R).reshape(n, R).astype(np.float32) for k, n in enumerate((N, N, L, B, B))]
+    outs = ws.mttkrp({k: dev(a) for k, a in zip(("fx", "fy", "fl", "fs", "ft"), u)})
+    torch.cuda.synchronize()
+    SF = cp.StructuredFootprint(s, t, L, B)
+    A = [a.astype(np.float64) for a in u]
+    for n in range(5):
+        ref = SF.mttkrp(A, n)
+        got = outs[n].double().cpu().numpy()
+        err = np.max(np.abs(got - ref) / np.maximum(ref, 1e-30 + np.max(ref) * 1e-6))
+        assert err <= MTTKRP_TOL[prec], (n, err)
+
+
 def _oracle_fits(X, R, init, sweeps):
     A0 = [init[k].astype(np.float32).astype(np.float64) for k in ("fx", "fy", "fl", "fs", "ft")]
     return cp.cp_als(X, R, A0, sweeps)
