@@ -178,7 +178,8 @@ size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precisi
  * that occur somewhere in the map (all other bins are zero in every
  * footprint): column c < n holds the c-th occurring bin (s*B + t, in
  * increasing order), columns n .. C-1 are zero, C = n rounded up to a multiple
- * of 128 (at most B*B); with B*B < 256, C = B*B and column c is bin c.  The
+ * of 16 for the tensor-core precisions and of 128 for GSP_PREC_FP32 (at most
+ * B*B); with B*B < 256, C = B*B and column c is bin c.  The
  * call synchronises `stream` once to learn C (gsp_cp_operand_cols reports
  * it).  Dropping the all-zero columns changes only the order of the FP32
  * accumulation against the full B*B operand.  Exactly one of d_hist

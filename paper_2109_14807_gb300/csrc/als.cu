@@ -184,9 +184,11 @@ __global__ void k_bin_occupancy(const uint16_t* __restrict__ bins, long long n, 
     if (m[i]) atomicOr(occ + i, m[i]);
 }
 
-// cols = {count, Bk, 0, 0, col -> bin [Bk] (-1: padding), bin -> col [B2] (-1:
-// absent)}.  Bk = B2 (identity columns) when B2 < 256, else the occupied count
-// rounded up to 128, at most B2.  One CTA of 512 threads, one word each.
+// cols = {count, Bk, Bt, 0, col -> bin [Bk] (-1: padding), bin -> col [B2]
+// (-1: absent)}.  Bk = B2 (identity columns) when B2 < 256, else the occupied
+// count rounded up to 128, at most B2; Bt = the count rounded up to 16 (B2 for
+// identity columns), the columns the tensor-core precisions store.  One CTA of
+// 512 threads, one word each.
 __global__ void __launch_bounds__(512) k_bin_compact(const uint32_t* __restrict__ occ, int B2,
                                                      int32_t* __restrict__ cols) {
   __shared__ int wbase[512];
@@ -211,7 +213,8 @@ __global__ void __launch_bounds__(512) k_bin_compact(const uint32_t* __restrict_
   if (w == 0) {
     cols[0] = ident ? B2 : count;
     cols[1] = Bk;
-    cols[2] = cols[3] = 0;
+    cols[2] = ident ? B2 : min(Bk, max(16, (count + 15) / 16 * 16));
+    cols[3] = 0;
   }
   if (w < words) {
     int rank = wbase[w] - __popc(bits);
@@ -773,7 +776,7 @@ int run_lst(const Ctx& c, const float* fx, const float* fy) {
                          c.at<float>(c.lay.Zp), d, c.prec, c.at<uint32_t>(c.lay.flags), c.s);
   // split-K chunks: within the partial buffer the layout sized for all B * B columns
   MttkrpDims dense = d;
-  dense.Bk = 0;
+  dense.Bk = dense.Bt = 0;
   int C = lst_chunks(d, c.prec);
   const long long cap = static_cast<long long>(lst_chunks(dense, c.prec)) * dense.B2() / d.B2();
   while (C > 1 && C > cap) C >>= 1;
@@ -920,33 +923,42 @@ int join_solve(const Ctx& c, const gsp_cp_factors& f, int mode) {
 // MTTKRPs launch without reading the device (and can be graph-captured).
 struct ColsEntry {
   const void* ws;
-  int N, L, B, R, prec, Bk;
+  int N, L, B, R, prec, Bk, Bt;
 };
 std::mutex g_cols_mu;
 std::vector<ColsEntry> g_cols;
 
-void remember_cols(const void* ws, const MttkrpDims& d, int prec, int Bk) {
+void remember_cols(const void* ws, const MttkrpDims& d, int prec, int Bk, int Bt) {
   std::lock_guard<std::mutex> lk(g_cols_mu);
   for (auto& e : g_cols)
     if (e.ws == ws) {
-      e = ColsEntry{ws, d.N, d.L, d.B, d.R, prec, Bk};
+      e = ColsEntry{ws, d.N, d.L, d.B, d.R, prec, Bk, Bt};
       return;
     }
   if (g_cols.size() >= 256) g_cols.erase(g_cols.begin());
-  g_cols.push_back(ColsEntry{ws, d.N, d.L, d.B, d.R, prec, Bk});
+  g_cols.push_back(ColsEntry{ws, d.N, d.L, d.B, d.R, prec, Bk, Bt});
 }
 
-int recall_cols(const void* ws, const MttkrpDims& d, int prec) {
+bool recall_cols(const void* ws, const MttkrpDims& d, int prec, int* Bk, int* Bt) {
   std::lock_guard<std::mutex> lk(g_cols_mu);
   for (const auto& e : g_cols)
-    if (e.ws == ws && e.N == d.N && e.L == d.L && e.B == d.B && e.R == d.R && e.prec == prec)
-      return e.Bk;
-  return -1;
+    if (e.ws == ws && e.N == d.N && e.L == d.L && e.B == d.B && e.R == d.R && e.prec == prec) {
+      *Bk = e.Bk;
+      *Bt = e.Bt;
+      return true;
+    }
+  return false;
 }
 
-bool valid_cols(const MttkrpDims& d, int Bk) {
+// Stored columns per operand row: the FP32 CUDA-core pass reads T with its
+// own tile grid and stores all Bk columns; the tensor-core passes store the
+// occupied bins rounded up to 16 (Bt16 from the column table).
+int stored_cols(int prec, int Bk, int Bt16) { return prec == GSP_PREC_FP32 ? Bk : Bt16; }
+
+bool valid_cols(const MttkrpDims& d, int Bk, int Bt) {
   const int B2 = d.B * d.B;
-  return B2 < 256 ? Bk == B2 : (Bk >= 128 && Bk <= B2 && Bk % 128 == 0);
+  if (B2 < 256) return Bk == B2 && Bt == B2;
+  return Bk >= 128 && Bk <= B2 && Bk % 128 == 0 && Bt >= 16 && Bt <= Bk && Bt % 16 == 0;
 }
 
 bool path_supported(const MttkrpDims& d, int prec) {
@@ -972,16 +984,18 @@ int make_ctx(int N, int L, int B, int R, int prec, void* d_ws, size_t ws_bytes, 
 // of its prepare, else read from the workspace.
 int resolve_cols(Ctx& c) {
   if (is_structured(c.prec)) return GSP_OK;
-  int Bk = recall_cols(c.ws, c.d, c.prec);
-  if (Bk < 0) {
-    int32_t h[2] = {0, 0};
+  int Bk = 0, Bt = 0;
+  if (!recall_cols(c.ws, c.d, c.prec, &Bk, &Bt)) {
+    int32_t h[3] = {0, 0, 0};
     GSP_CUDA(cudaMemcpyAsync(h, c.ws + c.lay.cols, sizeof(h), cudaMemcpyDeviceToHost, c.s));
     GSP_CUDA(cudaStreamSynchronize(c.s));
     Bk = h[1];
-    if (!valid_cols(c.d, Bk)) return GSP_ERR_INVALID_ARG;  // not a prepared workspace
-    remember_cols(c.ws, c.d, c.prec, Bk);
+    Bt = stored_cols(c.prec, h[1], h[2]);
+    if (!valid_cols(c.d, Bk, Bt)) return GSP_ERR_INVALID_ARG;  // not a prepared workspace
+    remember_cols(c.ws, c.d, c.prec, Bk, Bt);
   }
   c.d.Bk = Bk;
+  c.d.Bt = Bt;
   return GSP_OK;
 }
 
@@ -1148,13 +1162,13 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
   GSP_CHECK_LAUNCH();
   k_bin_compact<<<1, 512, 0, c.s>>>(occ, B2, cols);
   GSP_CHECK_LAUNCH();
-  int32_t hc[2] = {0, 0};
+  int32_t hc[3] = {0, 0, 0};
   GSP_CUDA(cudaMemcpyAsync(hc, cols, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
   GSP_CUDA(cudaStreamSynchronize(c.s));
-  const int Bk = hc[1];
-  if (!valid_cols(d, Bk)) return GSP_ERR_INVALID_ARG;
-  remember_cols(c.ws, d, c.prec, Bk);
-  const long long slice = d.N2() * Bk;  // operand elements per level
+  const int Bk = hc[1], Bt = stored_cols(c.prec, hc[1], hc[2]);
+  if (!valid_cols(d, Bk, Bt)) return GSP_ERR_INVALID_ARG;
+  remember_cols(c.ws, d, c.prec, Bk, Bt);
+  const long long slice = d.N2() * Bt;  // operand elements per level (Bt stored columns)
   if (d_hist) {
     for (int l = 0; l < levels; ++l) {
       const float scale =
@@ -1162,11 +1176,11 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
       const int32_t* hl = d_hist + d.N2() * B2 * l;
       if (is_bf16(c.prec))
         k_cast_cols<__nv_bfloat16><<<grid_for(slice, 256), 256, 0, c.s>>>(
-            hl, d.N2(), B2, Bk, cols, scale, 0, slice * l, c.at<__nv_bfloat16>(c.lay.T) + slice * l,
+            hl, d.N2(), B2, Bt, cols, scale, 0, slice * l, c.at<__nv_bfloat16>(c.lay.T) + slice * l,
             sumsq + l);
       else
         k_cast_cols<float><<<grid_for(slice, 256), 256, 0, c.s>>>(
-            hl, d.N2(), B2, Bk, cols, scale, c.prec == GSP_PREC_TF32, slice * l,
+            hl, d.N2(), B2, Bt, cols, scale, c.prec == GSP_PREC_TF32, slice * l,
             c.at<float>(c.lay.T) + slice * l, sumsq + l);
       GSP_CHECK_LAUNCH();
     }
@@ -1185,7 +1199,7 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
     else
       o.f32 = c.at<float>(c.lay.T);
     o.tf32 = c.prec == GSP_PREC_TF32;
-    GSP_TRY(launch_box_hist(bm, N, levels, Bk, o, c.s));
+    GSP_TRY(launch_box_hist(bm, N, levels, Bt, o, c.s));
   }
   k_norm2<<<1, 32, 0, c.s>>>(sumsq, levels, bins, opts->raw_counts, c.at<double>(c.lay.norm2));
   GSP_CHECK_LAUNCH();
@@ -1198,12 +1212,13 @@ extern "C" int gsp_cp_operand_cols(int N, int levels, int bins, int rank, int pr
   if (!h_cols || is_structured(precision)) return GSP_ERR_INVALID_ARG;
   Ctx c;
   GSP_TRY(make_ctx(N, levels, bins, rank, precision, const_cast<void*>(d_ws), ws_bytes, stream, c));
-  int32_t h[2] = {0, 0};
+  int32_t h[3] = {0, 0, 0};
   GSP_CUDA(cudaMemcpyAsync(h, c.ws + c.lay.cols, sizeof(h), cudaMemcpyDeviceToHost, c.s));
   GSP_CUDA(cudaStreamSynchronize(c.s));
-  if (!valid_cols(c.d, h[1])) return GSP_ERR_INVALID_ARG;
+  const int Bt = stored_cols(precision, h[1], h[2]);
+  if (!valid_cols(c.d, h[1], Bt)) return GSP_ERR_INVALID_ARG;
   h_cols[0] = h[0];
-  h_cols[1] = h[1];
+  h_cols[1] = Bt;
   return GSP_OK;
 }
 

@@ -14,14 +14,18 @@
 
 namespace gsp {
 
-// Bk: bin columns of the operand per footprint.  0 means all B * B bins; the
-// CP-ALS prepare sets it to the occupied bins of the map (rounded up to 128),
-// the operand then holding those columns only (see als.cu, bin compaction).
+// Bk: bin columns per footprint seen by the MTTKRP passes.  0 means all B * B
+// bins; the CP-ALS prepare sets it to the occupied bins of the map rounded up
+// to 128 (see als.cu, bin compaction).  Bt: columns stored per operand row
+// (0: Bk).  The tensor-core passes store the occupied bins rounded up to 16
+// only and read columns Bt .. Bk-1 as zeros through the TMA tensor bounds.
 struct MttkrpDims {
   int N, L, B, R;
   int Bk = 0;
+  int Bt = 0;
   long long N2() const { return static_cast<long long>(N) * N; }
   int B2() const { return Bk ? Bk : B * B; }
+  int B2t() const { return Bt ? Bt : B2(); }
 };
 
 // Number of split-K chunks per level used by the Z' pass (partials [L*C][B2][R]).

@@ -848,7 +848,8 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
   const bool split = precision != GSP_PREC_BF16_1X;  // BF16 and TF32 use hi + lo pairs
   const int brows = d.R * (split ? 2 : 1);
   CUtensorMap mT, mK;
-  GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2(), 128));
+  // T rows hold B2t() stored columns; the K chunks past them read zeros
+  GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2t(), 128));
   GSP_TRY(make_map(&mK, KRt, elem, brows, static_cast<long long>(d.L) * d.B2(), brows));
   const int n_tiles = static_cast<int>(d.N2() / 128);
   int grid = sm_count();
@@ -898,7 +899,7 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
     k_fx_cols<float><<<grid_for(nr, 256), 256, 0, s>>>(fx, d.N, d.R, 1, static_cast<float*>(FXt));
   GSP_CHECK_LAUNCH();
   CUtensorMap mT, mF;
-  GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2(), E128,
+  GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2t(), E128,
                    elem == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
   GSP_TRY(make_map(&mF, FXt, elem, brows, d.N, brows));
   int MB = 0;

@@ -80,15 +80,17 @@ def _map_of_bins(N, B, bins, seed):
                                      (32, 200), (32, 1024)])
 def test_operand_columns_and_mttkrp_at_every_occupancy(prec, B, n_occ):
     # the operand keeps the bins that occur (increasing order), padded to a
-    # multiple of 128 columns (all B^2 bins when B^2 < 256); the MTTKRPs are
-    # those of the full tensor whatever the occupancy
+    # multiple of 16 columns for the tensor-core precisions and of 128 for FP32
+    # (all B^2 bins when B^2 < 256); the MTTKRPs are those of the full tensor
+    # whatever the occupancy
     import paper_2109_14807_gb300 as g
     N, L, R = 64, 7, 16
     occ = np.sort(np.argsort(synth.uniform(40 + n_occ, B, B * B))[:n_occ])
     m = _map_of_bins(N, B, occ, 7 + n_occ)
     s, t = ndf.bin_index(m, B)
     assert np.array_equal(np.unique(s * B + t), occ)
-    cols = B * B if B * B < 256 else min(B * B, -(-n_occ // 128) * 128)
+    unit = 128 if prec == "fp32" else 16
+    cols = B * B if B * B < 256 else min(B * B, max(unit, -(-n_occ // unit) * unit))
     if not _supported(prec, N, L, B, R):
         pytest.skip(f"{prec} MTTKRP does not support the shape {(N, L, B, R)}")
     ws = g.CPWorkspace(N, L, B, R, prec)
@@ -117,8 +119,9 @@ def test_operand_columns_and_mttkrp_at_every_occupancy(prec, B, n_occ):
 @pytest.mark.parametrize("prec", ["fp32", "tf32"])
 def test_operand_columns_at_128_bins(prec):
     # B = 128 (16384 bins, the largest bin grid): 300 bins occur, 384 operand
-    # columns; the MTTKRPs against the structured oracle (pinned to the dense
-    # definition), which never forms the 16384-column tensor
+    # columns for FP32 (304 stored for TF32); the MTTKRPs against the
+    # structured oracle (pinned to the dense definition), which never forms the
+    # 16384-column tensor
     import paper_2109_14807_gb300 as g
     N, L, B, R = 64, 7, 128, 16
     if not _supported(prec, N, L, B, R):
@@ -128,7 +131,7 @@ def test_operand_columns_at_128_bins(prec):
     s, t = ndf.bin_index(m, B)
     ws = g.CPWorkspace(N, L, B, R, prec)
     ws.prepare(normal_xy=dev(m))
-    assert ws.operand_cols() == (300, 384)
+    assert ws.operand_cols() == (300, 384 if prec == "fp32" else 304)
     u = [synth.uniform(700, k, n * R).reshape(n, R).astype(np.float32) for k, n in enumerate((N, N, L, B, B))]
     outs = ws.mttkrp({k: dev(a) for k, a in zip(("fx", "fy", "fl", "fs", "ft"), u)})
     torch.cuda.synchronize()
@@ -204,9 +207,9 @@ def test_operand_rounding_is_exact_or_neighbour_and_unbiased(prec, drop):
     s, t = ndf.bin_index(m, B)
     H = ndf.footprint_histograms(s, t, L, B)
     # operand columns: the bins occurring in the map, in increasing order, then
-    # zero columns up to a multiple of 128
+    # zero columns up to a multiple of 16 (the tensor-core precisions)
     occ = np.unique(s * B + t)
-    Bk = min(B * B, max(128, -(-len(occ) // 128) * 128))
+    Bk = min(B * B, max(16, -(-len(occ) // 16) * 16))
     dense = ndf.normalised_tensor(H, B).reshape(L, N, N, B * B)
     exact = np.zeros((L, N, N, Bk), dtype=np.float32)
     exact[..., :len(occ)] = dense[..., occ]  # exact: counts * 2^k
