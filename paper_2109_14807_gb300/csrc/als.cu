@@ -159,11 +159,14 @@ __global__ void k_kr_cols(const float* __restrict__ fl, const float* __restrict_
 // Bins that no texel of the map falls in are zero in every footprint of every
 // level: the dense operand's columns for them carry nothing (Sec. 4.2 drops
 // blank NDF blocks for the same reason).  The operand keeps the occupied bins
-// only, in increasing order, padded with zero columns to a multiple of 128
-// (the tensor-core tiles); the bin map is renumbered to those columns, so the
-// histogram and MTTKRP kernels just see a smaller bin axis, and only the
-// Khatri-Rao operand and the (l, s, t) contractions map a column back to its
-// (s, t).  All results are those of the dense operand.
+// only, in increasing order: the MTTKRP passes see Bk columns (the count
+// padded with zero columns to a multiple of 128, the tensor-core tile), and
+// the tensor-core precisions store only Bt of them (the count rounded up to
+// 16), the TMA tensor bounds supplying the zeros past Bt.  The bin map is
+// renumbered to those columns, so the histogram and MTTKRP kernels just see a
+// smaller bin axis, and only the Khatri-Rao operand and the (l, s, t)
+// contractions map a column back to its (s, t).  All results are those of
+// the dense operand up to the order of FP32 accumulation.
 
 // occ bit b: bin b occurs in the map.  Lanes holding the same bin elect one
 // shared-memory OR; every CTA ORs its mask into the global one.
