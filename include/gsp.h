@@ -568,6 +568,9 @@ int gsp_selftest_recip(const double* d_in, int64_t n, double* d_out, gsp_stream 
 const char* gsp_strerror(int status);
 /* cudaError_t value of the last failing CUDA call in this thread (0 if none). */
 int gsp_last_cuda_error(void);
+/* Library version, major * 10000 + minor * 100 + patch.  2.0.0: query tables
+ * as hi / lo / value planes (gsp_query_table_floats changed) and the compacted
+ * CP-ALS operand (gsp_cp_operand_cols). */
 int gsp_version(void);
 
 #ifdef __cplusplus

@@ -127,4 +127,4 @@ extern "C" const char* gsp_strerror(int status) {
 
 extern "C" int gsp_last_cuda_error(void) { return gsp::last_cuda_error(); }
 
-extern "C" int gsp_version(void) { return 10000; }
+extern "C" int gsp_version(void) { return 20000; }
