@@ -49,7 +49,7 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
 int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, float* Zpart,
                   float* Zp, const MttkrpDims& d, int precision, uint32_t* err, cudaStream_t s);
 bool tc_supported(const MttkrpDims& d, int precision);
-constexpr int kLstMaxRanges = 256;
+constexpr int kLstMaxRanges = 320;  // >= 2 CTAs per SM x 152 SMs
 
 // Structured path (structured.cu): exact MTTKRPs from the bin map, the footprint
 // windows moved onto the spatial factors.  Buffers, all device, caller-owned:

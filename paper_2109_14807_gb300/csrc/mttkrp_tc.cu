@@ -774,7 +774,14 @@ int stages_for(size_t stage_bytes, size_t fixed) {
 }
 
 size_t xy_stage_bytes(int R, bool split) { return kTileBytes + static_cast<size_t>(R) * 128 * (split ? 2 : 1); }
-int xy_stages(int R, bool split) { return stages_for(xy_stage_bytes(R, split), 1024); }
+// Two Y' CTAs per SM, each with a ring of ~110 KB (at least 3 stages): two
+// independent TMA / MMA / epilogue pipelines per SM.  Their tensor memory
+// (two chunk accumulators of R columns each) fits twice in the 512 columns.
+constexpr int kXyCtasPerSm = 2;
+int xy_stages(int R, bool split) {
+  const int st = static_cast<int>((110 * 1024 - 1024) / xy_stage_bytes(R, split));
+  return st > kMaxStages ? kMaxStages : (st < 3 ? 3 : st);
+}
 size_t xy_smem(int R, bool split) { return 1024 + xy_stages(R, split) * xy_stage_bytes(R, split); }
 
 size_t lst_b_bytes(int R, bool split) { return static_cast<size_t>(R) * 128 * (split ? 2 : 1); }
@@ -788,8 +795,15 @@ struct LstCfg {
   int stages, bslots;
   size_t smem;
 };
+// Chunk accumulators of the Z' pass (two when three accumulators' columns fit).
+int lst_accs(int R, int MB) { return 3 * MB * R <= 512 ? 2 : 1; }
+// Z' CTAs per SM: two when two CTAs' tensor memory fits in the 512 columns.
+int lst_ctas_per_sm(int R, int MB) {
+  return 2 * static_cast<int>(tmem_cols_for((lst_accs(R, MB) + 1) * MB * R)) <= 512 ? 2 : 1;
+}
 LstCfg lst_cfg(int R, bool split, int MB) {
-  const size_t b = lst_b_bytes(R, split), budget = 200 * 1024 - 1024;
+  const int per_sm = lst_ctas_per_sm(R, MB);
+  const size_t b = lst_b_bytes(R, split), budget = (per_sm == 2 ? 110 : 200) * 1024 - 1024;
   LstCfg best{3, 2, 0};
   int lead = -1;
   for (int nb = 2; nb <= kMaxStages && nb * b + 3 * kTileBytes <= budget; ++nb) {
@@ -802,10 +816,10 @@ LstCfg lst_cfg(int R, bool split, int MB) {
       best = LstCfg{st, nb, 0};
     }
   }
-  // The Z' pass allocates up to all 512 TMEM columns, so it asks for enough
-  // shared memory that no second CTA fits on the SM.
+  // With one CTA per SM the Z' pass may allocate up to all 512 TMEM columns,
+  // so it then asks for enough shared memory that no second CTA fits.
   const size_t need = 1024 + best.stages * static_cast<size_t>(kTileBytes) + best.bslots * b;
-  best.smem = need < 120 * 1024 ? 120 * 1024 : need;
+  best.smem = per_sm == 1 && need < 120 * 1024 ? 120 * 1024 : need;
   return best;
 }
 
@@ -852,7 +866,7 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
   GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2t(), 128));
   GSP_TRY(make_map(&mK, KRt, elem, brows, static_cast<long long>(d.L) * d.B2(), brows));
   const int n_tiles = static_cast<int>(d.N2() / 128);
-  int grid = sm_count();
+  int grid = sm_count() * kXyCtasPerSm;
   if (grid > n_tiles) grid = n_tiles;
   const size_t smem = xy_smem(d.R, split);
   const int stages = xy_stages(d.R, split);
@@ -878,7 +892,7 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
 int tc_lst_ctas(const MttkrpDims& d) {
   int MB = 0;
   const int G = lst_groups(d, &MB);
-  int P = sm_count() / G;
+  int P = lst_ctas_per_sm(d.R, MB) * sm_count() / G;
   if (P < d.L) P = d.L;  // a range is then at most one level long: <= 2 segments
   if (P > kLstMaxRanges) P = kLstMaxRanges;
   return P;
@@ -909,7 +923,7 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
   const LstCfg cfg = lst_cfg(d.R, split, MB);
   const size_t smem = cfg.smem;
   const int stages = cfg.stages, nB = cfg.bslots;
-  const int nAcc = 3 * MB * d.R <= 512 ? 2 : 1;  // double-buffered chunk accumulator when it fits
+  const int nAcc = lst_accs(d.R, MB);  // double-buffered chunk accumulator when it fits
   const int logN = ilog2(d.N);
   prof_begin(PROF_MTTKRP_LST, s);
   if (elem == 4) {
