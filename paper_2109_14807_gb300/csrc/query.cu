@@ -356,19 +356,23 @@ __device__ __forceinline__ void red_add(float* p, const float* v) {
   }
 }
 
+constexpr int kBwdThreads = 256;
+constexpr int kBwdWarps = kBwdThreads / 32;
+
 // LANES lanes per query; lane j handles the VEC consecutive ranks
 // j*VEC + k*LANES*VEC .. + VEC-1, so that its fx / fy gradient updates are
 // vector reductions.  The per-CTA shared-memory tables store rank r of a row
 // at column (r mod VEC) * R/VEC + r / VEC, so that the lanes' atomics for one
 // v = r mod VEC hit consecutive words (no bank conflicts); the flush undoes it.
 template <int LANES, int VEC>
-__global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constant__ MatParams mp,
+__global__ void __launch_bounds__(kBwdThreads, 3) k_range_query_bwd(const __grid_constant__ MatParams mp,
                                                          const __grid_constant__ GradParams gp,
                                                          const gsp_query* __restrict__ q,
                                                          long long n,
                                                          const float* __restrict__ gout,
                                                          uint32_t* status) {
   extern __shared__ float sacc[];
+  __shared__ float4 tslots[kBwdWarps][32][5];  // per warp: the terms of its batch of 32 queries
   constexpr int QPW = 32 / LANES;
   const int lane = threadIdx.x & 31;
   const int sub = lane / LANES;
@@ -379,36 +383,66 @@ __global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constan
     for (int e = threadIdx.x; e < gp.soff[mp.n]; e += blockDim.x) sacc[e] = 0.0f;
     __syncthreads();
   }
-  // the next descriptor and upstream gradient of this group are loaded one
-  // query ahead, so their HBM latency overlaps the current query's work
+  // Query terms are formed once per query: a warp takes batches of 32
+  // queries, lane k loads query k of the batch (one batch ahead, so the HBM
+  // latency overlaps the current batch) and stores its terms in the warp's
+  // shared slots; each lane group then reads the slot of the query it
+  // processes (five broadcast 16-byte loads).
+  float4 (*slots)[5] = tslots[threadIdx.x >> 5];
+  const long long n_batches = (n + 31) / 32;
   gsp_query dn{};
   float gn = 0.0f;
-  if (warp_id * QPW + sub < n) {
-    load_query(q, warp_id * QPW + sub, dn);
-    gn = __ldg(gout + warp_id * QPW + sub);
+  if (warp_id < n_batches && warp_id * 32 + lane < n) {
+    load_query(q, warp_id * 32 + lane, dn);
+    gn = __ldg(gout + warp_id * 32 + lane);
   }
-  for (long long base = warp_id * QPW; base < n; base += n_warps * QPW) {
-    const long long qi = base + sub;
-    const gsp_query d = dn;
-    const float g = gn;
-    const long long qn = qi + n_warps * QPW;
-    if (qn < n) {
-      load_query(q, qn, dn);
-      gn = __ldg(gout + qn);
+  for (long long bt = warp_id; bt < n_batches; bt += n_warps) {
+    {
+      const long long qk = bt * 32 + lane;
+      const gsp_query dk = dn;
+      const float gk = gn;
+      const long long qn = (bt + n_warps) * 32 + lane;
+      if (bt + n_warps < n_batches && qn < n) {
+        load_query(q, qn, dn);
+        gn = __ldg(gout + qn);
+      }
+      int live = 0, mk = 0;
+      QTerms tk{};
+      if (qk < n) {
+        if (dk.material >= static_cast<uint32_t>(mp.n)) {
+          set_status(status, GSP_DEV_BAD_QUERY);
+        } else {
+          mk = static_cast<int>(dk.material);
+          tk = query_terms(dk, mp.m[mk]);
+          if (!tk.ok) set_status(status, GSP_DEV_BAD_QUERY);
+          live = tk.ok && gk != 0.0f;
+        }
+      }
+      __syncwarp();  // every lane is done with the previous batch's slots
+      slots[lane][0] = make_float4(__int_as_float(tk.x), __int_as_float(tk.y), __int_as_float(tk.l0),
+                                   __int_as_float(tk.l1));
+      slots[lane][1] = make_float4(tk.f, __int_as_float(tk.is0), __int_as_float(tk.is1), __int_as_float(tk.it0));
+      slots[lane][2] = make_float4(__int_as_float(tk.it1), tk.fs0, tk.fs1, tk.ft0);
+      slots[lane][3] = make_float4(tk.ft1, tk.inv_ws, tk.inv_wt, __int_as_float(tk.isz));
+      slots[lane][4] = make_float4(__int_as_float(tk.itz), __int_as_float(mk), gk, __int_as_float(live));
+      __syncwarp();
     }
-    if (qi >= n) continue;
-    if (d.material >= static_cast<uint32_t>(mp.n)) {
-      if (j == 0) set_status(status, GSP_DEV_BAD_QUERY);
-      continue;
-    }
-    const int m = d.material;
+    for (int it = 0; it < LANES; ++it) {
+    const int slot = it * QPW + sub;
+    const float4 w4 = slots[slot][4];
+    if (!__float_as_int(w4.w)) continue;  // past the end, malformed or a zero gradient
+    const float4 w0 = slots[slot][0], w1 = slots[slot][1], w2 = slots[slot][2], w3 = slots[slot][3];
+    QTerms t;
+    t.x = __float_as_int(w0.x); t.y = __float_as_int(w0.y);
+    t.l0 = __float_as_int(w0.z); t.l1 = __float_as_int(w0.w);
+    t.f = w1.x; t.is0 = __float_as_int(w1.y); t.is1 = __float_as_int(w1.z); t.it0 = __float_as_int(w1.w);
+    t.it1 = __float_as_int(w2.x); t.fs0 = w2.y; t.fs1 = w2.z; t.ft0 = w2.w;
+    t.ft1 = w3.x; t.inv_ws = w3.y; t.inv_wt = w3.z; t.isz = __float_as_int(w3.w);
+    t.itz = __float_as_int(w4.x);
+    t.ok = true;
+    const int m = __float_as_int(w4.y);
+    const float g = w4.z;
     const gsp_material& M = mp.m[m];
-    QTerms t = query_terms(d, M);
-    if (!t.ok) {
-      if (j == 0) set_status(status, GSP_DEV_BAD_QUERY);
-      continue;
-    }
-    if (g == 0.0f) continue;
     const int R = M.rank;
     const float* flw = M.tables;
     const float* sats = M.tables + flw_floats(M.levels, R);
@@ -472,6 +506,7 @@ __global__ void __launch_bounds__(256, 3) k_range_query_bwd(const __grid_constan
       }
       red_add<VEC>(G.dfx + t.x * R + rv, dx);
       red_add<VEC>(G.dfy + t.y * R + rv, dy);
+    }
     }
   }
   if (gp.use_smem) {
@@ -727,6 +762,13 @@ int launch_bwd_t(long long blocks, int threads, size_t dyn, cudaStream_t s, cons
                  uint32_t* d_status) {
   GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<LANES, VEC>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+  // one wave of resident CTAs (registers, shared memory): the grid-stride
+  // loop then spreads the batches evenly, with no partial second wave
+  int per_sm = 0;
+  GSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_range_query_bwd<LANES, VEC>,
+                                                         threads, dyn));
+  const long long cap = static_cast<long long>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+  if (blocks > cap) blocks = cap;
   k_range_query_bwd<LANES, VEC><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
   return GSP_OK;
 }
@@ -948,12 +990,13 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
     for (int i = 0; i < n_mats; ++i) rmax = rmax > h_mats[i].rank ? rmax : h_mats[i].rank;
     int lanes = 4;
     while (lanes * vec < rmax && lanes < 32) lanes *= 2;
-    const int threads = 256;
+    const int threads = kBwdThreads;
     const size_t dyn = gp.use_smem ? smem : 0;
-    long long warps = (n + (32 / lanes) - 1) / (32 / lanes);
+    long long warps = (n + 31) / 32;  // one batch of 32 queries per warp and step
     long long blocks = (warps * 32 + threads - 1) / threads;
-    // CTAs per SM: as many as the shared-memory tables allow, up to 8
-    long long per_sm = gp.use_smem ? static_cast<long long>((228 * 1024) / (smem + 1024)) : 8;
+    // CTAs per SM: as many as the shared memory (tables + query-term slots) allows, up to 8
+    const size_t slot_bytes = static_cast<size_t>(kBwdWarps) * 32 * 5 * sizeof(float4);
+    long long per_sm = static_cast<long long>((228 * 1024) / (dyn + slot_bytes + 1024));
     if (per_sm > 8) per_sm = 8;
     if (per_sm < 1) per_sm = 1;
     long long cap = static_cast<long long>(sm_count()) * per_sm;
