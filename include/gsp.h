@@ -284,7 +284,7 @@ typedef struct gsp_query_tuning {
   int32_t lanes_per_query; /* 4, 8, 16 or 32 */
   int32_t blocks_per_sm;   /* persistent CTAs per SM (1 .. 32)   */
   int32_t threads;         /* threads per CTA (32 .. 256, multiple of 32) */
-  int32_t chunk;           /* queries a warp claims per grab (1 .. 64) */
+  int32_t chunk;           /* batches of 32 queries a warp claims per grab (1 .. 64) */
 } gsp_query_tuning;
 
 /* Batched range queries (Eq. 5 extended to five modes):

@@ -217,43 +217,97 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
                                                      unsigned long long* counter, int chunk) {
   constexpr int QPW = 32 / LANES;  // queries per warp step
   constexpr int NC = 32 / LANES;   // conceptual lanes per lane
+  // per warp: the terms of its current batch of 32 queries (blockDim.x <= 256)
+  __shared__ float4 tslots[8][32][6];
   const int lane = threadIdx.x & 31;
   const int sub = lane / LANES;
   const int j = lane % LANES;
-  const long long per_grab = static_cast<long long>(chunk) * QPW;
+  float4 (*slots)[6] = tslots[threadIdx.x >> 5];
+  // a grab is `chunk` batches of 32 queries; lane k of the warp loads and
+  // evaluates query k of a batch (one batch ahead: the HBM latency of the
+  // descriptors overlaps the previous batch) and stores its terms in the
+  // warp's slots, which the lane group processing that query reads
+  const long long per_grab = static_cast<long long>(chunk) * 32;
   const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
   long long grab = 0;
-  for (;;) {
-    long long base;
+  auto next_grab = [&]() -> long long {
     if (counter) {
       unsigned long long b = 0;
       if (lane == 0) b = atomicAdd(counter, static_cast<unsigned long long>(per_grab));
-      base = static_cast<long long>(__shfl_sync(0xffffffffu, b, 0));
-    } else {
-      base = (warp_id + grab * n_warps) * per_grab;
-      ++grab;
+      return static_cast<long long>(__shfl_sync(0xffffffffu, b, 0));
     }
-    if (base >= n) break;
-    // the descriptor of the group's next query is loaded one query ahead, so
-    // its HBM latency overlaps the current query's table reads
-    gsp_query dn{};
-    if (base + sub < n) load_query(q, base + sub, dn);
-    for (int c = 0; c < chunk; ++c) {
-      const long long qi = base + static_cast<long long>(c) * QPW + sub;
-      const gsp_query d = dn;
-      if (c + 1 < chunk && qi + QPW < n) load_query(q, qi + QPW, dn);
+    return (warp_id + (grab++) * n_warps) * per_grab;
+  };
+  long long base = next_grab();
+  gsp_query dn{};
+  if (base + lane < n) load_query(q, base + lane, dn);
+  while (base < n) {
+    const long long following = next_grab();  // the grab after this one, claimed early
+    for (int bt = 0; bt < chunk; ++bt) {
+      const long long bbase = base + static_cast<long long>(bt) * 32;
+      {
+        const long long qk = bbase + lane;
+        const gsp_query dk = dn;
+        const long long nb = bt + 1 < chunk ? bbase + 32 : following;
+        if (nb < n && nb + lane < n) load_query(q, nb + lane, dn);
+        QTerms tk{};
+        int mk = 0, flags = 0, ixk = 0, iyk = 0;
+        float wxk = 0.f, wyk = 0.f;
+        if (qk < n) {
+          flags = 1;
+          if (dk.material >= static_cast<uint32_t>(mp.n)) {
+            flags |= 2;
+          } else {
+            mk = static_cast<int>(dk.material);
+            tk = query_terms(dk, mp.m[mk]);
+            bool bad = !tk.ok;
+            ixk = tk.x;
+            iyk = tk.y;
+            if constexpr (FXY) {
+              const float xf = __int_as_float(dk.x), yf = __int_as_float(dk.y);
+              if (!(fabsf(xf) < 1073741824.0f) || !(fabsf(yf) < 1073741824.0f)) bad = true;
+              const float x0 = bad ? 0.f : floorf(xf), y0 = bad ? 0.f : floorf(yf);
+              wxk = bad ? 0.f : xf - x0;
+              wyk = bad ? 0.f : yf - y0;
+              ixk = static_cast<int>(x0);
+              iyk = static_cast<int>(y0);
+            }
+            if (bad) flags |= 2;
+          }
+          if (flags & 2) set_status(status, GSP_DEV_BAD_QUERY);
+        }
+        __syncwarp();  // every lane is done with the previous batch's slots
+        slots[lane][0] = make_float4(__int_as_float(ixk), __int_as_float(iyk), __int_as_float(tk.l0),
+                                     __int_as_float(tk.l1));
+        slots[lane][1] = make_float4(tk.f, __int_as_float(tk.is0), __int_as_float(tk.is1),
+                                     __int_as_float(tk.it0));
+        slots[lane][2] = make_float4(__int_as_float(tk.it1), tk.fs0, tk.fs1, tk.ft0);
+        slots[lane][3] = make_float4(tk.ft1, tk.inv_ws, tk.inv_wt, __int_as_float(tk.isz));
+        slots[lane][4] = make_float4(__int_as_float(tk.itz), __int_as_float(mk), __int_as_float(flags), wxk);
+        slots[lane][5] = make_float4(wyk, 0.f, 0.f, 0.f);
+        __syncwarp();
+      }
+      for (int it = 0; it < LANES; ++it) {
+      const int slot = it * QPW + sub;
+      const long long qi = bbase + slot;
+      const float4 s4 = slots[slot][4];
+      const int flags = __float_as_int(s4.z);
       float acc[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) acc[k] = 0.0f;
-      bool bad = false;
-      if (qi < n) {
-        if (d.material >= static_cast<uint32_t>(mp.n)) {
-          bad = true;
-        } else {
-          const gsp_material& M = mp.m[d.material];
-          QTerms t = query_terms(d, M);
-          bad = !t.ok;
+      {
+        if (flags == 1) {  // in range and well formed
+          const float4 s0 = slots[slot][0], s1 = slots[slot][1], s2 = slots[slot][2], s3 = slots[slot][3];
+          QTerms t;
+          t.x = __float_as_int(s0.x); t.y = __float_as_int(s0.y);
+          t.l0 = __float_as_int(s0.z); t.l1 = __float_as_int(s0.w);
+          t.f = s1.x; t.is0 = __float_as_int(s1.y); t.is1 = __float_as_int(s1.z); t.it0 = __float_as_int(s1.w);
+          t.it1 = __float_as_int(s2.x); t.fs0 = s2.y; t.fs1 = s2.z; t.ft0 = s2.w;
+          t.ft1 = s3.x; t.inv_ws = s3.y; t.inv_wt = s3.z; t.isz = __float_as_int(s3.w);
+          t.itz = __float_as_int(s4.x);
+          t.ok = true;
+          const gsp_material& M = mp.m[__float_as_int(s4.y)];
           const int R = M.rank;
           const float* __restrict__ flw = M.tables;
           const float* sats = M.tables + flw_floats(M.levels, R);
@@ -263,13 +317,10 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           const float* __restrict__ fxr1 = fxr;
           const float* __restrict__ fyr1 = fyr;
           float wx = 0.f, wy = 0.f;
-          if constexpr (FXY) {
-            const float xf = __int_as_float(d.x), yf = __int_as_float(d.y);
-            if (!(fabsf(xf) < 1073741824.0f) || !(fabsf(yf) < 1073741824.0f)) bad = true;
-            const float x0 = bad ? 0.f : floorf(xf), y0 = bad ? 0.f : floorf(yf);
-            wx = bad ? 0.f : xf - x0;
-            wy = bad ? 0.f : yf - y0;
-            const int N = M.N, ix = static_cast<int>(x0), iy = static_cast<int>(y0);
+          if constexpr (FXY) {  // x, y hold floor of the float position; wx, wy the blend
+            wx = s4.w;
+            wy = slots[slot][5].x;
+            const int N = M.N, ix = t.x, iy = t.y;
             fxr = M.fx + static_cast<size_t>(ix & (N - 1)) * R;
             fxr1 = M.fx + static_cast<size_t>((ix + 1) & (N - 1)) * R;
             fyr = M.fy + static_cast<size_t>(iy & (N - 1)) * R;
@@ -333,15 +384,10 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           if (!(v & o)) acc[v] = acc[v] + acc[v | o];
       }
       const float v = acc[0];
-      if (qi < n && j == 0) {
-        if (bad) {
-          out[qi] = __int_as_float(0x7fc00000);
-          set_status(status, GSP_DEV_BAD_QUERY);
-        } else {
-          out[qi] = v;
-        }
+      if ((flags & 1) && j == 0) out[qi] = (flags & 2) ? __int_as_float(0x7fc00000) : v;
       }
     }
+    base = following;
   }
 }
 
@@ -893,7 +939,7 @@ int range_query_launch(const gsp_material* h_mats, int n_mats, const gsp_query* 
     counter = static_cast<unsigned long long*>(d_ws);
     GSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
   }
-  long long warps_needed = (n + (32 / lanes) * chunk - 1) / ((32 / lanes) * chunk);
+  long long warps_needed = (n + 32LL * chunk - 1) / (32LL * chunk);  // a grab: chunk batches of 32
   long long blocks = static_cast<long long>(sm_count()) * bpsm;
   long long need = (warps_needed * 32 + threads - 1) / threads;
   if (blocks > need) blocks = need;
