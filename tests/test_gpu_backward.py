@@ -51,6 +51,48 @@ def test_adjoint_matches_fp64_oracle(N, L, B, R):
         assert err <= 1e-4, (k, err)
 
 
+def test_adjoint_two_materials_and_malformed_queries():
+    # queries of two materials (ranks 16 and 64) in one launch, with malformed
+    # ones mixed in: each material's gradients are the oracle's adjoint of its
+    # own well-formed queries, and the malformed ones only raise the status bit
+    import paper_2109_14807_gb300 as g
+    shapes = [(32, 6, 16, 16), (64, 7, 32, 64)]
+    fs = [random_factors(N, L, B, R, 70 + i) for i, (N, L, B, R) in enumerate(shapes)]
+    parts = []
+    for i, (N, L, B, R) in enumerate(shapes):
+        qi = synth.queries_fractional(N, L, B, 2000 + 37 * i, 71 + i, frac_level=True)
+        qi["material"] = i
+        parts.append(qi)
+    q = np.concatenate(parts)
+    q = q[np.argsort(synth.uniform(72, 0, len(q)))]  # interleave the materials
+    q["level"][3] = np.nan
+    q["material"][40] = 7  # no such material
+    q["t1"][41] = np.inf
+    q["s0"][999] = -np.inf
+    g_up = (synth.uniform(73, 1, len(q)) - 0.5).astype(np.float32)
+    mats, grads = [], []
+    for f in fs:
+        fd = {k: dev(v) for k, v in f.items()}
+        mat = g.QueryMaterial.from_factors(fd)
+        g.build_query_tables(mat)
+        mats.append(mat)
+        grads.append({k: torch.zeros_like(fd[a if a != "flw" else "fl"]) for k, a in NAMES})
+    st = g.new_status()
+    g.range_query_backward(mats, g.queries_to_device(q), dev(g_up), grads, status=st)
+    torch.cuda.synchronize()
+    assert g.status_bits(st) & 0x2
+    # the oracle takes the material list and skips the malformed queries itself
+    oms = [oracle_material(f) for f in fs]
+    g64 = g_up.astype(np.float64)
+    ref = oq.cp_range_query_adjoint(oms, q, g64)
+    scale = oq.cp_range_query_adjoint([{k: np.abs(v) for k, v in om.items()} for om in oms], q, np.abs(g64))
+    for i in range(len(fs)):
+        for k, a in NAMES:
+            got = grads[i][k].double().cpu().numpy()
+            err = np.max(np.abs(got - ref[i][a]) / np.maximum(scale[i][a], 1e-30))
+            assert err <= 1e-4, (i, k, err)
+
+
 def test_adjoint_vs_fp32_central_differences():
     import paper_2109_14807_gb300 as g
     N, L, B, R = 16, 5, 8, 8
