@@ -9,8 +9,10 @@
 // plane.  The rank sum is a butterfly over the group (results do not depend
 // on LANES or V).  Every table row a query touches is read by the group as one
 // contiguous run (coalesced), and the small per-material tables stay resident
-// in L1/L2.  Warps claim `chunk` groups of queries at a time from a global
-// counter (persistent CTAs, dynamic balance over uneven materials).
+// in L1/L2.  Warps claim `chunk` batches of 32 queries at a time from a global
+// counter (persistent CTAs, dynamic balance over uneven materials); the
+// per-query terms of a batch are formed once, one query per lane, and shared
+// with the lane groups through shared memory.
 #include <math.h>
 
 #include <mutex>
