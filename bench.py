@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -158,12 +159,22 @@ def load_peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
+def _code_only(text):
+    """C++ source without its comments and blank space, so that an edit of a
+    comment does not void a measurement of unchanged code."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def _src_hash(names):
-    """sha256 prefix of the concatenated sources `names` (csrc file names)."""
+    """sha256 prefix of the code (comments stripped) of the sources `names`
+    (csrc file names)."""
     h = hashlib.sha256()
     try:
         for name in names:
-            h.update(open(os.path.join(ROOT, "paper_2109_14807_gb300", "csrc", name), "rb").read())
+            with open(os.path.join(ROOT, "paper_2109_14807_gb300", "csrc", name)) as fh:
+                h.update(_code_only(fh.read()).encode())
     except OSError:
         return None
     return h.hexdigest()[:12]
