@@ -291,102 +291,102 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
         __syncwarp();
       }
       for (int it = 0; it < LANES; ++it) {
-      const int slot = it * QPW + sub;
-      const long long qi = bbase + slot;
-      const float4 s4 = slots[slot][4];
-      const int flags = __float_as_int(s4.z);
-      float acc[NC];
+        const int slot = it * QPW + sub;
+        const long long qi = bbase + slot;
+        const float4 s4 = slots[slot][4];
+        const int flags = __float_as_int(s4.z);
+        float acc[NC];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) acc[k] = 0.0f;
-      {
-        if (flags == 1) {  // in range and well formed
-          const float4 s0 = slots[slot][0], s1 = slots[slot][1], s2 = slots[slot][2], s3 = slots[slot][3];
-          QTerms t;
-          t.x = __float_as_int(s0.x); t.y = __float_as_int(s0.y);
-          t.l0 = __float_as_int(s0.z); t.l1 = __float_as_int(s0.w);
-          t.f = s1.x; t.is0 = __float_as_int(s1.y); t.is1 = __float_as_int(s1.z); t.it0 = __float_as_int(s1.w);
-          t.it1 = __float_as_int(s2.x); t.fs0 = s2.y; t.fs1 = s2.z; t.ft0 = s2.w;
-          t.ft1 = s3.x; t.inv_ws = s3.y; t.inv_wt = s3.z; t.isz = __float_as_int(s3.w);
-          t.itz = __float_as_int(s4.x);
-          t.ok = true;
-          const gsp_material& M = mp.m[__float_as_int(s4.y)];
-          const int R = M.rank;
-          const float* __restrict__ flw = M.tables;
-          const float* sats = M.tables + flw_floats(M.levels, R);
-          const float* satt = sats + static_cast<size_t>(M.bins + 1) * kSatPlanes * R;
-          const float* __restrict__ fxr = M.fx + static_cast<size_t>(t.x) * R;
-          const float* __restrict__ fyr = M.fy + static_cast<size_t>(t.y) * R;
-          const float* __restrict__ fxr1 = fxr;
-          const float* __restrict__ fyr1 = fyr;
-          float wx = 0.f, wy = 0.f;
-          if constexpr (FXY) {  // x, y hold floor of the float position; wx, wy the blend
-            wx = s4.w;
-            wy = slots[slot][5].x;
-            const int N = M.N, ix = t.x, iy = t.y;
-            fxr = M.fx + static_cast<size_t>(ix & (N - 1)) * R;
-            fxr1 = M.fx + static_cast<size_t>((ix + 1) & (N - 1)) * R;
-            fyr = M.fy + static_cast<size_t>(iy & (N - 1)) * R;
-            fyr1 = M.fy + static_cast<size_t>((iy + 1) & (N - 1)) * R;
-          }
-          const float* __restrict__ fl0 = flw + static_cast<size_t>(t.l0) * R;
-          const float* __restrict__ fl1 = flw + static_cast<size_t>(t.l1) * R;
-          const float g0 = 1.0f - t.f;
-          for (int r0 = 0; r0 < R; r0 += 32) {
+        for (int k = 0; k < NC; ++k) acc[k] = 0.0f;
+        {
+          if (flags == 1) {  // in range and well formed
+            const float4 s0 = slots[slot][0], s1 = slots[slot][1], s2 = slots[slot][2], s3 = slots[slot][3];
+            QTerms t;
+            t.x = __float_as_int(s0.x); t.y = __float_as_int(s0.y);
+            t.l0 = __float_as_int(s0.z); t.l1 = __float_as_int(s0.w);
+            t.f = s1.x; t.is0 = __float_as_int(s1.y); t.is1 = __float_as_int(s1.z); t.it0 = __float_as_int(s1.w);
+            t.it1 = __float_as_int(s2.x); t.fs0 = s2.y; t.fs1 = s2.z; t.ft0 = s2.w;
+            t.ft1 = s3.x; t.inv_ws = s3.y; t.inv_wt = s3.z; t.isz = __float_as_int(s3.w);
+            t.itz = __float_as_int(s4.x);
+            t.ok = true;
+            const gsp_material& M = mp.m[__float_as_int(s4.y)];
+            const int R = M.rank;
+            const float* __restrict__ flw = M.tables;
+            const float* sats = M.tables + flw_floats(M.levels, R);
+            const float* satt = sats + static_cast<size_t>(M.bins + 1) * kSatPlanes * R;
+            const float* __restrict__ fxr = M.fx + static_cast<size_t>(t.x) * R;
+            const float* __restrict__ fyr = M.fy + static_cast<size_t>(t.y) * R;
+            const float* __restrict__ fxr1 = fxr;
+            const float* __restrict__ fyr1 = fyr;
+            float wx = 0.f, wy = 0.f;
+            if constexpr (FXY) {  // x, y hold floor of the float position; wx, wy the blend
+              wx = s4.w;
+              wy = slots[slot][5].x;
+              const int N = M.N, ix = t.x, iy = t.y;
+              fxr = M.fx + static_cast<size_t>(ix & (N - 1)) * R;
+              fxr1 = M.fx + static_cast<size_t>((ix + 1) & (N - 1)) * R;
+              fyr = M.fy + static_cast<size_t>(iy & (N - 1)) * R;
+              fyr1 = M.fy + static_cast<size_t>((iy + 1) & (N - 1)) * R;
+            }
+            const float* __restrict__ fl0 = flw + static_cast<size_t>(t.l0) * R;
+            const float* __restrict__ fl1 = flw + static_cast<size_t>(t.l1) * R;
+            const float g0 = 1.0f - t.f;
+            for (int r0 = 0; r0 < R; r0 += 32) {
 #pragma unroll
-            for (int k = 0; k < NC / V; ++k) {
-              const int rb = r0 + k * V * LANES + V * j;  // R % V == 0: the run is whole
-              if (rb < R) {
-                float a0[V], a1[V], xv[V], yv[V], S[V], T[V];
-                ldg_n<V>(fl0 + rb, a0);
-                ldg_n<V>(fl1 + rb, a1);
-                ldg_n<V>(fxr + rb, xv);
-                ldg_n<V>(fyr + rb, yv);
-                sat_mean<V>(sats, R, rb, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
-                sat_mean<V>(satt, R, rb, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, T);
-                if constexpr (FXY) {
-                  float x1[V], y1[V];
-                  ldg_n<V>(fxr1 + rb, x1);
-                  ldg_n<V>(fyr1 + rb, y1);
+              for (int k = 0; k < NC / V; ++k) {
+                const int rb = r0 + k * V * LANES + V * j;  // R % V == 0: the run is whole
+                if (rb < R) {
+                  float a0[V], a1[V], xv[V], yv[V], S[V], T[V];
+                  ldg_n<V>(fl0 + rb, a0);
+                  ldg_n<V>(fl1 + rb, a1);
+                  ldg_n<V>(fxr + rb, xv);
+                  ldg_n<V>(fyr + rb, yv);
+                  sat_mean<V>(sats, R, rb, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
+                  sat_mean<V>(satt, R, rb, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, T);
+                  if constexpr (FXY) {
+                    float x1[V], y1[V];
+                    ldg_n<V>(fxr1 + rb, x1);
+                    ldg_n<V>(fyr1 + rb, y1);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                      xv[v] = fmaf(wx, x1[v] - xv[v], xv[v]);
+                      yv[v] = fmaf(wy, y1[v] - yv[v], yv[v]);
+                    }
+                  }
 #pragma unroll
                   for (int v = 0; v < V; ++v) {
-                    xv[v] = fmaf(wx, x1[v] - xv[v], xv[v]);
-                    yv[v] = fmaf(wy, y1[v] - yv[v], yv[v]);
+                    const float lv = fmaf(t.f, a1[v], g0 * a0[v]);
+                    acc[k * V + v] = fmaf(xv[v] * yv[v], lv * S[v] * T[v], acc[k * V + v]);
                   }
-                }
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                  const float lv = fmaf(t.f, a1[v], g0 * a0[v]);
-                  acc[k * V + v] = fmaf(xv[v] * yv[v], lv * S[v] * T[v], acc[k * V + v]);
                 }
               }
             }
           }
         }
-      }
-      // butterfly: bits of k (registers), of j (shuffles), of v (registers)
+        // butterfly: bits of k (registers), of j (shuffles), of v (registers)
 #pragma unroll
-      for (int o = 16; o >= V * LANES; o >>= 1) {
-        const int h = o / (V * LANES);
+        for (int o = 16; o >= V * LANES; o >>= 1) {
+          const int h = o / (V * LANES);
 #pragma unroll
-        for (int k = 0; k < NC / V; ++k)
-          if (!(k & h)) {
+          for (int k = 0; k < NC / V; ++k)
+            if (!(k & h)) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[k * V + v] = acc[k * V + v] + acc[(k | h) * V + v];
-          }
-      }
+              for (int v = 0; v < V; ++v) acc[k * V + v] = acc[k * V + v] + acc[(k | h) * V + v];
+            }
+        }
 #pragma unroll
-      for (int o = V * LANES / 2; o >= V; o >>= 1) {
+        for (int o = V * LANES / 2; o >= V; o >>= 1) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = acc[v] + __shfl_xor_sync(0xffffffffu, acc[v], o / V);
-      }
+          for (int v = 0; v < V; ++v) acc[v] = acc[v] + __shfl_xor_sync(0xffffffffu, acc[v], o / V);
+        }
 #pragma unroll
-      for (int o = V / 2; o > 0; o >>= 1) {
+        for (int o = V / 2; o > 0; o >>= 1) {
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (!(v & o)) acc[v] = acc[v] + acc[v | o];
-      }
-      const float v = acc[0];
-      if ((flags & 1) && j == 0) out[qi] = (flags & 2) ? __int_as_float(0x7fc00000) : v;
+          for (int v = 0; v < V; ++v)
+            if (!(v & o)) acc[v] = acc[v] + acc[v | o];
+        }
+        const float v = acc[0];
+        if ((flags & 1) && j == 0) out[qi] = (flags & 2) ? __int_as_float(0x7fc00000) : v;
       }
     }
     base = following;
@@ -476,85 +476,85 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_range_query_bwd(const __grid
       __syncwarp();
     }
     for (int it = 0; it < LANES; ++it) {
-    const int slot = it * QPW + sub;
-    const float4 w4 = slots[slot][4];
-    if (!__float_as_int(w4.w)) continue;  // past the end, malformed or a zero gradient
-    const float4 w0 = slots[slot][0], w1 = slots[slot][1], w2 = slots[slot][2], w3 = slots[slot][3];
-    QTerms t;
-    t.x = __float_as_int(w0.x); t.y = __float_as_int(w0.y);
-    t.l0 = __float_as_int(w0.z); t.l1 = __float_as_int(w0.w);
-    t.f = w1.x; t.is0 = __float_as_int(w1.y); t.is1 = __float_as_int(w1.z); t.it0 = __float_as_int(w1.w);
-    t.it1 = __float_as_int(w2.x); t.fs0 = w2.y; t.fs1 = w2.z; t.ft0 = w2.w;
-    t.ft1 = w3.x; t.inv_ws = w3.y; t.inv_wt = w3.z; t.isz = __float_as_int(w3.w);
-    t.itz = __float_as_int(w4.x);
-    t.ok = true;
-    const int m = __float_as_int(w4.y);
-    const float g = w4.z;
-    const gsp_material& M = mp.m[m];
-    const int R = M.rank;
-    const float* flw = M.tables;
-    const float* sats = M.tables + flw_floats(M.levels, R);
-    const float* satt = sats + static_cast<size_t>(M.bins + 1) * kSatPlanes * R;
-    const gsp_material_grad& G = gp.g[m];
-    SmallGrad sg;
-    if (gp.use_smem) {
-      sg = small_tables(sacc + gp.soff[m], M);
-    } else {
-      sg.dflw = G.dflw;
-      sg.dps = gp.dps[m];
-      sg.dpt = gp.dpt[m];
-      sg.dfs = G.dfs;
-      sg.dft = G.dft;
-    }
-    const float g0 = 1.0f - t.f;
-    for (int rv = j * VEC; rv < R; rv += LANES * VEC) {
-      float a0v[VEC], a1v[VEC], xvv[VEC], yvv[VEC], dx[VEC], dy[VEC], Sv[VEC], Tv[VEC];
-      ldg_n<VEC>(flw + t.l0 * R + rv, a0v);
-      ldg_n<VEC>(flw + t.l1 * R + rv, a1v);
-      ldg_n<VEC>(M.fx + t.x * R + rv, xvv);
-      ldg_n<VEC>(M.fy + t.y * R + rv, yvv);
-      sat_mean<VEC>(sats, R, rv, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, Sv);
-      sat_mean<VEC>(satt, R, rv, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, Tv);
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) {
-        const int r0 = rv + v;
-        // column of rank r0 in this CTA's shared-memory tables (global: r0)
-        const int r = gp.use_smem ? v * (R / VEC) + rv / VEC : r0;
-        float lv = fmaf(t.f, a1v[v], g0 * a0v[v]);
-        float S = Sv[v];
-        float T = Tv[v];
-        float xv = xvv[v], yv = yvv[v];
-        float xy = xv * yv;
-        float st = S * T;
-        dx[v] = g * yv * lv * st;
-        dy[v] = g * xv * lv * st;
-        atomicAdd(sg.dflw + t.l0 * R + r, g * g0 * xy * st);
-        if (t.f != 0.0f) atomicAdd(sg.dflw + t.l1 * R + r, g * t.f * xy * st);
-        // Sbar = (F(s1) - F(s0)) / w with F(s) = P[floor s] + frac(s) fs[floor s]
-        float cs = g * xy * lv * T;
-        if (t.inv_ws > 0.0f) {
-          float a = cs * t.inv_ws;
-          atomicAdd(sg.dps + t.is1 * R + r, a);
-          atomicAdd(sg.dps + t.is0 * R + r, -a);
-          if (t.fs1 != 0.0f) atomicAdd(sg.dfs + t.is1 * R + r, a * t.fs1);
-          if (t.fs0 != 0.0f) atomicAdd(sg.dfs + t.is0 * R + r, -a * t.fs0);
-        } else {
-          atomicAdd(sg.dfs + t.isz * R + r, cs);
-        }
-        float ct = g * xy * lv * S;
-        if (t.inv_wt > 0.0f) {
-          float a = ct * t.inv_wt;
-          atomicAdd(sg.dpt + t.it1 * R + r, a);
-          atomicAdd(sg.dpt + t.it0 * R + r, -a);
-          if (t.ft1 != 0.0f) atomicAdd(sg.dft + t.it1 * R + r, a * t.ft1);
-          if (t.ft0 != 0.0f) atomicAdd(sg.dft + t.it0 * R + r, -a * t.ft0);
-        } else {
-          atomicAdd(sg.dft + t.itz * R + r, ct);
-        }
+      const int slot = it * QPW + sub;
+      const float4 w4 = slots[slot][4];
+      if (!__float_as_int(w4.w)) continue;  // past the end, malformed or a zero gradient
+      const float4 w0 = slots[slot][0], w1 = slots[slot][1], w2 = slots[slot][2], w3 = slots[slot][3];
+      QTerms t;
+      t.x = __float_as_int(w0.x); t.y = __float_as_int(w0.y);
+      t.l0 = __float_as_int(w0.z); t.l1 = __float_as_int(w0.w);
+      t.f = w1.x; t.is0 = __float_as_int(w1.y); t.is1 = __float_as_int(w1.z); t.it0 = __float_as_int(w1.w);
+      t.it1 = __float_as_int(w2.x); t.fs0 = w2.y; t.fs1 = w2.z; t.ft0 = w2.w;
+      t.ft1 = w3.x; t.inv_ws = w3.y; t.inv_wt = w3.z; t.isz = __float_as_int(w3.w);
+      t.itz = __float_as_int(w4.x);
+      t.ok = true;
+      const int m = __float_as_int(w4.y);
+      const float g = w4.z;
+      const gsp_material& M = mp.m[m];
+      const int R = M.rank;
+      const float* flw = M.tables;
+      const float* sats = M.tables + flw_floats(M.levels, R);
+      const float* satt = sats + static_cast<size_t>(M.bins + 1) * kSatPlanes * R;
+      const gsp_material_grad& G = gp.g[m];
+      SmallGrad sg;
+      if (gp.use_smem) {
+        sg = small_tables(sacc + gp.soff[m], M);
+      } else {
+        sg.dflw = G.dflw;
+        sg.dps = gp.dps[m];
+        sg.dpt = gp.dpt[m];
+        sg.dfs = G.dfs;
+        sg.dft = G.dft;
       }
-      red_add<VEC>(G.dfx + t.x * R + rv, dx);
-      red_add<VEC>(G.dfy + t.y * R + rv, dy);
-    }
+      const float g0 = 1.0f - t.f;
+      for (int rv = j * VEC; rv < R; rv += LANES * VEC) {
+        float a0v[VEC], a1v[VEC], xvv[VEC], yvv[VEC], dx[VEC], dy[VEC], Sv[VEC], Tv[VEC];
+        ldg_n<VEC>(flw + t.l0 * R + rv, a0v);
+        ldg_n<VEC>(flw + t.l1 * R + rv, a1v);
+        ldg_n<VEC>(M.fx + t.x * R + rv, xvv);
+        ldg_n<VEC>(M.fy + t.y * R + rv, yvv);
+        sat_mean<VEC>(sats, R, rv, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, Sv);
+        sat_mean<VEC>(satt, R, rv, t.it0, t.it1, t.ft0, t.ft1, t.inv_wt, t.itz, Tv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const int r0 = rv + v;
+          // column of rank r0 in this CTA's shared-memory tables (global: r0)
+          const int r = gp.use_smem ? v * (R / VEC) + rv / VEC : r0;
+          float lv = fmaf(t.f, a1v[v], g0 * a0v[v]);
+          float S = Sv[v];
+          float T = Tv[v];
+          float xv = xvv[v], yv = yvv[v];
+          float xy = xv * yv;
+          float st = S * T;
+          dx[v] = g * yv * lv * st;
+          dy[v] = g * xv * lv * st;
+          atomicAdd(sg.dflw + t.l0 * R + r, g * g0 * xy * st);
+          if (t.f != 0.0f) atomicAdd(sg.dflw + t.l1 * R + r, g * t.f * xy * st);
+          // Sbar = (F(s1) - F(s0)) / w with F(s) = P[floor s] + frac(s) fs[floor s]
+          float cs = g * xy * lv * T;
+          if (t.inv_ws > 0.0f) {
+            float a = cs * t.inv_ws;
+            atomicAdd(sg.dps + t.is1 * R + r, a);
+            atomicAdd(sg.dps + t.is0 * R + r, -a);
+            if (t.fs1 != 0.0f) atomicAdd(sg.dfs + t.is1 * R + r, a * t.fs1);
+            if (t.fs0 != 0.0f) atomicAdd(sg.dfs + t.is0 * R + r, -a * t.fs0);
+          } else {
+            atomicAdd(sg.dfs + t.isz * R + r, cs);
+          }
+          float ct = g * xy * lv * S;
+          if (t.inv_wt > 0.0f) {
+            float a = ct * t.inv_wt;
+            atomicAdd(sg.dpt + t.it1 * R + r, a);
+            atomicAdd(sg.dpt + t.it0 * R + r, -a);
+            if (t.ft1 != 0.0f) atomicAdd(sg.dft + t.it1 * R + r, a * t.ft1);
+            if (t.ft0 != 0.0f) atomicAdd(sg.dft + t.it0 * R + r, -a * t.ft0);
+          } else {
+            atomicAdd(sg.dft + t.itz * R + r, ct);
+          }
+        }
+        red_add<VEC>(G.dfx + t.x * R + rv, dx);
+        red_add<VEC>(G.dfy + t.y * R + rv, dy);
+      }
     }
   }
   if (gp.use_smem) {
