@@ -40,6 +40,7 @@ METRIC = "NDF range queries/s at 1e-5 rel err; CP-ALS sweep s; % HBM / tensor ro
 WORKLOAD = "flakes1024"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "kernel_traffic.txt")
+ONCHIP_FILE = os.path.join(ROOT, "profiles", "query_onchip_counters.txt")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -58,6 +59,13 @@ def parse_args():
                    help="lanes,blocks_per_sm,threads,chunk for the query kernel instead of the "
                         "autotuner's choice")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp32-sweep", action="store_true",
+                   help="skip timing the FP32 CUDA-core sweep after the timed region")
+    p.add_argument("--query-profile", action="store_true",
+                   help="instead of the step: the query tables, the range queries and their "
+                        "adjoint of the workload alone (rank-64 material from the seeded initial "
+                        "factors, no NDF tensor), a few hundred MB on the device: the case the "
+                        "query kernels' single-kernel ncu captures run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--report-precisions", default="fp32,tf32,bf16,bf16_1x,structured,structured_gaussian",
                    help="precisions the precision report covers (comma-separated)")
@@ -207,6 +215,30 @@ def ncu_traffic(kernel, precision):
         if len(parts) >= 5 and parts[0] == kernel and parts[1] == WORKLOAD and parts[2] == precision:
             return float(parts[3]) if parts[4] == _src_hash(src) else None
     return None
+
+
+def ncu_onchip(kernel, lanes):
+    """L1 data-pipe wavefronts per launch of a query kernel (ncu counter
+    l1tex__data_pipe_lsu_wavefronts.sum, single-kernel capture of
+    `bench.py --query-profile`) for this workload and lanes per query, or None
+    when absent or when query.cu's code changed since the capture."""
+    try:
+        lines = open(ONCHIP_FILE).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        if ln.startswith("#") or not ln.strip():
+            continue
+        parts = ln.split()
+        if (len(parts) >= 5 and parts[0] == kernel and parts[1] == WORKLOAD
+                and parts[2] == str(lanes)):
+            return float(parts[3]) if parts[4] == _src_hash(("query.cu",)) else None
+    return None
+
+
+def l1_peak_gbs(n_sm, sm_mhz):
+    """L1 data-pipe peak: one 128-byte wavefront per clock per SM."""
+    return n_sm * 128.0 * sm_mhz * 1e6 / 1e9
 
 
 # ------------------------------------------------------------ replicas --
@@ -426,7 +458,15 @@ def run_gsp(args, rank, world):
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
     n_occ, cols = ws.operand_cols()
-    roof = roofline(prof, w, prec, peaks, peak_src, n_occ, cols)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = roofline(prof, w, prec, peaks, peak_src, n_occ, cols, n_sm=n_sm, sm_mhz=clk.get("sm_mhz"),
+                    lanes={"range_query": q_tuning[0], "range_query_backward": "auto"})
+
+    # the plain FP32 CUDA-core path's sweep on the same operand shape, for the
+    # BF16-vs-FP32 comparison (after the timed region)
+    fp32_sweep = None
+    if rank == 0 and world == 1 and prec != "fp32" and not args.no_fp32_sweep:
+        fp32_sweep = time_sweep(g, w, normals, f_init, "fp32", dev)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -444,27 +484,49 @@ def run_gsp(args, rank, world):
                "sample": desc}
 
     if rank == 0:
+        qps = lambda k: (nq / (prof[k][1] / prof[k][0] / 1e3) if k in prof else None)  # noqa: E731
         line = {
             "metric": METRIC, "value": whole_job_rate(nq, world, ms_step), "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": config_block(w, prec),
-            "stages_ms": stages,
-            "als_sweep_s": stages["als_sweep_ms"] / 1e3,
-            "range_query_kernel_qps": nq / (prof["range_query"][1] / prof["range_query"][0] / 1e3)
-            if "range_query" in prof else None,
-            "query_parity": parity,
-            "query_tuning": list(q_tuning),
-            "device_status": st_bits,
-            "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in prof.items()},
-            "roofline": roof,
-            "clocks": clk,
             "gpu_launches": int(launches),
+            "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items()},
+            "query_tuning": list(q_tuning),
+            "device_status": st_bits,
+            "roofline": roof,
+            # kept last, so that they are inside the tail of the line a log keeps
+            "query_parity": parity,
+            "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+            "range_query_kernel_qps": qps("range_query"),
+            "adjoint_kernel_qps": qps("range_query_backward"),
+            "als_sweep_s": stages["als_sweep_ms"] / 1e3,
+            "als_sweep_s_fp32": fp32_sweep,
         }
         print(json.dumps(line), flush=True)
+
+
+def time_sweep(g, w, normals, f_init, prec, dev, sweeps=3):
+    """Seconds per CP-ALS sweep of `prec` on the step's map (operand prepared
+    once, one untimed sweep, then `sweeps` sweeps in one call, CUDA events)."""
+    import torch
+    N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
+    ws = g.CPWorkspace(N, L, B, R, prec, device=dev)
+    ws.prepare(normal_xy=normals)
+    f = g.init_factors_to_device(f_init, dev)
+    ws.sweeps(f, 1, report=False)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ws.sweeps(f, sweeps, report=False)
+    b.record()
+    torch.cuda.synchronize(dev)
+    del ws
+    torch.cuda.empty_cache()
+    return a.elapsed_time(b) / sweeps / 1e3
 
 
 # Per-query gather and update rows of the query kernels (fractional rectangle,
@@ -485,10 +547,21 @@ ALG_BYTES_DESC = {
 }
 
 
-def roofline(prof, w, prec, peaks, peak_src, n_occ, cols):
-    """Roofline of the dominant kernel.  The operand holds `cols` columns per
+QUERY_KERNELS = ("range_query", "range_query_backward")
+
+
+def roofline(prof, w, prec, peaks, peak_src, n_occ, cols, n_sm=152, sm_mhz=None, lanes=None):
+    """Roofline of the dominant kernel (largest share of the timed step) and
+    the other modelled kernels.  The operand holds `cols` columns per
     footprint (the n_occ bins occurring in the map, zero-padded), so
-    |X| = N^2 * L * cols."""
+    |X| = N^2 * L * cols.  Operand kernels are bound by HBM: algorithmic bytes
+    per launch / average launch time against the measured copy peak.  The
+    query kernels read table rows that stay in L1/L2 (DRAM sees the 36-byte
+    descriptor and result): their binding unit is the L1 data pipe, so they
+    report L1 wavefronts (counted by ncu for the same code and launch shape)
+    x 128 B / live launch time against one wavefront per clock per SM at the
+    median SM clock of the timed region; the gather bytes of the query
+    definition are kept beside it as a ratio to the HBM peak."""
     N, L, B, R, nq = w["N"], w["levels"], w["bins"], w["rank"], w["queries"]
     esize = 2 if prec == "bf16" else 4
     X = N * N * L * cols
@@ -498,31 +571,39 @@ def roofline(prof, w, prec, peaks, peak_src, n_occ, cols):
         "range_query": nq * (QUERY_ROWS * R * 4 + 36),
         "range_query_backward": nq * (2 * QUERY_ROWS * R * 4 + 36),
     }
-    peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
-    src = f"{peak_src} (MEASURED_PEAKS hbm_gbs)" if peak_src == "measured" else "fallback"
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    hbm_src = f"{peak_src} (MEASURED_PEAKS hbm_gbs)" if peak_src == "measured" else "fallback"
+    clk = float(sm_mhz or peaks.get("sm_max_mhz", 2070.0))
+    l1 = l1_peak_gbs(n_sm, clk)
+    lanes = lanes or {}
 
     def entry(k):
         n_l, ms = prof[k]
         avg_s = ms / n_l / 1e3
         achieved = per_launch[k] / avg_s / 1e9
-        return {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(k, prec),
-                "algorithmic_bytes_per_launch": per_launch[k], "avg_launch_ms": avg_s * 1e3,
-                "bytes_definition": ALG_BYTES_DESC[k], "peak_source": src}
+        if k not in QUERY_KERNELS:
+            return {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": ncu_traffic(k, prec),
+                    "algorithmic_bytes_per_launch": per_launch[k], "avg_launch_ms": avg_s * 1e3,
+                    "peak_source": hbm_src, "bytes_definition": ALG_BYTES_DESC[k]}
+        wf = ncu_onchip(k, lanes.get(k))
+        l1_gbs = wf * 128.0 / avg_s / 1e9 if wf is not None else None
+        return {"kernel": k, "bound": "l1", "achieved": l1_gbs, "peak": l1, "unit": "GB/s",
+                "frac": l1_gbs / l1 if l1_gbs is not None else None,
+                "traffic": ncu_traffic(k, prec), "l1_wavefronts_per_launch": wf,
+                "avg_launch_ms": avg_s * 1e3,
+                "peak_source": f"derived: {n_sm} SMs x 128 B/clk x {clk:.0f} MHz",
+                "gather_bytes_per_launch": per_launch[k], "gather_gbs": achieved,
+                "gather_vs_hbm_peak": achieved / hbm}
 
-    # the kernel with the largest share of the step, over every profiled kernel
     top = max(prof, key=lambda k: prof[k][1]) if prof else None
     if top not in per_launch:
         return None
     out = entry(top)
-    if top.startswith("range_query"):
-        out["note"] = ("gather bytes as the query roofline defines them; the table rows are served from "
-                       "L1/L2 and DRAM sees the 32-byte descriptor and 4-byte result per query (traffic), "
-                       "so the fraction exceeds 1; the binding units are on chip: L1 wavefronts and issue "
-                       "(forward), shared-memory float atomics (adjoint)")
     out["occupied_bins"], out["operand_columns"] = n_occ, cols
-    out["others"] = [{k2: v for k2, v in entry(k).items() if k2 in ("kernel", "achieved", "frac", "traffic",
-                                                                    "avg_launch_ms")}
+    out["others"] = [{k2: (round(v, 4) if isinstance(v, float) else v) for k2, v in entry(k).items()
+                      if k2 in ("kernel", "bound", "achieved", "frac", "traffic", "avg_launch_ms",
+                                "gather_vs_hbm_peak")}
                      for k in sorted(per_launch, key=lambda k: -prof.get(k, (1, 0.0))[1])
                      if k in prof and k != top]
     return out
@@ -602,6 +683,65 @@ def run_e2e(args, g, dev, m_np, q_np, normals, qd, out, step, barrier, world):
             "h2d_bytes_per_step": int(h_norm.numel() * 4 + h_q.numel() * 4),
             "d2h_bytes_per_step": int(h_out[0].numel() * 4),
             "overlap": "two buffer sets; copies on their own streams overlap the previous / next step"}
+
+
+# --------------------------------------------------------- query profile --
+def query_profile(args):
+    """The step's query kernels alone (rows a5-a7 without the NDF tensor):
+    the workload's material shape with the seeded initial factors (the kernels'
+    work does not depend on the values), its query tables, the step's 10^7
+    fractional range queries and their adjoint with the results as upstream
+    gradients.  A few hundred MB on the device, so that single-kernel ncu
+    captures of the query kernels run at the bench's rank and query count."""
+    import torch
+    import paper_2109_14807_gb300 as g
+    from paper_2109_14807_gb300 import _lib, build
+    build.build()
+    lib = _lib.load()
+    torch.cuda.set_device(0)
+    w = workload(args.workload)
+    N, L, B, R, nq = w["N"], w["levels"], w["bins"], w["rank"], w["queries"]
+    fac = g.init_factors_to_device(synth.init_factors(N, L, B, R, 2000 + w["seed"]))
+    mat = g.QueryMaterial.from_factors(fac)
+    g.build_query_tables(mat)
+    qd = g.queries_to_device(synth.queries_fractional(N, L, B, nq, 1000 + w["seed"]))
+    out = torch.empty(nq, dtype=torch.float32, device="cuda")
+    status = g.new_status()
+    qws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    grads = {k: torch.zeros_like(fac[a]) for k, a in
+             (("dfx", "fx"), ("dfy", "fy"), ("dflw", "fl"), ("dfs", "fs"), ("dft", "ft"))}
+    bws = torch.empty(g.backward_workspace_bytes(mat), dtype=torch.uint8, device="cuda")
+    if args.query_tuning:
+        tuning = tuple(int(v) for v in args.query_tuning.split(","))
+    else:
+        from paper_2109_14807_gb300 import tune
+        tuning = tune.autotune_query(mat, qd, sample=2_000_000, repeats=2)
+
+    def run():
+        g.range_query(mat, qd, out=out, status=status, workspace=qws, tuning=tuning)
+        g.range_query_backward(mat, qd, out, [grads], status=status, workspace=bws)
+
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    lib.gsp_profile_reset()
+    lib.gsp_profile_enable(1)
+    for _ in range(args.steps):
+        run()
+    lib.gsp_profile_enable(0)
+    rec = {}
+    for pid in range(15):
+        n_l, ms = _lib.c_int64(), _lib.c_double()
+        _lib.check("gsp_profile_read", lib.gsp_profile_read(pid, n_l, ms))
+        name = lib.gsp_profile_name(pid).decode()
+        if n_l.value and name in QUERY_KERNELS:
+            rec[name] = {"launches": n_l.value, "avg_launch_ms": ms.value / n_l.value,
+                         "queries_per_s": nq / (ms.value / n_l.value / 1e3)}
+    print(json.dumps({"metric": "query kernels alone (tables, range queries, adjoint)",
+                      "workload": WORKLOAD, "N": N, "levels": L, "bins": B, "rank": R,
+                      "queries": nq, "query_tuning": list(tuning), "kernels": rec,
+                      "device_status": g.status_bits(status),
+                      "device_gb": torch.cuda.max_memory_allocated() / 1e9}), flush=True)
 
 
 # ------------------------------------------------------ precision report --
@@ -937,6 +1077,9 @@ def env_report(args):
 
 def main():
     args = parse_args()
+    if args.query_profile:
+        query_profile(args)
+        return
     if args.env_report:
         env_report(args)
         return

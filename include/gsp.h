@@ -508,10 +508,18 @@ int gsp_range_query_backward(const gsp_material* h_mats, int n_mats, const gsp_q
  *  GSP_BACKWARD_NOALLOC_MAX_BYTES in device memory that the library defines;
  *  every GPU that loads the library holds it until the process exits.  Larger
  *  material sets are rejected with GSP_ERR_WORKSPACE before anything is
- *  enqueued.  The call allocates nothing and calls no allocating routine.
+ *  enqueued, and malformed materials with GSP_ERR_INVALID_ARG.  The call
+ *  allocates nothing and calls no allocating routine.
  *  The first call on a device looks up the array's device address with that
- *  device current (no work is enqueued by that step); make that first call
- *  before any stream capture.  All calls share the one array and it keeps the
+ *  device current (no work is enqueued by that step).  If no kernel of the
+ *  library has run on that device yet, that lookup is what loads the
+ *  library's device code there (CUDA loads modules lazily): the loader then
+ *  places the module's own globals, this array among them, in device memory
+ *  and may synchronise the device.  So make the first call at initialisation,
+ *  before any stream capture and before the frame loop that must not stall.
+ *  The address is kept per device for the life of the process: after a
+ *  cudaDeviceReset() in the calling process it is stale, and this call must
+ *  not be used on that device again.  All calls share the one array and it keeps the
  *  last call's contents: each call clears the part it uses on `stream` before
  *  its kernels run, so calls must not overlap on the GPU (two streams running
  *  this call at the same time race on the array).  Arguments and results are

@@ -1209,6 +1209,12 @@ extern "C" int gsp_range_query_backward_noalloc(const gsp_material* h_mats, int 
                                                 uint32_t* d_status, gsp_stream stream) {
   if (!h_mats || !h_grads || n_mats < 1 || n_mats > GSP_MAX_MATERIALS || n < 0)
     return GSP_ERR_INVALID_ARG;
+  // malformed materials are argument errors, whatever scratch they would need
+  for (int i = 0; i < n_mats; ++i) {
+    const gsp_material_grad& g = h_grads[i];
+    if (!valid_material(h_mats[i]) || !g.dfx || !g.dfy || !g.dflw || !g.dfs || !g.dft)
+      return GSP_ERR_INVALID_ARG;
+  }
   const size_t need = gsp_backward_workspace_bytes(h_mats, n_mats);
   if (need == 0) return GSP_ERR_INVALID_ARG;
   if (need > GSP_BACKWARD_NOALLOC_MAX_BYTES) return GSP_ERR_WORKSPACE;

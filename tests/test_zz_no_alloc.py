@@ -61,10 +61,17 @@ def test_backward_noalloc_matches_workspace_version():
         got = [_zero_grads(f) for f in fs]
         garr = (_lib.MaterialGrad * len(mats))(*[
             _lib.MaterialGrad(*(gr[k].data_ptr() for k, _ in NAMES)) for gr in got])
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         rc = L_.gsp_range_query_backward_noalloc(arr, len(mats), qd.data_ptr(), qd.shape[0],
                                                  gd.data_ptr(), garr, status.data_ptr(), stream)
         assert rc == 0, rc
         torch.cuda.synchronize()
+        if call == 1:
+            # the device's free memory is the same after the call: the library
+            # took no device memory of its own (the first call may have loaded
+            # the module, whose globals hold the scratch array)
+            assert torch.cuda.mem_get_info()[0] == free0
         assert g.status_bits(status) == 0
         for mi in range(len(mats)):
             for k, a in NAMES:
@@ -84,3 +91,8 @@ def test_backward_noalloc_rejects_oversized_scratch():
     assert L_.gsp_backward_workspace_bytes(arr, 16) > (4 << 20)
     rc = L_.gsp_range_query_backward_noalloc(arr, 16, None, 0, None, garr, None, None)
     assert rc == -3  # GSP_ERR_WORKSPACE, nothing enqueued
+    # a malformed material (map side not a power of two) is an argument error,
+    # even where the scratch it asks for is also too large
+    bad = _lib.Material(1000, 11, 128, 256, 1, 1, 1, 1, 1, 1, 256)
+    arr_bad = (_lib.Material * 16)(*([bad] * 16))
+    assert L_.gsp_range_query_backward_noalloc(arr_bad, 16, None, 0, None, garr, None, None) == -1
