@@ -368,7 +368,7 @@ def run_gsp(args, rank, world):
     qd = g.queries_to_device(q_np, dev)
     out = torch.empty(nq, dtype=torch.float32, device=dev)
     status = g.new_status(dev)
-    ws = g.CPWorkspace(N, L, B, R, prec, device=dev)
+    ws = g.CPWorkspace.for_map(L, B, R, prec, normal_xy=normals)  # sized for the occurring bins
     fac = g.init_factors_to_device(f_init, dev)
     mat = g.QueryMaterial.from_factors(fac)
     mat.struct()
@@ -515,7 +515,7 @@ def time_sweep(g, w, normals, f_init, prec, dev, sweeps=3):
     once, one untimed sweep, then `sweeps` sweeps in one call, CUDA events)."""
     import torch
     N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
-    ws = g.CPWorkspace(N, L, B, R, prec, device=dev)
+    ws = g.CPWorkspace.for_map(L, B, R, prec, normal_xy=normals)
     ws.prepare(normal_xy=normals)
     f = g.init_factors_to_device(f_init, dev)
     ws.sweeps(f, 1, report=False)
@@ -688,11 +688,11 @@ def run_e2e(args, g, dev, m_np, q_np, normals, qd, out, step, barrier, world):
 # --------------------------------------------------------- query profile --
 def query_profile(args):
     """The step's query kernels alone (rows a5-a7 without the NDF tensor):
-    the workload's material shape with the seeded initial factors (the kernels'
-    work does not depend on the values), its query tables, the step's 10^7
-    fractional range queries and their adjoint with the results as upstream
-    gradients.  A few hundred MB on the device, so that single-kernel ncu
-    captures of the query kernels run at the bench's rank and query count."""
+    the workload's material after one structured ALS sweep from the seeded
+    init, its query tables, the step's 10^7 fractional range queries and their
+    adjoint with the results as upstream gradients.  A few hundred MB on the
+    device, so that single-kernel ncu captures of the query kernels run at the
+    bench's rank, query count and live-query mix."""
     import torch
     import paper_2109_14807_gb300 as g
     from paper_2109_14807_gb300 import _lib, build
@@ -701,7 +701,17 @@ def query_profile(args):
     torch.cuda.set_device(0)
     w = workload(args.workload)
     N, L, B, R, nq = w["N"], w["levels"], w["bins"], w["rank"], w["queries"]
+    # factors after one ALS sweep from the seeded init, as in the step: the
+    # factor rows of angular bins that no texel falls in are then exactly zero,
+    # so are the range queries over them and (with the results as upstream
+    # gradients) the adjoint skips them as the step's does.  The structured
+    # sweep needs no tensor (tens of MB).
+    normals = torch.from_numpy(synth.make_map(w)).cuda()
     fac = g.init_factors_to_device(synth.init_factors(N, L, B, R, 2000 + w["seed"]))
+    sws = g.CPWorkspace(N, L, B, R, "structured")
+    sws.prepare(normal_xy=normals)
+    sws.sweeps(fac, 1, report=False)
+    del sws
     mat = g.QueryMaterial.from_factors(fac)
     g.build_query_tables(mat)
     qd = g.queries_to_device(synth.queries_fractional(N, L, B, nq, 1000 + w["seed"]))
@@ -766,7 +776,7 @@ def precision_report(args):
         m = torch.from_numpy(synth.make_map(w)).cuda()
         init = synth.init_factors(N, L, B, R, 2000 + w["seed"])
         for prec in args.report_precisions.split(","):
-            ws = g.CPWorkspace(N, L, B, R, prec)
+            ws = g.CPWorkspace.for_map(L, B, R, prec, normal_xy=m)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             ws.prepare(normal_xy=m)

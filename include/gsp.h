@@ -167,14 +167,43 @@ typedef struct gsp_als_report {
   double fit[GSP_MAX_SWEEPS];
 } gsp_als_report;
 
-/* Workspace bytes for gsp_cp_prepare / gsp_cp_sweeps / gsp_cp_mttkrp (for
+/* Workspace bytes for gsp_cp_prepare / gsp_cp_sweeps / gsp_cp_mttkrp for any
+ * map of this shape: the operand sized for all B*B bins (for
  * GSP_PREC_STRUCTURED tens of MB instead of the tensor). */
 size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, int precision);
 
+/* The same for a map in which `occupied_bins` of the B*B bins occur (as
+ * counted by gsp_cp_count_bins): the operand and every array sized by its
+ * columns hold only the columns gsp_cp_prepare keeps (see there), e.g. 2.5 GB
+ * instead of 23 GB for the BF16 operand of a 1024^2 map with 11 levels, 32x32
+ * bins of which 67 occur, rank 64.  0 for invalid arguments
+ * (occupied_bins outside 1 .. B*B).  gsp_cp_prepare returns
+ * GSP_ERR_WORKSPACE, having enqueued only the bin count, when the map it is
+ * given needs more. */
+size_t gsp_cp_workspace_bytes_for_bins(int N, int levels, int bins, int rank, int precision,
+                                       int occupied_bins);
+
+/* Count the bins that occur in the normal map (d_normal_xy, binned as in
+ * gsp_bin_normals) or in the level-0 slice of d_hist, the count that sizes a
+ * workspace by gsp_cp_workspace_bytes_for_bins.  B*B when B*B < 256 (the
+ * operand then keeps every bin).  d_ws: gsp_cp_count_bins_workspace_bytes()
+ * bytes of scratch (the first bytes of any CP workspace of this N and B
+ * will do).  Synchronises `stream` to write *h_occupied (host). */
+size_t gsp_cp_count_bins_workspace_bytes(int N, int bins);
+int gsp_cp_count_bins(const int32_t* d_hist, const float* d_normal_xy, int N, int levels,
+                      int bins, void* d_ws, size_t ws_bytes, int32_t* h_occupied,
+                      uint32_t* d_status, gsp_stream stream);
+
+/* Byte offset in a CP workspace of the operand gsp_cp_prepare builds
+ * (dense-path precisions; 0 for GSP_PREC_STRUCTURED, which builds none).
+ * The workspace starts with a head of fixed size (bin map, column tables,
+ * the FP64 ALS arrays), then the operand. */
+size_t gsp_cp_operand_offset(int N, int levels, int bins, int rank, int precision);
+
 /* Build the MTTKRP operand (the NDF tensor in the precision's input type,
  * [l][y][x][c]: BF16 for GSP_PREC_BF16 / _BF16_1X, else FP32, on the TF32
- * grid for GSP_PREC_TF32; it occupies the first levels*N*N*C elements of
- * d_ws) and ||T||^2 inside the workspace.  The operand keeps only the bins
+ * grid for GSP_PREC_TF32; it occupies levels*N*N*C elements from byte
+ * gsp_cp_operand_offset() of d_ws) and ||T||^2 inside the workspace.  The operand keeps only the bins
  * that occur somewhere in the map (all other bins are zero in every
  * footprint): column c < n holds the c-th occurring bin (s*B + t, in
  * increasing order), columns n .. C-1 are zero, C = n rounded up to a multiple

@@ -66,6 +66,11 @@ _SIGS = {
     "gsp_build_footprint_ndfs": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
                                          c_size_t, c_void_p, c_void_p]),
     "gsp_cp_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
+    "gsp_cp_workspace_bytes_for_bins": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
+    "gsp_cp_count_bins_workspace_bytes": (c_size_t, [c_int, c_int]),
+    "gsp_cp_count_bins": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_size_t,
+                                  POINTER(c_int32), c_void_p, c_void_p]),
+    "gsp_cp_operand_offset": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
     "gsp_cp_prepare": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, POINTER(AlsOpts),
                                c_void_p, c_size_t, c_void_p, c_void_p]),
     "gsp_cp_sweeps": (c_int, [c_int, c_int, c_int, c_int, POINTER(AlsOpts), POINTER(CpFactors),

@@ -88,17 +88,53 @@ def _factors_struct(f: dict) -> CpFactors:
                      _ptr(f["lambda"], torch.float32, "lambda"))
 
 
-class CPWorkspace:
-    """Device workspace of one CP decomposition (operand tensor + scratch)."""
+def count_bins(levels, bins, hist=None, normal_xy=None, status=None) -> int:
+    """Bins that occur in the normal map (or the level-0 slice of `hist`): the
+    count gsp_cp_workspace_bytes_for_bins sizes a workspace by."""
+    lib = load()
+    src = hist if hist is not None else normal_xy
+    N = hist.shape[1] if hist is not None else normal_xy.shape[0]
+    ws = torch.empty(max(lib.gsp_cp_count_bins_workspace_bytes(N, bins), 1), dtype=torch.uint8,
+                     device=src.device)
+    h = ctypes.c_int32()
+    check("gsp_cp_count_bins", lib.gsp_cp_count_bins(
+        _ptr(hist, torch.int32, "hist"), _ptr(normal_xy, torch.float32, "normal_xy"), N, levels,
+        bins, _ptr(ws), ws.numel(), ctypes.byref(h), _ptr(status), _stream()))
+    return int(h.value)
 
-    def __init__(self, N, levels, bins, rank, precision="fp32", device="cuda"):
+
+class CPWorkspace:
+    """Device workspace of one CP decomposition (operand tensor + scratch).
+    With `occupied_bins` (from count_bins) it is sized for maps in which that
+    many bins occur, else for all B * B bins."""
+
+    def __init__(self, N, levels, bins, rank, precision="fp32", device="cuda", occupied_bins=None):
         lib = load()
         self.N, self.levels, self.bins, self.rank = N, levels, bins, rank
         self.precision = _lib.PREC[precision] if isinstance(precision, str) else int(precision)
-        nbytes = lib.gsp_cp_workspace_bytes(N, levels, bins, rank, self.precision)
+        if occupied_bins is None:
+            nbytes = lib.gsp_cp_workspace_bytes(N, levels, bins, rank, self.precision)
+        else:
+            nbytes = lib.gsp_cp_workspace_bytes_for_bins(N, levels, bins, rank, self.precision,
+                                                         int(occupied_bins))
         if nbytes == 0:
             raise ValueError("unsupported CP shape")
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    @classmethod
+    def for_map(cls, levels, bins, rank, precision="fp32", hist=None, normal_xy=None,
+                status=None):
+        """A workspace sized for the bins that occur in this map."""
+        src = hist if hist is not None else normal_xy
+        N = hist.shape[1] if hist is not None else normal_xy.shape[0]
+        n = count_bins(levels, bins, hist=hist, normal_xy=normal_xy, status=status)
+        return cls(N, levels, bins, rank, precision, device=src.device, occupied_bins=n)
+
+    def operand_view(self, nbytes):
+        """The first `nbytes` bytes of the prepared operand (uint8 view)."""
+        off = load().gsp_cp_operand_offset(self.N, self.levels, self.bins, self.rank,
+                                           self.precision)
+        return self.buf[off: off + nbytes]
 
     def _opts(self, sweeps=1, tol=0.0, raw_counts=False):
         return AlsOpts(int(sweeps), self.precision, float(tol), int(bool(raw_counts)), 0)
@@ -167,7 +203,8 @@ def cp_decompose(rank, init: dict, hist=None, normal_xy=None, levels=None, bins=
         levels, N, _, bins, _ = hist.shape
     else:
         N = normal_xy.shape[0]
-    ws = CPWorkspace(N, levels, bins, rank, precision, device=src.device)
+    ws = CPWorkspace.for_map(levels, bins, rank, precision, hist=hist, normal_xy=normal_xy,
+                             status=status)
     ws.prepare(hist=hist, normal_xy=normal_xy, raw_counts=raw_counts, status=status)
     f = init_factors_to_device(init, src.device) if not isinstance(init["fx"], torch.Tensor) else init
     fits, fallbacks = ws.sweeps(f, sweeps, tol)

@@ -16,6 +16,7 @@
 // FP64; the two passes over T are the MTTKRP kernels (FP32 FFMA or tcgen05).
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -30,8 +31,13 @@ constexpr int kMaxCpRank = 64;
 constexpr int kJacobiMaxRank = 64;
 constexpr int kGramRows = 64;  // rows of a factor per partial Gram matrix
 
+// Workspace layout.  The head (bin map, column tables, the small FP64 ALS
+// arrays and flags) depends only on the shape and precision and comes first,
+// so that the operand's columns can be counted into it before the rest is
+// laid out; the operand and the arrays sized by its columns follow.
 struct CpLayout {
-  size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, Gpart, W, lam, fit, sumsq, norm2, flags, cols, total;
+  size_t T, bins, Yp, Zp, Zpart, KR, FX, M, G, Gpart, W, lam, fit, sumsq, norm2, flags, cols, head,
+      total;
   // GSP_PREC_STRUCTURED only (zero-sized otherwise)
   size_t binsT, AL, BE, part, pre, sig, sig64, segtot, off, stpart, lscale;
   // GSP_PREC_STRUCTURED_GAUSSIAN only
@@ -42,6 +48,53 @@ size_t esize(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1
 bool is_bf16(int prec) { return prec == GSP_PREC_BF16 || prec == GSP_PREC_BF16_1X; }
 bool is_structured(int prec) {
   return prec == GSP_PREC_STRUCTURED || prec == GSP_PREC_STRUCTURED_GAUSSIAN;
+}
+
+// Bytes of the bin map (+ the occupied-group mask) and of the column tables
+// {count, Bk, Bt, 0}, column -> bin [B2], bin -> column [B2], occupancy mask
+// [B2 / 32]: the first two entries of every CP workspace.
+size_t bins_bytes(int N) { return static_cast<size_t>(N) * N * sizeof(uint16_t) + kGroupBytes; }
+size_t cols_bytes(int B) {
+  const size_t B2 = static_cast<size_t>(B) * B;
+  return (4 + 2 * B2 + (B2 + 31) / 32) * sizeof(int32_t);
+}
+size_t count_ws_bytes(int N, int B) { return align_up(bins_bytes(N), 256) + align_up(cols_bytes(B), 256); }
+
+// Stored columns per operand row: the FP32 CUDA-core pass reads T with its
+// own tile grid and stores all Bk columns; the tensor-core passes store the
+// occupied bins rounded up to 16 (Bt16 from the column table).
+int stored_cols(int prec, int Bk, int Bt16) { return prec == GSP_PREC_FP32 ? Bk : Bt16; }
+
+// Walked (Bk) and stored (Bt) operand columns for `count` occupied bins: the
+// rule k_bin_compact applies on the device.
+void cols_for(int B2, int count, int prec, int* Bk, int* Bt) {
+  const bool ident = B2 < 256;
+  int bk = ident ? B2 : ((count + 127) / 128) * 128;
+  if (bk < 128 && !ident) bk = 128;
+  if (bk > B2) bk = B2;
+  int bt16 = ident ? B2 : (count + 15) / 16 * 16;
+  if (bt16 < 16) bt16 = 16;
+  if (bt16 > bk) bt16 = bk;
+  *Bk = bk;
+  *Bt = stored_cols(prec, bk, bt16);
+}
+
+// FP32 split-K partials of the Z' pass: L * chunks * Bk * R floats for the
+// walked columns Bk; with the columns unknown (d.Bk == 0) the largest over
+// every column count the compaction can produce.
+size_t simt_part_floats(const MttkrpDims& d) {
+  auto part = [&](int bk) {
+    MttkrpDims e = d;
+    e.Bk = bk;
+    e.Bt = bk;
+    return static_cast<size_t>(d.L) * lst_chunks(e, GSP_PREC_FP32) * bk * d.R;
+  };
+  if (d.Bk) return part(d.Bk);
+  const int B2 = d.B * d.B;
+  if (B2 < 256) return part(B2);
+  size_t best = 0;
+  for (int bk = 128; bk <= B2; bk += 128) best = std::max(best, part(bk));
+  return best;
 }
 
 CpLayout cp_layout(const MttkrpDims& d, int prec) {
@@ -57,13 +110,26 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   const bool st = prec == GSP_PREC_STRUCTURED || prec == GSP_PREC_STRUCTURED_GAUSSIAN;
   const bool ga = prec == GSP_PREC_STRUCTURED_GAUSSIAN;
   const size_t dense = st ? 0 : 1;  // the structured path builds no tensor
-  o.T = take(dense * N2 * L * B2 * esize(prec));
-  o.bins = take(N2 * sizeof(uint16_t) + kGroupBytes);
+  // ---- head: fixed by (N, L, B, R, precision)
+  o.bins = take(bins_bytes(d.N));
+  o.cols = take(cols_bytes(d.B));
+  size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
+  o.M = take(imax * R * sizeof(double));
+  o.G = take(5 * R * R * sizeof(double));
+  o.Gpart = take((imax + kGramRows - 1) / kGramRows * R * R * sizeof(double));
+  o.W = take((3 * R * R + R) * sizeof(double) + 16);  // L, Z^T, 1/diag(L), mode, then W
+  o.lam = take(R * sizeof(double));
+  o.fit = take(GSP_MAX_SWEEPS * sizeof(double));
+  o.sumsq = take(L * sizeof(unsigned long long));
+  o.norm2 = take(sizeof(double));
+  o.flags = take(16);
+  o.head = off;
+  // ---- the operand (B2t() stored columns) and the arrays sized by its columns
+  o.T = take(dense * N2 * L * static_cast<size_t>(d.B2t()) * esize(prec));
   o.Yp = take(dense * N2 * R * sizeof(float));
   o.Zp = take(dense * L * B2 * R * sizeof(float));
-  const size_t simt_part = L * static_cast<size_t>(lst_chunks(d, GSP_PREC_FP32)) * B2 * R;
   const size_t tc_part = static_cast<size_t>(kLstMaxRanges) * 2 * B2 * R;
-  o.Zpart = take(dense * (prec == GSP_PREC_FP32 ? simt_part : tc_part) * sizeof(float));
+  o.Zpart = take(dense * (prec == GSP_PREC_FP32 ? simt_part_floats(d) : tc_part) * sizeof(float));
   o.KR = take(dense * 2 * R * L * B2 * sizeof(float));  // FP32 rows, or a hi + lo operand pair
   o.FX = take(dense * 2 * R * static_cast<size_t>(d.N) * sizeof(float));  // Z' fx operand
   const StructSizes z = st ? struct_sizes(d) : StructSizes{0, 0, 0, 0, 0, 0, 0, 0};
@@ -84,19 +150,6 @@ CpLayout cp_layout(const MttkrpDims& d, int prec) {
   o.conv = take(ga ? z.table_floats * sizeof(float) : 0);
   o.A = take(ga ? z.autocorr_ints * sizeof(int32_t) : 0);
   o.normpart = take(ga ? z.normpart_doubles * sizeof(double) : 0);
-  size_t imax = static_cast<size_t>(d.N > d.B ? (d.N > d.L ? d.N : d.L) : (d.B > d.L ? d.B : d.L));
-  o.M = take(imax * R * sizeof(double));
-  o.G = take(5 * R * R * sizeof(double));
-  o.Gpart = take((imax + kGramRows - 1) / kGramRows * R * R * sizeof(double));
-  o.W = take((3 * R * R + R) * sizeof(double) + 16);  // L, Z^T, 1/diag(L), mode, then W
-  o.lam = take(R * sizeof(double));
-  o.fit = take(GSP_MAX_SWEEPS * sizeof(double));
-  o.sumsq = take(L * sizeof(unsigned long long));
-  o.norm2 = take(sizeof(double));
-  o.flags = take(16);
-  // bin compaction: {count, Bk, pad, pad}, column -> dense bin [B2], dense bin ->
-  // column [B2] (int32), occupancy bitmask [B2 / 32]
-  o.cols = take((4 + 2 * B2 + (B2 + 31) / 32) * sizeof(int32_t));
   o.total = off;
   return o;
 }
@@ -705,6 +758,7 @@ struct Ctx {
   int prec;
   CpLayout lay;
   char* ws;
+  size_t ws_bytes;
   cudaStream_t s;
   // Side stream for the part of a mode update that does not need the mode's
   // MTTKRP (null: everything runs on s).
@@ -777,12 +831,8 @@ int run_lst(const Ctx& c, const float* fx, const float* fy) {
   if (c.prec != GSP_PREC_FP32)
     return tc_mttkrp_lst(c.ws + c.lay.T, fx, fy, c.ws + c.lay.FX, c.at<float>(c.lay.Zpart),
                          c.at<float>(c.lay.Zp), d, c.prec, c.at<uint32_t>(c.lay.flags), c.s);
-  // split-K chunks: within the partial buffer the layout sized for all B * B columns
-  MttkrpDims dense = d;
-  dense.Bk = dense.Bt = 0;
-  int C = lst_chunks(d, c.prec);
-  const long long cap = static_cast<long long>(lst_chunks(dense, c.prec)) * dense.B2() / d.B2();
-  while (C > 1 && C > cap) C >>= 1;
+  // split-K chunks (the partial buffer is laid out for this many)
+  const int C = lst_chunks(d, c.prec);
   GSP_TRY(simt_mttkrp_lst(c.at<float>(c.lay.T), fx, fy, c.at<float>(c.lay.Zpart), d, C, c.s));
   long long per_level = static_cast<long long>(d.B2()) * d.R;
   k_zreduce<<<grid_for(per_level * d.L, 256), 256, 0, c.s>>>(c.at<float>(c.lay.Zpart),
@@ -953,11 +1003,6 @@ bool recall_cols(const void* ws, const MttkrpDims& d, int prec, int* Bk, int* Bt
   return false;
 }
 
-// Stored columns per operand row: the FP32 CUDA-core pass reads T with its
-// own tile grid and stores all Bk columns; the tensor-core passes store the
-// occupied bins rounded up to 16 (Bt16 from the column table).
-int stored_cols(int prec, int Bk, int Bt16) { return prec == GSP_PREC_FP32 ? Bk : Bt16; }
-
 bool valid_cols(const MttkrpDims& d, int Bk, int Bt) {
   const int B2 = d.B * d.B;
   if (B2 < 256) return Bk == B2 && Bt == B2;
@@ -970,6 +1015,9 @@ bool path_supported(const MttkrpDims& d, int prec) {
   return tc_supported(d, prec);
 }
 
+// A context whose head offsets are valid; the dense-path arrays behind the
+// head are laid out once the operand's columns are known (set_cols).  The
+// structured path's layout is complete at once.
 int make_ctx(int N, int L, int B, int R, int prec, void* d_ws, size_t ws_bytes, gsp_stream st,
              Ctx& c) {
   if (!valid_cp(N, L, B, R, prec)) return GSP_ERR_INVALID_ARG;
@@ -977,14 +1025,25 @@ int make_ctx(int N, int L, int B, int R, int prec, void* d_ws, size_t ws_bytes, 
   c.prec = prec;
   if (!path_supported(c.d, prec)) return GSP_ERR_UNSUPPORTED;
   c.lay = cp_layout(c.d, prec);
-  if (!d_ws || ws_bytes < c.lay.total) return GSP_ERR_WORKSPACE;
+  const size_t need = is_structured(prec) ? c.lay.total : c.lay.head;
+  if (!d_ws || ws_bytes < need) return GSP_ERR_WORKSPACE;
   c.ws = static_cast<char*>(d_ws);
+  c.ws_bytes = ws_bytes;
   c.s = to_stream(st);
   return ensure_smem_attr();
 }
 
+// Lay out the operand of Bk walked / Bt stored columns behind the head; the
+// workspace must hold it.
+int set_cols(Ctx& c, int Bk, int Bt) {
+  c.d.Bk = Bk;
+  c.d.Bt = Bt;
+  c.lay = cp_layout(c.d, c.prec);
+  return c.ws_bytes < c.lay.total ? GSP_ERR_WORKSPACE : GSP_OK;
+}
+
 // The operand columns of a prepared dense-path workspace: from the host record
-// of its prepare, else read from the workspace.
+// of its prepare, else read from the workspace; then the full layout.
 int resolve_cols(Ctx& c) {
   if (is_structured(c.prec)) return GSP_OK;
   int Bk = 0, Bt = 0;
@@ -995,11 +1054,11 @@ int resolve_cols(Ctx& c) {
     Bk = h[1];
     Bt = stored_cols(c.prec, h[1], h[2]);
     if (!valid_cols(c.d, Bk, Bt)) return GSP_ERR_INVALID_ARG;  // not a prepared workspace
+    GSP_TRY(set_cols(c, Bk, Bt));
     remember_cols(c.ws, c.d, c.prec, Bk, Bt);
+    return GSP_OK;
   }
-  c.d.Bk = Bk;
-  c.d.Bt = Bt;
-  return GSP_OK;
+  return set_cols(c, Bk, Bt);
 }
 
 bool valid_factors(const gsp_cp_factors* f) {
@@ -1110,6 +1169,27 @@ int structured_sweep(const Ctx& c, const gsp_cp_factors& f) {
   return join_solve(c, f, 4);
 }
 
+// Bin map into bm, the occupied bins and the column tables into cols (the
+// first two entries of a CP workspace), then {count, Bk, Bt16} read back into
+// hc (synchronises s).
+int count_columns(const int32_t* d_hist, const float* d_normal_xy, int N, int bins, uint16_t* bm,
+                  int32_t* cols, uint32_t* d_status, cudaStream_t s, int32_t* hc) {
+  const int B2 = bins * bins;
+  uint32_t* occ = reinterpret_cast<uint32_t*>(cols + 4 + 2 * B2);
+  if (d_hist)
+    GSP_TRY(struct_bins_from_level0(d_hist, N, bins, bm, d_status, s));
+  else
+    GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, nullptr, s));
+  GSP_CUDA(cudaMemsetAsync(occ, 0, (B2 + 31) / 32 * sizeof(uint32_t), s));
+  k_bin_occupancy<<<sm_count() * 2, 256, 0, s>>>(bm, static_cast<long long>(N) * N, B2, occ);
+  GSP_CHECK_LAUNCH();
+  k_bin_compact<<<1, 512, 0, s>>>(occ, B2, cols);
+  GSP_CHECK_LAUNCH();
+  GSP_CUDA(cudaMemcpyAsync(hc, cols, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GSP_CUDA(cudaStreamSynchronize(s));
+  return GSP_OK;
+}
+
 }  // namespace
 }  // namespace gsp
 
@@ -1139,6 +1219,46 @@ extern "C" size_t gsp_cp_workspace_bytes(int N, int levels, int bins, int rank, 
   return cp_layout(d, precision).total;
 }
 
+extern "C" size_t gsp_cp_workspace_bytes_for_bins(int N, int levels, int bins, int rank,
+                                                  int precision, int occupied_bins) {
+  if (!valid_cp(N, levels, bins, rank, precision)) return 0;
+  MttkrpDims d{N, levels, bins, rank};
+  if (!path_supported(d, precision)) return 0;
+  if (is_structured(precision)) return cp_layout(d, precision).total;
+  const int B2 = bins * bins;
+  if (occupied_bins < 1 || occupied_bins > B2) return 0;
+  int Bk = 0, Bt = 0;
+  cols_for(B2, occupied_bins, precision, &Bk, &Bt);
+  d.Bk = Bk;
+  d.Bt = Bt;
+  return cp_layout(d, precision).total;
+}
+
+extern "C" size_t gsp_cp_operand_offset(int N, int levels, int bins, int rank, int precision) {
+  if (!valid_cp(N, levels, bins, rank, precision) || is_structured(precision)) return 0;
+  return cp_layout(MttkrpDims{N, levels, bins, rank}, precision).T;
+}
+
+extern "C" size_t gsp_cp_count_bins_workspace_bytes(int N, int bins) {
+  if (!valid_map(N, 1, bins) || N < 8 || bins < 8) return 0;
+  return count_ws_bytes(N, bins);
+}
+
+extern "C" int gsp_cp_count_bins(const int32_t* d_hist, const float* d_normal_xy, int N,
+                                 int levels, int bins, void* d_ws, size_t ws_bytes,
+                                 int32_t* h_occupied, uint32_t* d_status, gsp_stream stream) {
+  if (!h_occupied || (d_hist == nullptr) == (d_normal_xy == nullptr)) return GSP_ERR_INVALID_ARG;
+  if (!valid_map(N, levels, bins) || N < 8 || bins < 8) return GSP_ERR_INVALID_ARG;
+  if (!d_ws || ws_bytes < count_ws_bytes(N, bins)) return GSP_ERR_WORKSPACE;
+  char* w = static_cast<char*>(d_ws);
+  int32_t hc[3] = {0, 0, 0};
+  GSP_TRY(count_columns(d_hist, d_normal_xy, N, bins, reinterpret_cast<uint16_t*>(w),
+                        reinterpret_cast<int32_t*>(w + align_up(bins_bytes(N), 256)), d_status,
+                        to_stream(stream), hc));
+  *h_occupied = hc[0];
+  return GSP_OK;
+}
+
 extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, int N, int levels,
                               int bins, int rank, const gsp_als_opts* opts, void* d_ws,
                               size_t ws_bytes, uint32_t* d_status, gsp_stream stream) {
@@ -1155,21 +1275,11 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
   uint16_t* bm = c.at<uint16_t>(c.lay.bins);
   uint32_t* groups = reinterpret_cast<uint32_t*>(c.ws + c.lay.bins + d.N2() * sizeof(uint16_t));
   int32_t* cols = c.at<int32_t>(c.lay.cols);
-  uint32_t* occ = reinterpret_cast<uint32_t*>(cols + 4 + 2 * B2);
-  if (d_hist)
-    GSP_TRY(struct_bins_from_level0(d_hist, N, bins, bm, d_status, c.s));
-  else
-    GSP_TRY(launch_bins(d_normal_xy, N, bins, bm, d_status, nullptr, c.s));
-  GSP_CUDA(cudaMemsetAsync(occ, 0, (B2 + 31) / 32 * sizeof(uint32_t), c.s));
-  k_bin_occupancy<<<sm_count() * 2, 256, 0, c.s>>>(bm, d.N2(), B2, occ);
-  GSP_CHECK_LAUNCH();
-  k_bin_compact<<<1, 512, 0, c.s>>>(occ, B2, cols);
-  GSP_CHECK_LAUNCH();
   int32_t hc[3] = {0, 0, 0};
-  GSP_CUDA(cudaMemcpyAsync(hc, cols, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
-  GSP_CUDA(cudaStreamSynchronize(c.s));
+  GSP_TRY(count_columns(d_hist, d_normal_xy, N, bins, bm, cols, d_status, c.s, hc));
   const int Bk = hc[1], Bt = stored_cols(c.prec, hc[1], hc[2]);
   if (!valid_cols(d, Bk, Bt)) return GSP_ERR_INVALID_ARG;
+  GSP_TRY(set_cols(c, Bk, Bt));  // the workspace must hold the operand of these columns
   remember_cols(c.ws, d, c.prec, Bk, Bt);
   const long long slice = d.N2() * Bt;  // operand elements per level (Bt stored columns)
   if (d_hist) {

@@ -49,6 +49,27 @@ def test_host_side_sizes_and_validation(lib):
     assert lib.gsp_cp_workspace_bytes(32, 6, 16, 8, 0) > 32 * 32 * 6 * 256 * 4
     assert lib.gsp_cp_workspace_bytes(32, 6, 16, 12, 0) == 0      # rank not a power of two
     assert lib.gsp_cp_workspace_bytes(32, 6, 16, 8, 3) == 0       # unknown precision
+    # workspace sized by the occupied bins: all bins give the worst case, fewer
+    # a smaller one with the same head (operand offset).  The FP32 path stores
+    # the occupied bins rounded up to 128 columns: 67 bins of the 1024^2 / 11
+    # levels / 32^2 bins / rank 64 shape take 128 columns (5.9 GB of operand)
+    # instead of 1024 (47 GB).  (The tensor-core precisions need the driver's
+    # tensor-map encoder, absent without a GPU: their sizes are tested on one.)
+    fp32 = _lib.PREC["fp32"]
+    full = lib.gsp_cp_workspace_bytes(1024, 11, 32, 64, fp32)
+    assert lib.gsp_cp_workspace_bytes_for_bins(1024, 11, 32, 64, fp32, 1024) <= full
+    occ = lib.gsp_cp_workspace_bytes_for_bins(1024, 11, 32, 64, fp32, 67)
+    assert 1024 * 1024 * 11 * 128 * 4 < occ < 7 << 30 < full
+    assert lib.gsp_cp_workspace_bytes_for_bins(1024, 11, 32, 64, fp32, 0) == 0
+    assert lib.gsp_cp_workspace_bytes_for_bins(1024, 11, 32, 64, fp32, 1025) == 0
+    sizes = [lib.gsp_cp_workspace_bytes_for_bins(128, 8, 32, 16, fp32, n) for n in (1, 100, 300, 1024)]
+    assert sizes == sorted(sizes) and sizes[-1] <= lib.gsp_cp_workspace_bytes(128, 8, 32, 16, fp32)
+    assert sizes[0] == sizes[1] and sizes[1] < sizes[2]  # 1 and 100 bins: both 128 columns
+    off = lib.gsp_cp_operand_offset(1024, 11, 32, 64, fp32)
+    assert off >= 1024 * 1024 * 2 and off % 256 == 0
+    assert lib.gsp_cp_operand_offset(1024, 11, 32, 64, _lib.PREC["structured"]) == 0
+    assert lib.gsp_cp_count_bins_workspace_bytes(1024, 32) >= 1024 * 1024 * 2
+    assert lib.gsp_cp_count_bins(None, None, 32, 6, 16, None, 0, None, None, None) == -1
     # argument errors are returned before anything is enqueued
     assert lib.gsp_build_footprint_ndfs(None, 32, 6, 16, None, None, 0, None, None) == -1
     assert lib.gsp_range_query(None, 1, None, 10, None, None, None, None, 0, None) == -1

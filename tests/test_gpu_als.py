@@ -113,7 +113,7 @@ def test_operand_columns_and_mttkrp_at_every_occupancy(prec, B, n_occ):
     ws2.prepare(hist=dev(H, torch.int32))
     assert ws2.operand_cols() == ws.operand_cols()
     nb = L * N * N * cols * (2 if prec == "bf16" else 4)
-    assert torch.equal(ws.buf[:nb], ws2.buf[:nb])
+    assert torch.equal(ws.operand_view(nb), ws2.operand_view(nb))
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32"])
@@ -192,8 +192,8 @@ def test_als_from_normals_equals_from_histograms(prec):
 
 @pytest.mark.parametrize("prec,drop", [("bf16", 16), ("tf32", 13)])
 def test_operand_rounding_is_exact_or_neighbour_and_unbiased(prec, drop):
-    # The tensor-core operand (documented as the first levels*N^2*columns
-    # elements of the workspace) holds every exactly representable density unchanged and
+    # The tensor-core operand (documented as levels*N^2*columns elements from
+    # the workspace's operand offset) holds every exactly representable density unchanged and
     # every other one as its lower or upper neighbour on the BF16 / TF32 grid,
     # without bias: the summed rounding error stays within six standard
     # deviations of a sum of independent zero-mean errors of at most one ulp.
@@ -221,9 +221,9 @@ def test_operand_rounding_is_exact_or_neighbour_and_unbiased(prec, drop):
     assert ws.operand_cols() == (len(occ), Bk)
     n = exact.size
     if prec == "bf16":
-        raw = ws.buf[: 2 * n].cpu().numpy().view(np.uint16).astype(np.uint64) << 16
+        raw = ws.operand_view(2 * n).cpu().numpy().view(np.uint16).astype(np.uint64) << 16
     else:
-        raw = ws.buf[: 4 * n].cpu().numpy().view(np.uint32).astype(np.uint64)
+        raw = ws.operand_view(4 * n).cpu().numpy().view(np.uint32).astype(np.uint64)
     u = exact.view(np.uint32).astype(np.uint64)
     lo = (u >> drop) << drop
     up = lo + (1 << drop)
@@ -309,3 +309,53 @@ def test_solve_reciprocal_is_within_one_ulp():
     ref = 1.0 / d
     assert np.all(np.abs(got - ref) <= np.spacing(ref)), np.max(np.abs(got - ref) / np.spacing(ref))
     assert g.selftest_recip(dev(d[:0], torch.float64)).numel() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "tf32"])
+def test_workspace_sized_by_occupied_bins(prec):
+    # a workspace sized for the bins that occur gives bit-identical sweeps to
+    # one sized for all B^2 bins; one sized for fewer bins than occur is
+    # refused by the prepare
+    import paper_2109_14807_gb300 as g
+    from paper_2109_14807_gb300._lib import GspError
+    N, L, B, R = 64, 7, 32, 16
+    if not _supported(prec, N, L, B, R):
+        pytest.skip(f"{prec} path unavailable")
+    m = synth.flake_map(N, 1000, 0.6, 3)  # 389 of the 1024 bins occur
+    s, t = ndf.bin_index(m, B)
+    n_occ = len(np.unique(s * B + t))
+    assert 256 < n_occ < 512
+    md = dev(m)
+    assert g.count_bins(L, B, normal_xy=md) == n_occ
+    H = g.build_footprint_ndfs(md, L, B)
+    assert g.count_bins(L, B, hist=H) == n_occ
+    small = g.CPWorkspace.for_map(L, B, R, prec, normal_xy=md)
+    full = g.CPWorkspace(N, L, B, R, prec)
+    assert small.buf.numel() < full.buf.numel()
+    init = synth.init_factors(N, L, B, R, 5)
+    fits = []
+    for ws in (small, full):
+        ws.prepare(normal_xy=md)
+        f = g.init_factors_to_device(init)
+        fits.append(ws.sweeps(f, 3)[0])
+    assert fits[0] == fits[1]
+    tight = g.CPWorkspace(N, L, B, R, prec, occupied_bins=200)  # 256 columns instead of 384
+    with pytest.raises(GspError) as e:
+        tight.prepare(normal_xy=md)
+    assert e.value.code == -3
+
+
+def test_bench_shape_workspace_is_a_few_gb():
+    # the 1024^2 flake map with 11 levels and 32^2 bins (67 occur) at rank 64:
+    # BF16 operand 1.85 GB, the whole workspace under 4 GB instead of 23 GB
+    from paper_2109_14807_gb300 import _lib
+    lib_ = _lib.load()
+    w = synth.WORKLOADS["flakes1024"]
+    m = dev(synth.make_map(w))
+    import paper_2109_14807_gb300 as g
+    n = g.count_bins(w["levels"], w["bins"], normal_xy=m)
+    s, t = ndf.bin_index(synth.make_map(w), w["bins"])
+    assert n == len(np.unique(s * w["bins"] + t))
+    nb = lib_.gsp_cp_workspace_bytes_for_bins(w["N"], w["levels"], w["bins"], w["rank"],
+                                              _lib.PREC["bf16"], n)
+    assert 0 < nb < 4 << 30

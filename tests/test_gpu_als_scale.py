@@ -64,8 +64,9 @@ def test_tensor_core_mttkrp_at_bench_shape(prec, scale_workload):
     N, L, B, R = w["N"], w["levels"], w["bins"], w["rank"]
     if not _supported(prec, w):
         pytest.skip(f"{prec} tensor-core MTTKRP does not support the bench shape")
-    ws = g.CPWorkspace(N, L, B, R, prec)
-    ws.prepare(normal_xy=dev(m))
+    md = dev(m)
+    ws = g.CPWorkspace.for_map(L, B, R, prec, normal_xy=md)  # sized for the 67 occurring bins
+    ws.prepare(normal_xy=md)
     n_occ, cols = ws.operand_cols()
     assert (n_occ, cols) == (len(np.unique(s * B + t)), -(-n_occ // 16) * 16)
     # signed factors, so that a dropped or misplaced term cannot hide in a sum
