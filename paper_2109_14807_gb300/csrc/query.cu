@@ -397,7 +397,11 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
 // Atomic add of VEC consecutive floats as one vector reduction.
 template <int VEC>
 __device__ __forceinline__ void red_add(float* p, const float* v) {
-  if constexpr (VEC == 2) {
+  if constexpr (VEC == 4) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3])
+                 : "memory");
+  } else if constexpr (VEC == 2) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v[0]), "f"(v[1]) : "memory");
   } else {
     atomicAdd(p, v[0]);
@@ -407,13 +411,67 @@ __device__ __forceinline__ void red_add(float* p, const float* v) {
 constexpr int kBwdThreads = 256;
 constexpr int kBwdWarps = kBwdThreads / 32;
 
+// One small gradient table: in shared memory (SMEM, a 32-bit shared address;
+// additions are shared-memory reductions) or in global memory (atomics).  The
+// address space is explicit: a generic atomic whose pointer may be either runs
+// at less than half the rate on shared memory.
+template <bool SMEM>
+struct GTab;
+template <>
+struct GTab<true> {
+  uint32_t a;
+  __device__ __forceinline__ void add(int i, float v) const {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a + 4u * static_cast<uint32_t>(i)), "f"(v)
+                 : "memory");
+  }
+};
+template <>
+struct GTab<false> {
+  float* p;
+  __device__ __forceinline__ void add(int i, float v) const { atomicAdd(p + i, v); }
+};
+
+template <bool SMEM>
+struct GTabs {
+  GTab<SMEM> dflw, dps, dpt, dfs, dft;
+};
+
+// Gradient of one side's range average S with respect to its table (Sec. 4.4,
+// the form the forward evaluates):
+//   S = f[i0]                                             (i0 == i1)
+//   S = ((1 - f0) f[i0] + P[i1] - P[i0+1] + f1 f[i1]) / w  (i0 < i1)
+//   S = f[iz]                                             (zero width)
+// scaled by c: df[i0], df[i1] get the end-bin weights and dP[i1], dP[i0+1]
+// +-c / w, the prefix rows only when whole bins lie between the ends (for
+// i1 = i0 + 1 they cancel exactly).  Every weight is at most 1 in magnitude.
+template <bool SMEM>
+__device__ __forceinline__ void side_grad(const GTab<SMEM>& dp, const GTab<SMEM>& df, int R, int r,
+                                          float c, int i0, int i1, float f0, float f1, float inv_w,
+                                          int iz) {
+  if (inv_w > 0.0f) {
+    if (i0 == i1) {
+      df.add(i0 * R + r, c);
+    } else {
+      const float a = c * inv_w;
+      df.add(i0 * R + r, a * (1.0f - f0));
+      if (f1 != 0.0f) df.add(i1 * R + r, a * f1);
+      if (i1 > i0 + 1) {
+        dp.add(i1 * R + r, a);
+        dp.add((i0 + 1) * R + r, -a);
+      }
+    }
+  } else {
+    df.add(iz * R + r, c);
+  }
+}
+
 // LANES lanes per query; lane j handles the VEC consecutive ranks
 // j*VEC + k*LANES*VEC .. + VEC-1, so that its fx / fy gradient updates are
 // vector reductions.  The per-CTA shared-memory tables store rank r of a row
 // at column (r mod VEC) * R/VEC + r / VEC, so that the lanes' atomics for one
 // v = r mod VEC hit consecutive words (no bank conflicts); the flush undoes it.
-template <int LANES, int VEC>
-__global__ void __launch_bounds__(kBwdThreads, 3) k_range_query_bwd(const __grid_constant__ MatParams mp,
+template <int LANES, int VEC, bool SMEM>
+__global__ void __launch_bounds__(kBwdThreads, 2) k_range_query_bwd(const __grid_constant__ MatParams mp,
                                                          const __grid_constant__ GradParams gp,
                                                          const gsp_query* __restrict__ q,
                                                          long long n,
@@ -427,7 +485,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_range_query_bwd(const __grid
   const int j = lane % LANES;
   const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
-  if (gp.use_smem) {
+  if (SMEM) {
     for (int e = threadIdx.x; e < gp.soff[mp.n]; e += blockDim.x) sacc[e] = 0.0f;
     __syncthreads();
   }
@@ -496,15 +554,21 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_range_query_bwd(const __grid
       const float* sats = M.tables + flw_floats(M.levels, R);
       const float* satt = sats + static_cast<size_t>(M.bins + 1) * kSatPlanes * R;
       const gsp_material_grad& G = gp.g[m];
-      SmallGrad sg;
-      if (gp.use_smem) {
-        sg = small_tables(sacc + gp.soff[m], M);
+      GTabs<SMEM> sg;
+      if constexpr (SMEM) {
+        const SmallGrad st = small_tables(sacc + gp.soff[m], M);
+        auto sa = [](const float* q) { return static_cast<uint32_t>(__cvta_generic_to_shared(q)); };
+        sg.dflw.a = sa(st.dflw);
+        sg.dps.a = sa(st.dps);
+        sg.dpt.a = sa(st.dpt);
+        sg.dfs.a = sa(st.dfs);
+        sg.dft.a = sa(st.dft);
       } else {
-        sg.dflw = G.dflw;
-        sg.dps = gp.dps[m];
-        sg.dpt = gp.dpt[m];
-        sg.dfs = G.dfs;
-        sg.dft = G.dft;
+        sg.dflw.p = G.dflw;
+        sg.dps.p = gp.dps[m];
+        sg.dpt.p = gp.dpt[m];
+        sg.dfs.p = G.dfs;
+        sg.dft.p = G.dft;
       }
       const float g0 = 1.0f - t.f;
       for (int rv = j * VEC; rv < R; rv += LANES * VEC) {
@@ -519,7 +583,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_range_query_bwd(const __grid
         for (int v = 0; v < VEC; ++v) {
           const int r0 = rv + v;
           // column of rank r0 in this CTA's shared-memory tables (global: r0)
-          const int r = gp.use_smem ? v * (R / VEC) + rv / VEC : r0;
+          const int r = SMEM ? v * (R / VEC) + rv / VEC : r0;
           float lv = fmaf(t.f, a1v[v], g0 * a0v[v]);
           float S = Sv[v];
           float T = Tv[v];
@@ -528,36 +592,19 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_range_query_bwd(const __grid
           float st = S * T;
           dx[v] = g * yv * lv * st;
           dy[v] = g * xv * lv * st;
-          atomicAdd(sg.dflw + t.l0 * R + r, g * g0 * xy * st);
-          if (t.f != 0.0f) atomicAdd(sg.dflw + t.l1 * R + r, g * t.f * xy * st);
-          // Sbar = (F(s1) - F(s0)) / w with F(s) = P[floor s] + frac(s) fs[floor s]
-          float cs = g * xy * lv * T;
-          if (t.inv_ws > 0.0f) {
-            float a = cs * t.inv_ws;
-            atomicAdd(sg.dps + t.is1 * R + r, a);
-            atomicAdd(sg.dps + t.is0 * R + r, -a);
-            if (t.fs1 != 0.0f) atomicAdd(sg.dfs + t.is1 * R + r, a * t.fs1);
-            if (t.fs0 != 0.0f) atomicAdd(sg.dfs + t.is0 * R + r, -a * t.fs0);
-          } else {
-            atomicAdd(sg.dfs + t.isz * R + r, cs);
-          }
-          float ct = g * xy * lv * S;
-          if (t.inv_wt > 0.0f) {
-            float a = ct * t.inv_wt;
-            atomicAdd(sg.dpt + t.it1 * R + r, a);
-            atomicAdd(sg.dpt + t.it0 * R + r, -a);
-            if (t.ft1 != 0.0f) atomicAdd(sg.dft + t.it1 * R + r, a * t.ft1);
-            if (t.ft0 != 0.0f) atomicAdd(sg.dft + t.it0 * R + r, -a * t.ft0);
-          } else {
-            atomicAdd(sg.dft + t.itz * R + r, ct);
-          }
+          sg.dflw.add(t.l0 * R + r, g * g0 * xy * st);
+          if (t.f != 0.0f) sg.dflw.add(t.l1 * R + r, g * t.f * xy * st);
+          side_grad<SMEM>(sg.dps, sg.dfs, R, r, g * xy * lv * T, t.is0, t.is1, t.fs0, t.fs1,
+                          t.inv_ws, t.isz);
+          side_grad<SMEM>(sg.dpt, sg.dft, R, r, g * xy * lv * S, t.it0, t.it1, t.ft0, t.ft1,
+                          t.inv_wt, t.itz);
         }
         red_add<VEC>(G.dfx + t.x * R + rv, dx);
         red_add<VEC>(G.dfy + t.y * R + rv, dy);
       }
     }
   }
-  if (gp.use_smem) {
+  if (SMEM) {
     __syncthreads();
     for (int m = 0; m < mp.n; ++m) {
       const gsp_material& M = mp.m[m];
@@ -804,21 +851,30 @@ int pick_lanes(const gsp_material* mats, int n_mats, const gsp_query_tuning* tn)
   return rmax >= 64 ? 8 : 4;
 }
 
-template <int LANES, int VEC>
-int launch_bwd_t(long long blocks, int threads, size_t dyn, cudaStream_t s, const MatParams& mp,
+template <int LANES, int VEC, bool SMEM>
+int launch_bwd_k(long long blocks, int threads, size_t dyn, cudaStream_t s, const MatParams& mp,
                  const GradParams& gp, const gsp_query* d_q, long long n, const float* d_gout,
                  uint32_t* d_status) {
-  GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<LANES, VEC>,
+  GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd<LANES, VEC, SMEM>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
   // one wave of resident CTAs (registers, shared memory): the grid-stride
   // loop then spreads the batches evenly, with no partial second wave
   int per_sm = 0;
-  GSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_range_query_bwd<LANES, VEC>,
-                                                         threads, dyn));
+  GSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, k_range_query_bwd<LANES, VEC, SMEM>, threads, dyn));
   const long long cap = static_cast<long long>(sm_count()) * (per_sm > 0 ? per_sm : 1);
   if (blocks > cap) blocks = cap;
-  k_range_query_bwd<LANES, VEC><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
+  k_range_query_bwd<LANES, VEC, SMEM><<<blocks, threads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
   return GSP_OK;
+}
+
+template <int LANES, int VEC>
+int launch_bwd_t(long long blocks, int threads, size_t dyn, cudaStream_t s, const MatParams& mp,
+                 const GradParams& gp, const gsp_query* d_q, long long n, const float* d_gout,
+                 uint32_t* d_status) {
+  if (gp.use_smem)
+    return launch_bwd_k<LANES, VEC, true>(blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
+  return launch_bwd_k<LANES, VEC, false>(blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
 }
 
 template <int VEC>
@@ -836,6 +892,7 @@ int launch_bwd_v(int lanes, long long blocks, int threads, size_t dyn, cudaStrea
 int launch_bwd(int lanes, int vec, long long blocks, int threads, size_t dyn, cudaStream_t s,
                const MatParams& mp, const GradParams& gp, const gsp_query* d_q, long long n,
                const float* d_gout, uint32_t* d_status) {
+  if (vec == 4) return launch_bwd_v<4>(lanes, blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
   if (vec == 2) return launch_bwd_v<2>(lanes, blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
   return launch_bwd_v<1>(lanes, blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
 }
@@ -1021,8 +1078,11 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
   GSP_CUDA(cudaMemsetAsync(d_ws, 0, need, s));
   if (n > 0) {
     // VEC: 2 when it divides every rank (with at least four vectors per rank
-    // row) and keeps the factor rows and gradients aligned, else 1.  (Four
-    // ranks per lane needed 128 registers and cost a third of the occupancy.)
+    // row) and keeps the factor rows and gradients aligned, else 1; LANES x
+    // VEC covers the largest rank.  (Runs of 4 ranks, or several queries per
+    // warp, were slower at rank 64: 4.0 - 5.8 ms instead of 2.6 ms per 10^7
+    // queries, the lane groups' shared-memory reductions to one column of
+    // different rows falling on one bank.)
     int vec = 2;
     for (int i = 0; i < n_mats; ++i) {
       const gsp_material& m = h_mats[i];
