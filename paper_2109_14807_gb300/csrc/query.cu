@@ -67,6 +67,11 @@ struct GradParams {
   // adds them to global memory once at the end.
   int soff[GSP_MAX_MATERIALS + 1];
   int use_smem;
+  // Packed-query kernel (k_range_query_bwd_q): per-material offsets within
+  // one copy of the shared tables (dflw [L][RS], dP_s [B+1][RS], dP_t [B+1][RS],
+  // RS = R rounded up to 32) and the stride between the copies.
+  int qoff[GSP_MAX_MATERIALS + 1];
+  int copy_stride;
 };
 
 struct SmallGrad {
@@ -628,6 +633,211 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_range_query_bwd(const __grid
   }
 }
 
+// ------------------------------------------------- packed-query adjoint --
+// The adjoint with the forward's lane mapping: LANES lanes per query (W =
+// LANES * 4 <= 32 ranks per block, runs of 4 consecutive ranks per lane,
+// float4 gathers), 32 / LANES queries per warp step.  The per-query work (terms,
+// addresses, branches) is then shared by a quarter of a warp instead of all of
+// it.  Each lane-group position of a warp has its own copy of the small
+// gradient tables in shared memory; the copies start LANES banks apart and a
+// group's lanes write consecutive words, so the groups' reductions never share
+// a bank.  The angular gradients go to the prefix rows only: with
+// E[j] = dP[j + 1] and dS/df[k] = sum_{j >= k} E[j], a side's update is
+//   zero width / one bin i0:  dP[i0 + 1] += c, dP[i0] -= c
+//   i0 < i1, a = c / w:       dP[i1 + 1] += a f1, dP[i1] += a (1 - f1) (i1 > i0 + 1),
+//                             dP[i0 + 1] += a (1 - f0) - a_{i0+1}, dP[i0] -= a (1 - f0)
+// with a_{i0+1} = a (i1 > i0 + 1) or a f1 (i1 = i0 + 1); k_suffix turns the
+// prefix rows into the bin gradients (dP[0] is never read).  A batch's live
+// queries (well formed, non-zero upstream gradient) are packed to the front of
+// the warp's slots, so no lane group waits on a skipped query.
+// The four prefix-row updates of one side, without branches (every lane
+// group of a warp then takes the same path whatever its query's range): rows
+// that a range does not touch receive 0.  The table reductions carry no
+// memory clobber, so the compiler may issue the next query's slot loads ahead
+// of them: the tables are read only after the kernel's final __syncthreads(),
+// and volatile asm is not moved across it.
+__device__ __forceinline__ void side_grad_p(uint32_t dp, int RS, int col, float c, int i0, int i1,
+                                            float f0, float f1, float inv_w, int iz, int B) {
+  const bool span = inv_w > 0.0f && i0 != i1;  // the range crosses a bin border
+  const bool wide = i1 > i0 + 1;               // whole bins between the ends
+  const float a = c * inv_w;
+  const float e0 = a * (1.0f - f0);
+  const int i = inv_w > 0.0f ? i0 : iz;
+  const int r1 = span ? min(i1 + 1, B) : i + 1;  // f1 = 0 when i1 = B
+  const float v1 = span ? a * f1 : c;
+  const float v2 = span && wide ? a - a * f1 : 0.0f;
+  const float v3 = span ? (wide ? e0 - a : e0 - a * f1) : 0.0f;
+  const float v4 = span ? -e0 : -c;
+  auto add = [&](int row, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(dp + 4u * static_cast<uint32_t>(row * RS + col)),
+                 "f"(v));
+  };
+  add(r1, v1);
+  add(span ? i1 : i, v2);
+  add(span ? i0 + 1 : i, v3);
+  add(i, v4);
+}
+
+// One CTA of 16 warps per SM: its warps share one set of table copies, which
+// leaves most of the SM's 256 KB of L1 / shared memory to cache the query
+// tables (two CTAs of 8 warps with their own copies starved L1 to a 35 % hit
+// rate).
+constexpr int kBwdQThreads = 512;
+constexpr int kBwdQWarps = kBwdQThreads / 32;
+
+template <int LANES>
+__global__ void __launch_bounds__(kBwdQThreads, 1) k_range_query_bwd_q(
+    const __grid_constant__ MatParams mp, const __grid_constant__ GradParams gp,
+    const gsp_query* __restrict__ q, long long n, const float* __restrict__ gout, uint32_t* status) {
+  constexpr int V = 4;
+  constexpr int W = V * LANES;  // ranks per block
+  constexpr int QPW = 32 / LANES;
+  extern __shared__ float sacc[];  // QPW copies of gp.copy_stride floats
+  __shared__ float4 tslots[kBwdQWarps][32][5];
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LANES;
+  const int j = lane % LANES;
+  const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+  const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  const int total = QPW * gp.copy_stride;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) sacc[e] = 0.0f;
+  __syncthreads();
+  const uint32_t copy =
+      static_cast<uint32_t>(__cvta_generic_to_shared(sacc)) + 4u * static_cast<uint32_t>(sub * gp.copy_stride);
+  float4 (*slots)[5] = tslots[threadIdx.x >> 5];
+  const long long n_batches = (n + 31) / 32;
+  gsp_query dn{};
+  float gn = 0.0f;
+  if (warp_id < n_batches && warp_id * 32 + lane < n) {
+    load_query(q, warp_id * 32 + lane, dn);
+    gn = __ldg(gout + warp_id * 32 + lane);
+  }
+  for (long long bt = warp_id; bt < n_batches; bt += n_warps) {
+    int n_live;
+    {
+      const long long qk = bt * 32 + lane;
+      const gsp_query dk = dn;
+      const float gk = gn;
+      const long long qn = (bt + n_warps) * 32 + lane;
+      if (bt + n_warps < n_batches && qn < n) {
+        load_query(q, qn, dn);
+        gn = __ldg(gout + qn);
+      }
+      bool live = false;
+      int mk = 0;
+      QTerms tk{};
+      if (qk < n) {
+        if (dk.material >= static_cast<uint32_t>(mp.n)) {
+          set_status(status, GSP_DEV_BAD_QUERY);
+        } else {
+          mk = static_cast<int>(dk.material);
+          tk = query_terms(dk, mp.m[mk]);
+          if (!tk.ok) set_status(status, GSP_DEV_BAD_QUERY);
+          live = tk.ok && gk != 0.0f;
+        }
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, live);
+      n_live = __popc(ball);
+      const int pos = __popc(ball & ((1u << lane) - 1u));
+      __syncwarp();  // every lane is done with the previous batch's slots
+      if (live) {
+        slots[pos][0] = make_float4(__int_as_float(tk.x), __int_as_float(tk.y), __int_as_float(tk.l0),
+                                    __int_as_float(tk.l1));
+        slots[pos][1] = make_float4(tk.f, __int_as_float(tk.is0), __int_as_float(tk.is1),
+                                    __int_as_float(tk.it0));
+        slots[pos][2] = make_float4(__int_as_float(tk.it1), tk.fs0, tk.fs1, tk.ft0);
+        slots[pos][3] = make_float4(tk.ft1, tk.inv_ws, tk.inv_wt, __int_as_float(tk.isz));
+        slots[pos][4] = make_float4(__int_as_float(tk.itz), __int_as_float(mk), gk, 0.0f);
+      }
+      __syncwarp();
+    }
+    for (int s0 = 0; s0 < n_live; s0 += QPW) {
+      const int slot = s0 + sub;
+      if (slot >= n_live) continue;
+      const float4 w0 = slots[slot][0], w1 = slots[slot][1], w2 = slots[slot][2],
+                   w3 = slots[slot][3], w4 = slots[slot][4];
+      const int x = __float_as_int(w0.x), y = __float_as_int(w0.y);
+      const int l0 = __float_as_int(w0.z), l1 = __float_as_int(w0.w);
+      const float f = w1.x;
+      const int is0 = __float_as_int(w1.y), is1 = __float_as_int(w1.z), it0 = __float_as_int(w1.w);
+      const int it1 = __float_as_int(w2.x);
+      const float fs0 = w2.y, fs1 = w2.z, ft0 = w2.w, ft1 = w3.x, inv_ws = w3.y, inv_wt = w3.z;
+      const int isz = __float_as_int(w3.w), itz = __float_as_int(w4.x);
+      const int m = __float_as_int(w4.y);
+      const float g = w4.z;
+      const gsp_material& M = mp.m[m];
+      const int R = M.rank, L = M.levels, B = M.bins;
+      const int RS = (R + 31) & ~31;
+      const float* flw = M.tables;
+      const float* sats = M.tables + flw_floats(L, R);
+      const float* satt = sats + static_cast<size_t>(B + 1) * kSatPlanes * R;
+      const gsp_material_grad& G = gp.g[m];
+      const uint32_t tflw = copy + 4u * static_cast<uint32_t>(gp.qoff[m]);
+      const uint32_t tps = tflw + 4u * static_cast<uint32_t>(L * RS);
+      const uint32_t tpt = tps + 4u * static_cast<uint32_t>((B + 1) * RS);
+      const float g0 = 1.0f - f;
+      // the second level row only when a query of this step blends two levels
+      // (warp-uniform over the active lane groups, so no divergence)
+      const bool blend = __any_sync(__activemask(), f != 0.0f);
+      for (int r0 = 0; r0 < R; r0 += W) {
+        const int rb = r0 + V * j;
+        float a0[V], a1[V], xv[V], yv[V], S[V], T[V], dx[V], dy[V];
+        ldg_n<V>(flw + l0 * R + rb, a0);
+        ldg_n<V>(flw + l1 * R + rb, a1);
+        ldg_n<V>(M.fx + static_cast<size_t>(x) * R + rb, xv);
+        ldg_n<V>(M.fy + static_cast<size_t>(y) * R + rb, yv);
+        sat_mean<V>(sats, R, rb, is0, is1, fs0, fs1, inv_ws, isz, S);
+        sat_mean<V>(satt, R, rb, it0, it1, ft0, ft1, inv_wt, itz, T);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int col = r0 + v * LANES + j;  // consecutive words across the group
+          const float lv = fmaf(f, a1[v], g0 * a0[v]);
+          const float xy = xv[v] * yv[v];
+          const float st = S[v] * T[v];
+          dx[v] = g * yv[v] * lv * st;
+          dy[v] = g * xv[v] * lv * st;
+          const float gxs = g * xy * st;
+          asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(tflw + 4u * static_cast<uint32_t>(l0 * RS + col)),
+                       "f"(gxs * g0));
+          if (blend)
+            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(tflw + 4u * static_cast<uint32_t>(l1 * RS + col)),
+                         "f"(gxs * f));
+          const float gxl = g * xy * lv;
+          side_grad_p(tps, RS, col, gxl * T[v], is0, is1, fs0, fs1, inv_ws, isz, B);
+          side_grad_p(tpt, RS, col, gxl * S[v], it0, it1, ft0, ft1, inv_wt, itz, B);
+        }
+        red_add<V>(G.dfx + static_cast<size_t>(x) * R + rb, dx);
+        red_add<V>(G.dfy + static_cast<size_t>(y) * R + rb, dy);
+      }
+    }
+  }
+  __syncthreads();
+  // add the copies and flush: entry (row, r) sits at column r0 + v * LANES + j
+  // of its row, r = r0 + 4 j + v
+  for (int mm = 0; mm < mp.n; ++mm) {
+    const gsp_material& M = mp.m[mm];
+    const int R = M.rank, L = M.levels, B = M.bins;
+    const int RS = (R + 31) & ~31;
+    const int rows = L + 2 * (B + 1);
+    const gsp_material_grad& G = gp.g[mm];
+    for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
+      const int row = e / R, r = e - row * R;
+      const int r0 = r / W * W, jj = (r - r0) / V, vv = (r - r0) % V;
+      const int at = gp.qoff[mm] + row * RS + r0 + vv * LANES + jj;
+      float sum = 0.0f;
+#pragma unroll
+      for (int c = 0; c < QPW; ++c) sum += sacc[c * gp.copy_stride + at];
+      if (sum == 0.0f) continue;
+      if (row < L)
+        atomicAdd(G.dflw + row * R + r, sum);
+      else if (row < L + B + 1)
+        atomicAdd(gp.dps[mm] + (row - L) * R + r, sum);
+      else
+        atomicAdd(gp.dpt[mm] + (row - L - B - 1) * R + r, sum);
+    }
+  }
+}
+
 // dP[i] is the gradient w.r.t. P[i] = sum_{k<i} f[k]; so df[k] += sum_{i>k} dP[i].
 __global__ void k_suffix(const float* __restrict__ dp, float* __restrict__ df, int B, int R) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -877,6 +1087,21 @@ int launch_bwd_t(long long blocks, int threads, size_t dyn, cudaStream_t s, cons
   return launch_bwd_k<LANES, VEC, false>(blocks, threads, dyn, s, mp, gp, d_q, n, d_gout, d_status);
 }
 
+template <int LANES>
+int launch_bwd_q(long long blocks, size_t dyn, cudaStream_t s, const MatParams& mp,
+                 const GradParams& gp, const gsp_query* d_q, long long n, const float* d_gout,
+                 uint32_t* d_status) {
+  GSP_CUDA(cudaFuncSetAttribute(k_range_query_bwd_q<LANES>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn)));
+  int per_sm = 0;
+  GSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_range_query_bwd_q<LANES>,
+                                                         kBwdQThreads, dyn));
+  const long long cap = static_cast<long long>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+  if (blocks > cap) blocks = cap;
+  k_range_query_bwd_q<LANES><<<blocks, kBwdQThreads, dyn, s>>>(mp, gp, d_q, n, d_gout, d_status);
+  return GSP_OK;
+}
+
 template <int VEC>
 int launch_bwd_v(int lanes, long long blocks, int threads, size_t dyn, cudaStream_t s,
                  const MatParams& mp, const GradParams& gp, const gsp_query* d_q, long long n,
@@ -1076,7 +1301,43 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
   gp.use_smem = smem <= 96 * 1024 ? 1 : 0;
   cudaStream_t s = to_stream(stream);
   GSP_CUDA(cudaMemsetAsync(d_ws, 0, need, s));
-  if (n > 0) {
+  // Packed-query kernel: every rank a multiple of W = min(32, R) >= 8 (the
+  // same W for all materials), factor and gradient rows 16-byte aligned, and
+  // 32 / (W / 4) copies of the small tables in shared memory.
+  int pw = 0;
+  bool packed = true;
+  int qo = 0;
+  for (int i = 0; i < n_mats && packed; ++i) {
+    const gsp_material& m = h_mats[i];
+    const gsp_material_grad& g = h_grads[i];
+    const int wm = m.rank < 32 ? m.rank : 32;
+    if (pw == 0) pw = wm;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(m.fx) | reinterpret_cast<uintptr_t>(m.fy) |
+                         reinterpret_cast<uintptr_t>(g.dfx) | reinterpret_cast<uintptr_t>(g.dfy);
+    packed = wm == pw && wm >= 8 && (wm & (wm - 1)) == 0 && m.rank % wm == 0 && (al & 15) == 0;
+    gp.qoff[i] = qo;
+    const int RS = (m.rank + 31) & ~31;
+    qo += RS * (m.levels + 2 * (m.bins + 1));  // a multiple of 32 floats
+  }
+  gp.qoff[n_mats] = qo;
+  const int plan = pw / 4;  // lanes per query
+  gp.copy_stride = qo + plan;  // copies start plan banks apart
+  const size_t qdyn = packed ? static_cast<size_t>(32 / plan) * gp.copy_stride * sizeof(float) : 0;
+  if (packed && qdyn > 200 * 1024) packed = false;
+  if (n > 0 && packed) {
+    const long long blocks = ((n + 31) / 32 * 32 + kBwdQThreads - 1) / kBwdQThreads;
+    prof_begin(PROF_QUERY_BWD, s);
+    int rc = GSP_OK;
+    if (plan == 8)
+      rc = launch_bwd_q<8>(blocks, qdyn, s, mp, gp, d_q, n, d_gout, d_status);
+    else if (plan == 4)
+      rc = launch_bwd_q<4>(blocks, qdyn, s, mp, gp, d_q, n, d_gout, d_status);
+    else
+      rc = launch_bwd_q<2>(blocks, qdyn, s, mp, gp, d_q, n, d_gout, d_status);
+    GSP_TRY(rc);
+    prof_end(PROF_QUERY_BWD, s);
+    GSP_CHECK_LAUNCH();
+  } else if (n > 0) {
     // VEC: 2 when it divides every rank (with at least four vectors per rank
     // row) and keeps the factor rows and gradients aligned, else 1; LANES x
     // VEC covers the largest rank.  (Runs of 4 ranks, or several queries per

@@ -93,6 +93,84 @@ def test_adjoint_two_materials_and_malformed_queries():
             assert err <= 1e-4, (i, k, err)
 
 
+@pytest.mark.parametrize("ranks", [(32, 64), (64, 64, 32)])
+def test_packed_adjoint_several_materials_of_one_rank_block(ranks):
+    # materials whose ranks share the 32-rank block run the packed-query
+    # kernel (several queries per warp, one table copy per lane group):
+    # the same oracle parity, with zero-width and malformed queries mixed in
+    import paper_2109_14807_gb300 as g
+    shapes = [(32 << i, 6 + i, 16 * (1 + i % 2), R) for i, R in enumerate(ranks)]
+    fs = [random_factors(N, L, B, R, 80 + i) for i, (N, L, B, R) in enumerate(shapes)]
+    parts = []
+    for i, (N, L, B, R) in enumerate(shapes):
+        qi = synth.queries_fractional(N, L, B, 1500 + 11 * i, 81 + i, wmin=0.05, wmax=B, frac_level=True)
+        qi["material"] = i
+        parts.append(qi)
+    q = np.concatenate(parts)
+    q = q[np.argsort(synth.uniform(82, 0, len(q)))]
+    q["s1"][10] = q["s0"][10]
+    q["t0"][11] = q["t1"][11]
+    q["level"][12] = np.nan
+    g_up = (synth.uniform(83, 1, len(q)) - 0.5).astype(np.float32)
+    g_up[100:140] = 0.0  # zero upstream gradients: skipped queries
+    mats, grads = [], []
+    for f in fs:
+        fd = {k: dev(v) for k, v in f.items()}
+        mat = g.QueryMaterial.from_factors(fd)
+        g.build_query_tables(mat)
+        mats.append(mat)
+        grads.append({k: torch.zeros_like(fd[a if a != "flw" else "fl"]) for k, a in NAMES})
+    st = g.new_status()
+    g.range_query_backward(mats, g.queries_to_device(q), dev(g_up), grads, status=st)
+    torch.cuda.synchronize()
+    assert g.status_bits(st) & 0x2
+    oms = [oracle_material(f) for f in fs]
+    g64 = g_up.astype(np.float64)
+    ref = oq.cp_range_query_adjoint(oms, q, g64)
+    scale = oq.cp_range_query_adjoint([{k: np.abs(v) for k, v in om.items()} for om in oms], q, np.abs(g64))
+    for i in range(len(fs)):
+        for k, a in NAMES:
+            got = grads[i][k].double().cpu().numpy()
+            err = np.max(np.abs(got - ref[i][a]) / np.maximum(scale[i][a], 1e-30))
+            assert err <= 1e-4, (ranks, i, k, err)
+
+
+def test_packed_and_rank_lane_adjoints_agree():
+    # the same material with 16-byte aligned factor rows (packed-query kernel)
+    # and with factor storage 4 bytes off alignment (the kernel that gives each
+    # query a whole warp, one rank per lane): both match the oracle and each other
+    import paper_2109_14807_gb300 as g
+    N, L, B, R = 64, 7, 32, 64
+    f = random_factors(N, L, B, R, 90)
+    q = synth.queries_fractional(N, L, B, 4000, 91, wmin=0.05, wmax=B, frac_level=True)
+    g_up = (synth.uniform(92, 1, len(q)) - 0.5).astype(np.float32)
+    qd, gd = g.queries_to_device(q), dev(g_up)
+    out = []
+    for shift in (0, 1):
+        fd = {}
+        for k, v in f.items():
+            if shift and k in ("fx", "fy"):
+                buf = torch.zeros(v.size + 1, dtype=torch.float32, device="cuda")
+                buf[1:] = dev(v).reshape(-1)
+                fd[k] = buf[1:].view(v.shape)  # rows 4 bytes off a 16-byte boundary
+            else:
+                fd[k] = dev(v)
+        mat = g.QueryMaterial.from_factors(fd)
+        g.build_query_tables(mat)
+        grads = {k: torch.zeros(fd[a if a != "flw" else "fl"].shape, dtype=torch.float32, device="cuda")
+                 for k, a in NAMES}
+        g.range_query_backward(mat, qd, gd, [grads])
+        torch.cuda.synchronize()
+        out.append({k: v.double().cpu().numpy() for k, v in grads.items()})
+    om = oracle_material(f)
+    ref = oq.cp_range_query_adjoint(om, q, g_up.astype(np.float64))
+    scale = _oracle_grad_scale(om, q, g_up.astype(np.float64))
+    for k, a in NAMES:
+        for o in out:
+            assert np.max(np.abs(o[k] - ref[a]) / np.maximum(scale[a], 1e-30)) <= 1e-4, k
+        assert np.max(np.abs(out[0][k] - out[1][k]) / np.maximum(scale[a], 1e-30)) <= 2e-4, k
+
+
 def test_adjoint_vs_fp32_central_differences():
     import paper_2109_14807_gb300 as g
     N, L, B, R = 16, 5, 8, 8
