@@ -247,7 +247,9 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 // ------------------------------------------------------------ Y' pass --
 // ELEM: 2 (BF16) or 4 (TF32/FP32 storage).  E128 = elements per 128 bytes.
 // SPLIT: the B operand holds 2R rows, a hi part and its remainder (BF16 or
-// TF32); each K slice then issues two MMAs into the same accumulator.
+// TF32); each K slice then issues one MMA of N = 2R over both, into an
+// accumulator whose columns R .. 2R-1 hold the remainder's sums (one N = 128
+// MMA instead of two of N = 64 at rank 64: the tensor pipe was 66 % busy).
 template <int ELEM, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_xy_tc(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapKR,
@@ -263,7 +265,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kpl = B2 / E128;  // 128-byte K chunks per level
   const int kiters = L * kpl;
-  const uint32_t ncols = tmem_cols_for(2 * R);
+  // SPLIT: one MMA of N = 2R per K slice covers the hi and lo rows of the B
+  // tile (they are contiguous), into an accumulator of 2R columns (hi sums,
+  // then lo sums) that the epilogue adds; two such chunk accumulators.
+  constexpr int AW = SPLIT ? 2 : 1;  // accumulator columns per rank
+  const uint32_t ncols = tmem_cols_for(2 * AW * R);
   volatile int* abort = &bar.abort;
 
   if (threadIdx.x == 0) {
@@ -322,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 5) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t id = idesc(FMT, 0, static_cast<uint32_t>(R));
+      const uint32_t id = idesc(FMT, 0, static_cast<uint32_t>(AW * R));
       int s = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
       bool any = false;
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int it0 = 0; it0 < kiters; it0 += kChunk) {  // a fresh accumulator per chunk
           if (!mbar_wait(smem_u32(&bar.acc_empty[acc]), aph ^ 1u, abort)) goto mma_done;
           tc_fence_after();
-          const uint32_t d = tmem + static_cast<uint32_t>(acc * R);
+          const uint32_t d = tmem + static_cast<uint32_t>(acc * AW * R);
           const int it1 = it0 + kChunk < kiters ? it0 + kChunk : kiters;
           for (int it = it0; it < it1; ++it) {
             if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
@@ -338,12 +344,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sa = smem_u32(smem + s * stage_bytes);
             // descriptor address fields are in 16-byte units: slice j adds 2 j
             const uint64_t a0 = sdesc(sa, 16, 1024), b0 = sdesc(sa + kTileBytes, 16, 1024);
-            const uint64_t blo = static_cast<uint64_t>(R * 128 / 16);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {  // four K slices of 32 bytes per 128-byte row
+            for (int j = 0; j < 4; ++j)  // four K slices of 32 bytes per 128-byte row
               umma<ELEM>(d, a0 + 2 * j, b0 + 2 * j, id, (it > it0 || j > 0) ? 1u : 0u);
-              if constexpr (SPLIT) umma<ELEM>(d, a0 + 2 * j, b0 + blo + 2 * j, id, 1u);
-            }
             any = true;
             umma_commit(smem_u32(&bar.empty[s]));
             if (++s == kStages) {
@@ -379,10 +382,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int c = 0; c < kMaxRankTc / 16; ++c) {
           if (c * 16 < R) {
-            float v[16];
-            tmem_ld16(lane_base + acc * R + c * 16, v);
+            const uint32_t col = static_cast<uint32_t>(acc * AW * R + c * 16);
+            if constexpr (SPLIT) {  // hi sums + lo sums
+              uint32_t h[16], lo[16];
+              tmem_ld16_nowait(lane_base + col, h);
+              tmem_ld16_nowait(lane_base + col + R, lo);
+              tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 16; ++i) sum[c * 16 + i] += v[i];
+              for (int i = 0; i < 16; ++i)
+                sum[c * 16 + i] += __uint_as_float(h[i]) + __uint_as_float(lo[i]);
+            } else {
+              float v[16];
+              tmem_ld16(lane_base + col, v);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) sum[c * 16 + i] += v[i];
+            }
           }
         }
         tc_fence_before();
