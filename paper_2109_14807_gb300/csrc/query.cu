@@ -224,12 +224,15 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
                                                      unsigned long long* counter, int chunk) {
   constexpr int QPW = 32 / LANES;  // queries per warp step
   constexpr int NC = 32 / LANES;   // conceptual lanes per lane
-  // per warp: the terms of its current batch of 32 queries (blockDim.x <= 256)
-  __shared__ float4 tslots[8][32][6];
+  // per warp: the terms of its current batch of 32 queries (blockDim.x <= 256),
+  // packed into 3 float4 (4 with fractional x, y): small integers share words
+  // and the zero-width bins are derived from the material by the reader
+  constexpr int NS = FXY ? 4 : 3;
+  __shared__ float4 tslots[8][32][NS];
   const int lane = threadIdx.x & 31;
   const int sub = lane / LANES;
   const int j = lane % LANES;
-  float4 (*slots)[6] = tslots[threadIdx.x >> 5];
+  float4 (*slots)[NS] = tslots[threadIdx.x >> 5];
   // a grab is `chunk` batches of 32 queries; lane k of the warp loads and
   // evaluates query k of a batch (one batch ahead: the HBM latency of the
   // descriptors overlaps the previous batch) and stores its terms in the
@@ -285,36 +288,44 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
           if (flags & 2) set_status(status, GSP_DEV_BAD_QUERY);
         }
         __syncwarp();  // every lane is done with the previous batch's slots
-        slots[lane][0] = make_float4(__int_as_float(ixk), __int_as_float(iyk), __int_as_float(tk.l0),
-                                     __int_as_float(tk.l1));
-        slots[lane][1] = make_float4(tk.f, __int_as_float(tk.is0), __int_as_float(tk.is1),
-                                     __int_as_float(tk.it0));
-        slots[lane][2] = make_float4(__int_as_float(tk.it1), tk.fs0, tk.fs1, tk.ft0);
-        slots[lane][3] = make_float4(tk.ft1, tk.inv_ws, tk.inv_wt, __int_as_float(tk.isz));
-        slots[lane][4] = make_float4(__int_as_float(tk.itz), __int_as_float(mk), __int_as_float(flags), wxk);
-        slots[lane][5] = make_float4(wyk, 0.f, 0.f, 0.f);
+        // l0, l1 < 64 levels, material < 256, flags < 4; bins <= 4096 < 2^16
+        const int small = tk.l0 | (tk.l1 << 8) | (mk << 16) | (flags << 24);
+        slots[lane][0] = make_float4(__int_as_float(ixk), __int_as_float(iyk), __int_as_float(small),
+                                     __int_as_float(tk.is0 | (tk.is1 << 16)));
+        slots[lane][1] = make_float4(__int_as_float(tk.it0 | (tk.it1 << 16)), tk.f, tk.fs0, tk.fs1);
+        slots[lane][2] = make_float4(tk.ft0, tk.ft1, tk.inv_ws, tk.inv_wt);
+        if constexpr (FXY) slots[lane][3] = make_float4(wxk, wyk, 0.f, 0.f);
         __syncwarp();
       }
       for (int it = 0; it < LANES; ++it) {
         const int slot = it * QPW + sub;
         const long long qi = bbase + slot;
-        const float4 s4 = slots[slot][4];
-        const int flags = __float_as_int(s4.z);
+        const float4 s0 = slots[slot][0];
+        const int small = __float_as_int(s0.z);
+        const int flags = small >> 24;
+        float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (flags == 1) s1 = slots[slot][1];
+        // the second level row only when a query of this warp step blends two
+        // levels (with weight 0 the blend is the first row exactly)
+        const bool blend = __any_sync(0xffffffffu, flags == 1 && s1.y != 0.0f);
         float acc[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) acc[k] = 0.0f;
         {
           if (flags == 1) {  // in range and well formed
-            const float4 s0 = slots[slot][0], s1 = slots[slot][1], s2 = slots[slot][2], s3 = slots[slot][3];
+            const float4 s2 = slots[slot][2];
+            const int mi = (small >> 16) & 0xFF;
+            const gsp_material& M = mp.m[mi];
             QTerms t;
             t.x = __float_as_int(s0.x); t.y = __float_as_int(s0.y);
-            t.l0 = __float_as_int(s0.z); t.l1 = __float_as_int(s0.w);
-            t.f = s1.x; t.is0 = __float_as_int(s1.y); t.is1 = __float_as_int(s1.z); t.it0 = __float_as_int(s1.w);
-            t.it1 = __float_as_int(s2.x); t.fs0 = s2.y; t.fs1 = s2.z; t.ft0 = s2.w;
-            t.ft1 = s3.x; t.inv_ws = s3.y; t.inv_wt = s3.z; t.isz = __float_as_int(s3.w);
-            t.itz = __float_as_int(s4.x);
+            t.l0 = small & 0xFF; t.l1 = (small >> 8) & 0xFF;
+            const int ps = __float_as_int(s0.w), pt = __float_as_int(s1.x);
+            t.is0 = ps & 0xFFFF; t.is1 = ps >> 16; t.it0 = pt & 0xFFFF; t.it1 = pt >> 16;
+            t.f = s1.y; t.fs0 = s1.z; t.fs1 = s1.w;
+            t.ft0 = s2.x; t.ft1 = s2.y; t.inv_ws = s2.z; t.inv_wt = s2.w;
+            t.isz = min(t.is0, M.bins - 1);
+            t.itz = min(t.it0, M.bins - 1);
             t.ok = true;
-            const gsp_material& M = mp.m[__float_as_int(s4.y)];
             const int R = M.rank;
             const float* __restrict__ flw = M.tables;
             const float* sats = M.tables + flw_floats(M.levels, R);
@@ -325,8 +336,9 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
             const float* __restrict__ fyr1 = fyr;
             float wx = 0.f, wy = 0.f;
             if constexpr (FXY) {  // x, y hold floor of the float position; wx, wy the blend
-              wx = s4.w;
-              wy = slots[slot][5].x;
+              const float4 s3 = slots[slot][3];
+              wx = s3.x;
+              wy = s3.y;
               const int N = M.N, ix = t.x, iy = t.y;
               fxr = M.fx + static_cast<size_t>(ix & (N - 1)) * R;
               fxr1 = M.fx + static_cast<size_t>((ix + 1) & (N - 1)) * R;
@@ -343,7 +355,12 @@ __global__ void __launch_bounds__(256) k_range_query(const __grid_constant__ Mat
                 if (rb < R) {
                   float a0[V], a1[V], xv[V], yv[V], S[V], T[V];
                   ldg_n<V>(fl0 + rb, a0);
-                  ldg_n<V>(fl1 + rb, a1);
+                  if (blend) {
+                    ldg_n<V>(fl1 + rb, a1);
+                  } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) a1[v] = 0.0f;
+                  }
                   ldg_n<V>(fxr + rb, xv);
                   ldg_n<V>(fyr + rb, yv);
                   sat_mean<V>(sats, R, rb, t.is0, t.is1, t.fs0, t.fs1, t.inv_ws, t.isz, S);
