@@ -837,6 +837,15 @@ LstCfg lst_cfg(int R, bool split, int MB) {
   return best;
 }
 
+// SMs the persistent passes occupy: all but one, which stays free for the
+// FP64 Gram solve that gsp_cp_sweeps runs on its side stream under each pass
+// (a single-CTA kernel: with every SM held by the pass it waited for the
+// pass to end, 0.2 ms per sweep at rank 64).
+int pass_sms() {
+  const int n = sm_count();
+  return n > 1 ? n - 1 : 1;
+}
+
 template <typename K>
 int set_smem(K kernel, size_t bytes) {
   GSP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -880,7 +889,7 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
   GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2t(), 128));
   GSP_TRY(make_map(&mK, KRt, elem, brows, static_cast<long long>(d.L) * d.B2(), brows));
   const int n_tiles = static_cast<int>(d.N2() / 128);
-  int grid = sm_count() * kXyCtasPerSm;
+  int grid = pass_sms() * kXyCtasPerSm;
   if (grid > n_tiles) grid = n_tiles;
   const size_t smem = xy_smem(d.R, split);
   const int stages = xy_stages(d.R, split);
@@ -906,7 +915,7 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
 int tc_lst_ctas(const MttkrpDims& d) {
   int MB = 0;
   const int G = lst_groups(d, &MB);
-  int P = lst_ctas_per_sm(d.R, MB) * sm_count() / G;
+  int P = lst_ctas_per_sm(d.R, MB) * pass_sms() / G;
   if (P < d.L) P = d.L;  // a range is then at most one level long: <= 2 segments
   if (P > kLstMaxRanges) P = kLstMaxRanges;
   return P;
