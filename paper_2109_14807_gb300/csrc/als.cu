@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
   hadamard_v(G, R, skip, V, ld);
   __syncthreads();
   const double mx = max_diag(V, R, ld);
-  bool ok = cholesky_inplace(V, R, ld, R * eps * mx, invd_s);
+  bool ok = cholesky_packed(V, R, ld, R * eps * mx, invd_s);
   if (!ok) {
     if (threadIdx.x == 0 && flags) atomicOr(flags, GSP_DEV_NUMERIC);
     if (R <= kJacobiMaxRank) {
@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
       if (threadIdx.x == 0)
         for (int k = 0; k < R; ++k) V[k * ld + k] += deltas[t] * mx;
       __syncthreads();
-      ok = cholesky_inplace(V, R, ld, R * eps * mx, invd_s);
+      ok = cholesky_packed(V, R, ld, R * eps * mx, invd_s);
     }
     if (!ok) {  // give up on this update: A = 0, lambda = 0 for the mode
       for (int e = threadIdx.x; e < R * R; e += blockDim.x) ss.W[e] = 0.0;

@@ -63,6 +63,50 @@ __device__ inline bool cholesky_inplace(double* V, int R, int ld, double thresh,
   return true;
 }
 
+// The same factorisation with the work of every step packed densely over the
+// CTA's threads.  FP64 runs at about two FMAs per clock per SM on this GPU, so
+// a warp instruction with idle lanes costs as much as a full one; a fixed
+// thread grid over the shrinking trailing triangle left most lanes idle.  Step
+// j: threads j < i < R form s_i = A_ij / A_jj; after a barrier the
+// (R-1-j)(R-j)/2 trailing elements A_ik (j < k <= i) are dealt out to the
+// threads in turn (row of element e from a table), A_ik -= s_i A_kj; a second
+// barrier ends the step.  Columns are scaled at the end as in
+// cholesky_inplace, with the same result: L in the lower triangle of V and
+// invd = 1 / diag(L).
+__device__ inline bool cholesky_packed(double* V, int R, int ld, double thresh, double* invd) {
+  __shared__ double srow[kMaxSolveRank];
+  __shared__ double piv[kMaxSolveRank];
+  __shared__ unsigned char tri_row[kMaxSolveRank * (kMaxSolveRank - 1) / 2];
+  // row r of element e = r (r + 1) / 2 + c (c <= r) of a triangle enumerated by rows
+  for (int r = threadIdx.x; r < R - 1; r += blockDim.x)
+    for (int c = 0; c <= r; ++c) tri_row[r * (r + 1) / 2 + c] = static_cast<unsigned char>(r);
+  __syncthreads();
+  for (int j = 0; j < R; ++j) {
+    const double d = V[j * ld + j];  // final since step j - 1
+    if (!(d > thresh)) return false;  // every thread reads the same pivot
+    const int i = j + 1 + static_cast<int>(threadIdx.x);
+    if (threadIdx.x == 0) piv[j] = d;
+    if (i < R) srow[i] = V[i * ld + j] * recip_newton(d);
+    __syncthreads();
+    const int n = R - 1 - j;
+    const int ne = n * (n + 1) / 2;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const int r = tri_row[e];
+      const int ii = j + 1 + r, kk = j + 1 + (e - r * (r + 1) / 2);
+      V[ii * ld + kk] = fma(-srow[ii], V[kk * ld + j], V[ii * ld + kk]);
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < R; j += blockDim.x) invd[j] = 1.0 / sqrt(piv[j]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, j = e % R;
+    if (j <= i) V[i * ld + j] *= invd[j];
+  }
+  __syncthreads();
+  return true;
+}
+
 __device__ inline double max_diag(const double* V, int R, int ld) {
   __shared__ double mx;
   if (threadIdx.x == 0) {

@@ -359,3 +359,34 @@ def test_bench_shape_workspace_is_a_few_gb():
     nb = lib_.gsp_cp_workspace_bytes_for_bins(w["N"], w["levels"], w["bins"], w["rank"],
                                               _lib.PREC["bf16"], n)
     assert 0 < nb < 4 << 30
+
+
+@pytest.mark.parametrize("prec", ["fp32", "structured"])
+def test_singular_gram_system_takes_the_pseudo_inverse(prec):
+    # every texel has the same normal, so T = B^2/4 e_b (x) e_b on every footprint:
+    # an exactly rank-1 tensor.  After the first sweep the x, y, s and t factors
+    # have rank 1, so the Hadamard products of the Gram matrices have rank at
+    # most L < R: the Cholesky must fail and the update comes from the Jacobi
+    # pseudo-inverse (a numeric fallback).  The factors still fit the tensor:
+    # the residual of their reconstruction, computed explicitly on the dense
+    # tensor, is at FP32 level.  The fit the sweeps report comes from the Gram
+    # formula 1 - sqrt(|T|^2 + |T^|^2 - 2 <T, T^>) / |T|, which cancels near a
+    # fit of 1: FP32-level MTTKRP rounding (~1e-7) leaves it within ~1e-3 of the
+    # FP64 oracle's CP-ALS (numpy pinv), which reaches 1.
+    import paper_2109_14807_gb300 as g
+    N, L, B, R, sweeps = 16, 5, 8, 16, 4
+    m = np.zeros((N, N, 2), dtype=np.float32)
+    m[..., 0], m[..., 1] = 0.3, -0.2
+    s, t = ndf.bin_index(m, B)
+    assert len(np.unique(s * B + t)) == 1
+    X = ndf.logical(ndf.normalised_tensor(ndf.footprint_histograms(s, t, L, B), B))
+    init = synth.init_factors(N, L, B, R, 4100)
+    _, _, ofits = _oracle_fits(X, R, init, sweeps)
+    f, fits, fb = g.cp_decompose(R, init, normal_xy=dev(m), levels=L, bins=B, sweeps=sweeps,
+                                 precision=prec)
+    assert fb > 0
+    assert np.max(np.abs(np.array(fits) - ofits)) <= 2e-3, (fits, ofits)
+    fd = {k: v.double().cpu().numpy() for k, v in f.items()}
+    That = cp.reconstruct(fd["lambda"], [fd[k] for k in ("fx", "fy", "fl", "fs", "ft")])
+    resid = np.linalg.norm((X - That).ravel()) / np.linalg.norm(X.ravel())
+    assert resid <= 1e-5, resid
