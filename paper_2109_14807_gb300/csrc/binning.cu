@@ -6,11 +6,18 @@
 // box sums of per-bin indicators staged in shared memory, so the only HBM
 // traffic is the output itself.  Every value is an integer count, exact in
 // the types it passes through (FP16 <= 2^11, FP32 < 2^24), hence bit-exact.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
+
+#include <cstring>
 
 #include "ndf_build.cuh"
 
 namespace gsp {
+
+// The driver's tensor-map encoder (mttkrp_tc.cu), null without a driver.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 
 namespace {
 
@@ -89,362 +96,461 @@ __device__ __forceinline__ void sink_sumsq(const LevelSink& o, int4 v, bool acti
 //
 // CTA (group of 16 bins, band of `ychunk` rows, level l): shared memory holds
 // V[x][b] = number of texels of bin g0 + b in column x among the window rows
-// [y - a, y - a + w) (w = 2^l, a = w/2, wrapped).  Moving from row y to y+1
-// removes one texel and adds one per column.  For each row the histograms of
-// all N footprints are window sums of V along x, read from the prefix sum S
-// over x: two look-ups per count, three across the wrap.
-//  - updates: thread t owns the columns x = t, t + 512, ... (no atomics); V
-//    holds FP16 counts (<= 2^10, exact), updated by exact +-1 adds;
-//  - prefix: warp w covers a contiguous x range in blocks of 32 columns; the
-//    inclusive prefix of a block is a lower-triangular ones matrix times the
-//    block's [32 x 16] counts, six warp MMAs (m16n8k16, FP16 in, FP32 out,
-//    exact since every sum is an integer below 2^24); block totals carry in
-//    FP32, and S is stored (as int) once the offsets of the earlier ranges
-//    are known;
-//  - rows of V (48 B) are padded so that the ldmatrix row reads of consecutive
-//    columns fall on distinct banks; S is kept as two planes of 8 bins (32-byte
-//    rows) whose offsets differ by 16 mod 128 bytes, so the output's reads
-//    (lane pairs per column, one plane each) fall on distinct banks;
-//  - S is double-buffered, so the scan of row y and the output of row y - 1
-//    share one phase: two barriers per row.
-constexpr int kHistG = 16;
-constexpr int kHistThreads = 512;
-constexpr int kHistWarps = kHistThreads / 32;
-constexpr int kVRow = 24;  // uint16 per column count row (16 + 8 padding)
-constexpr int kSRow = 8;   // ints per prefix row of one 8-bin plane
-constexpr int kMaxBlocks = 2;  // 32-column blocks per scanning warp (N <= 1024)
+// [y - a, y - a + w) (w = 2^l, a = w/2, wrapped), exact FP16 counts (<= 2^10).
+// Moving from row y to y + 1 removes one texel and adds one per column.  The
+// counts of the footprints of row y are window sums of V along x, taken by
+// warp MMAs: the 16 footprints x = X0 + i (i < 16) have the window columns
+// s0 + i + [0, w), s0 = X0 - a, so that
+//     C = A1 V[s0, s0 + 16) + A2 V[s0 + w2, s0 + w2 + 16) + M,
+//     A1[i][j] = [i <= j < i + w],  A2[i][j] = [w2 + j < i + w],  w2 = max(w, 16),
+// with M the sum of V over [s0 + 16, s0 + w) (w > 16): whole 16-column tiles
+// (s0 is a multiple of 16 there), added from per-tile totals TT of V.  Every
+// product is a count times 0 or 1 and every partial sum an integer below
+// 2^24, exact in FP32 whatever the order.  The accumulator starts at
+// M + 2^23, so that the FP32 bits of the result are 0x4B000000 + count.
+//  - warp w owns a contiguous range of columns: it updates their V and TT
+//    (the TT by shared-memory integer reductions) and computes the footprints
+//    x of that range, so one barrier separates the reads of V and TT from
+//    their update and one the update from the next row's reads;
+//  - V rows are 32 bytes with their 16-byte halves swapped on bit 2 of x, so
+//    the ldmatrix row reads of 8 consecutive columns fall on distinct banks;
+//  - BF16 results go by stmatrix into a per-warp staging buffer in the same
+//    swizzle (the TMA 32-byte swizzle) and out by one TMA bulk store per warp
+//    and row; the other outputs are stored from the accumulator fragments.
+constexpr int kBhG = 16;
+constexpr int kBhThreads = 256;
+constexpr int kBhWarps = kBhThreads / 32;
+constexpr int kBhCtasPerSm = 3;
+constexpr int kTTRow = 20;     // ints per tile-total row (16 + 4 padding)
+constexpr int kFillRows = 16;  // window rows loaded per batch of the fill
 
-// Ints per S plane: N + 1 rows of 8, padded so that the second plane starts 4
-// ints (16 bytes) past a multiple of 32 ints from the first.
-__host__ __device__ constexpr int s_plane_ints(int N) {
-  return (N + 1) * kSRow + (((4 - (N + 1) * kSRow) % 32) + 32) % 32;
+// Columns owned by one warp (N <= 1024): N / 8 from N = 128 on, else 16 (the
+// first N / 16 warps) or N (one warp, N < 16).
+__host__ __device__ constexpr int bh_cols_per_warp(int N) {
+  return N >= 128 ? N / kBhWarps : (N >= 16 ? 16 : N);
 }
+
+// Byte offset of half h (bins 8h .. 8h + 7) of row x in a buffer of 32-byte
+// rows (16 BF16 / FP16 values), halves swapped on bit 2 of x.
+__device__ __forceinline__ uint32_t row32_off(int x, int h) {
+  return static_cast<uint32_t>(x) * 32u + static_cast<uint32_t>((h ^ (x >> 2)) & 1) * 16u;
+}
+
+// Position of bin b in a tile-total row: the bins fc, fc + 1, fc + 8, fc + 9
+// of the accumulator lanes with fc = 2g are the 4 ints at 4g.
+__device__ __forceinline__ int tt_pos(int b) { return 4 * ((b & 7) >> 1) + 2 * (b >> 3) + (b & 1); }
 
 // Four 8x8 b16 matrices from shared memory, transposed into the B-fragment
 // layout of mma.m16n8k16 (lanes 8i..8i+7 give the row addresses of matrix i).
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr)
+  asm("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+      : "r"(addr)
+      : "memory");
+}
+
+// Four 8x8 b16 matrices in the accumulator-fragment layout (lane: row lane/4,
+// elements 2 (lane%4) and +1) to shared memory (lanes 8i..8i+7: rows of matrix i).
+__device__ __forceinline__ void stsm_x4(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2,
+                                        uint32_t r3) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+               "r"(r0), "r"(r1), "r"(r2), "r"(r3)
                : "memory");
 }
 
 // D = A B + C, A 16x16 and B 16x8 FP16, C and D FP32 (warp-level MMA).
 __device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                           uint32_t b1, const float (&c)[4]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
       "{%8, %9}, {%10, %11, %12, %13};"
       : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]),
         "f"(c[2]), "f"(c[3]));
 }
 
-// An exact non-negative integer below 2^23 held in a float, as an int.
-__device__ __forceinline__ int float_to_int_exact(float v) {
-  return __float_as_int(v + 8388608.0f) - 0x4B000000;
+// (x, y) * s + nb in one packed FP32 instruction, each lane rounded once.
+__device__ __forceinline__ float2 fma2(float x, float y, float s, float nb) {
+  unsigned long long v, sv, nv, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(x), "f"(y));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(sv) : "f"(s));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(nv) : "f"(nb));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(v), "l"(sv), "l"(nv));
+  float2 o;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+  return o;
 }
 
-__global__ void __launch_bounds__(kHistThreads, 1)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(src), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// The staging buffer may be written again once the copies have read it.
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait0() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+// Generic-proxy writes of shared memory made visible to the TMA (async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The bin codes of CPL consecutive columns (CPL = 1, 2, 4) of one row, packed
+// as in memory; missing ones read 0xFFFF (no bin).
+template <int CPL>
+__device__ __forceinline__ uint2 load_codes(const uint16_t* p) {
+  if constexpr (CPL == 1) {
+    return make_uint2(0xFFFF0000u | __ldg(p), 0xFFFFFFFFu);
+  } else if constexpr (CPL == 2) {
+    return make_uint2(__ldg(reinterpret_cast<const unsigned int*>(p)), 0xFFFFFFFFu);
+  } else {
+    return __ldg(reinterpret_cast<const uint2*>(p));
+  }
+}
+__device__ __forceinline__ int code_at(uint2 v, int c) {
+  const uint32_t u = c < 2 ? v.x : v.y;
+  return static_cast<int>((c & 1) ? u >> 16 : u & 0xFFFFu);
+}
+
+// V[x][b] += d (one owner thread per column x).
+__device__ __forceinline__ void v_add(uint8_t* Vb, int x, int b, __half d) {
+  __half* p = reinterpret_cast<__half*>(Vb + row32_off(x, b >> 3) + (b & 7) * 2);
+  *p = __hadd(*p, d);
+}
+
+// Output of one launch: exactly one of int32 counts, FP32 values, BF16 values
+// (through the TMA), or none (sums of squares only).
+enum BhMode { kBhSumsq = 0, kBhBf16 = 1, kBhF32 = 2, kBhInt = 3 };
+
+// Zero counts for a CTA whose 16-bin group holds no texel of the map.
+__device__ void box_hist_zero(int logN, int B2, int ychunk, int y0, int l, int g0,
+                              const HistOut& o) {
+  const int N = 1 << logN;
+  const int row_log = logN + 1;  // N * (16 / 8) items of 8 bins per row
+  const long long items = static_cast<long long>(ychunk) << row_log;
+  const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+  for (long long e = threadIdx.x; e < items; e += kBhThreads) {
+    const int yy = y0 + static_cast<int>(e >> row_log);
+    const int rem = static_cast<int>(e & ((1LL << row_log) - 1));
+    const int x = rem >> 1, h = rem & 1;
+    const long long i8 = (((static_cast<long long>(l) * N + yy) * N * B2) >> 3) +
+                         ((static_cast<long long>(x) * B2 + g0) >> 3) + h;
+    if (o.h) {
+      reinterpret_cast<uint4*>(o.h)[2 * i8] = z4;
+      reinterpret_cast<uint4*>(o.h)[2 * i8 + 1] = z4;
+    }
+    if (o.f32) {
+      reinterpret_cast<uint4*>(o.f32)[2 * i8] = z4;
+      reinterpret_cast<uint4*>(o.f32)[2 * i8 + 1] = z4;
+    }
+    if (o.bf16) reinterpret_cast<uint4*>(o.bf16)[i8] = z4;
+  }
+}
+
+// CPL: columns per lane (N / 256 for N >= 512, else 1).  MODE kBhBf16 writes
+// through `tmap`: the BF16 tensor as [levels * N * N][B2], box 16 bins x
+// bh_cols_per_warp(N) rows, 32-byte swizzle.
+template <int CPL, int MODE>
+__global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     k_box_hist(const uint16_t* __restrict__ bins_map, int logN, int B2, int ychunk,
-               const __grid_constant__ HistOut o) {
-  constexpr int G = kHistG;
-  extern __shared__ __align__(16) uint8_t smem_b[];
-  __shared__ __align__(16) float WT[kHistWarps * G];
+               const __grid_constant__ HistOut o, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ uint8_t smem_raw[];
   const int N = 1 << logN, m = N - 1;
-  const int vrows = N < 32 ? 32 : N;                                          // whole 32-column blocks
-  __half* V = reinterpret_cast<__half*>(smem_b);                              // [vrows][24]
-  int* S = reinterpret_cast<int*>(smem_b + vrows * kVRow * sizeof(__half));  // [2][2][N + 1][8]
-  const int plane = s_plane_ints(N), sbuf = 2 * plane;
-  const int g0 = blockIdx.x * G;
+  const int g0 = blockIdx.x * kBhG;
   const int y0 = blockIdx.y * ychunk;
   const int l = gridDim.z - 1 - blockIdx.z;  // coarsest level first: its window fill is the longest
   const int w = 1 << l, a = w >> 1;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (o.groups && !((o.groups[blockIdx.x >> 5] >> (blockIdx.x & 31)) & 1u)) {
-    // no texel of the map falls in this bin group: every count is zero
-    // items of 8 bins (16-byte BF16 stores; two 16-byte stores for 32-bit outputs)
-    const int row_log = logN + 1;  // N * (G / 8) items per row
-    const long long items = static_cast<long long>(ychunk) << row_log;
-    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-    for (long long e = tid; e < items; e += kHistThreads) {
-      const int yy = y0 + static_cast<int>(e >> row_log);
-      const int rem = static_cast<int>(e & ((1LL << row_log) - 1));
-      const int x = rem >> 1, h = rem & 1;
-      const long long i8 = (((static_cast<long long>(l) * N + yy) * N * B2) >> 3) +
-                           ((static_cast<long long>(x) * B2 + g0) >> 3) + h;
-      if (o.h) {
-        reinterpret_cast<uint4*>(o.h)[2 * i8] = z4;
-        reinterpret_cast<uint4*>(o.h)[2 * i8 + 1] = z4;
-      }
-      if (o.f32) {
-        reinterpret_cast<uint4*>(o.f32)[2 * i8] = z4;
-        reinterpret_cast<uint4*>(o.f32)[2 * i8 + 1] = z4;
-      }
-      if (o.bf16) reinterpret_cast<uint4*>(o.bf16)[i8] = z4;
-    }
+    if (MODE != kBhSumsq) box_hist_zero(logN, B2, ychunk, y0, l, g0, o);
     return;
   }
-  const int scan_warps = N >= 32 * kHistWarps ? kHistWarps : (N >= 32 ? N >> 5 : 1);
-  const int xr = N / scan_warps;               // columns per scanning warp
-  const int nblk = xr >= 32 ? xr >> 5 : 1;     // 32-column blocks per warp
-  // Prefix over a 32-column block by warp MMA: S_block = [Tri; Ones Tri] V_block
-  // with Tri the 16x16 lower-triangular ones.  Counts (<= 2^10) are exact in
-  // FP16 and every sum (< 2^24) in FP32, whatever the accumulation order.
-  const int fr = lane >> 2, fc = 2 * (lane & 3);  // fragment row / column pair of this lane
-  uint32_t aTri[4], aOne[4];
-  {
-    auto tri = [](int mm, int kk) -> uint32_t { return kk <= mm ? 0x3C00u : 0u; };
-    aTri[0] = tri(fr, fc) | (tri(fr, fc + 1) << 16);
-    aTri[1] = tri(fr + 8, fc) | (tri(fr + 8, fc + 1) << 16);
-    aTri[2] = tri(fr, fc + 8) | (tri(fr, fc + 9) << 16);
-    aTri[3] = tri(fr + 8, fc + 8) | (tri(fr + 8, fc + 9) << 16);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) aOne[i] = 0x3C003C00u;
-  }
-  // ldmatrix row address of this lane: matrix q = lane / 8 covers k rows
-  // (q & 1) * 8 .. + 7 and bins (q >> 1) * 8 .. + 7 of a 16-column half block
-  const uint32_t v_lane = static_cast<uint32_t>(__cvta_generic_to_shared(V)) +
-                          static_cast<uint32_t>((((lane >> 3) & 1) * 8 + (lane & 7)) * kVRow +
-                                                (lane >> 4) * 8) * 2u;
+  const int cw = bh_cols_per_warp(N);
+  const int T = N >= 16 ? N >> 4 : 1;  // 16-column tiles
+  const int xw = warp * cw;            // first column of this warp
+  const bool owner = xw < N;
+  const bool lane_cols = owner && lane * CPL < cw;
+  const int xl = xw + lane * CPL;  // first column of this lane
+  const int ntile = cw >= 16 ? cw >> 4 : 1;
+  const int vcols = N < 16 ? 16 : N;
+  const uint32_t raw_s = static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw));
+  const uint32_t pad = (1024u - (raw_s & 1023u)) & 1023u;
+  const uint32_t srow_bytes = static_cast<uint32_t>((cw < 16 ? 16 : cw) * 32);  // staging per warp
+  const uint32_t stage_bytes = MODE == kBhBf16 ? kBhWarps * srow_bytes : 0u;
+  uint8_t* Vb = smem_raw + pad + stage_bytes;
+  int* TT = reinterpret_cast<int*>(Vb + vcols * 32);  // [T][kTTRow] tile totals of V (tt_pos order)
+  const uint32_t v_s = raw_s + pad + stage_bytes;
+  const uint32_t st_s = raw_s + pad + static_cast<uint32_t>(warp) * srow_bytes;
 
-  for (int i = tid; i < vrows * kVRow / 8; i += kHistThreads)
-    reinterpret_cast<uint4*>(V)[i] = make_uint4(0, 0, 0, 0);
-  if (tid < 8)  // S[0] = 0 in both planes of both buffers
-    reinterpret_cast<int4*>(S + (tid >> 2) * sbuf + ((tid >> 1) & 1) * plane)[tid & 1] =
-        make_int4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < vcols * 2; i += kBhThreads)
+    reinterpret_cast<uint4*>(Vb)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
-  {
-    // the window's rows for this thread's columns x = tid, tid + 512:
-    // 16 rows x 2 columns of independent loads in flight (N <= 2 * kHistThreads)
-    constexpr int kRows = 16;
-    for (int j0 = 0; j0 < w; j0 += kRows) {
-      uint16_t code[2][kRows];
+  const __half one = __float2half(1.0f), mone = __float2half(-1.0f);
+  if (lane_cols) {
+    // the window rows of row y0, kFillRows rows of loads in flight
+    for (int j0 = 0; j0 < w; j0 += kFillRows) {
+      uint2 raw[kFillRows];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int x = tid + k * kHistThreads;
+      for (int u = 0; u < kFillRows; ++u)
+        raw[u] = j0 + u < w ? load_codes<CPL>(bins_map + (((y0 - a + j0 + u) & m) << logN) + xl)
+                            : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
 #pragma unroll
-        for (int u = 0; u < kRows; ++u)
-          code[k][u] = (x < N && j0 + u < w) ? bins_map[(((y0 - a + j0 + u) & m) << logN) + x]
-                                              : static_cast<uint16_t>(0xFFFFu);
-      }
+      for (int u = 0; u < kFillRows; ++u) {
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int x = tid + k * kHistThreads;
-#pragma unroll
-        for (int u = 0; u < kRows; ++u) {
-          const int b = static_cast<int>(code[k][u]) - g0;
-          if (static_cast<unsigned>(b) < static_cast<unsigned>(G))
-            V[x * kVRow + b] = __hadd(V[x * kVRow + b], __float2half(1.0f));
+        for (int c = 0; c < CPL; ++c) {
+          const int b = code_at(raw[u], c) - g0;
+          if (static_cast<unsigned>(b) < static_cast<unsigned>(kBhG)) v_add(Vb, xl + c, b, one);
         }
       }
     }
   }
-  const float sc = o.scale[l];
-  const float nb = -8388608.0f * sc;  // -2^23 * scale, exact
-  // codes leaving / entering the window at the next row step, loaded one row
-  // ahead so the L2 latency overlaps this row's work (N <= 2 * kHistThreads)
-  int nxt_out[2], nxt_in[2];
-  auto fetch = [&](int yn) {
-    const int ro = (yn - 1 - a) & m, ri = (yn - 1 - a + w) & m;
+
+  const int fr = lane >> 2, fc = 2 * (lane & 3);  // accumulator row / column pair of this lane
+  // row and half of the 8x8 matrices this lane addresses in ldmatrix /
+  // stmatrix: matrix q = lane / 8 covers rows (q & 1) * 8 .. + 7 and bins
+  // (q >> 1) * 8 .. + 7 of a 16 x 16 block
+  const int lrow = ((lane >> 3) & 1) * 8 + (lane & 7), lhalf = lane >> 4;
+  const bool need_tt = l >= 5;  // whole tiles inside the window
+  const float kOff = 8388608.0f;  // 2^23
+  const uint32_t kOffBits = 0x4B000000u;
+  if (need_tt && owner) {  // tile totals of row y0: an all-ones A times each tile
+    __syncwarp();
+    uint32_t ones[4];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int x = tid + k * kHistThreads;
-      nxt_out[k] = x < N ? static_cast<int>(bins_map[(ro << logN) + x]) : 0xFFFF;
-      nxt_in[k] = x < N ? static_cast<int>(bins_map[(ri << logN) + x]) : 0xFFFF;
+    for (int i = 0; i < 4; ++i) ones[i] = 0x3C003C00u;
+    const float off4[4] = {kOff, kOff, kOff, kOff};
+    for (int k = 0; k < ntile; ++k) {
+      const int x0 = xw + 16 * k;
+      uint32_t bv[4];
+      ldsm_x4_trans(v_s + row32_off(x0 + lrow, lhalf), bv);
+      float t0[4], t1[4];
+      mma_16816(t0, ones, bv[0], bv[1], off4);
+      mma_16816(t1, ones, bv[2], bv[3], off4);
+      if (lane < 4)  // bins fc, fc + 1, fc + 8, fc + 9 at tt_pos
+        *reinterpret_cast<int4*>(TT + (x0 >> 4) * kTTRow + 4 * lane) =
+            make_int4(static_cast<int>(__float_as_uint(t0[0]) - kOffBits),
+                      static_cast<int>(__float_as_uint(t0[1]) - kOffBits),
+                      static_cast<int>(__float_as_uint(t1[0]) - kOffBits),
+                      static_cast<int>(__float_as_uint(t1[1]) - kOffBits));
+    }
+  }
+
+  // A fragments (row-major 16 x 16 FP16; lane: rows fr, fr + 8, columns fc,
+  // fc + 1 and fc + 8, fc + 9) of the two window matrices
+  const int w2 = w > 16 ? w : 16;
+  uint32_t A1[4], A2[4];
+  {
+    auto a1 = [&](int i, int j) -> uint32_t { return (i <= j && j < i + w) ? 0x3C00u : 0u; };
+    auto a2 = [&](int i, int j) -> uint32_t { return (w2 + j < i + w) ? 0x3C00u : 0u; };
+    A1[0] = a1(fr, fc) | (a1(fr, fc + 1) << 16);
+    A1[1] = a1(fr + 8, fc) | (a1(fr + 8, fc + 1) << 16);
+    A1[2] = a1(fr, fc + 8) | (a1(fr, fc + 9) << 16);
+    A1[3] = a1(fr + 8, fc + 8) | (a1(fr + 8, fc + 9) << 16);
+    A2[0] = a2(fr, fc) | (a2(fr, fc + 1) << 16);
+    A2[1] = a2(fr + 8, fc) | (a2(fr + 8, fc + 1) << 16);
+    A2[2] = a2(fr, fc + 8) | (a2(fr, fc + 9) << 16);
+    A2[3] = a2(fr + 8, fc + 8) | (a2(fr + 8, fc + 9) << 16);
+  }
+  // This lane's ldmatrix rows of the two column ranges of the warp's first
+  // tile: a byte offset into V that advances by 16 columns (512 bytes) per
+  // tile, modulo the N columns, plus the half swap (bit 2 of the column, the
+  // same for every tile since N and the step are multiples of 16).
+  const int x1 = (xw - a + lrow) & m, x2 = (xw - a + w2 + lrow) & m;
+  const uint32_t vmask = static_cast<uint32_t>(N * 32 - 1);
+  const uint32_t va1 = v_s + (static_cast<uint32_t>((lhalf ^ (x1 >> 2)) & 1) << 4);
+  const uint32_t va2 = v_s + (static_cast<uint32_t>((lhalf ^ (x2 >> 2)) & 1) << 4);
+  const uint32_t vo1 = static_cast<uint32_t>(x1) * 32u, vo2 = static_cast<uint32_t>(x2) * 32u;
+  // stmatrix row of this lane in the staging buffer (tile k adds 512 bytes)
+  const uint32_t st_lane = st_s + static_cast<uint32_t>(lrow) * 32u +
+                           (static_cast<uint32_t>((lhalf ^ (lrow >> 2)) & 1) << 4);
+
+  // codes leaving / entering the window at the next row step, loaded one row
+  // ahead so the L2 latency overlaps this row's work
+  uint2 nxt_out = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu), nxt_in = nxt_out;
+  auto fetch = [&](int yn) {
+    if (lane_cols) {
+      nxt_out = load_codes<CPL>(bins_map + (((yn - 1 - a) & m) << logN) + xl);
+      nxt_in = load_codes<CPL>(bins_map + (((yn - 1 - a + w) & m) << logN) + xl);
     }
   };
-  fetch(y0 + 1);
-  unsigned long long sumsq = 0;
-  // The output items of this thread (x = e / 2, plane h = e % 2 for
-  // e = tid + k * 512, k < 2N / 512) are the same in every row: their prefix
-  // offsets within an S buffer (ints), the wrap term and the column part of
-  // the output index are computed once.  S[N] + S[en - N] replaces S[en] for
-  // a window that wraps (wr >= 0).
-  constexpr int kMaxItems = 4;  // 2N / kHistThreads for N <= 1024
-  int it_lo[kMaxItems], it_hi[kMaxItems], it_wr[kMaxItems], it_col[kMaxItems];
-#pragma unroll
-  for (int k = 0; k < kMaxItems; ++k) {
-    const int e = tid + k * kHistThreads;
-    const int h = e & 1, x = e >> 1;
-    const int st = (x - a) & m, en = st + w;
-    it_lo[k] = h * plane + st * kSRow;
-    it_hi[k] = h * plane + (en <= N ? en : N) * kSRow;
-    it_wr[k] = en <= N ? -1 : h * plane + (en - N) * kSRow;
-    it_col[k] = ((x * B2 + g0) >> 3) + h;
-  }
-  __syncthreads();  // V of row y0 complete (columns are initialised by other warps)
+  if (ychunk > 1) fetch(y0 + 1);
 
-  // Pipelined over rows with S double-buffered: iteration y scans row y (V
-  // holds its window) while writing the counts of row y - 1 from the other S
-  // buffer; after the barrier the scan's range offsets are applied, S of row y
-  // is stored and V moves on to row y + 1.  Two barriers per row.
-  for (int y = y0; y <= y0 + ychunk; ++y) {
-    const bool scan_row = y < y0 + ychunk;
-    int* Sc = S + ((y - y0) & 1) * sbuf;        // S of row y
-    const int* Sp = S + ((y - y0 + 1) & 1) * sbuf;  // S of row y - 1
-    // inclusive prefix of each block, per lane: [block][nt][row group][2 bins]
-    float pre[kMaxBlocks][2][4][2];
-    if (scan_row && warp < scan_warps) {
-      float carry[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-      const int xbeg = warp * xr;
-#pragma unroll
-      for (int blk = 0; blk < kMaxBlocks; ++blk) {
-        if (blk < nblk) {
-          const int xb = xbeg + blk * 32;
-          uint32_t bk0[4], bk1[4];  // B fragments of columns xb..xb+15 and xb+16..xb+31
-          ldsm_x4_trans(v_lane + static_cast<uint32_t>(xb * kVRow * 2), bk0);
-          ldsm_x4_trans(v_lane + static_cast<uint32_t>((xb + 16) * kVRow * 2), bk1);
-          const float zero[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-          for (int nt = 0; nt < 2; ++nt) {
-            float top[4], bot[4];
-            mma_16816(top, aTri, bk0[2 * nt], bk0[2 * nt + 1], zero);
-            mma_16816(bot, aOne, bk0[2 * nt], bk0[2 * nt + 1], zero);
-            mma_16816(bot, aTri, bk1[2 * nt], bk1[2 * nt + 1], bot);
-            pre[blk][nt][0][0] = top[0] + carry[nt][0];
-            pre[blk][nt][0][1] = top[1] + carry[nt][1];
-            pre[blk][nt][1][0] = top[2] + carry[nt][0];
-            pre[blk][nt][1][1] = top[3] + carry[nt][1];
-            pre[blk][nt][2][0] = bot[0] + carry[nt][0];
-            pre[blk][nt][2][1] = bot[1] + carry[nt][1];
-            pre[blk][nt][3][0] = bot[2] + carry[nt][0];
-            pre[blk][nt][3][1] = bot[3] + carry[nt][1];
-            // block total: row 31 (lanes 28..31 hold it for their bin pairs)
-            carry[nt][0] = __shfl_sync(0xffffffffu, pre[blk][nt][3][0], 28 + (lane & 3));
-            carry[nt][1] = __shfl_sync(0xffffffffu, pre[blk][nt][3][1], 28 + (lane & 3));
-          }
+  const float sc = o.scale[l];
+  const float nb = -kOff * sc;  // -2^23 * scale, exact
+  const uint32_t dK8r = static_cast<uint32_t>(8 * B2) * kWeyl;    // dither step of 8 rows
+  const uint32_t dKtile = static_cast<uint32_t>(16 * B2) * kWeyl;  // ... and of one tile
+  const int ta = a >> 4, wt = w >> 4;                              // in tiles (l >= 5)
+  const int* tt_lane = TT + 2 * fc;  // this lane's 4 bins of a tile-total row
+  unsigned long long sumsq = 0;
+  __syncthreads();  // V and TT of row y0 complete
+
+  for (int y = y0; y < y0 + ychunk; ++y) {
+    if (owner) {
+      // middle sums of the warp's first tile: the 8 lanes of one column pair
+      // take every 8th tile, then add up
+      uint32_t Mb[4] = {0u, 0u, 0u, 0u};  // bins fc, fc + 1, fc + 8, fc + 9
+      if (need_tt) {
+        const int u0 = (xw >> 4) - ta + 1;
+        for (int q = fr; q < wt - 1; q += 8) {
+          const int4 p = *reinterpret_cast<const int4*>(tt_lane + ((u0 + q) & (T - 1)) * kTTRow);
+          Mb[0] += p.x; Mb[1] += p.y; Mb[2] += p.z; Mb[3] += p.w;
         }
+#pragma unroll
+        for (int off = 4; off < 32; off <<= 1)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) Mb[i] += __shfl_xor_sync(0xffffffffu, Mb[i], off);
       }
-      if (lane < 4) {  // range totals of bins fc, fc + 1 (plane 0) and fc + 8, fc + 9
-        WT[warp * G + fc] = carry[0][0];
-        WT[warp * G + fc + 1] = carry[0][1];
-        WT[warp * G + 8 + fc] = carry[1][0];
-        WT[warp * G + 8 + fc + 1] = carry[1][1];
+      // accumulator inputs per n-tile (rows fr, fr + 8 alike): FP32 bits of 2^23 + M
+      uint32_t Cq[2][4];
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        Cq[n][0] = Cq[n][2] = Mb[2 * n] + kOffBits;
+        Cq[n][1] = Cq[n][3] = Mb[2 * n + 1] + kOffBits;
       }
-    }
-    if (y > y0) {
-      // counts of every footprint of row y - 1, eight bins per item; the lanes
-      // of a warp take consecutive x, so their 16-byte prefix reads (80-byte
-      // rows) fall on distinct banks
-      const long long row8 = ((static_cast<long long>(l) * N + (y - 1)) * N * B2) >> 3;
+      if (MODE == kBhBf16 && y > y0) {  // the previous row's store has read the staging buffer
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+      }
+      const long long e_row = (static_cast<long long>(l) * N + y) * N;  // footprint index of x = 0
+      uint32_t d00 = (static_cast<uint32_t>(e_row) * static_cast<uint32_t>(B2) +
+                      static_cast<uint32_t>((xw + fr) * B2 + g0 + fc)) * kWeyl;
+      uint32_t o1 = vo1, o2 = vo2;
+#pragma unroll 2
+      for (int k = 0; k < ntile; ++k) {
+        uint32_t bA[4], bB[4];
+        ldsm_x4_trans(va1 + o1, bA);
+        ldsm_x4_trans(va2 + o2, bB);
+        o1 = (o1 + 512u) & vmask;
+        o2 = (o2 + 512u) & vmask;
+        float D[2][4];
+        mma_16816(D[0], A1, bA[0], bA[1], reinterpret_cast<const float(&)[4]>(Cq[0]));
+        mma_16816(D[1], A1, bA[2], bA[3], reinterpret_cast<const float(&)[4]>(Cq[1]));
+        mma_16816(D[0], A2, bB[0], bB[1], D[0]);
+        mma_16816(D[1], A2, bB[2], bB[3], D[1]);
+        if (need_tt && k + 1 < ntile) {  // middle sums of the next tile
+          const int t = (xw >> 4) + k;
+          const int4 lo = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + 1) & (T - 1)) * kTTRow);
+          const int4 hi = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + wt) & (T - 1)) * kTTRow);
+          const int dm[4] = {hi.x - lo.x, hi.y - lo.y, hi.z - lo.z, hi.w - lo.w};
 #pragma unroll
-      for (int k = 0; k < kMaxItems; ++k) {
-        if (tid + k * kHistThreads >= 2 * N) break;  // lane pairs write 32 contiguous bytes
-        const int4* lo4 = reinterpret_cast<const int4*>(Sp + it_lo[k]);
-        const int4* hi4 = reinterpret_cast<const int4*>(Sp + it_hi[k]);
-        int c[8];
-        {
-          const int4 l0 = lo4[0], l1 = lo4[1];
-          int4 h0 = hi4[0], h1 = hi4[1];
-          if (it_wr[k] >= 0) {  // window wraps: S[N] - S[st] + S[en - N]
-            const int4* wr = reinterpret_cast<const int4*>(Sp + it_wr[k]);
-            const int4 w0 = wr[0], w1 = wr[1];
-            h0 = make_int4(h0.x + w0.x, h0.y + w0.y, h0.z + w0.z, h0.w + w0.w);
-            h1 = make_int4(h1.x + w1.x, h1.y + w1.y, h1.z + w1.z, h1.w + w1.w);
+          for (int n = 0; n < 2; ++n) {
+            Cq[n][0] += dm[2 * n]; Cq[n][2] += dm[2 * n];
+            Cq[n][1] += dm[2 * n + 1]; Cq[n][3] += dm[2 * n + 1];
           }
-          c[0] = h0.x - l0.x; c[1] = h0.y - l0.y; c[2] = h0.z - l0.z; c[3] = h0.w - l0.w;
-          c[4] = h1.x - l1.x; c[5] = h1.y - l1.y; c[6] = h1.z - l1.z; c[7] = h1.w - l1.w;
         }
-        const long long i8 = row8 + it_col[k];
-        if (o.h) {
-          reinterpret_cast<int4*>(o.h)[2 * i8] = make_int4(c[0], c[1], c[2], c[3]);
-          reinterpret_cast<int4*>(o.h)[2 * i8 + 1] = make_int4(c[4], c[5], c[6], c[7]);
-        }
-        // c * scale, exactly: 2^23 + c as a float (c < 2^23), times the
-        // power-of-two scale, minus 2^23 * scale, in one rounding
-        float f[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) f[k] = fmaf(__int_as_float(c[k] | 0x4B000000), sc, nb);
-        const uint32_t d = weyl_dither(static_cast<unsigned long long>(i8) * 8);
-        if (o.f32) {
-          if (o.tf32 && l >= 6) {  // counts <= 4^5 are exact on the TF32 grid
-#pragma unroll
-            for (int k = 0; k < 8; ++k) f[k] = tf32_dither(f[k], d + k * kWeyl);
-          }
-          reinterpret_cast<float4*>(o.f32)[2 * i8] = make_float4(f[0], f[1], f[2], f[3]);
-          reinterpret_cast<float4*>(o.f32)[2 * i8 + 1] = make_float4(f[4], f[5], f[6], f[7]);
-        }
-        if (o.bf16 && l <= 4) {  // counts <= 256: exact in BF16
-          uint4 p;
-          p.x = __byte_perm(__float_as_uint(f[0]), __float_as_uint(f[1]), 0x7632);
-          p.y = __byte_perm(__float_as_uint(f[2]), __float_as_uint(f[3]), 0x7632);
-          p.z = __byte_perm(__float_as_uint(f[4]), __float_as_uint(f[5]), 0x7632);
-          p.w = __byte_perm(__float_as_uint(f[6]), __float_as_uint(f[7]), 0x7632);
-          reinterpret_cast<uint4*>(o.bf16)[i8] = p;
-        } else if (o.bf16) {
-          uint4 p;
-          p.x = bf16_pair_dither(f[0], d, f[1], d + kWeyl);
-          p.y = bf16_pair_dither(f[2], d + 2 * kWeyl, f[3], d + 3 * kWeyl);
-          p.z = bf16_pair_dither(f[4], d + 4 * kWeyl, f[5], d + 5 * kWeyl);
-          p.w = bf16_pair_dither(f[6], d + 6 * kWeyl, f[7], d + 7 * kWeyl);
-          reinterpret_cast<uint4*>(o.bf16)[i8] = p;
-        }
+        // D[n][2r + e]: bits 0x4B000000 + count of footprint x = X0 + fr + 8r, bin g0 + 8n + fc + e
         if (o.sumsq) {
           if (l <= 7) {  // counts <= 4^7: eight squares fit in 32 bits
             uint32_t q = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) q += static_cast<uint32_t>(c[k]) * static_cast<uint32_t>(c[k]);
+            for (int i = 0; i < 8; ++i) {
+              const uint32_t c = __float_as_uint(D[i >> 2][i & 3]) - kOffBits;
+              q += c * c;
+            }
             sumsq += q;
           } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-              sumsq += static_cast<unsigned long long>(static_cast<uint32_t>(c[k])) * static_cast<uint32_t>(c[k]);
+            for (int i = 0; i < 8; ++i) {
+              const uint32_t c = __float_as_uint(D[i >> 2][i & 3]) - kOffBits;
+              sumsq += static_cast<unsigned long long>(c) * c;
+            }
           }
+        }
+        if constexpr (MODE == kBhBf16 || MODE == kBhF32) {
+          // c * scale, exactly: (2^23 + c) * scale - 2^23 * scale in one rounding
+          float2 f[2][2];
+#pragma unroll
+          for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) f[n][r] = fma2(D[n][2 * r], D[n][2 * r + 1], sc, nb);
+          // Weyl dither of element (n, r, e): d00 + r * dK8r + (8n + e) * kWeyl
+          if constexpr (MODE == kBhBf16) {
+            uint32_t wd[2][2];
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+              for (int r = 0; r < 2; ++r) {
+                if (l <= 4) {  // counts <= 256: exact in BF16
+                  wd[n][r] = __byte_perm(__float_as_uint(f[n][r].x), __float_as_uint(f[n][r].y), 0x7632);
+                } else {
+                  const uint32_t d = d00 + (r ? dK8r : 0u) + static_cast<uint32_t>(8 * n) * kWeyl;
+                  wd[n][r] = bf16_pair_dither(f[n][r].x, d, f[n][r].y, d + kWeyl);
+                }
+              }
+            stsm_x4(st_lane + 512u * static_cast<uint32_t>(k), wd[0][0], wd[0][1], wd[1][0], wd[1][1]);
+          } else {
+            const long long e00 = (e_row + xw + 16 * k + fr) * B2 + g0 + fc;
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+              for (int r = 0; r < 2; ++r) {
+                float2 v = f[n][r];
+                if (o.tf32 && l >= 6) {  // counts <= 4^5 are exact on the TF32 grid
+                  const uint32_t d = d00 + (r ? dK8r : 0u) + static_cast<uint32_t>(8 * n) * kWeyl;
+                  v = make_float2(tf32_dither(v.x, d), tf32_dither(v.y, d + kWeyl));
+                }
+                if (N >= 16 || fr + 8 * r < N)
+                  *reinterpret_cast<float2*>(o.f32 + e00 + r * 8LL * B2 + 8 * n) = v;
+              }
+          }
+        } else if constexpr (MODE == kBhInt) {
+          const long long e00 = (e_row + xw + 16 * k + fr) * B2 + g0 + fc;
+#pragma unroll
+          for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+              if (N >= 16 || fr + 8 * r < N)
+                *reinterpret_cast<int2*>(o.h + e00 + r * 8LL * B2 + 8 * n) =
+                    make_int2(static_cast<int>(__float_as_uint(D[n][2 * r]) - kOffBits),
+                              static_cast<int>(__float_as_uint(D[n][2 * r + 1]) - kOffBits));
+        }
+        d00 += dKtile;
+      }
+      if constexpr (MODE == kBhBf16) {  // this warp's footprints of row y: one bulk store
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&tmap, st_s, g0, static_cast<int>(e_row + xw));
+          bulk_commit();
         }
       }
     }
-    __syncthreads();  // range totals WT complete; V and S of row y - 1 no longer read
-    if (scan_row) {
-      if (warp < scan_warps) {
-        // offset of this warp's range: lanes 0..15 sum one bin each over the earlier warps
-        float my = 0.f;
-        if (lane < G) {
+    __syncthreads();  // V and TT of row y no longer read
+    if (y + 1 < y0 + ychunk) {
+      if (lane_cols) {  // V and TT: window of row y + 1
+        int* tr = TT + (xl >> 4) * kTTRow;  // the lane's columns share one tile
 #pragma unroll
-          for (int k = 0; k < kHistWarps; ++k)  // independent loads, then the sum
-            if (k < warp) my += WT[k * G + lane];
-        }
-        float off[2][2];
-        off[0][0] = __shfl_sync(0xffffffffu, my, fc);
-        off[0][1] = __shfl_sync(0xffffffffu, my, fc + 1);
-        off[1][0] = __shfl_sync(0xffffffffu, my, fc + 8);
-        off[1][1] = __shfl_sync(0xffffffffu, my, fc + 9);
-        const int xbeg = warp * xr;
-#pragma unroll
-        for (int blk = 0; blk < kMaxBlocks; ++blk) {
-          if (blk < nblk) {
-#pragma unroll
-            for (int rg = 0; rg < 4; ++rg) {
-              const int x = xbeg + blk * 32 + rg * 8 + fr;  // rows fr, fr+8, 16+fr, 24+fr
-              if (x < N) {
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                  int2* dst = reinterpret_cast<int2*>(Sc + nt * plane + (x + 1) * kSRow + fc);
-                  *dst = make_int2(float_to_int_exact(pre[blk][nt][rg][0] + off[nt][0]),
-                                   float_to_int_exact(pre[blk][nt][rg][1] + off[nt][1]));
-                }
-              }
+        for (int c = 0; c < CPL; ++c) {
+          const int co = code_at(nxt_out, c), ci = code_at(nxt_in, c);
+          if (co != ci) {
+            const int bo = co - g0, bi = ci - g0;
+            if (static_cast<unsigned>(bo) < static_cast<unsigned>(kBhG)) {
+              v_add(Vb, xl + c, bo, mone);
+              if (need_tt) atomicAdd(tr + tt_pos(bo), -1);
+            }
+            if (static_cast<unsigned>(bi) < static_cast<unsigned>(kBhG)) {
+              v_add(Vb, xl + c, bi, one);
+              if (need_tt) atomicAdd(tr + tt_pos(bi), 1);
             }
           }
         }
       }
-      if (y + 1 < y0 + ychunk) {  // V: window of row y + 1
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int x = tid + k * kHistThreads;
-          const int bo = nxt_out[k] - g0, bi = nxt_in[k] - g0;
-          if (x < N && static_cast<unsigned>(bo) < static_cast<unsigned>(G))
-            V[x * kVRow + bo] = __hsub(V[x * kVRow + bo], __float2half(1.0f));
-          if (x < N && static_cast<unsigned>(bi) < static_cast<unsigned>(G))
-            V[x * kVRow + bi] = __hadd(V[x * kVRow + bi], __float2half(1.0f));
-        }
-        if (y + 2 < y0 + ychunk) fetch(y + 2);
-      }
+      if (y + 2 < y0 + ychunk) fetch(y + 2);
+      __syncthreads();  // V and TT of row y + 1 complete
     }
-    __syncthreads();  // S of row y and V of row y + 1 complete; WT read
   }
+  if (MODE == kBhBf16 && owner && lane == 0) bulk_wait0();
   if (o.sumsq) {
     for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
+    // N < 16: the 16 rows of the one tile hold each footprint 16 / N times
+    if (N < 16) sumsq >>= 4 - logN;
     if (lane == 0 && sumsq) atomicAdd(o.sumsq + l, sumsq);
   }
 }
@@ -462,6 +568,52 @@ __global__ void k_cast(const int4* __restrict__ in, long long total, LevelSink o
 
 constexpr int kThreads = 256;
 
+size_t box_hist_smem(int N, bool bf16) {
+  const size_t cw = static_cast<size_t>(bh_cols_per_warp(N));
+  const size_t stage = bf16 ? kBhWarps * (cw < 16 ? 16 : cw) * 32 : 0;
+  const size_t v = static_cast<size_t>(N < 16 ? 16 : N) * 32;
+  const size_t tt = static_cast<size_t>(N >= 16 ? N / 16 : 1) * kTTRow * sizeof(int);
+  return 1024 + stage + v + tt;  // 1024: alignment of the staging buffers
+}
+
+// TMA store map of the BF16 tensor viewed as [rows][B2], box 16 bins x
+// box_rows rows, 32-byte swizzle (the staging layout of k_box_hist).
+int make_bf16_store_map(CUtensorMap* map, void* base, long long rows, int B2, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return GSP_ERR_UNSUPPORTED;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(B2), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(B2) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBhG), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? GSP_OK : GSP_ERR_CUDA;
+}
+
+template <int CPL, int MODE>
+int launch_box_hist_mode(const uint16_t* d_bins, int N, int B2, int ychunk, dim3 grid, size_t smem,
+                         const HistOut& o, const CUtensorMap& tm, cudaStream_t s) {
+  GSP_CUDA(cudaFuncSetAttribute(k_box_hist<CPL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem)));
+  prof_begin(PROF_DOUBLE, s);
+  k_box_hist<CPL, MODE><<<grid, kBhThreads, smem, s>>>(d_bins, ilog2(N), B2, ychunk, o, tm);
+  prof_end(PROF_DOUBLE, s);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
+template <int CPL>
+int launch_box_hist_cpl(const uint16_t* d_bins, int N, int B2, int ychunk, dim3 grid, size_t smem,
+                        const HistOut& o, int mode, const CUtensorMap& tm, cudaStream_t s) {
+  switch (mode) {
+    case kBhBf16: return launch_box_hist_mode<CPL, kBhBf16>(d_bins, N, B2, ychunk, grid, smem, o, tm, s);
+    case kBhF32: return launch_box_hist_mode<CPL, kBhF32>(d_bins, N, B2, ychunk, grid, smem, o, tm, s);
+    case kBhInt: return launch_box_hist_mode<CPL, kBhInt>(d_bins, N, B2, ychunk, grid, smem, o, tm, s);
+    default: return launch_box_hist_mode<CPL, kBhSumsq>(d_bins, N, B2, ychunk, grid, smem, o, tm, s);
+  }
+}
+
 }  // namespace
 
 int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins, uint32_t* d_status,
@@ -476,41 +628,30 @@ int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins, uin
   return GSP_OK;
 }
 
-size_t box_hist_smem(int N) {
-  return static_cast<size_t>(N < 32 ? 32 : N) * kVRow * sizeof(__half) +
-         4 * static_cast<size_t>(s_plane_ints(N)) * sizeof(int);
-}
-
 int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const HistOut& o,
                     cudaStream_t s) {
-  if (B2 % kHistG) return GSP_ERR_UNSUPPORTED;
-  // Rows per CTA: of 256, 128 and 64 (at most N), the largest whose grid fills
-  // the waves of one-CTA-per-SM residency to at least 90 %, else the best
-  // filling one (the window fill, at most N rows of 2-byte L2 reads, is small
-  // next to 64 rows of output).
-  const int sms = sm_count();
-  int ychunk = N >= 256 ? 256 : N;
-  double best = -1.0;
-  for (int yc = ychunk; yc >= 64; yc >>= 1) {
-    const long long ctas = static_cast<long long>(B2 / kHistG) * (N / yc) * levels;
-    const long long waves = (ctas + sms - 1) / sms;
-    const double fill = static_cast<double>(ctas) / static_cast<double>(waves * sms);
-    if (fill > best + 1e-9) {
-      best = fill;
-      ychunk = yc;
-    }
-    if (fill >= 0.9) break;
+  if (B2 % kBhG || N > 1024) return GSP_ERR_UNSUPPORTED;
+  if ((o.h != nullptr) + (o.f32 != nullptr) + (o.bf16 != nullptr) > 1) return GSP_ERR_UNSUPPORTED;
+  const int mode = o.h ? kBhInt : o.f32 ? kBhF32 : o.bf16 ? kBhBf16 : kBhSumsq;
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  if (mode == kBhBf16) {
+    if (reinterpret_cast<uintptr_t>(o.bf16) & 15) return GSP_ERR_UNSUPPORTED;
+    GSP_TRY(make_bf16_store_map(&tm, o.bf16, static_cast<long long>(levels) * N * N, B2,
+                                bh_cols_per_warp(N)));
   }
-  const size_t smem = box_hist_smem(N);
+  // Rows per CTA: 64 (at most N).  A CTA of level l takes about a window fill
+  // of w = 2^l rows (2-byte L2 reads per column) plus 64 rows of output; with
+  // the coarsest levels launched first and two or more waves of kBhCtasPerSm
+  // CTAs per SM, the short fine-level CTAs fill in behind the long ones (256,
+  // 128 and 32 rows were slower on the 1024^2, 11-level, 80-column operand).
+  const int ychunk = N < 64 ? N : 64;
+  const size_t smem = box_hist_smem(N, mode == kBhBf16);
   if (smem > 227 * 1024) return GSP_ERR_UNSUPPORTED;
-  dim3 grid(B2 / kHistG, N / ychunk, levels);
-  GSP_CUDA(cudaFuncSetAttribute(k_box_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem)));
-  prof_begin(PROF_DOUBLE, s);
-  k_box_hist<<<grid, kHistThreads, smem, s>>>(d_bins, ilog2(N), B2, ychunk, o);
-  prof_end(PROF_DOUBLE, s);
-  GSP_CHECK_LAUNCH();
-  return GSP_OK;
+  dim3 grid(B2 / kBhG, N / ychunk, levels);
+  if (N >= 1024) return launch_box_hist_cpl<4>(d_bins, N, B2, ychunk, grid, smem, o, mode, tm, s);
+  if (N >= 512) return launch_box_hist_cpl<2>(d_bins, N, B2, ychunk, grid, smem, o, mode, tm, s);
+  return launch_box_hist_cpl<1>(d_bins, N, B2, ychunk, grid, smem, o, mode, tm, s);
 }
 
 int launch_cast(const int32_t* d_in, int N, int bins, LevelSink o, cudaStream_t s) {

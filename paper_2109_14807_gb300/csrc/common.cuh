@@ -108,9 +108,19 @@ __device__ __forceinline__ uint32_t bf16_dither(float v, uint32_t d) {
   return (__float_as_uint(v) + (d >> 16)) >> 16;
 }
 
-// Two BF16 values (element 0 in the low half) as one 32-bit word.
+// Two BF16 values (element 0 in the low half) as one 32-bit word, each the
+// bf16_dither of its own value and dither.  The stochastic-rounding convert
+// takes the random bits of element 0 from the low half of its operand and
+// those of element 1 from the high half, adds them below the kept bits and
+// truncates: given the top halves of d0 and d1, the same as bf16_dither (the
+// CP operand prepared from histograms takes bf16_dither and the one from the
+// normal map this form; the GPU tests require the two to agree).
 __device__ __forceinline__ uint32_t bf16_pair_dither(float v0, uint32_t d0, float v1, uint32_t d1) {
-  return __byte_perm(__float_as_uint(v0) + (d0 >> 16), __float_as_uint(v1) + (d1 >> 16), 0x7632);
+  uint32_t r;
+  asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;"
+      : "=r"(r)
+      : "f"(v1), "f"(v0), "r"(__byte_perm(d0, d1, 0x7632)));
+  return r;
 }
 
 // v >= 0 on the TF32 grid (10 fraction bits), rounded without bias.

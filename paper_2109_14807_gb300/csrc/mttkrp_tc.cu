@@ -750,6 +750,10 @@ __global__ void k_lst_reduce(const float* __restrict__ Zpart, float* __restrict_
 
 // ----------------------------------------------------------- host side --
 
+}  // namespace
+
+// The driver's cuTensorMapEncodeTiled (null without a driver); shared with the
+// histogram build.
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -763,6 +767,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   });
   return fn;
 }
+
+namespace {
 
 // 2D map over a row-major [rows][cols] matrix, box = [box_rows][128 bytes], 128B swizzle.
 int make_map(CUtensorMap* map, const void* base, int elem, long long rows, long long cols,
