@@ -1312,6 +1312,11 @@ extern "C" int gsp_cp_prepare(const int32_t* d_hist, const float* d_normal_xy, i
     else
       o.f32 = c.at<float>(c.lay.T);
     o.tf32 = c.prec == GSP_PREC_TF32;
+    // the Y' array is not read before the first sweep: it holds the column
+    // prefix scratch of the histogram build when that fits
+    const size_t yp_bytes = static_cast<size_t>(N) * N * static_cast<size_t>(d.R) * sizeof(float);
+    const size_t cp_bytes = col_prefix_bytes(N, Bt);
+    if (cp_bytes > 0 && cp_bytes <= yp_bytes) o.colp = c.at<__half>(c.lay.Yp);
     GSP_TRY(launch_box_hist(bm, N, levels, Bt, o, c.s));
   }
   k_norm2<<<1, 32, 0, c.s>>>(sumsq, levels, bins, opts->raw_counts, c.at<double>(c.lay.norm2));

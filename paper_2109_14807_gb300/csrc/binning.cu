@@ -225,6 +225,68 @@ __device__ __forceinline__ void v_add(uint8_t* Vb, int x, int b, __half d) {
   *p = __hadd(*p, d);
 }
 
+// Column prefix sums over 64-row blocks, the starting windows of the coarse
+// levels: P[k][x][b] = number of texels of bin b in column x among the rows
+// [0, 64k), k = 0 .. N / 64, as exact FP16 counts (<= N <= 1024).  First the
+// count of each block (thread: column x, block k, 16-bin group; counts of 2
+// bins per 32-bit word), then the running sum over k in place.
+__global__ void k_col_blocks(const uint16_t* __restrict__ bins_map, int logN, int B2,
+                             const uint32_t* __restrict__ groups, __half* __restrict__ P) {
+  const int N = 1 << logN;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y, g = blockIdx.z;
+  if (x >= N || (groups && !((groups[g >> 5] >> (g & 31)) & 1u))) return;
+  const int g0 = g * 16;
+  uint32_t cnt[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll 8
+  for (int r = 0; r < 64; ++r) {
+    const int b = static_cast<int>(__ldg(bins_map + ((64 * k + r) << logN) + x)) - g0;
+    const uint32_t inc = static_cast<unsigned>(b) < 16u ? 1u << ((b & 1) << 4) : 0u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cnt[q] += q == (b >> 1) ? inc : 0u;
+  }
+  // count c (< 1024) as FP16: the bits of 1024 + c are 0x6400 + c; minus 1024
+  uint32_t hw[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const __half2 v = __hsub2(__halves2half2(__ushort_as_half(static_cast<unsigned short>(0x6400u + (cnt[q] & 0xFFFFu))),
+                                             __ushort_as_half(static_cast<unsigned short>(0x6400u + (cnt[q] >> 16)))),
+                              __float2half2_rn(1024.0f));
+    hw[q] = *reinterpret_cast<const uint32_t*>(&v);
+  }
+  uint4* dst = reinterpret_cast<uint4*>(P + (static_cast<long long>(k + 1) * N + x) * B2 + g0);
+  dst[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  dst[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+  if (k == 0) {
+    uint4* z = reinterpret_cast<uint4*>(P + static_cast<long long>(x) * B2 + g0);
+    z[0] = z[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// Thread: column x, half h (8 bins) of a 16-bin group; K = N / 64 <= 16.
+__global__ void k_col_prefix(int logN, int B2, const uint32_t* __restrict__ groups,
+                             __half* __restrict__ P) {
+  const int N = 1 << logN, K = N >> 6;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
+  if (t >= 2 * N || (groups && !((groups[g >> 5] >> (g & 31)) & 1u))) return;
+  const int x = t >> 1, h = t & 1;
+  uint4* col = reinterpret_cast<uint4*>(P + static_cast<long long>(x) * B2 + g * 16 + 8 * h);
+  const long long stride = static_cast<long long>(N) * B2 / 8;  // uint4 per P row
+  uint4 v[16];
+#pragma unroll
+  for (int k = 1; k <= 16; ++k)
+    if (k <= K) v[k - 1] = col[k * stride];
+#pragma unroll
+  for (int k = 2; k <= 16; ++k) {
+    if (k <= K) {
+      __half2* a = reinterpret_cast<__half2*>(&v[k - 1]);
+      const __half2* b = reinterpret_cast<const __half2*>(&v[k - 2]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = __hadd2(a[i], b[i]);
+      col[k * stride] = v[k - 1];
+    }
+  }
+}
+
 // Output of one launch: exactly one of int32 counts, FP32 values, BF16 values
 // (through the TMA), or none (sums of squares only).
 enum BhMode { kBhSumsq = 0, kBhBf16 = 1, kBhF32 = 2, kBhInt = 3 };
@@ -293,7 +355,34 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     reinterpret_cast<uint4*>(Vb)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   const __half one = __float2half(1.0f), mone = __float2half(-1.0f);
-  if (lane_cols) {
+  if (lane_cols && o.colp && l >= 7) {
+    // window rows [s, s + w) of row y0, s a multiple of 64: differences of the
+    // column prefix sums (all counts <= N, exact in FP16)
+    const int K = N >> 6;
+    const int s = (y0 - a) & m, e = s + w;
+    const int ks = s >> 6, ke = e <= N ? e >> 6 : K, kw = e > N ? (e - N) >> 6 : -1;
+#pragma unroll 1
+    for (int c = 0; c < CPL; ++c) {
+      const __half* col = o.colp + static_cast<long long>(xl + c) * B2 + g0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long rs = static_cast<long long>(N) * B2;
+        uint4 vs = *reinterpret_cast<const uint4*>(col + ks * rs + 8 * h);
+        uint4 ve = *reinterpret_cast<const uint4*>(col + ke * rs + 8 * h);
+        __half2* pe = reinterpret_cast<__half2*>(&ve);
+        const __half2* ps = reinterpret_cast<const __half2*>(&vs);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pe[i] = __hsub2(pe[i], ps[i]);
+        if (kw >= 0) {
+          uint4 vw = *reinterpret_cast<const uint4*>(col + kw * rs + 8 * h);
+          const __half2* pw = reinterpret_cast<const __half2*>(&vw);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) pe[i] = __hadd2(pe[i], pw[i]);
+        }
+        *reinterpret_cast<uint4*>(Vb + row32_off(xl + c, h)) = ve;
+      }
+    }
+  } else if (lane_cols) {
     // the window rows of row y0, kFillRows rows of loads in flight
     for (int j0 = 0; j0 < w; j0 += kFillRows) {
       uint2 raw[kFillRows];
@@ -568,6 +657,17 @@ __global__ void k_cast(const int4* __restrict__ in, long long total, LevelSink o
 
 constexpr int kThreads = 256;
 
+int launch_col_prefix(const uint16_t* d_bins, int N, int B2, const uint32_t* groups, __half* P,
+                      cudaStream_t s) {
+  const int logN = ilog2(N);
+  const int tb = N < 256 ? N : 256;
+  k_col_blocks<<<dim3(N / tb, N / 64, B2 / 16), tb, 0, s>>>(d_bins, logN, B2, groups, P);
+  GSP_CHECK_LAUNCH();
+  k_col_prefix<<<dim3(2 * N / tb, B2 / 16), tb, 0, s>>>(logN, B2, groups, P);
+  GSP_CHECK_LAUNCH();
+  return GSP_OK;
+}
+
 size_t box_hist_smem(int N, bool bf16) {
   const size_t cw = static_cast<size_t>(bh_cols_per_warp(N));
   const size_t stage = bf16 ? kBhWarps * (cw < 16 ? 16 : cw) * 32 : 0;
@@ -596,9 +696,7 @@ int launch_box_hist_mode(const uint16_t* d_bins, int N, int B2, int ychunk, dim3
                          const HistOut& o, const CUtensorMap& tm, cudaStream_t s) {
   GSP_CUDA(cudaFuncSetAttribute(k_box_hist<CPL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(smem)));
-  prof_begin(PROF_DOUBLE, s);
   k_box_hist<CPL, MODE><<<grid, kBhThreads, smem, s>>>(d_bins, ilog2(N), B2, ychunk, o, tm);
-  prof_end(PROF_DOUBLE, s);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
 }
@@ -628,6 +726,11 @@ int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins, uin
   return GSP_OK;
 }
 
+size_t col_prefix_bytes(int N, int B2) {
+  if (N < 128) return 0;
+  return static_cast<size_t>(N / 64 + 1) * N * B2 * sizeof(__half);
+}
+
 int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const HistOut& o,
                     cudaStream_t s) {
   if (B2 % kBhG || N > 1024) return GSP_ERR_UNSUPPORTED;
@@ -648,10 +751,21 @@ int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const His
   const int ychunk = N < 64 ? N : 64;
   const size_t smem = box_hist_smem(N, mode == kBhBf16);
   if (smem > 227 * 1024) return GSP_ERR_UNSUPPORTED;
+  HistOut oo = o;
+  if (col_prefix_bytes(N, B2) == 0 || levels <= 7) oo.colp = nullptr;
   dim3 grid(B2 / kBhG, N / ychunk, levels);
-  if (N >= 1024) return launch_box_hist_cpl<4>(d_bins, N, B2, ychunk, grid, smem, o, mode, tm, s);
-  if (N >= 512) return launch_box_hist_cpl<2>(d_bins, N, B2, ychunk, grid, smem, o, mode, tm, s);
-  return launch_box_hist_cpl<1>(d_bins, N, B2, ychunk, grid, smem, o, mode, tm, s);
+  prof_begin(PROF_DOUBLE, s);  // one interval: the prefix table and the histograms
+  int rc = oo.colp ? launch_col_prefix(d_bins, N, B2, o.groups, oo.colp, s) : GSP_OK;
+  if (rc == GSP_OK) {
+    if (N >= 1024)
+      rc = launch_box_hist_cpl<4>(d_bins, N, B2, ychunk, grid, smem, oo, mode, tm, s);
+    else if (N >= 512)
+      rc = launch_box_hist_cpl<2>(d_bins, N, B2, ychunk, grid, smem, oo, mode, tm, s);
+    else
+      rc = launch_box_hist_cpl<1>(d_bins, N, B2, ychunk, grid, smem, oo, mode, tm, s);
+  }
+  prof_end(PROF_DOUBLE, s);
+  return rc;
 }
 
 int launch_cast(const int32_t* d_in, int N, int bins, LevelSink o, cudaStream_t s) {
