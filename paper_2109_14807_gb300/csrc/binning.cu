@@ -11,6 +11,7 @@
 #include <cuda_fp16.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "ndf_build.cuh"
 
@@ -123,6 +124,7 @@ constexpr int kBhWarps = kBhThreads / 32;
 constexpr int kBhCtasPerSm = 3;
 constexpr int kTTRow = 20;     // ints per tile-total row (16 + 4 padding)
 constexpr int kFillRows = 16;  // window rows loaded per batch of the fill
+constexpr int kBhRows = 32;    // rows per CTA, and per block of the column prefix sums
 
 // Columns owned by one warp (N <= 1024): N / 8 from N = 128 on, else 16 (the
 // first N / 16 warps) or N (one warp, N < 16).
@@ -219,17 +221,25 @@ __device__ __forceinline__ int code_at(uint2 v, int c) {
   return static_cast<int>((c & 1) ? u >> 16 : u & 0xFFFFu);
 }
 
-// V[x][b] += d (one owner thread per column x).
-__device__ __forceinline__ void v_add(uint8_t* Vb, int x, int b, __half d) {
-  __half* p = reinterpret_cast<__half*>(Vb + row32_off(x, b >> 3) + (b & 7) * 2);
-  *p = __hadd(*p, d);
+// *p += v for an FP16 value in shared memory (exact here: small integers).
+__device__ __forceinline__ void red_add_f16(uint8_t* p, __half v) {
+  asm volatile("red.shared.add.noftz.f16 [%0], %1;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(p))),
+               "h"(__half_as_ushort(v))
+               : "memory");
 }
 
-// Column prefix sums over 64-row blocks, the starting windows of the coarse
-// levels: P[k][x][b] = number of texels of bin b in column x among the rows
-// [0, 64k), k = 0 .. N / 64, as exact FP16 counts (<= N <= 1024).  First the
-// count of each block (thread: column x, block k, 16-bin group; counts of 2
-// bins per 32-bit word), then the running sum over k in place.
+// V[x][b] += d (one owner thread per column x).
+__device__ __forceinline__ void v_add(uint8_t* Vb, int x, int b, __half d) {
+  red_add_f16(Vb + row32_off(x, b >> 3) + (b & 7) * 2, d);
+}
+
+// Column prefix sums over blocks of kBhRows rows, the starting windows of the
+// coarse levels: P[k][x][b] = number of texels of bin b in column x among the
+// rows [0, k kBhRows), k = 0 .. N / kBhRows, as exact FP16 counts (<= N <=
+// 1024).  First the count of each block (thread: column x, block k, 16-bin
+// group; counts of 2 bins per 32-bit word), then the running sum over k in
+// place.
 __global__ void k_col_blocks(const uint16_t* __restrict__ bins_map, int logN, int B2,
                              const uint32_t* __restrict__ groups, __half* __restrict__ P) {
   const int N = 1 << logN;
@@ -238,8 +248,8 @@ __global__ void k_col_blocks(const uint16_t* __restrict__ bins_map, int logN, in
   const int g0 = g * 16;
   uint32_t cnt[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll 8
-  for (int r = 0; r < 64; ++r) {
-    const int b = static_cast<int>(__ldg(bins_map + ((64 * k + r) << logN) + x)) - g0;
+  for (int r = 0; r < kBhRows; ++r) {
+    const int b = static_cast<int>(__ldg(bins_map + ((kBhRows * k + r) << logN) + x)) - g0;
     const uint32_t inc = static_cast<unsigned>(b) < 16u ? 1u << ((b & 1) << 4) : 0u;
 #pragma unroll
     for (int q = 0; q < 8; ++q) cnt[q] += q == (b >> 1) ? inc : 0u;
@@ -262,27 +272,31 @@ __global__ void k_col_blocks(const uint16_t* __restrict__ bins_map, int logN, in
   }
 }
 
-// Thread: column x, half h (8 bins) of a 16-bin group; K = N / 64 <= 16.
+// Thread: column x, half h (8 bins) of a 16-bin group; rows k = 1 .. N / kBhRows
+// in batches of 8 loads in flight.
 __global__ void k_col_prefix(int logN, int B2, const uint32_t* __restrict__ groups,
                              __half* __restrict__ P) {
-  const int N = 1 << logN, K = N >> 6;
+  const int N = 1 << logN, K = N / kBhRows;
   const int t = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
   if (t >= 2 * N || (groups && !((groups[g >> 5] >> (g & 31)) & 1u))) return;
   const int x = t >> 1, h = t & 1;
   uint4* col = reinterpret_cast<uint4*>(P + static_cast<long long>(x) * B2 + g * 16 + 8 * h);
   const long long stride = static_cast<long long>(N) * B2 / 8;  // uint4 per P row
-  uint4 v[16];
+  __half2 acc[4] = {__float2half2_rn(0.f), __float2half2_rn(0.f), __float2half2_rn(0.f),
+                    __float2half2_rn(0.f)};
+  for (int k0 = 1; k0 <= K; k0 += 8) {
+    uint4 v[8];
 #pragma unroll
-  for (int k = 1; k <= 16; ++k)
-    if (k <= K) v[k - 1] = col[k * stride];
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j <= K) v[j] = col[(k0 + j) * stride];
 #pragma unroll
-  for (int k = 2; k <= 16; ++k) {
-    if (k <= K) {
-      __half2* a = reinterpret_cast<__half2*>(&v[k - 1]);
-      const __half2* b = reinterpret_cast<const __half2*>(&v[k - 2]);
+    for (int j = 0; j < 8; ++j) {
+      if (k0 + j <= K) {
+        __half2* a = reinterpret_cast<__half2*>(&v[j]);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = __hadd2(a[i], b[i]);
-      col[k * stride] = v[k - 1];
+        for (int i = 0; i < 4; ++i) a[i] = acc[i] = __hadd2(acc[i], a[i]);
+        col[(k0 + j) * stride] = v[j];
+      }
     }
   }
 }
@@ -355,12 +369,12 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     reinterpret_cast<uint4*>(Vb)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   const __half one = __float2half(1.0f), mone = __float2half(-1.0f);
-  if (lane_cols && o.colp && l >= 7) {
-    // window rows [s, s + w) of row y0, s a multiple of 64: differences of the
-    // column prefix sums (all counts <= N, exact in FP16)
-    const int K = N >> 6;
+  if (lane_cols && o.colp && a >= kBhRows) {
+    // window rows [s, s + w) of row y0, s a multiple of kBhRows: differences
+    // of the column prefix sums (all counts <= N, exact in FP16)
+    const int K = N / kBhRows;
     const int s = (y0 - a) & m, e = s + w;
-    const int ks = s >> 6, ke = e <= N ? e >> 6 : K, kw = e > N ? (e - N) >> 6 : -1;
+    const int ks = s / kBhRows, ke = e <= N ? e / kBhRows : K, kw = e > N ? (e - N) / kBhRows : -1;
 #pragma unroll 1
     for (int c = 0; c < CPL; ++c) {
       const __half* col = o.colp + static_cast<long long>(xl + c) * B2 + g0;
@@ -480,50 +494,55 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
   unsigned long long sumsq = 0;
   __syncthreads();  // V and TT of row y0 complete
 
-  for (int y = y0; y < y0 + ychunk; ++y) {
-    if (owner) {
-      // middle sums of the warp's first tile: the 8 lanes of one column pair
-      // take every 8th tile, then add up
-      uint32_t Mb[4] = {0u, 0u, 0u, 0u};  // bins fc, fc + 1, fc + 8, fc + 9
-      if (need_tt) {
-        const int u0 = (xw >> 4) - ta + 1;
-        for (int q = fr; q < wt - 1; q += 8) {
-          const int4 p = *reinterpret_cast<const int4*>(tt_lane + ((u0 + q) & (T - 1)) * kTTRow);
-          Mb[0] += p.x; Mb[1] += p.y; Mb[2] += p.z; Mb[3] += p.w;
-        }
-#pragma unroll
-        for (int off = 4; off < 32; off <<= 1)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) Mb[i] += __shfl_xor_sync(0xffffffffu, Mb[i], off);
+  // One row of footprints for the level class LC of l (compile-time, so the
+  // tile loop has no level branches): 0: l <= 4 (counts <= 256, exact in BF16;
+  // no whole tiles in the window), 1: 5 <= l <= 7 (squares of 8 counts fit 32
+  // bits), 2: l >= 8.
+  auto row_out = [&](int y, auto lc_tag) {
+    constexpr int LC = decltype(lc_tag)::value;
+    // middle sums of the warp's first tile: the 8 lanes of one column pair
+    // take every 8th tile, then add up
+    uint32_t Mb[4] = {0u, 0u, 0u, 0u};  // bins fc, fc + 1, fc + 8, fc + 9
+    if constexpr (LC >= 1) {
+      const int u0 = (xw >> 4) - ta + 1;
+      for (int q = fr; q < wt - 1; q += 8) {
+        const int4 p = *reinterpret_cast<const int4*>(tt_lane + ((u0 + q) & (T - 1)) * kTTRow);
+        Mb[0] += p.x; Mb[1] += p.y; Mb[2] += p.z; Mb[3] += p.w;
       }
-      // accumulator inputs per n-tile (rows fr, fr + 8 alike): FP32 bits of 2^23 + M
-      uint32_t Cq[2][4];
 #pragma unroll
-      for (int n = 0; n < 2; ++n) {
-        Cq[n][0] = Cq[n][2] = Mb[2 * n] + kOffBits;
-        Cq[n][1] = Cq[n][3] = Mb[2 * n + 1] + kOffBits;
-      }
-      if (MODE == kBhBf16 && y > y0) {  // the previous row's store has read the staging buffer
-        if (lane == 0) bulk_wait_read0();
-        __syncwarp();
-      }
-      const long long e_row = (static_cast<long long>(l) * N + y) * N;  // footprint index of x = 0
-      uint32_t d00 = (static_cast<uint32_t>(e_row) * static_cast<uint32_t>(B2) +
-                      static_cast<uint32_t>((xw + fr) * B2 + g0 + fc)) * kWeyl;
-      uint32_t o1 = vo1, o2 = vo2;
+      for (int off = 4; off < 32; off <<= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Mb[i] += __shfl_xor_sync(0xffffffffu, Mb[i], off);
+    }
+    // accumulator inputs per n-tile (rows fr, fr + 8 alike): FP32 bits of 2^23 + M
+    uint32_t Cq[2][4];
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      Cq[n][0] = Cq[n][2] = Mb[2 * n] + kOffBits;
+      Cq[n][1] = Cq[n][3] = Mb[2 * n + 1] + kOffBits;
+    }
+    if (MODE == kBhBf16 && y > y0) {  // the previous row's store has read the staging buffer
+      if (lane == 0) bulk_wait_read0();
+      __syncwarp();
+    }
+    const long long e_row = (static_cast<long long>(l) * N + y) * N;  // footprint index of x = 0
+    uint32_t d00 = (static_cast<uint32_t>(e_row) * static_cast<uint32_t>(B2) +
+                    static_cast<uint32_t>((xw + fr) * B2 + g0 + fc)) * kWeyl;
+    uint32_t o1 = vo1, o2 = vo2;
 #pragma unroll 2
-      for (int k = 0; k < ntile; ++k) {
-        uint32_t bA[4], bB[4];
-        ldsm_x4_trans(va1 + o1, bA);
-        ldsm_x4_trans(va2 + o2, bB);
-        o1 = (o1 + 512u) & vmask;
-        o2 = (o2 + 512u) & vmask;
-        float D[2][4];
-        mma_16816(D[0], A1, bA[0], bA[1], reinterpret_cast<const float(&)[4]>(Cq[0]));
-        mma_16816(D[1], A1, bA[2], bA[3], reinterpret_cast<const float(&)[4]>(Cq[1]));
-        mma_16816(D[0], A2, bB[0], bB[1], D[0]);
-        mma_16816(D[1], A2, bB[2], bB[3], D[1]);
-        if (need_tt && k + 1 < ntile) {  // middle sums of the next tile
+    for (int k = 0; k < ntile; ++k) {
+      uint32_t bA[4], bB[4];
+      ldsm_x4_trans(va1 + o1, bA);
+      ldsm_x4_trans(va2 + o2, bB);
+      o1 = (o1 + 512u) & vmask;
+      o2 = (o2 + 512u) & vmask;
+      float D[2][4];
+      mma_16816(D[0], A1, bA[0], bA[1], reinterpret_cast<const float(&)[4]>(Cq[0]));
+      mma_16816(D[1], A1, bA[2], bA[3], reinterpret_cast<const float(&)[4]>(Cq[1]));
+      mma_16816(D[0], A2, bB[0], bB[1], D[0]);
+      mma_16816(D[1], A2, bB[2], bB[3], D[1]);
+      if constexpr (LC >= 1) {
+        if (k + 1 < ntile) {  // middle sums of the next tile
           const int t = (xw >> 4) + k;
           const int4 lo = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + 1) & (T - 1)) * kTTRow);
           const int4 hi = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + wt) & (T - 1)) * kTTRow);
@@ -534,98 +553,114 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
             Cq[n][1] += dm[2 * n + 1]; Cq[n][3] += dm[2 * n + 1];
           }
         }
-        // D[n][2r + e]: bits 0x4B000000 + count of footprint x = X0 + fr + 8r, bin g0 + 8n + fc + e
-        if (o.sumsq) {
-          if (l <= 7) {  // counts <= 4^7: eight squares fit in 32 bits
-            uint32_t q = 0;
+      }
+      // D[n][2r + e]: bits 0x4B000000 + count of footprint x = X0 + fr + 8r, bin g0 + 8n + fc + e
+      if (o.sumsq) {
+        if constexpr (LC <= 1) {  // counts <= 4^7: eight squares fit in 32 bits
+          uint32_t q = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const uint32_t c = __float_as_uint(D[i >> 2][i & 3]) - kOffBits;
-              q += c * c;
-            }
-            sumsq += q;
-          } else {
+          for (int i = 0; i < 8; ++i) {
+            const uint32_t c = __float_as_uint(D[i >> 2][i & 3]) - kOffBits;
+            q += c * c;
+          }
+          sumsq += q;
+        } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const uint32_t c = __float_as_uint(D[i >> 2][i & 3]) - kOffBits;
-              sumsq += static_cast<unsigned long long>(c) * c;
-            }
+          for (int i = 0; i < 8; ++i) {
+            const uint32_t c = __float_as_uint(D[i >> 2][i & 3]) - kOffBits;
+            sumsq += static_cast<unsigned long long>(c) * c;
           }
         }
-        if constexpr (MODE == kBhBf16 || MODE == kBhF32) {
-          // c * scale, exactly: (2^23 + c) * scale - 2^23 * scale in one rounding
-          float2 f[2][2];
+      }
+      if constexpr (MODE == kBhBf16 || MODE == kBhF32) {
+        // c * scale, exactly: (2^23 + c) * scale - 2^23 * scale in one rounding
+        float2 f[2][2];
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+          for (int r = 0; r < 2; ++r) f[n][r] = fma2(D[n][2 * r], D[n][2 * r + 1], sc, nb);
+        // Weyl dither of element (n, r, e): d00 + r * dK8r + (8n + e) * kWeyl
+        if constexpr (MODE == kBhBf16) {
+          uint32_t wd[2][2];
 #pragma unroll
           for (int n = 0; n < 2; ++n)
 #pragma unroll
-            for (int r = 0; r < 2; ++r) f[n][r] = fma2(D[n][2 * r], D[n][2 * r + 1], sc, nb);
-          // Weyl dither of element (n, r, e): d00 + r * dK8r + (8n + e) * kWeyl
-          if constexpr (MODE == kBhBf16) {
-            uint32_t wd[2][2];
-#pragma unroll
-            for (int n = 0; n < 2; ++n)
-#pragma unroll
-              for (int r = 0; r < 2; ++r) {
-                if (l <= 4) {  // counts <= 256: exact in BF16
-                  wd[n][r] = __byte_perm(__float_as_uint(f[n][r].x), __float_as_uint(f[n][r].y), 0x7632);
-                } else {
-                  const uint32_t d = d00 + (r ? dK8r : 0u) + static_cast<uint32_t>(8 * n) * kWeyl;
-                  wd[n][r] = bf16_pair_dither(f[n][r].x, d, f[n][r].y, d + kWeyl);
-                }
+            for (int r = 0; r < 2; ++r) {
+              if constexpr (LC == 0) {  // counts <= 256: exact in BF16
+                wd[n][r] = __byte_perm(__float_as_uint(f[n][r].x), __float_as_uint(f[n][r].y), 0x7632);
+              } else {
+                const uint32_t d = d00 + (r ? dK8r : 0u) + static_cast<uint32_t>(8 * n) * kWeyl;
+                wd[n][r] = bf16_pair_dither(f[n][r].x, d, f[n][r].y, d + kWeyl);
               }
-            stsm_x4(st_lane + 512u * static_cast<uint32_t>(k), wd[0][0], wd[0][1], wd[1][0], wd[1][1]);
-          } else {
-            const long long e00 = (e_row + xw + 16 * k + fr) * B2 + g0 + fc;
-#pragma unroll
-            for (int n = 0; n < 2; ++n)
-#pragma unroll
-              for (int r = 0; r < 2; ++r) {
-                float2 v = f[n][r];
-                if (o.tf32 && l >= 6) {  // counts <= 4^5 are exact on the TF32 grid
-                  const uint32_t d = d00 + (r ? dK8r : 0u) + static_cast<uint32_t>(8 * n) * kWeyl;
-                  v = make_float2(tf32_dither(v.x, d), tf32_dither(v.y, d + kWeyl));
-                }
-                if (N >= 16 || fr + 8 * r < N)
-                  *reinterpret_cast<float2*>(o.f32 + e00 + r * 8LL * B2 + 8 * n) = v;
-              }
-          }
-        } else if constexpr (MODE == kBhInt) {
+            }
+          stsm_x4(st_lane + 512u * static_cast<uint32_t>(k), wd[0][0], wd[0][1], wd[1][0], wd[1][1]);
+        } else {
           const long long e00 = (e_row + xw + 16 * k + fr) * B2 + g0 + fc;
 #pragma unroll
           for (int n = 0; n < 2; ++n)
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+            for (int r = 0; r < 2; ++r) {
+              float2 v = f[n][r];
+              if (o.tf32 && l >= 6) {  // counts <= 4^5 are exact on the TF32 grid
+                const uint32_t d = d00 + (r ? dK8r : 0u) + static_cast<uint32_t>(8 * n) * kWeyl;
+                v = make_float2(tf32_dither(v.x, d), tf32_dither(v.y, d + kWeyl));
+              }
               if (N >= 16 || fr + 8 * r < N)
-                *reinterpret_cast<int2*>(o.h + e00 + r * 8LL * B2 + 8 * n) =
-                    make_int2(static_cast<int>(__float_as_uint(D[n][2 * r]) - kOffBits),
-                              static_cast<int>(__float_as_uint(D[n][2 * r + 1]) - kOffBits));
+                *reinterpret_cast<float2*>(o.f32 + e00 + r * 8LL * B2 + 8 * n) = v;
+            }
         }
-        d00 += dKtile;
+      } else if constexpr (MODE == kBhInt) {
+        const long long e00 = (e_row + xw + 16 * k + fr) * B2 + g0 + fc;
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+            if (N >= 16 || fr + 8 * r < N)
+              *reinterpret_cast<int2*>(o.h + e00 + r * 8LL * B2 + 8 * n) =
+                  make_int2(static_cast<int>(__float_as_uint(D[n][2 * r]) - kOffBits),
+                            static_cast<int>(__float_as_uint(D[n][2 * r + 1]) - kOffBits));
       }
-      if constexpr (MODE == kBhBf16) {  // this warp's footprints of row y: one bulk store
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          tma_store_2d(&tmap, st_s, g0, static_cast<int>(e_row + xw));
-          bulk_commit();
-        }
+      d00 += dKtile;
+    }
+    if constexpr (MODE == kBhBf16) {  // this warp's footprints of row y: one bulk store
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d(&tmap, st_s, g0, static_cast<int>(e_row + xw));
+        bulk_commit();
       }
+    }
+  };
+  // V of this lane's columns: byte offset of bin b in column xl + c is
+  // v_col + 32 c + (2 b ^ v_swz) (the columns share bit 2 of x)
+  uint8_t* const v_col = Vb + static_cast<uint32_t>(xl) * 32u;
+  const uint32_t v_swz = static_cast<uint32_t>((xl >> 2) & 1) << 4;
+  int* const tr = TT + (xl >> 4) * kTTRow;  // the lane's columns share one tile
+  const int lc = l <= 4 ? 0 : (l <= 7 ? 1 : 2);
+
+  for (int y = y0; y < y0 + ychunk; ++y) {
+    if (owner) {
+      if (lc == 0)
+        row_out(y, std::integral_constant<int, 0>{});
+      else if (lc == 1)
+        row_out(y, std::integral_constant<int, 1>{});
+      else
+        row_out(y, std::integral_constant<int, 2>{});
     }
     __syncthreads();  // V and TT of row y no longer read
     if (y + 1 < y0 + ychunk) {
       if (lane_cols) {  // V and TT: window of row y + 1
-        int* tr = TT + (xl >> 4) * kTTRow;  // the lane's columns share one tile
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const int co = code_at(nxt_out, c), ci = code_at(nxt_in, c);
           if (co != ci) {
             const int bo = co - g0, bi = ci - g0;
             if (static_cast<unsigned>(bo) < static_cast<unsigned>(kBhG)) {
-              v_add(Vb, xl + c, bo, mone);
+              red_add_f16(v_col + 32 * c + ((2 * bo) ^ v_swz), mone);
               if (need_tt) atomicAdd(tr + tt_pos(bo), -1);
             }
             if (static_cast<unsigned>(bi) < static_cast<unsigned>(kBhG)) {
-              v_add(Vb, xl + c, bi, one);
+              red_add_f16(v_col + 32 * c + ((2 * bi) ^ v_swz), one);
               if (need_tt) atomicAdd(tr + tt_pos(bi), 1);
             }
           }
@@ -661,7 +696,7 @@ int launch_col_prefix(const uint16_t* d_bins, int N, int B2, const uint32_t* gro
                       cudaStream_t s) {
   const int logN = ilog2(N);
   const int tb = N < 256 ? N : 256;
-  k_col_blocks<<<dim3(N / tb, N / 64, B2 / 16), tb, 0, s>>>(d_bins, logN, B2, groups, P);
+  k_col_blocks<<<dim3(N / tb, N / kBhRows, B2 / 16), tb, 0, s>>>(d_bins, logN, B2, groups, P);
   GSP_CHECK_LAUNCH();
   k_col_prefix<<<dim3(2 * N / tb, B2 / 16), tb, 0, s>>>(logN, B2, groups, P);
   GSP_CHECK_LAUNCH();
@@ -727,8 +762,8 @@ int launch_bins(const float* d_normal_xy, int N, int bins, uint16_t* d_bins, uin
 }
 
 size_t col_prefix_bytes(int N, int B2) {
-  if (N < 128) return 0;
-  return static_cast<size_t>(N / 64 + 1) * N * B2 * sizeof(__half);
+  if (N < 2 * kBhRows) return 0;  // no level has a window that starts on a block
+  return static_cast<size_t>(N / kBhRows + 1) * N * B2 * sizeof(__half);
 }
 
 int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const HistOut& o,
@@ -743,16 +778,16 @@ int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const His
     GSP_TRY(make_bf16_store_map(&tm, o.bf16, static_cast<long long>(levels) * N * N, B2,
                                 bh_cols_per_warp(N)));
   }
-  // Rows per CTA: 64 (at most N).  A CTA of level l takes about a window fill
-  // of w = 2^l rows (2-byte L2 reads per column) plus 64 rows of output; with
-  // the coarsest levels launched first and two or more waves of kBhCtasPerSm
-  // CTAs per SM, the short fine-level CTAs fill in behind the long ones (256,
-  // 128 and 32 rows were slower on the 1024^2, 11-level, 80-column operand).
-  const int ychunk = N < 64 ? N : 64;
+  // Rows per CTA: kBhRows (at most N).  The coarsest levels are launched
+  // first; with their windows started from the column prefix sums every CTA
+  // is kBhRows rows of output plus at most 32 rows of window fill, and the
+  // ~4 waves of kBhCtasPerSm CTAs per SM pack well (on the 1024^2, 11-level,
+  // 80-column operand: 32 rows 0.69 ms, 64 rows 0.72 ms).
+  const int ychunk = N < kBhRows ? N : kBhRows;
   const size_t smem = box_hist_smem(N, mode == kBhBf16);
   if (smem > 227 * 1024) return GSP_ERR_UNSUPPORTED;
   HistOut oo = o;
-  if (col_prefix_bytes(N, B2) == 0 || levels <= 7) oo.colp = nullptr;
+  if (col_prefix_bytes(N, B2) == 0 || (1 << (levels - 1)) < 2 * kBhRows) oo.colp = nullptr;
   dim3 grid(B2 / kBhG, N / ychunk, levels);
   prof_begin(PROF_DOUBLE, s);  // one interval: the prefix table and the histograms
   int rc = oo.colp ? launch_col_prefix(d_bins, N, B2, o.groups, oo.colp, s) : GSP_OK;

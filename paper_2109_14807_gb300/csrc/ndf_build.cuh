@@ -39,12 +39,12 @@ struct HistOut {
   int tf32;                // f32 values rounded to the TF32 grid without bias
   // Optional scratch of col_prefix_bytes(N, B2) (null: none).  With it the
   // window counts of the coarse levels start from column prefix sums over
-  // 64-row blocks instead of from the 2^l map rows of the window.
+  // blocks of rows instead of from the 2^l map rows of the window.
   __half* colp;
 };
 
-// Bytes of the column-prefix scratch of launch_box_hist: (N / 64 + 1) rows of
-// N x B2 FP16 counts; 0 when N < 128 (no level has a window of 128 rows).
+// Bytes of the column-prefix scratch of launch_box_hist: N / 32 + 1 rows of
+// N x B2 FP16 counts; 0 when N < 64 (no window starts on a 32-row block).
 size_t col_prefix_bytes(int N, int B2);
 
 // Bytes of the occupied-bin-group bitmask (one bit per 16 bins, B <= 128).
