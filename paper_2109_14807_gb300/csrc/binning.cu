@@ -113,8 +113,10 @@ __device__ __forceinline__ void sink_sumsq(const LevelSink& o, int4 v, bool acti
 //    (the TT by shared-memory integer reductions) and computes the footprints
 //    x of that range, so one barrier separates the reads of V and TT from
 //    their update and one the update from the next row's reads;
-//  - V rows are 32 bytes with their 16-byte halves swapped on bit 2 of x, so
-//    the ldmatrix row reads of 8 consecutive columns fall on distinct banks;
+//  - V rows are 32 bytes with 16 bytes of padding after every 4 columns, so
+//    that the ldmatrix row reads of 8 consecutive columns (from a multiple of
+//    4) and the window updates of the lanes (each owning 1, 2 or 4 adjacent
+//    columns) spread over the banks;
 //  - BF16 results go by stmatrix into a per-warp staging buffer in the same
 //    swizzle (the TMA 32-byte swizzle) and out by one TMA bulk store per warp
 //    and row; the other outputs are stored from the accumulator fragments.
@@ -132,8 +134,13 @@ __host__ __device__ constexpr int bh_cols_per_warp(int N) {
   return N >= 128 ? N / kBhWarps : (N >= 16 ? 16 : N);
 }
 
+// Byte offset of column x of V (32-byte rows, 16 bytes of padding after every 4).
+__host__ __device__ constexpr uint32_t v_off(int x) {
+  return static_cast<uint32_t>(x) * 32u + static_cast<uint32_t>(x >> 2) * 16u;
+}
+
 // Byte offset of half h (bins 8h .. 8h + 7) of row x in a buffer of 32-byte
-// rows (16 BF16 / FP16 values), halves swapped on bit 2 of x.
+// rows (16 BF16 values), halves swapped on bit 2 of x: the 32-byte TMA swizzle.
 __device__ __forceinline__ uint32_t row32_off(int x, int h) {
   return static_cast<uint32_t>(x) * 32u + static_cast<uint32_t>((h ^ (x >> 2)) & 1) * 16u;
 }
@@ -221,17 +228,10 @@ __device__ __forceinline__ int code_at(uint2 v, int c) {
   return static_cast<int>((c & 1) ? u >> 16 : u & 0xFFFFu);
 }
 
-// *p += v for an FP16 value in shared memory (exact here: small integers).
-__device__ __forceinline__ void red_add_f16(uint8_t* p, __half v) {
-  asm volatile("red.shared.add.noftz.f16 [%0], %1;" ::"r"(
-                   static_cast<uint32_t>(__cvta_generic_to_shared(p))),
-               "h"(__half_as_ushort(v))
-               : "memory");
-}
-
 // V[x][b] += d (one owner thread per column x).
 __device__ __forceinline__ void v_add(uint8_t* Vb, int x, int b, __half d) {
-  red_add_f16(Vb + row32_off(x, b >> 3) + (b & 7) * 2, d);
+  __half* p = reinterpret_cast<__half*>(Vb + v_off(x) + 2 * b);
+  *p = __hadd(*p, d);
 }
 
 // Column prefix sums over blocks of kBhRows rows, the starting windows of the
@@ -361,11 +361,11 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
   const uint32_t srow_bytes = static_cast<uint32_t>((cw < 16 ? 16 : cw) * 32);  // staging per warp
   const uint32_t stage_bytes = MODE == kBhBf16 ? kBhWarps * srow_bytes : 0u;
   uint8_t* Vb = smem_raw + pad + stage_bytes;
-  int* TT = reinterpret_cast<int*>(Vb + vcols * 32);  // [T][kTTRow] tile totals of V (tt_pos order)
+  int* TT = reinterpret_cast<int*>(Vb + v_off(vcols));  // [T][kTTRow] tile totals of V (tt_pos order)
   const uint32_t v_s = raw_s + pad + stage_bytes;
   const uint32_t st_s = raw_s + pad + static_cast<uint32_t>(warp) * srow_bytes;
 
-  for (int i = threadIdx.x; i < vcols * 2; i += kBhThreads)
+  for (int i = threadIdx.x; i < static_cast<int>(v_off(vcols) / 16); i += kBhThreads)
     reinterpret_cast<uint4*>(Vb)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   const __half one = __float2half(1.0f), mone = __float2half(-1.0f);
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
 #pragma unroll
           for (int i = 0; i < 4; ++i) pe[i] = __hadd2(pe[i], pw[i]);
         }
-        *reinterpret_cast<uint4*>(Vb + row32_off(xl + c, h)) = ve;
+        *reinterpret_cast<uint4*>(Vb + v_off(xl + c) + 16 * h) = ve;
       }
     }
   } else if (lane_cols) {
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     for (int k = 0; k < ntile; ++k) {
       const int x0 = xw + 16 * k;
       uint32_t bv[4];
-      ldsm_x4_trans(v_s + row32_off(x0 + lrow, lhalf), bv);
+      ldsm_x4_trans(v_s + v_off(x0 + lrow) + 16 * lhalf, bv);
       float t0[4], t1[4];
       mma_16816(t0, ones, bv[0], bv[1], off4);
       mma_16816(t1, ones, bv[2], bv[3], off4);
@@ -462,17 +462,14 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     A2[3] = a2(fr + 8, fc + 8) | (a2(fr + 8, fc + 9) << 16);
   }
   // This lane's ldmatrix rows of the two column ranges of the warp's first
-  // tile: a byte offset into V that advances by 16 columns (512 bytes) per
-  // tile, modulo the N columns, plus the half swap (bit 2 of the column, the
-  // same for every tile since N and the step are multiples of 16).
+  // tile: a byte offset into V that advances by 16 columns (v_off(16) bytes)
+  // per tile, modulo the N columns (v_off(N) bytes), plus the bin half.
   const int x1 = (xw - a + lrow) & m, x2 = (xw - a + w2 + lrow) & m;
-  const uint32_t vmask = static_cast<uint32_t>(N * 32 - 1);
-  const uint32_t va1 = v_s + (static_cast<uint32_t>((lhalf ^ (x1 >> 2)) & 1) << 4);
-  const uint32_t va2 = v_s + (static_cast<uint32_t>((lhalf ^ (x2 >> 2)) & 1) << 4);
-  const uint32_t vo1 = static_cast<uint32_t>(x1) * 32u, vo2 = static_cast<uint32_t>(x2) * 32u;
+  const uint32_t vend = v_off(N), vstep = v_off(16);
+  const uint32_t va = v_s + 16u * static_cast<uint32_t>(lhalf);
+  const uint32_t vo1 = v_off(x1), vo2 = v_off(x2);
   // stmatrix row of this lane in the staging buffer (tile k adds 512 bytes)
-  const uint32_t st_lane = st_s + static_cast<uint32_t>(lrow) * 32u +
-                           (static_cast<uint32_t>((lhalf ^ (lrow >> 2)) & 1) << 4);
+  const uint32_t st_lane = st_s + row32_off(lrow, lhalf);
 
   // codes leaving / entering the window at the next row step, loaded one row
   // ahead so the L2 latency overlaps this row's work
@@ -532,10 +529,12 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
 #pragma unroll 2
     for (int k = 0; k < ntile; ++k) {
       uint32_t bA[4], bB[4];
-      ldsm_x4_trans(va1 + o1, bA);
-      ldsm_x4_trans(va2 + o2, bB);
-      o1 = (o1 + 512u) & vmask;
-      o2 = (o2 + 512u) & vmask;
+      ldsm_x4_trans(va + o1, bA);
+      ldsm_x4_trans(va + o2, bB);
+      o1 += vstep;
+      o2 += vstep;
+      if (o1 >= vend) o1 -= vend;
+      if (o2 >= vend) o2 -= vend;
       float D[2][4];
       mma_16816(D[0], A1, bA[0], bA[1], reinterpret_cast<const float(&)[4]>(Cq[0]));
       mma_16816(D[1], A1, bA[2], bA[3], reinterpret_cast<const float(&)[4]>(Cq[1]));
@@ -631,10 +630,9 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
       }
     }
   };
-  // V of this lane's columns: byte offset of bin b in column xl + c is
-  // v_col + 32 c + (2 b ^ v_swz) (the columns share bit 2 of x)
-  uint8_t* const v_col = Vb + static_cast<uint32_t>(xl) * 32u;
-  const uint32_t v_swz = static_cast<uint32_t>((xl >> 2) & 1) << 4;
+  // V of this lane's columns: bin b of column xl + c at v_col + 32 c + 2 b
+  // (the CPL columns lie within one group of 4)
+  uint8_t* const v_col = Vb + v_off(xl);
   int* const tr = TT + (xl >> 4) * kTTRow;  // the lane's columns share one tile
   const int lc = l <= 4 ? 0 : (l <= 7 ? 1 : 2);
 
@@ -650,19 +648,35 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     __syncthreads();  // V and TT of row y no longer read
     if (y + 1 < y0 + ychunk) {
       if (lane_cols) {  // V and TT: window of row y + 1
+        // predicates and addresses first, then every load, then every store
+        // (each column has one owner, so plain read-modify-writes; the tile
+        // totals are shared by the lanes of a tile: integer atomics)
+        bool po[CPL], pi[CPL];
+        int bo[CPL], bi[CPL];
+        __half vo[CPL], vi[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const int co = code_at(nxt_out, c), ci = code_at(nxt_in, c);
-          if (co != ci) {
-            const int bo = co - g0, bi = ci - g0;
-            if (static_cast<unsigned>(bo) < static_cast<unsigned>(kBhG)) {
-              red_add_f16(v_col + 32 * c + ((2 * bo) ^ v_swz), mone);
-              if (need_tt) atomicAdd(tr + tt_pos(bo), -1);
-            }
-            if (static_cast<unsigned>(bi) < static_cast<unsigned>(kBhG)) {
-              red_add_f16(v_col + 32 * c + ((2 * bi) ^ v_swz), one);
-              if (need_tt) atomicAdd(tr + tt_pos(bi), 1);
-            }
+          bo[c] = co - g0;
+          bi[c] = ci - g0;
+          po[c] = co != ci && static_cast<unsigned>(bo[c]) < static_cast<unsigned>(kBhG);
+          pi[c] = co != ci && static_cast<unsigned>(bi[c]) < static_cast<unsigned>(kBhG);
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          if (po[c]) vo[c] = *reinterpret_cast<const __half*>(v_col + 32 * c + 2 * bo[c]);
+          if (pi[c]) vi[c] = *reinterpret_cast<const __half*>(v_col + 32 * c + 2 * bi[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          if (po[c]) *reinterpret_cast<__half*>(v_col + 32 * c + 2 * bo[c]) = __hadd(vo[c], mone);
+          if (pi[c]) *reinterpret_cast<__half*>(v_col + 32 * c + 2 * bi[c]) = __hadd(vi[c], one);
+        }
+        if (need_tt) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            if (po[c]) atomicAdd(tr + tt_pos(bo[c]), -1);
+            if (pi[c]) atomicAdd(tr + tt_pos(bi[c]), 1);
           }
         }
       }
@@ -706,7 +720,7 @@ int launch_col_prefix(const uint16_t* d_bins, int N, int B2, const uint32_t* gro
 size_t box_hist_smem(int N, bool bf16) {
   const size_t cw = static_cast<size_t>(bh_cols_per_warp(N));
   const size_t stage = bf16 ? kBhWarps * (cw < 16 ? 16 : cw) * 32 : 0;
-  const size_t v = static_cast<size_t>(N < 16 ? 16 : N) * 32;
+  const size_t v = v_off(N < 16 ? 16 : N);
   const size_t tt = static_cast<size_t>(N >= 16 ? N / 16 : 1) * kTTRow * sizeof(int);
   return 1024 + stage + v + tt;  // 1024: alignment of the staging buffers
 }
