@@ -330,7 +330,8 @@ __device__ void box_hist_zero(int logN, int B2, int ychunk, int y0, int l, int g
   }
 }
 
-// CPL: columns per lane (N / 256 for N >= 512, else 1).  MODE kBhBf16 writes
+// CPL: columns per lane (N / 256 for N >= 512, else 1).  MODE kBhInt writes
+// counts only; the others add the sums of squares to o.sumsq.  kBhBf16 writes
 // through `tmap`: the BF16 tensor as [levels * N * N][B2], box 16 bins x
 // bh_cols_per_warp(N) rows, 32-byte swizzle.
 template <int CPL, int MODE>
@@ -344,6 +345,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
   const int l = gridDim.z - 1 - blockIdx.z;  // coarsest level first: its window fill is the longest
   const int w = 1 << l, a = w >> 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr bool kSumsq = MODE != kBhInt;  // the counts alone carry no sums of squares
   if (o.groups && !((o.groups[blockIdx.x >> 5] >> (blockIdx.x & 31)) & 1u)) {
     if (MODE != kBhSumsq) box_hist_zero(logN, B2, ychunk, y0, l, g0, o);
     return;
@@ -526,7 +528,9 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     uint32_t d00 = (static_cast<uint32_t>(e_row) * static_cast<uint32_t>(B2) +
                     static_cast<uint32_t>((xw + fr) * B2 + g0 + fc)) * kWeyl;
     uint32_t o1 = vo1, o2 = vo2;
-#pragma unroll 2
+    // 4 tiles in flight for the BF16 operand (2 in the other modes, whose
+    // direct stores need the registers)
+#pragma unroll(MODE == kBhBf16 ? 4 : 2)
     for (int k = 0; k < ntile; ++k) {
       uint32_t bA[4], bB[4];
       ldsm_x4_trans(va + o1, bA);
@@ -554,13 +558,17 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
         }
       }
       // D[n][2r + e]: bits 0x4B000000 + count of footprint x = X0 + fr + 8r, bin g0 + 8n + fc + e
-      if (o.sumsq) {
-        if constexpr (LC <= 1) {  // counts <= 4^7: eight squares fit in 32 bits
-          uint32_t q = 0;
+      if constexpr (kSumsq) {
+        if constexpr (LC <= 1) {
+          // counts <= 4^7: the eight squares of a tile sum below 2^32, so they
+          // may be formed modulo 2^32 from the FP32 bits u = K + c (K =
+          // 0x4B000000): c^2 = u u - 2K u + K^2, two multiply-adds per count
+          uint32_t q = 8u * (kOffBits * kOffBits);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const uint32_t c = __float_as_uint(D[i >> 2][i & 3]) - kOffBits;
-            q += c * c;
+            const uint32_t u = __float_as_uint(D[i >> 2][i & 3]);
+            asm("mad.lo.u32 %0, %1, %1, %0;" : "+r"(q) : "r"(u));
+            asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(q) : "r"(u), "r"(0u - 2u * kOffBits));
           }
           sumsq += q;
         } else {
@@ -685,7 +693,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     }
   }
   if (MODE == kBhBf16 && owner && lane == 0) bulk_wait0();
-  if (o.sumsq) {
+  if constexpr (kSumsq) {
     for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
     // N < 16: the 16 rows of the one tile hold each footprint 16 / N times
     if (N < 16) sumsq >>= 4 - logN;
@@ -784,6 +792,8 @@ int launch_box_hist(const uint16_t* d_bins, int N, int levels, int B2, const His
                     cudaStream_t s) {
   if (B2 % kBhG || N > 1024) return GSP_ERR_UNSUPPORTED;
   if ((o.h != nullptr) + (o.f32 != nullptr) + (o.bf16 != nullptr) > 1) return GSP_ERR_UNSUPPORTED;
+  // int32 counts come without sums of squares, the other modes with them
+  if ((o.h != nullptr) == (o.sumsq != nullptr)) return GSP_ERR_UNSUPPORTED;
   const int mode = o.h ? kBhInt : o.f32 ? kBhF32 : o.bf16 ? kBhBf16 : kBhSumsq;
   CUtensorMap tm;
   memset(&tm, 0, sizeof(tm));
