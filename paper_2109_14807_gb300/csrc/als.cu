@@ -332,11 +332,11 @@ __global__ void k_cast_cols(const int32_t* __restrict__ h, long long fps, int B2
     const int v = b < 0 ? 0 : h[fp * B2 + b];
     q = static_cast<unsigned long long>(static_cast<long long>(v) * v);
     const float f = static_cast<float>(v) * scale;
-    const uint32_t d = weyl_dither(static_cast<unsigned long long>(base + i));
+    const unsigned long long e = static_cast<unsigned long long>(base + i);
     if constexpr (sizeof(OutT) == 2) {
-      out[i] = __ushort_as_bfloat16(static_cast<unsigned short>(bf16_dither(f, d)));
+      out[i] = __ushort_as_bfloat16(static_cast<unsigned short>(bf16_dither(f, bf16_dither16(e))));
     } else {
-      out[i] = tf32 ? tf32_dither(f, d) : f;
+      out[i] = tf32 ? tf32_dither(f, weyl_dither(e)) : f;
     }
   }
   for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);

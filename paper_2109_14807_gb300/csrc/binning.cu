@@ -74,8 +74,9 @@ __device__ __forceinline__ void sink_store(const LevelSink& o, long long i, int4
   }
   if (o.bf16) {
     uint2 p;
-    p.x = bf16_pair_dither(f0, d, f1, d + kWeyl);
-    p.y = bf16_pair_dither(f2, d + 2 * kWeyl, f3, d + 3 * kWeyl);
+    const uint32_t rb = bf16_pair_bits(static_cast<unsigned long long>(o.base + 4 * i));
+    p.x = bf16_pair_dither(f0, f1, rb);
+    p.y = bf16_pair_dither(f2, f3, rb + kWeyl);
     reinterpret_cast<uint2*>(o.bf16)[i] = p;
   }
 }
@@ -482,12 +483,14 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
       nxt_in = load_codes<CPL>(bins_map + (((yn - 1 - a + w) & m) << logN) + xl);
     }
   };
-  if (ychunk > 1) fetch(y0 + 1);
+  if (ychunk > 1 && w < N) fetch(y0 + 1);
 
   const float sc = o.scale[l];
   const float nb = -kOff * sc;  // -2^23 * scale, exact
   const uint32_t dK8r = static_cast<uint32_t>(8 * B2) * kWeyl;    // dither step of 8 rows
   const uint32_t dKtile = static_cast<uint32_t>(16 * B2) * kWeyl;  // ... and of one tile
+  const uint32_t dP8r = static_cast<uint32_t>(4 * B2) * kWeyl;    // pair dither: 8 rows
+  const uint32_t dPtile = static_cast<uint32_t>(8 * B2) * kWeyl;  // ... and one tile
   const int ta = a >> 4, wt = w >> 4;                              // in tiles (l >= 5)
   const int* tt_lane = TT + 2 * fc;  // this lane's 4 bins of a tile-total row
   unsigned long long sumsq = 0;
@@ -525,8 +528,11 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
       __syncwarp();
     }
     const long long e_row = (static_cast<long long>(l) * N + y) * N;  // footprint index of x = 0
-    uint32_t d00 = (static_cast<uint32_t>(e_row) * static_cast<uint32_t>(B2) +
-                    static_cast<uint32_t>((xw + fr) * B2 + g0 + fc)) * kWeyl;
+    // element index of (x = xw + fr, bin g0 + fc), its Weyl value (TF32) and
+    // that of its pair (BF16)
+    const long long e_lane = (e_row + xw + fr) * B2 + g0 + fc;
+    uint32_t d00 = MODE == kBhF32 ? static_cast<uint32_t>(e_lane) * kWeyl : 0u;
+    uint32_t p00 = MODE == kBhBf16 ? static_cast<uint32_t>(e_lane >> 1) * kWeyl : 0u;
     uint32_t o1 = vo1, o2 = vo2;
     // 4 tiles in flight for the BF16 operand (2 in the other modes, whose
     // direct stores need the registers)
@@ -586,7 +592,8 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
         for (int n = 0; n < 2; ++n)
 #pragma unroll
           for (int r = 0; r < 2; ++r) f[n][r] = fma2(D[n][2 * r], D[n][2 * r + 1], sc, nb);
-        // Weyl dither of element (n, r, e): d00 + r * dK8r + (8n + e) * kWeyl
+        // Weyl values of element (n, r, e): d00 + r * dK8r + (8n + e) * kWeyl
+        // (TF32); of its pair: p00 + r * dP8r + 4n * kWeyl (BF16)
         if constexpr (MODE == kBhBf16) {
           uint32_t wd[2][2];
 #pragma unroll
@@ -596,8 +603,8 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
               if constexpr (LC == 0) {  // counts <= 256: exact in BF16
                 wd[n][r] = __byte_perm(__float_as_uint(f[n][r].x), __float_as_uint(f[n][r].y), 0x7632);
               } else {
-                const uint32_t d = d00 + (r ? dK8r : 0u) + static_cast<uint32_t>(8 * n) * kWeyl;
-                wd[n][r] = bf16_pair_dither(f[n][r].x, d, f[n][r].y, d + kWeyl);
+                wd[n][r] = bf16_pair_dither(
+                    f[n][r].x, f[n][r].y, p00 + (r ? dP8r : 0u) + static_cast<uint32_t>(4 * n) * kWeyl);
               }
             }
           stsm_x4(st_lane + 512u * static_cast<uint32_t>(k), wd[0][0], wd[0][1], wd[1][0], wd[1][1]);
@@ -627,7 +634,8 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
                   make_int2(static_cast<int>(__float_as_uint(D[n][2 * r]) - kOffBits),
                             static_cast<int>(__float_as_uint(D[n][2 * r + 1]) - kOffBits));
       }
-      d00 += dKtile;
+      if constexpr (MODE == kBhF32) d00 += dKtile;
+      if constexpr (MODE == kBhBf16) p00 += dPtile;
     }
     if constexpr (MODE == kBhBf16) {  // this warp's footprints of row y: one bulk store
       fence_proxy_async_smem();
@@ -644,6 +652,8 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
   int* const tr = TT + (xl >> 4) * kTTRow;  // the lane's columns share one tile
   const int lc = l <= 4 ? 0 : (l <= 7 ? 1 : 2);
 
+  // w = N: the window is the whole map in every row, V and TT never change
+  const bool sliding = w < N;
   for (int y = y0; y < y0 + ychunk; ++y) {
     if (owner) {
       if (lc == 0)
@@ -653,6 +663,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
       else
         row_out(y, std::integral_constant<int, 2>{});
     }
+    if (!sliding) continue;
     __syncthreads();  // V and TT of row y no longer read
     if (y + 1 < y0 + ychunk) {
       if (lane_cols) {  // V and TT: window of row y + 1

@@ -87,11 +87,13 @@ __device__ __forceinline__ float round_tf32(float v) {
 // rounding noise, is what moves an ALS fit.  Instead a dither d in [0, 2^drop)
 // is added below the kept bits and the sum truncated, so that a value between
 // two representable neighbours goes up with probability equal to its distance
-// from the lower one.  d is the Weyl sequence frac(i * phi) of the element's
-// linear index i (32-bit fixed point, phi = golden ratio; Knuth, TAOCP vol. 3,
-// Sec. 6.4): equidistributed, cheap and the same wherever element i is
-// produced.  Representable values (low bits zero) are unchanged, so counts
-// with at most 8 (BF16) or 11 (TF32) significant bits stay exact.
+// from the lower one.  The dithers come from the Weyl sequence frac(i * phi)
+// (32-bit fixed point, phi = golden ratio; Knuth, TAOCP vol. 3, Sec. 6.4):
+// equidistributed, cheap and the same wherever an element is produced.  TF32
+// element e takes the top bits of the Weyl value of e; BF16 elements 2p and
+// 2p + 1 take the low and the high 16 bits of the Weyl value of their pair p.
+// Representable values (low bits zero) are unchanged, so counts with at most
+// 8 (BF16) or 11 (TF32) significant bits stay exact.
 constexpr uint32_t kWeyl = 0x9E3779B9u;
 
 __device__ __forceinline__ uint32_t weyl_dither(unsigned long long i) {
@@ -103,23 +105,31 @@ __device__ __forceinline__ uint32_t dither_round(float v, uint32_t d, int drop) 
   return (__float_as_uint(v) + (d >> (32 - drop))) & ~((1u << drop) - 1u);
 }
 
-// BF16 bits of v >= 0 rounded without bias.
-__device__ __forceinline__ uint32_t bf16_dither(float v, uint32_t d) {
-  return (__float_as_uint(v) + (d >> 16)) >> 16;
+// The two 16-bit BF16 dithers of the element pair that starts at even e.
+__device__ __forceinline__ uint32_t bf16_pair_bits(unsigned long long e) {
+  return static_cast<uint32_t>(e >> 1) * kWeyl;
 }
 
-// Two BF16 values (element 0 in the low half) as one 32-bit word, each the
-// bf16_dither of its own value and dither.  The stochastic-rounding convert
-// takes the random bits of element 0 from the low half of its operand and
-// those of element 1 from the high half, adds them below the kept bits and
-// truncates: given the top halves of d0 and d1, the same as bf16_dither (the
-// CP operand prepared from histograms takes bf16_dither and the one from the
-// normal map this form; the GPU tests require the two to agree).
-__device__ __forceinline__ uint32_t bf16_pair_dither(float v0, uint32_t d0, float v1, uint32_t d1) {
+// The 16-bit BF16 dither of element e.
+__device__ __forceinline__ uint32_t bf16_dither16(unsigned long long e) {
+  const uint32_t r = bf16_pair_bits(e);
+  return (e & 1) ? r >> 16 : r & 0xFFFFu;
+}
+
+// BF16 bits of v >= 0 rounded without bias, dither d16 < 2^16.
+__device__ __forceinline__ uint32_t bf16_dither(float v, uint32_t d16) {
+  return (__float_as_uint(v) + d16) >> 16;
+}
+
+// Two BF16 values (element 0 in the low half) as one 32-bit word, rounded
+// without bias with the dithers in the low and high halves of rbits: the
+// stochastic-rounding convert adds each half below the kept bits of its value
+// and truncates, the same as bf16_dither (the CP operand prepared from
+// histograms takes bf16_dither and the one from the normal map this form; the
+// GPU tests require the two to agree).
+__device__ __forceinline__ uint32_t bf16_pair_dither(float v0, float v1, uint32_t rbits) {
   uint32_t r;
-  asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;"
-      : "=r"(r)
-      : "f"(v1), "f"(v0), "r"(__byte_perm(d0, d1, 0x7632)));
+  asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(v1), "f"(v0), "r"(rbits));
   return r;
 }
 
