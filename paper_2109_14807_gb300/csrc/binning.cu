@@ -190,6 +190,15 @@ __device__ __forceinline__ float2 fma2(float x, float y, float s, float nb) {
   return o;
 }
 
+// (x, y) += (a, b) in one packed FP32 instruction, each lane rounded once.
+__device__ __forceinline__ void add2(float& x, float& y, float a, float b) {
+  unsigned long long v, u, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(x), "f"(y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(a), "f"(b));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(v), "l"(u));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+}
+
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
   asm volatile(
       "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
@@ -426,12 +435,12 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
   const bool need_tt = l >= 5;  // whole tiles inside the window
   const float kOff = 8388608.0f;  // 2^23
   const uint32_t kOffBits = 0x4B000000u;
+  const float off4[4] = {kOff, kOff, kOff, kOff}, zero4[4] = {0.f, 0.f, 0.f, 0.f};
   if (need_tt && owner) {  // tile totals of row y0: an all-ones A times each tile
     __syncwarp();
     uint32_t ones[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) ones[i] = 0x3C003C00u;
-    const float off4[4] = {kOff, kOff, kOff, kOff};
     for (int k = 0; k < ntile; ++k) {
       const int x0 = xw + 16 * k;
       uint32_t bv[4];
@@ -516,13 +525,9 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
 #pragma unroll
         for (int i = 0; i < 4; ++i) Mb[i] += __shfl_xor_sync(0xffffffffu, Mb[i], off);
     }
-    // accumulator inputs per n-tile (rows fr, fr + 8 alike): FP32 bits of 2^23 + M
-    uint32_t Cq[2][4];
+    // FP32 bits of 2^23 + M, added to the accumulators of both rows fr, fr + 8
 #pragma unroll
-    for (int n = 0; n < 2; ++n) {
-      Cq[n][0] = Cq[n][2] = Mb[2 * n] + kOffBits;
-      Cq[n][1] = Cq[n][3] = Mb[2 * n + 1] + kOffBits;
-    }
+    for (int i = 0; i < 4; ++i) Mb[i] += kOffBits;
     if (MODE == kBhBf16 && y > y0) {  // the previous row's store has read the staging buffer
       if (lane == 0) bulk_wait_read0();
       __syncwarp();
@@ -546,21 +551,28 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
       if (o1 >= vend) o1 -= vend;
       if (o2 >= vend) o2 -= vend;
       float D[2][4];
-      mma_16816(D[0], A1, bA[0], bA[1], reinterpret_cast<const float(&)[4]>(Cq[0]));
-      mma_16816(D[1], A1, bA[2], bA[3], reinterpret_cast<const float(&)[4]>(Cq[1]));
+      if constexpr (LC == 0) {  // no middle sums: the accumulators start at 2^23
+        mma_16816(D[0], A1, bA[0], bA[1], off4);
+        mma_16816(D[1], A1, bA[2], bA[3], off4);
+      } else {
+        mma_16816(D[0], A1, bA[0], bA[1], zero4);
+        mma_16816(D[1], A1, bA[2], bA[3], zero4);
+      }
       mma_16816(D[0], A2, bB[0], bB[1], D[0]);
       mma_16816(D[1], A2, bB[2], bB[3], D[1]);
       if constexpr (LC >= 1) {
+        // + (2^23 + M), exact (integers below 2^24), two rows per packed add
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+            add2(D[n][2 * r], D[n][2 * r + 1], __uint_as_float(Mb[2 * n]), __uint_as_float(Mb[2 * n + 1]));
         if (k + 1 < ntile) {  // middle sums of the next tile
           const int t = (xw >> 4) + k;
           const int4 lo = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + 1) & (T - 1)) * kTTRow);
           const int4 hi = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + wt) & (T - 1)) * kTTRow);
-          const int dm[4] = {hi.x - lo.x, hi.y - lo.y, hi.z - lo.z, hi.w - lo.w};
-#pragma unroll
-          for (int n = 0; n < 2; ++n) {
-            Cq[n][0] += dm[2 * n]; Cq[n][2] += dm[2 * n];
-            Cq[n][1] += dm[2 * n + 1]; Cq[n][3] += dm[2 * n + 1];
-          }
+          Mb[0] += hi.x - lo.x; Mb[1] += hi.y - lo.y;
+          Mb[2] += hi.z - lo.z; Mb[3] += hi.w - lo.w;
         }
       }
       // D[n][2r + e]: bits 0x4B000000 + count of footprint x = X0 + fr + 8r, bin g0 + 8n + fc + e
