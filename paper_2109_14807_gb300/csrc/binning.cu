@@ -505,16 +505,17 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
   unsigned long long sumsq = 0;
   __syncthreads();  // V and TT of row y0 complete
 
+  const bool sliding = w < N;  // else every window is the whole map
   // One row of footprints for the level class LC of l (compile-time, so the
   // tile loop has no level branches): 0: l <= 4 (counts <= 256, exact in BF16;
   // no whole tiles in the window), 1: 5 <= l <= 7 (squares of 8 counts fit 32
-  // bits), 2: l >= 8.
-  auto row_out = [&](int y, auto lc_tag) {
+  // bits), 2: l >= 8, 3: w = N >= 32 (the counts Dc of every tile).
+  auto row_out = [&](int y, auto lc_tag, const float (&Dc)[2][4], unsigned long long qc) {
     constexpr int LC = decltype(lc_tag)::value;
     // middle sums of the warp's first tile: the 8 lanes of one column pair
     // take every 8th tile, then add up
     uint32_t Mb[4] = {0u, 0u, 0u, 0u};  // bins fc, fc + 1, fc + 8, fc + 9
-    if constexpr (LC >= 1) {
+    if constexpr (LC == 1 || LC == 2) {
       const int u0 = (xw >> 4) - ta + 1;
       for (int q = fr; q < wt - 1; q += 8) {
         const int4 p = *reinterpret_cast<const int4*>(tt_lane + ((u0 + q) & (T - 1)) * kTTRow);
@@ -538,45 +539,56 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
     const long long e_lane = (e_row + xw + fr) * B2 + g0 + fc;
     uint32_t d00 = MODE == kBhF32 ? static_cast<uint32_t>(e_lane) * kWeyl : 0u;
     uint32_t p00 = MODE == kBhBf16 ? static_cast<uint32_t>(e_lane >> 1) * kWeyl : 0u;
+    (void)d00;
+    (void)p00;
     uint32_t o1 = vo1, o2 = vo2;
     // 4 tiles in flight for the BF16 operand (2 in the other modes, whose
     // direct stores need the registers)
 #pragma unroll(MODE == kBhBf16 ? 4 : 2)
     for (int k = 0; k < ntile; ++k) {
-      uint32_t bA[4], bB[4];
-      ldsm_x4_trans(va + o1, bA);
-      ldsm_x4_trans(va + o2, bB);
-      o1 += vstep;
-      o2 += vstep;
-      if (o1 >= vend) o1 -= vend;
-      if (o2 >= vend) o2 -= vend;
       float D[2][4];
-      if constexpr (LC == 0) {  // no middle sums: the accumulators start at 2^23
-        mma_16816(D[0], A1, bA[0], bA[1], off4);
-        mma_16816(D[1], A1, bA[2], bA[3], off4);
-      } else {
-        mma_16816(D[0], A1, bA[0], bA[1], zero4);
-        mma_16816(D[1], A1, bA[2], bA[3], zero4);
-      }
-      mma_16816(D[0], A2, bB[0], bB[1], D[0]);
-      mma_16816(D[1], A2, bB[2], bB[3], D[1]);
-      if constexpr (LC >= 1) {
-        // + (2^23 + M), exact (integers below 2^24), two rows per packed add
+      if constexpr (LC == 3) {
 #pragma unroll
         for (int n = 0; n < 2; ++n)
 #pragma unroll
-          for (int r = 0; r < 2; ++r)
-            add2(D[n][2 * r], D[n][2 * r + 1], __uint_as_float(Mb[2 * n]), __uint_as_float(Mb[2 * n + 1]));
-        if (k + 1 < ntile) {  // middle sums of the next tile
-          const int t = (xw >> 4) + k;
-          const int4 lo = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + 1) & (T - 1)) * kTTRow);
-          const int4 hi = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + wt) & (T - 1)) * kTTRow);
-          Mb[0] += hi.x - lo.x; Mb[1] += hi.y - lo.y;
-          Mb[2] += hi.z - lo.z; Mb[3] += hi.w - lo.w;
+          for (int i = 0; i < 4; ++i) D[n][i] = Dc[n][i];
+      } else {
+        uint32_t bA[4], bB[4];
+        ldsm_x4_trans(va + o1, bA);
+        ldsm_x4_trans(va + o2, bB);
+        o1 += vstep;
+        o2 += vstep;
+        if (o1 >= vend) o1 -= vend;
+        if (o2 >= vend) o2 -= vend;
+        if constexpr (LC == 0) {  // no middle sums: the accumulators start at 2^23
+          mma_16816(D[0], A1, bA[0], bA[1], off4);
+          mma_16816(D[1], A1, bA[2], bA[3], off4);
+        } else {
+          mma_16816(D[0], A1, bA[0], bA[1], zero4);
+          mma_16816(D[1], A1, bA[2], bA[3], zero4);
+        }
+        mma_16816(D[0], A2, bB[0], bB[1], D[0]);
+        mma_16816(D[1], A2, bB[2], bB[3], D[1]);
+        if constexpr (LC >= 1) {
+          // + (2^23 + M), exact (integers below 2^24), two rows per packed add
+#pragma unroll
+          for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+              add2(D[n][2 * r], D[n][2 * r + 1], __uint_as_float(Mb[2 * n]), __uint_as_float(Mb[2 * n + 1]));
+          if (k + 1 < ntile) {  // middle sums of the next tile
+            const int t = (xw >> 4) + k;
+            const int4 lo = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + 1) & (T - 1)) * kTTRow);
+            const int4 hi = *reinterpret_cast<const int4*>(tt_lane + ((t - ta + wt) & (T - 1)) * kTTRow);
+            Mb[0] += hi.x - lo.x; Mb[1] += hi.y - lo.y;
+            Mb[2] += hi.z - lo.z; Mb[3] += hi.w - lo.w;
+          }
         }
       }
       // D[n][2r + e]: bits 0x4B000000 + count of footprint x = X0 + fr + 8r, bin g0 + 8n + fc + e
-      if constexpr (kSumsq) {
+      if constexpr (kSumsq && LC == 3) {
+        sumsq += qc;
+      } else if constexpr (kSumsq) {
         if constexpr (LC <= 1) {
           // counts <= 4^7: the eight squares of a tile sum below 2^32, so they
           // may be formed modulo 2^32 from the FP32 bits u = K + c (K =
@@ -662,57 +674,82 @@ __global__ void __launch_bounds__(kBhThreads, kBhCtasPerSm)
   // (the CPL columns lie within one group of 4)
   uint8_t* const v_col = Vb + v_off(xl);
   int* const tr = TT + (xl >> 4) * kTTRow;  // the lane's columns share one tile
-  const int lc = l <= 4 ? 0 : (l <= 7 ? 1 : 2);
+  const int lc = !sliding && need_tt ? 3 : (l <= 4 ? 0 : (l <= 7 ? 1 : 2));
 
-  // w = N: the window is the whole map in every row, V and TT never change
-  const bool sliding = w < N;
-  for (int y = y0; y < y0 + ychunk; ++y) {
+  if (lc == 3) {
+    // w = N (from l = 5 on): every window is the whole map, so the count of a
+    // bin is its total in every footprint, taken from the tile totals once
     if (owner) {
-      if (lc == 0)
-        row_out(y, std::integral_constant<int, 0>{});
-      else if (lc == 1)
-        row_out(y, std::integral_constant<int, 1>{});
-      else
-        row_out(y, std::integral_constant<int, 2>{});
+      uint32_t tot[4] = {0u, 0u, 0u, 0u};  // bins fc, fc + 1, fc + 8, fc + 9
+      for (int q = fr; q < T; q += 8) {
+        const int4 p = *reinterpret_cast<const int4*>(tt_lane + q * kTTRow);
+        tot[0] += p.x; tot[1] += p.y; tot[2] += p.z; tot[3] += p.w;
+      }
+#pragma unroll
+      for (int off = 4; off < 32; off <<= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tot[i] += __shfl_xor_sync(0xffffffffu, tot[i], off);
+      float Dc[2][4];             // accumulator values 2^23 + total of this lane
+      unsigned long long qc = 0;  // the sum of their squared counts in one tile
+#pragma unroll
+      for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Dc[n][i] = __uint_as_float(kOffBits + tot[2 * n + (i & 1)]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) qc += 2ull * tot[i] * tot[i];  // rows fr and fr + 8
+      for (int y = y0; y < y0 + ychunk; ++y) row_out(y, std::integral_constant<int, 3>{}, Dc, qc);
     }
-    if (!sliding) continue;
-    __syncthreads();  // V and TT of row y no longer read
-    if (y + 1 < y0 + ychunk) {
-      if (lane_cols) {  // V and TT: window of row y + 1
-        // predicates and addresses first, then every load, then every store
-        // (each column has one owner, so plain read-modify-writes; the tile
-        // totals are shared by the lanes of a tile: integer atomics)
-        bool po[CPL], pi[CPL];
-        int bo[CPL], bi[CPL];
-        __half vo[CPL], vi[CPL];
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const int co = code_at(nxt_out, c), ci = code_at(nxt_in, c);
-          bo[c] = co - g0;
-          bi[c] = ci - g0;
-          po[c] = co != ci && static_cast<unsigned>(bo[c]) < static_cast<unsigned>(kBhG);
-          pi[c] = co != ci && static_cast<unsigned>(bi[c]) < static_cast<unsigned>(kBhG);
-        }
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          if (po[c]) vo[c] = *reinterpret_cast<const __half*>(v_col + 32 * c + 2 * bo[c]);
-          if (pi[c]) vi[c] = *reinterpret_cast<const __half*>(v_col + 32 * c + 2 * bi[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          if (po[c]) *reinterpret_cast<__half*>(v_col + 32 * c + 2 * bo[c]) = __hadd(vo[c], mone);
-          if (pi[c]) *reinterpret_cast<__half*>(v_col + 32 * c + 2 * bi[c]) = __hadd(vi[c], one);
-        }
-        if (need_tt) {
+  } else {
+    float D0[2][4];  // unused outside the constant-window path
+    // w = N below 32 columns: V and TT never change, no barriers
+    for (int y = y0; y < y0 + ychunk; ++y) {
+      if (owner) {
+        if (lc == 0)
+          row_out(y, std::integral_constant<int, 0>{}, D0, 0ull);
+        else if (lc == 1)
+          row_out(y, std::integral_constant<int, 1>{}, D0, 0ull);
+        else
+          row_out(y, std::integral_constant<int, 2>{}, D0, 0ull);
+      }
+      if (!sliding) continue;
+      __syncthreads();  // V and TT of row y no longer read
+      if (y + 1 < y0 + ychunk) {
+        if (lane_cols) {  // V and TT: window of row y + 1
+          // predicates and addresses first, then every load, then every store
+          // (each column has one owner, so plain read-modify-writes; the tile
+          // totals are shared by the lanes of a tile: integer atomics)
+          bool po[CPL], pi[CPL];
+          int bo[CPL], bi[CPL];
+          __half vo[CPL], vi[CPL];
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
-            if (po[c]) atomicAdd(tr + tt_pos(bo[c]), -1);
-            if (pi[c]) atomicAdd(tr + tt_pos(bi[c]), 1);
+            const int co = code_at(nxt_out, c), ci = code_at(nxt_in, c);
+            bo[c] = co - g0;
+            bi[c] = ci - g0;
+            po[c] = co != ci && static_cast<unsigned>(bo[c]) < static_cast<unsigned>(kBhG);
+            pi[c] = co != ci && static_cast<unsigned>(bi[c]) < static_cast<unsigned>(kBhG);
+          }
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            if (po[c]) vo[c] = *reinterpret_cast<const __half*>(v_col + 32 * c + 2 * bo[c]);
+            if (pi[c]) vi[c] = *reinterpret_cast<const __half*>(v_col + 32 * c + 2 * bi[c]);
+          }
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            if (po[c]) *reinterpret_cast<__half*>(v_col + 32 * c + 2 * bo[c]) = __hadd(vo[c], mone);
+            if (pi[c]) *reinterpret_cast<__half*>(v_col + 32 * c + 2 * bi[c]) = __hadd(vi[c], one);
+          }
+          if (need_tt) {
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              if (po[c]) atomicAdd(tr + tt_pos(bo[c]), -1);
+              if (pi[c]) atomicAdd(tr + tt_pos(bi[c]), 1);
+            }
           }
         }
+        if (y + 2 < y0 + ychunk) fetch(y + 2);
+        __syncthreads();  // V and TT of row y + 1 complete
       }
-      if (y + 2 < y0 + ychunk) fetch(y + 2);
-      __syncthreads();  // V and TT of row y + 1 complete
     }
   }
   if (MODE == kBhBf16 && owner && lane == 0) bulk_wait0();
