@@ -515,6 +515,12 @@ typedef struct gsp_material_grad {
   float* dft;
 } gsp_material_grad;
 
+/* Scratch of gsp_range_query_backward for these materials: the gradients of
+ * each material's summed-area-table prefix sums (2 (bins + 1) rank floats),
+ * then 128 private copies of every material's small gradient tables ((levels
+ * + 2 (bins + 1)) rank floats each), which the adjoint's CTAs accumulate into
+ * (a copy is shared by at most two CTAs) and one kernel sums afterwards.
+ * 0 for invalid arguments. */
 size_t gsp_backward_workspace_bytes(const gsp_material* h_mats, int n_mats);
 
 /* Accumulate (+=) d(sum_i g_i q_i)/d(factors) into h_grads[m] for every
@@ -532,8 +538,9 @@ int gsp_range_query_backward(const gsp_material* h_mats, int n_mats, const gsp_q
  * own, or a frame loop that must not call cudaMalloc because it synchronises
  * the whole device.  The paper has no counterpart; this is a calling
  * convention of this library.
- *  The scratch (the per-material gradients of the summed-area-table prefix
- *  sums, gsp_backward_workspace_bytes() of them) comes from one fixed array of
+ *  The scratch (gsp_backward_workspace_bytes() of it: the per-material
+ *  gradients of the summed-area-table prefix sums and the private copies of
+ *  the small gradient tables) comes from one fixed array of
  *  GSP_BACKWARD_NOALLOC_MAX_BYTES in device memory that the library defines;
  *  every GPU that loads the library holds it until the process exits.  Larger
  *  material sets are rejected with GSP_ERR_WORKSPACE before anything is

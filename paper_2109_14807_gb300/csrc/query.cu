@@ -67,11 +67,12 @@ struct GradParams {
   // adds them to global memory once at the end.
   int soff[GSP_MAX_MATERIALS + 1];
   int use_smem;
-  // Packed-query kernel (k_range_query_bwd_q): per-material offsets within
-  // one copy of the shared tables (dflw [L][RS], dP_s [B+1][RS], dP_t [B+1][RS],
-  // RS = R rounded up to 32) and the stride between the copies.
-  int qoff[GSP_MAX_MATERIALS + 1];
-  int copy_stride;
+  // Packed-query kernel (k_range_query_bwd_q): kBwdCopies private copies of
+  // the small tables in the workspace, priv_floats floats each; material m's
+  // tables (dflw [L][R], dP_s [B+1][R], dP_t [B+1][R]) at poff[m] in a copy.
+  float* priv;
+  int poff[GSP_MAX_MATERIALS + 1];
+  int priv_floats;
 };
 
 struct SmallGrad {
@@ -655,11 +656,14 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_range_query_bwd(const __grid
 // LANES * 4 <= 32 ranks per block, runs of 4 consecutive ranks per lane,
 // float4 gathers), 32 / LANES queries per warp step.  The per-query work (terms,
 // addresses, branches) is then shared by a quarter of a warp instead of all of
-// it.  Each lane-group position of a warp has its own copy of the small
-// gradient tables in shared memory; the copies start LANES banks apart and a
-// group's lanes write consecutive words, so the groups' reductions never share
-// a bank.  The angular gradients go to the prefix rows only: with
-// E[j] = dP[j + 1] and dS/df[k] = sum_{j >= k} E[j], a side's update is
+// it.  The small gradient tables (level rows, and the angular gradients in the
+// prefix rows only, below) are accumulated in kBwdCopies private copies in
+// global memory, CTA b adding to copy b mod kBwdCopies: a lane adds its run of
+// 4 ranks to a row with one 16-byte reduction, which the L2's atomic units
+// take (shared-memory float reductions, 10 per query and rank, were the
+// kernel's bound: 2.24 ms against 1.5 ms per 10^7 bench queries).  k_bwd_flush
+// sums the copies afterwards.  With E[j] = dP[j + 1] and dS/df[k] =
+// sum_{j >= k} E[j], a side's update is
 //   zero width / one bin i0:  dP[i0 + 1] += c, dP[i0] -= c
 //   i0 < i1, a = c / w:       dP[i1 + 1] += a f1, dP[i1] += a (1 - f1) (i1 > i0 + 1),
 //                             dP[i0 + 1] += a (1 - f0) - a_{i0+1}, dP[i0] -= a (1 - f0)
@@ -667,38 +671,39 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_range_query_bwd(const __grid
 // prefix rows into the bin gradients (dP[0] is never read).  A batch's live
 // queries (well formed, non-zero upstream gradient) are packed to the front of
 // the warp's slots, so no lane group waits on a skipped query.
-// The four prefix-row updates of one side, without branches (every lane
-// group of a warp then takes the same path whatever its query's range): rows
-// that a range does not touch receive 0.  The table reductions carry no
-// memory clobber, so the compiler may issue the next query's slot loads ahead
-// of them: the tables are read only after the kernel's final __syncthreads(),
-// and volatile asm is not moved across it.
-__device__ __forceinline__ void side_grad_p(uint32_t dp, int RS, int col, float c, int i0, int i1,
-                                            float f0, float f1, float inv_w, int iz, int B) {
-  const bool span = inv_w > 0.0f && i0 != i1;  // the range crosses a bin border
-  const bool wide = i1 > i0 + 1;               // whole bins between the ends
-  const float a = c * inv_w;
-  const float e0 = a * (1.0f - f0);
-  const int i = inv_w > 0.0f ? i0 : iz;
-  const int r1 = span ? min(i1 + 1, B) : i + 1;  // f1 = 0 when i1 = B
-  const float v1 = span ? a * f1 : c;
-  const float v2 = span && wide ? a - a * f1 : 0.0f;
-  const float v3 = span ? (wide ? e0 - a : e0 - a * f1) : 0.0f;
-  const float v4 = span ? -e0 : -c;
-  auto add = [&](int row, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(dp + 4u * static_cast<uint32_t>(row * RS + col)),
-                 "f"(v));
-  };
-  add(r1, v1);
-  add(span ? i1 : i, v2);
-  add(span ? i0 + 1 : i, v3);
-  add(i, v4);
+constexpr int kBwdCopies = 128;
+
+// Add v to p (4 consecutive floats) at the L2, without a memory clobber: the
+// private copies are read only by the next kernel.
+__device__ __forceinline__ void red_add4_nc(float* p, const float (&v)[4]) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]));
 }
 
-// One CTA of 16 warps per SM: its warps share one set of table copies, which
-// leaves most of the SM's 256 KB of L1 / shared memory to cache the query
-// tables (two CTAs of 8 warps with their own copies starved L1 to a 35 % hit
-// rate).
+// The prefix-row updates of one side for 4 ranks (values c[v]): rows and
+// values as above; a row whose value is zero for this query is not added.
+__device__ __forceinline__ void side_grad4(float* dp, int R, int rb, const float (&c)[4], int i0,
+                                           int i1, float f0, float f1, float inv_w, int iz, int B) {
+  const bool span = inv_w > 0.0f && i0 != i1;  // the range crosses a bin border
+  const bool wide = i1 > i0 + 1;               // whole bins between the ends
+  const int i = inv_w > 0.0f ? i0 : iz;
+  float v1[4], v2[4], v3[4], v4[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const float a = c[v] * inv_w;
+    const float e0 = a * (1.0f - f0);
+    v1[v] = span ? a * f1 : c[v];
+    v2[v] = a - a * f1;
+    v3[v] = wide ? e0 - a : e0 - a * f1;
+    v4[v] = span ? -e0 : -c[v];
+  }
+  red_add4_nc(dp + (span ? min(i1 + 1, B) : i + 1) * R + rb, v1);  // f1 = 0 when i1 = B
+  if (span && wide) red_add4_nc(dp + i1 * R + rb, v2);
+  if (span) red_add4_nc(dp + (i0 + 1) * R + rb, v3);
+  red_add4_nc(dp + i * R + rb, v4);
+}
+
+// One CTA of 16 warps per SM.
 constexpr int kBwdQThreads = 512;
 constexpr int kBwdQWarps = kBwdQThreads / 32;
 
@@ -709,18 +714,13 @@ __global__ void __launch_bounds__(kBwdQThreads, 1) k_range_query_bwd_q(
   constexpr int V = 4;
   constexpr int W = V * LANES;  // ranks per block
   constexpr int QPW = 32 / LANES;
-  extern __shared__ float sacc[];  // QPW copies of gp.copy_stride floats
   __shared__ float4 tslots[kBwdQWarps][32][5];
   const int lane = threadIdx.x & 31;
   const int sub = lane / LANES;
   const int j = lane % LANES;
   const long long warp_id = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
-  const int total = QPW * gp.copy_stride;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) sacc[e] = 0.0f;
-  __syncthreads();
-  const uint32_t copy =
-      static_cast<uint32_t>(__cvta_generic_to_shared(sacc)) + 4u * static_cast<uint32_t>(sub * gp.copy_stride);
+  float* const copy = gp.priv + static_cast<size_t>(blockIdx.x % kBwdCopies) * gp.priv_floats;
   float4 (*slots)[5] = tslots[threadIdx.x >> 5];
   const long long n_batches = (n + 31) / 32;
   gsp_query dn{};
@@ -784,14 +784,13 @@ __global__ void __launch_bounds__(kBwdQThreads, 1) k_range_query_bwd_q(
       const float g = w4.z;
       const gsp_material& M = mp.m[m];
       const int R = M.rank, L = M.levels, B = M.bins;
-      const int RS = (R + 31) & ~31;
       const float* flw = M.tables;
       const float* sats = M.tables + flw_floats(L, R);
       const float* satt = sats + static_cast<size_t>(B + 1) * kSatPlanes * R;
       const gsp_material_grad& G = gp.g[m];
-      const uint32_t tflw = copy + 4u * static_cast<uint32_t>(gp.qoff[m]);
-      const uint32_t tps = tflw + 4u * static_cast<uint32_t>(L * RS);
-      const uint32_t tpt = tps + 4u * static_cast<uint32_t>((B + 1) * RS);
+      float* const tflw = copy + gp.poff[m];   // [L][R]
+      float* const tps = tflw + L * R;         // [B + 1][R]
+      float* const tpt = tps + (B + 1) * R;    // [B + 1][R]
       const float g0 = 1.0f - f;
       // the second level row only when a query of this step blends two levels
       // (warp-uniform over the active lane groups, so no divergence)
@@ -805,54 +804,62 @@ __global__ void __launch_bounds__(kBwdQThreads, 1) k_range_query_bwd_q(
         ldg_n<V>(M.fy + static_cast<size_t>(y) * R + rb, yv);
         sat_mean<V>(sats, R, rb, is0, is1, fs0, fs1, inv_ws, isz, S);
         sat_mean<V>(satt, R, rb, it0, it1, ft0, ft1, inv_wt, itz, T);
+        // each group of reductions goes out as soon as its values exist
+        float lv[V], gxl[V], t4[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const int col = r0 + v * LANES + j;  // consecutive words across the group
-          const float lv = fmaf(f, a1[v], g0 * a0[v]);
-          const float xy = xv[v] * yv[v];
+          lv[v] = fmaf(f, a1[v], g0 * a0[v]);
+          t4[v] = g * xv[v] * yv[v] * S[v] * T[v] * g0;  // level row l0
+        }
+        red_add4_nc(tflw + l0 * R + rb, t4);
+        if (blend) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) t4[v] = g * xv[v] * yv[v] * S[v] * T[v] * f;
+          red_add4_nc(tflw + l1 * R + rb, t4);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          gxl[v] = g * xv[v] * yv[v] * lv[v];
+          t4[v] = gxl[v] * T[v];
+        }
+        side_grad4(tps, R, rb, t4, is0, is1, fs0, fs1, inv_ws, isz, B);
+#pragma unroll
+        for (int v = 0; v < V; ++v) t4[v] = gxl[v] * S[v];
+        side_grad4(tpt, R, rb, t4, it0, it1, ft0, ft1, inv_wt, itz, B);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
           const float st = S[v] * T[v];
-          dx[v] = g * yv[v] * lv * st;
-          dy[v] = g * xv[v] * lv * st;
-          const float gxs = g * xy * st;
-          asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(tflw + 4u * static_cast<uint32_t>(l0 * RS + col)),
-                       "f"(gxs * g0));
-          if (blend)
-            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(tflw + 4u * static_cast<uint32_t>(l1 * RS + col)),
-                         "f"(gxs * f));
-          const float gxl = g * xy * lv;
-          side_grad_p(tps, RS, col, gxl * T[v], is0, is1, fs0, fs1, inv_ws, isz, B);
-          side_grad_p(tpt, RS, col, gxl * S[v], it0, it1, ft0, ft1, inv_wt, itz, B);
+          dx[v] = g * yv[v] * lv[v] * st;
+          dy[v] = g * xv[v] * lv[v] * st;
         }
         red_add<V>(G.dfx + static_cast<size_t>(x) * R + rb, dx);
         red_add<V>(G.dfy + static_cast<size_t>(y) * R + rb, dy);
       }
     }
   }
-  __syncthreads();
-  // add the copies and flush: entry (row, r) sits at column r0 + v * LANES + j
-  // of its row, r = r0 + 4 j + v
-  for (int mm = 0; mm < mp.n; ++mm) {
-    const gsp_material& M = mp.m[mm];
-    const int R = M.rank, L = M.levels, B = M.bins;
-    const int RS = (R + 31) & ~31;
-    const int rows = L + 2 * (B + 1);
-    const gsp_material_grad& G = gp.g[mm];
-    for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
-      const int row = e / R, r = e - row * R;
-      const int r0 = r / W * W, jj = (r - r0) / V, vv = (r - r0) % V;
-      const int at = gp.qoff[mm] + row * RS + r0 + vv * LANES + jj;
-      float sum = 0.0f;
-#pragma unroll
-      for (int c = 0; c < QPW; ++c) sum += sacc[c * gp.copy_stride + at];
-      if (sum == 0.0f) continue;
-      if (row < L)
-        atomicAdd(G.dflw + row * R + r, sum);
-      else if (row < L + B + 1)
-        atomicAdd(gp.dps[mm] + (row - L) * R + r, sum);
-      else
-        atomicAdd(gp.dpt[mm] + (row - L - B - 1) * R + r, sum);
-    }
-  }
+}
+
+// The private copies of k_range_query_bwd_q summed into the level-row
+// gradients (the caller's dflw, added to) and the prefix-row gradients (the
+// workspace's dps, dpt); thread: one entry of one material's tables.
+__global__ void k_bwd_flush(const __grid_constant__ MatParams mp, const __grid_constant__ GradParams gp,
+                            int copies) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  const gsp_material& M = mp.m[m];
+  const int R = M.rank, L = M.levels, B = M.bins;
+  if (e >= (L + 2 * (B + 1)) * R) return;
+  const float* src = gp.priv + gp.poff[m] + e;
+  float sum = 0.0f;
+#pragma unroll 8
+  for (int c = 0; c < copies; ++c) sum += __ldcg(src + static_cast<size_t>(c) * gp.priv_floats);
+  if (sum == 0.0f) return;
+  if (e < L * R)
+    atomicAdd(gp.g[m].dflw + e, sum);  // materials may share their gradient arrays
+  else if (e < (L + B + 1) * R)
+    gp.dps[m][e - L * R] += sum;
+  else
+    gp.dpt[m][e - (L + B + 1) * R] += sum;
 }
 
 // dP[i] is the gradient w.r.t. P[i] = sum_{k<i} f[k]; so df[k] += sum_{i>k} dP[i].
@@ -1273,12 +1280,17 @@ extern "C" int gsp_range_query_interp(const gsp_material* h_mats, int n_mats,
                                   d_out, d_status, tuning, d_ws, ws_bytes, stream);
 }
 
+// The prefix-row gradients dP_s, dP_t of every material, then kBwdCopies
+// private copies of the small tables (level rows and both prefix-row sets).
 extern "C" size_t gsp_backward_workspace_bytes(const gsp_material* h_mats, int n_mats) {
   if (!h_mats || n_mats < 1 || n_mats > GSP_MAX_MATERIALS) return 0;
-  size_t total = 0;
-  for (int i = 0; i < n_mats; ++i)
-    total += 2 * align_up(static_cast<size_t>(h_mats[i].bins + 1) * h_mats[i].rank * sizeof(float), 256);
-  return total;
+  size_t total = 0, copy = 0;
+  for (int i = 0; i < n_mats; ++i) {
+    const gsp_material& m = h_mats[i];
+    total += 2 * align_up(static_cast<size_t>(m.bins + 1) * m.rank * sizeof(float), 256);
+    copy += static_cast<size_t>(m.levels + 2 * (m.bins + 1)) * m.rank;
+  }
+  return total + align_up(kBwdCopies * copy * sizeof(float), 256);
 }
 
 extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
@@ -1306,6 +1318,14 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
     gp.dpt[i] = reinterpret_cast<float*>(w + b);
     w += 2 * b;
   }
+  gp.priv = reinterpret_cast<float*>(w);  // 256-aligned
+  int po = 0;
+  for (int i = 0; i < n_mats; ++i) {
+    gp.poff[i] = po;
+    po += h_mats[i].rank * (h_mats[i].levels + 2 * (h_mats[i].bins + 1));
+  }
+  gp.poff[n_mats] = po;
+  gp.priv_floats = po;
   // small tables of all materials in shared memory when they fit in 96 KB
   int off = 0;
   for (int i = 0; i < n_mats; ++i) {
@@ -1319,11 +1339,9 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
   cudaStream_t s = to_stream(stream);
   GSP_CUDA(cudaMemsetAsync(d_ws, 0, need, s));
   // Packed-query kernel: every rank a multiple of W = min(32, R) >= 8 (the
-  // same W for all materials), factor and gradient rows 16-byte aligned, and
-  // 32 / (W / 4) copies of the small tables in shared memory.
+  // same W for all materials), factor and gradient rows 16-byte aligned.
   int pw = 0;
   bool packed = true;
-  int qo = 0;
   for (int i = 0; i < n_mats && packed; ++i) {
     const gsp_material& m = h_mats[i];
     const gsp_material_grad& g = h_grads[i];
@@ -1332,28 +1350,27 @@ extern "C" int gsp_range_query_backward(const gsp_material* h_mats, int n_mats,
     const uintptr_t al = reinterpret_cast<uintptr_t>(m.fx) | reinterpret_cast<uintptr_t>(m.fy) |
                          reinterpret_cast<uintptr_t>(g.dfx) | reinterpret_cast<uintptr_t>(g.dfy);
     packed = wm == pw && wm >= 8 && (wm & (wm - 1)) == 0 && m.rank % wm == 0 && (al & 15) == 0;
-    gp.qoff[i] = qo;
-    const int RS = (m.rank + 31) & ~31;
-    qo += RS * (m.levels + 2 * (m.bins + 1));  // a multiple of 32 floats
   }
-  gp.qoff[n_mats] = qo;
   const int plan = pw / 4;  // lanes per query
-  gp.copy_stride = qo + plan;  // copies start plan banks apart
-  const size_t qdyn = packed ? static_cast<size_t>(32 / plan) * gp.copy_stride * sizeof(float) : 0;
-  if (packed && qdyn > 200 * 1024) packed = false;
   if (n > 0 && packed) {
     const long long blocks = ((n + 31) / 32 * 32 + kBwdQThreads - 1) / kBwdQThreads;
+    int lmax = 0;
+    for (int i = 0; i < n_mats; ++i)
+      lmax = std::max(lmax, h_mats[i].rank * (h_mats[i].levels + 2 * (h_mats[i].bins + 1)));
     prof_begin(PROF_QUERY_BWD, s);
     int rc = GSP_OK;
     if (plan == 8)
-      rc = launch_bwd_q<8>(blocks, qdyn, s, mp, gp, d_q, n, d_gout, d_status);
+      rc = launch_bwd_q<8>(blocks, 0, s, mp, gp, d_q, n, d_gout, d_status);
     else if (plan == 4)
-      rc = launch_bwd_q<4>(blocks, qdyn, s, mp, gp, d_q, n, d_gout, d_status);
+      rc = launch_bwd_q<4>(blocks, 0, s, mp, gp, d_q, n, d_gout, d_status);
     else
-      rc = launch_bwd_q<2>(blocks, qdyn, s, mp, gp, d_q, n, d_gout, d_status);
-    GSP_TRY(rc);
+      rc = launch_bwd_q<2>(blocks, 0, s, mp, gp, d_q, n, d_gout, d_status);
+    if (rc == GSP_OK) {
+      k_bwd_flush<<<dim3((lmax + 255) / 256, n_mats), 256, 0, s>>>(mp, gp, kBwdCopies);
+      rc = cudaGetLastError() == cudaSuccess ? GSP_OK : GSP_ERR_CUDA;
+    }
     prof_end(PROF_QUERY_BWD, s);
-    GSP_CHECK_LAUNCH();
+    GSP_TRY(rc);
   } else if (n > 0) {
     // VEC: 2 when it divides every rank (with at least four vectors per rank
     // row) and keeps the factor rows and gradients aligned, else 1; LANES x
