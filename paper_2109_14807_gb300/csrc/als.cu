@@ -462,6 +462,69 @@ __global__ void __launch_bounds__(256) k_contract(CParams p) {
   }
 }
 
+// M[i][r] = sum_j W[i * wi + j * w1][r] * A1[j][r] (the x and y contractions
+// of Y'), rows of R floats read as float4: one CTA per i, its threads = groups
+// of j x R / 4 runs of 4 ranks, 4 row pairs in flight per thread (16-byte
+// loads: one 4-byte load per thread and row left these passes at half the HBM
+// rate); the group sums are combined in shared memory in a fixed order.
+// R % 4 == 0, W and A1 16-byte aligned.
+__global__ void __launch_bounds__(256) k_contract4(const float* __restrict__ W, long long wi,
+                                                   long long w1, int J, const float* __restrict__ A1,
+                                                   int R, double* __restrict__ M,
+                                                   float* __restrict__ Mf) {
+  __shared__ float4 part[256];
+  const int RV = R >> 2;
+  const int G = blockDim.x / RV;
+  const int i = blockIdx.x;
+  const int gj = threadIdx.x / RV, r4 = threadIdx.x % RV;
+  const float4* W4 = reinterpret_cast<const float4*>(W);
+  const float4* A4 = reinterpret_cast<const float4*>(A1);
+  float4 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto fma4 = [](float4& c, float4 a, float4 b) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.y = fmaf(a.y, b.y, c.y);
+    c.z = fmaf(a.z, b.z, c.z);
+    c.w = fmaf(a.w, b.w, c.w);
+  };
+  if (gj < G) {
+    int j = gj;
+    for (; j + 3 * G < J; j += 4 * G) {
+      float4 w[4], a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long jj = j + u * G;
+        w[u] = __ldg(W4 + (i * wi + jj * w1) * RV + r4);
+        a[u] = __ldg(A4 + jj * RV + r4);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) fma4(acc[u], w[u], a[u]);
+    }
+    for (; j < J; j += G)
+      fma4(acc[0], __ldg(W4 + (i * wi + static_cast<long long>(j) * w1) * RV + r4),
+           __ldg(A4 + static_cast<long long>(j) * RV + r4));
+    part[threadIdx.x] = make_float4((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
+                                    (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
+                                    (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z),
+                                    (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w));
+  }
+  __syncthreads();
+  if (gj == 0) {
+    float4 t = part[r4];
+    for (int k = 1; k < G; ++k) {
+      const float4 v = part[k * RV + r4];
+      t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+    }
+    const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (M) M[i * R + 4 * r4 + c] = static_cast<double>(tv[c]);
+      if (Mf) Mf[i * R + 4 * r4 + c] = tv[c];
+    }
+  }
+}
+
 // M[i][r] = sum_j W[(i + j*w1)][r] * A1[j][r] for rows i of stride 1: one CTA
 // per row i, its 256 threads = 256/R groups of j (j = g, g + G, ...) x R
 // ranks, 8 loads in flight per thread; the group sums are combined in shared
@@ -534,11 +597,27 @@ __global__ void k_gram_sum(const double* __restrict__ Gpart, int chunks, int R2,
 // Hadamard product of the four Gram matrices other than `skip`.
 // V (row stride ld) = Hadamard product of the Gram matrices of all modes but `skip`.
 __device__ void hadamard_v(const double* __restrict__ G, int R, int skip, double* V, int ld) {
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    double v = 1.0;
-    for (int m = 0; m < 5; ++m)
-      if (m != skip) v *= G[m * R * R + e];
-    V[(e / R) * ld + e % R] = v;
+  // four elements per thread and pass, their 16 Gram loads issued together
+  const int RR = R * R;
+  for (int e0 = threadIdx.x; e0 < RR; e0 += 4 * blockDim.x) {
+    double v[4] = {1.0, 1.0, 1.0, 1.0};
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      if (m == skip) continue;
+      double g[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = e0 + k * static_cast<int>(blockDim.x);
+        g[k] = e < RR ? G[m * RR + e] : 1.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] *= g[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = e0 + k * static_cast<int>(blockDim.x);
+      if (e < RR) V[(e / R) * ld + e % R] = v[k];
+    }
   }
 }
 
@@ -564,11 +643,15 @@ __host__ __device__ inline SolveScratch solve_scratch(double* fac, int R) {
   return s;
 }
 
+// Threads of k_chol (1024 made its latency-bound FP64 steps slower: the
+// steps' barriers span more warps).
+constexpr int kCholThreads = 256;
+
 // One CTA: factor V (Hadamard product of the other modes' Grams) for the
 // least-squares update: L and 1/diag(L), mode 0.  When V is not numerically
 // positive definite: W = V^+ from a Jacobi eigendecomposition, mode 1, and
 // GSP_DEV_NUMERIC.
-__global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int R, int skip,
+__global__ void __launch_bounds__(kCholThreads) k_chol(const double* __restrict__ G, int R, int skip,
                                               double* __restrict__ out, uint32_t* flags) {
   extern __shared__ double smem[];
   __shared__ double invd_s[kMaxCpRank];
@@ -873,7 +956,11 @@ int contract(const Ctx& c, int mode, const gsp_cp_factors& f, double* M, float* 
       break;
   }
   prof_begin(PROF_ALS_SMALL, c.s);
-  if (mode == 0)
+  const bool v4 = d.R % 4 == 0 && d.R <= 256 &&
+                  ((reinterpret_cast<uintptr_t>(p.W) | reinterpret_cast<uintptr_t>(p.A1)) & 15) == 0;
+  if (mode <= 1 && v4)
+    k_contract4<<<I, 256, 0, c.s>>>(p.W, p.wi, p.w1, p.J1, p.A1, d.R, M, Mf);
+  else if (mode == 0)
     k_contract_rows<<<I, 256, 0, c.s>>>(p.W, p.w1, p.J1, p.A1, d.R, M, Mf);
   else if (mode == 1)
     k_contract<<<I, 256, 0, c.s>>>(p);
@@ -923,7 +1010,8 @@ int solve_factor(const Ctx& c, int mode, cudaStream_t st) {
                 (R <= kJacobiMaxRank ? static_cast<size_t>(R) * R * sizeof(double) : 0);
   double* fac = c.at<double>(c.lay.W);
   prof_begin(PROF_SOLVE, st);
-  k_chol<<<1, 256, smem, st>>>(c.at<double>(c.lay.G), R, mode, fac, c.at<uint32_t>(c.lay.flags));
+  k_chol<<<1, kCholThreads, smem, st>>>(c.at<double>(c.lay.G), R, mode, fac,
+                                       c.at<uint32_t>(c.lay.flags));
   GSP_CHECK_LAUNCH();
   k_inv_cols<<<(R + 3) / 4, 128, 0, st>>>(fac, R);
   GSP_CHECK_LAUNCH();

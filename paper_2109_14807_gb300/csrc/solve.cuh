@@ -107,12 +107,14 @@ __device__ inline bool cholesky_packed(double* V, int R, int ld, double thresh, 
   return true;
 }
 
+// Largest |V_aa| (one warp; a maximum does not depend on the order).
 __device__ inline double max_diag(const double* V, int R, int ld) {
   __shared__ double mx;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     double m = 0.0;
-    for (int a = 0; a < R; ++a) m = fmax(m, fabs(V[a * ld + a]));
-    mx = m;
+    for (int a = threadIdx.x; a < R; a += 32) m = fmax(m, fabs(V[a * ld + a]));
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (threadIdx.x == 0) mx = m;
   }
   __syncthreads();
   return mx;
