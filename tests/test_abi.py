@@ -81,3 +81,22 @@ def test_host_side_sizes_and_validation(lib):
     f = _lib.CpFactors()
     assert lib.gsp_cp_sweeps(32, 6, 16, 8, ctypes.byref(opts), ctypes.byref(f), None, None, 0,
                              None) == -1
+
+
+def test_backward_workspace_holds_the_private_copies(lib):
+    # the adjoint's scratch: each material's summed-area-table prefix-row
+    # gradients (2 (B+1) R floats, 256-byte aligned each), then 128 private
+    # copies of every material's small gradient tables ((L + 2 (B+1)) R floats)
+    def align(b):
+        return -(-b // 256) * 256
+
+    shapes = [(1024, 11, 32, 64), (64, 7, 32, 64), (32, 6, 16, 16)]
+    mats = [_lib.Material(N, L, B, R, 1, 1, 1, 1, 1, 1, 1) for N, L, B, R in shapes]
+    arr = (_lib.Material * len(mats))(*mats)
+    want = sum(2 * align((B + 1) * R * 4) for _, _, B, R in shapes)
+    want += align(128 * sum((L + 2 * (B + 1)) * R for _, L, B, R in shapes) * 4)
+    assert lib.gsp_backward_workspace_bytes(arr, len(mats)) == want
+    # one material of the 1024^2 / 11-level / 32^2-bin / rank-64 shape fits the
+    # no-allocation entry's fixed array
+    assert lib.gsp_backward_workspace_bytes(arr, 1) <= 4 << 20
+    assert lib.gsp_backward_workspace_bytes(arr, 0) == 0
