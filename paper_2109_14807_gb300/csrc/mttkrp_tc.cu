@@ -121,9 +121,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 
 // Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
-// A major-ness (0 = K-major, 1 = MN-major), B K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t a_mn, uint32_t n) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | (a_mn << 15) | ((n >> 3) << 17) |
+// A and B major-ness (0 = K-major, 1 = MN-major), M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t a_mn, uint32_t n,
+                                             uint32_t b_mn = 0) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (a_mn << 15) | (b_mn << 16) | ((n >> 3) << 17) |
          ((128u >> 4) << 24);
 }
 
@@ -236,6 +237,7 @@ struct Barriers {
   uint64_t b_full[kMaxStages];
   uint64_t b_empty[kMaxStages];
   uint64_t drain;
+  uint64_t xchg[2];  // rank-row Z' pass: hi sums stored, per segment
   uint32_t tmem_base;
   int abort;
 };
@@ -692,6 +694,248 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------- Z' pass, rank rows --
+// The same contraction with the operands' roles exchanged, for the BF16 hi + lo
+// pair at rank 64: the FXt tile (hi rows 0..63, lo rows 64..127) is the K-major
+// A operand (M = 128) and the W st columns of the CTA's group the MN-major B
+// operand, loaded as boxes of 16 columns x E128 rows with 32-byte swizzling.
+// One MMA of N = W per K slice then covers the hi and lo parts, and no
+// accumulator row is padding (with st as M, 48 of the 128 rows were padding at
+// 80 stored columns, and hi and lo took an MMA each).  TMEM lane
+// r2 = 32 warp + lane holds rank r2 mod 64 of the hi (r2 < 64) or lo part, so
+// fy[y][r] is one scalar per thread.  At a segment's last row the hi threads
+// store their sums to the partial slice; the lo threads keep theirs in the
+// running sums and, once the hi threads have arrived at the segment's exchange
+// barrier, add them to the slice.  Columns at or past Bt (the stored columns)
+// are not written.
+constexpr int kSwRank = 64;          // M = 2R = 128
+constexpr int kSwMaxCols = 80;       // 3 W <= 256 TMEM columns: two CTAs per SM
+constexpr int kSwBox = 64 * 16 * 2;  // one box: E128 = 64 rows x 16 BF16 columns
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_lst_tc_rows(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapFX,
+                  const float* __restrict__ fy, float* __restrict__ Zpart, int P, int logN, int L,
+                  int B2, int Bt, int W, int G, int kStages, int nB, int nAcc, uint32_t* err) {
+  constexpr int E128 = 64;
+  constexpr int R = kSwRank;
+  constexpr int b_bytes = 2 * R * 128;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ Barriers bar;
+  uint8_t* smem = align1024(smem_raw);
+  const int t_bytes = W * 128;  // W / 16 boxes; a multiple of 2048 bytes
+  uint8_t* bslots = smem + kStages * t_bytes;
+  const int nbox = W / 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N = 1 << logN;
+  const long long N2 = static_cast<long long>(N) * N;
+  const int spr = N / E128;
+  const long long spl = N2 / E128;
+  const long long K = spl * L;
+  const int g = blockIdx.x % G, p = blockIdx.x / G;
+  const int st0 = g * W;
+  const LstRange rg = lst_range(p, P, K, spl);
+  const uint32_t ncols = tmem_cols_for((nAcc + 1) * W);
+  volatile int* abort = &bar.abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar.full[s]), 1);
+      mbar_init(smem_u32(&bar.empty[s]), 1);
+    }
+    for (int b = 0; b < nAcc; ++b) {
+      mbar_init(smem_u32(&bar.acc_full[b]), 1);
+      mbar_init(smem_u32(&bar.acc_empty[b]), 128);
+    }
+    for (int b = 0; b < nB; ++b) {
+      mbar_init(smem_u32(&bar.b_full[b]), 1);
+      mbar_init(smem_u32(&bar.b_empty[b]), 1);
+    }
+    mbar_init(smem_u32(&bar.drain), 1);
+    mbar_init(smem_u32(&bar.xchg[0]), 64);
+    mbar_init(smem_u32(&bar.xchg[1]), 64);
+    bar.abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 5) tmem_alloc(smem_u32(&bar.tmem_base), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bar.tmem_base;
+
+  if (warp == 4) {
+    if (lane == 0) {  // ---- TMA producer: per step the FXt tile, then the T tile
+      int s = 0, bs = 0;
+      uint32_t ph = 0, bph = 0;
+      uint32_t issued_parity[kMaxStages], b_parity[kMaxStages];
+      bool issued[kMaxStages], b_issued[kMaxStages];
+      for (int i = 0; i < kMaxStages; ++i) issued[i] = b_issued[i] = false;
+      int xb = static_cast<int>(rg.k0 % spr);
+      for (long long k = rg.k0; k < rg.k1 && !*abort; ++k, xb = xb + 1 == spr ? 0 : xb + 1) {
+        if (!mbar_wait(smem_u32(&bar.b_empty[bs]), bph ^ 1u, abort)) goto producer_done;
+        {
+          const uint32_t bb = smem_u32(&bar.b_full[bs]);
+          mbar_expect_tx(bb, static_cast<uint32_t>(b_bytes));
+          tma_load_2d(smem_u32(bslots + bs * b_bytes), &mapFX, xb * E128, 0, bb);
+          b_issued[bs] = true;
+          b_parity[bs] = bph;
+          if (++bs == nB) {
+            bs = 0;
+            bph ^= 1u;
+          }
+        }
+        if (!mbar_wait(smem_u32(&bar.empty[s]), ph ^ 1u, abort)) goto producer_done;
+        {
+          const uint32_t sa = smem_u32(smem + s * t_bytes);
+          const uint32_t fb = smem_u32(&bar.full[s]);
+          mbar_expect_tx(fb, static_cast<uint32_t>(t_bytes));
+          const int trow = static_cast<int>(k * E128);
+          for (int b = 0; b < nbox; ++b) tma_load_2d(sa + b * kSwBox, &mapT, st0 + 16 * b, trow, fb);
+          issued[s] = true;
+          issued_parity[s] = ph;
+          if (++s == kStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    producer_done:
+      if (*abort) {  // wait for this CTA's own copies still in flight
+        for (int i = 0; i < kStages; ++i)
+          if (issued[i]) mbar_drain(smem_u32(&bar.full[i]), issued_parity[i]);
+        for (int i = 0; i < nB; ++i)
+          if (b_issued[i]) mbar_drain(smem_u32(&bar.b_full[i]), b_parity[i]);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {  // ---- MMA issuer
+      const uint32_t id = idesc(1u, 0u, static_cast<uint32_t>(W), 1u);
+      int s = 0, bs = 0;
+      uint32_t ph = 0, bph = 0, uph = 0;
+      int ab = 0;
+      bool any = false;
+      for (int seg = 0; seg < 2; ++seg) {
+        const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
+        for (long long c0 = kb; c0 < ke;) {  // one chunk (accumulator) per map row
+          const long long row_end = (c0 / spr + 1) * spr;
+          const long long c1 = row_end < ke ? row_end : ke;
+          if (!mbar_wait(smem_u32(&bar.acc_empty[ab]), uph ^ 1u, abort)) goto mma_done;
+          tc_fence_after();
+          const uint32_t d = tmem + static_cast<uint32_t>(ab * W);
+          for (long long k = c0; k < c1; ++k) {
+            if (!mbar_wait(smem_u32(&bar.b_full[bs]), bph, abort)) goto mma_done;
+            if (!mbar_wait(smem_u32(&bar.full[s]), ph, abort)) goto mma_done;
+            tc_fence_after();
+            // A: 128 FXt rows of 128 bytes, 8-row groups 1024 bytes apart.
+            // B: 16-column boxes kSwBox apart (LBO), 8-row groups of 32-byte rows
+            // 256 bytes apart (SBO); a K slice of 16 rows is 512 bytes.
+            const uint64_t a0 = sdesc(smem_u32(bslots + bs * b_bytes), 16, 1024);
+            const uint64_t b0 = sdesc(smem_u32(smem + s * t_bytes), kSwBox, 256, 6);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              umma<2>(d, a0 + 2 * j, b0 + 32 * j, id, (k > c0 || j > 0) ? 1u : 0u);
+            any = true;
+            umma_commit(smem_u32(&bar.empty[s]));
+            umma_commit(smem_u32(&bar.b_empty[bs]));
+            if (++s == kStages) {
+              s = 0;
+              ph ^= 1u;
+            }
+            if (++bs == nB) {
+              bs = 0;
+              bph ^= 1u;
+            }
+          }
+          umma_commit(smem_u32(&bar.acc_full[ab]));
+          if (++ab == nAcc) {
+            ab = 0;
+            uph ^= 1u;
+          }
+          c0 = c1;
+        }
+      }
+    mma_done:
+      if (*abort && any) {
+        umma_commit(smem_u32(&bar.drain));
+        mbar_drain(smem_u32(&bar.drain), 0);
+      }
+    }
+  } else {  // ---- warps 0-3: per map row, running sums += fy[y][r] * chunk
+    uint32_t uph = 0;
+    int ab = 0;
+    const int r2 = warp * 32 + lane, r = r2 & (R - 1);
+    const bool hi = r2 < R;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    const uint32_t sum_col = static_cast<uint32_t>(nAcc * W);
+    for (int seg = 0; seg < 2; ++seg) {
+      const long long kb = seg == 0 ? rg.k0 : rg.mid, ke = seg == 0 ? rg.mid : rg.k1;
+      if (kb >= ke) continue;
+      const long long row0 = kb / spr, row1 = (ke - 1) / spr;  // map rows (l N + y)
+      float* out = Zpart + (static_cast<size_t>(p) * 2 + seg) * B2 * R + static_cast<size_t>(st0) * R + r;
+      for (long long row = row0; row <= row1; ++row) {
+        const bool first = row == row0, last = row == row1;
+        const bool to_slice = last && hi;
+        const float f = __ldg(fy + static_cast<size_t>(row & (N - 1)) * R + r);
+        if (!mbar_wait(smem_u32(&bar.acc_full[ab]), uph, abort)) goto epi_done;
+        tc_fence_after();
+        for (int cb = 0; cb < nbox; ++cb) {
+          const uint32_t col = static_cast<uint32_t>(cb * 16);
+          uint32_t a[16], b[16];
+          tmem_ld16_nowait(lane_base + static_cast<uint32_t>(ab * W) + col, a);
+          if (!first) tmem_ld16_nowait(lane_base + sum_col + col, b);
+          tmem_ld_wait();
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            v[i] = first ? f * __uint_as_float(a[i]) : fmaf(f, __uint_as_float(a[i]), __uint_as_float(b[i]));
+          if (to_slice) {
+            if (st0 + 16 * cb < Bt) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) out[static_cast<size_t>(16 * cb + i) * R] = v[i];
+            }
+          } else {
+            tmem_st16(lane_base + sum_col + col, v);
+          }
+        }
+        if (!to_slice) tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bar.acc_empty[ab]));
+        if (++ab == nAcc) {
+          ab = 0;
+          uph ^= 1u;
+        }
+        if (last) {  // hi + lo into the partial slice
+          if (hi) {
+            mbar_arrive(smem_u32(&bar.xchg[seg]));
+          } else {
+            if (!mbar_wait(smem_u32(&bar.xchg[seg]), 0u, abort)) goto epi_done;
+            tc_fence_after();
+            for (int cb = 0; cb < nbox; ++cb) {
+              uint32_t b[16];
+              tmem_ld16_nowait(lane_base + sum_col + static_cast<uint32_t>(cb * 16), b);
+              tmem_ld_wait();
+              if (st0 + 16 * cb < Bt) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  float* o = out + static_cast<size_t>(16 * cb + i) * R;
+                  *o = *o + __uint_as_float(b[i]);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  epi_done:;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && bar.abort && err) atomicOr(err, GSP_DEV_TIMEOUT);
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
 // One CTA waits for a phase of an mbarrier that nothing arrives at: the
 // bounded wait gives up after kTimeoutCycles and the status path runs.
 __global__ void k_selftest_timeout(uint32_t* err) {
@@ -733,14 +977,19 @@ struct LstSegments {
 };
 
 // Z'[l][st][r] = sum over CTAs p (in order) of the partial slices whose segment
-// lies in level l.
+// lies in level l; zero for st rows at or past `rows` (not written by the pass).
 __global__ void k_lst_reduce(const float* __restrict__ Zpart, float* __restrict__ Zp, int P,
-                             int L, long long per_level, const __grid_constant__ LstSegments sg) {
+                             int L, long long per_level, long long rows_elems,
+                             const __grid_constant__ LstSegments sg) {
   const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (e >= per_level * L) return;
   const int l = static_cast<int>(e / per_level);
   const long long rem = e - l * per_level;
   float acc = 0.0f;
+  if (rem >= rows_elems) {
+    Zp[e] = 0.0f;
+    return;
+  }
   for (int p = 0; p < P; ++p) {
     if (sg.level[p][0] == l) acc += Zpart[(static_cast<long long>(p) * 2) * per_level + rem];
     if (sg.level[p][1] == l) acc += Zpart[(static_cast<long long>(p) * 2 + 1) * per_level + rem];
@@ -770,14 +1019,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 namespace {
 
-// 2D map over a row-major [rows][cols] matrix, box = [box_rows][128 bytes], 128B swizzle.
+// 2D map over a row-major [rows][cols] matrix, box = [box_rows][box_cols]
+// (default: 128 bytes of columns), 128B swizzle by default.
 int make_map(CUtensorMap* map, const void* base, int elem, long long rows, long long cols,
-             int box_rows, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
+             int box_rows, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B, int box_cols = 0) {
   auto fn = encode_fn();
   if (!fn) return GSP_ERR_UNSUPPORTED;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * elem};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols ? box_cols : 128 / elem),
+                       static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                   2, const_cast<void*>(base), dims, strides, box, estr,
@@ -840,6 +1091,36 @@ LstCfg lst_cfg(int R, bool split, int MB) {
   // so it then asks for enough shared memory that no second CTA fits.
   const size_t need = 1024 + best.stages * static_cast<size_t>(kTileBytes) + best.bslots * b;
   best.smem = per_sm == 1 && need < 120 * 1024 ? 120 * 1024 : need;
+  return best;
+}
+
+// The rank-row Z' pass (k_lst_tc_rows) serves the BF16 hi + lo pair at rank 64.
+// Its st groups: G groups of W <= kSwMaxCols stored columns (a multiple of 16).
+bool lst_rows(const MttkrpDims& d, int elem, bool split) {
+  return elem == 2 && split && d.R == kSwRank;
+}
+int lst_rows_groups(const MttkrpDims& d, int* W) {
+  const int bt = d.B2t();
+  const int G = (bt + kSwMaxCols - 1) / kSwMaxCols;
+  *W = ((bt + G - 1) / G + 15) / 16 * 16;
+  return G;
+}
+// Its ring: T stages of W x 128 bytes and FXt slots of 2R x 128 bytes in ~110 KB
+// (two CTAs per SM), the split that lets the producer run furthest ahead.
+LstCfg lst_rows_cfg(int W) {
+  const size_t t = static_cast<size_t>(W) * 128, b = 2 * kSwRank * 128, budget = 110 * 1024 - 1024;
+  LstCfg best{3, 2, 0};
+  int lead = -1;
+  for (int nb = 2; nb <= kMaxStages && nb * b + 3 * t <= budget; ++nb) {
+    int st = static_cast<int>((budget - nb * b) / t);
+    if (st > kMaxStages) st = kMaxStages;
+    const int ahead = nb < st ? nb : st;
+    if (ahead > lead) {
+      lead = ahead;
+      best = LstCfg{st, nb, 0};
+    }
+  }
+  best.smem = 1024 + best.stages * t + best.bslots * b;
   return best;
 }
 
@@ -918,10 +1199,10 @@ int tc_mttkrp_xy(const void* T, const void* KRt, float* Yp, const MttkrpDims& d,
   return GSP_OK;
 }
 
-int tc_lst_ctas(const MttkrpDims& d) {
-  int MB = 0;
-  const int G = lst_groups(d, &MB);
-  int P = lst_ctas_per_sm(d.R, MB) * pass_sms() / G;
+int tc_lst_ctas(const MttkrpDims& d, bool rows) {
+  int MB = 0, W = 0;
+  const int G = rows ? lst_rows_groups(d, &W) : lst_groups(d, &MB);
+  int P = (rows ? 2 : lst_ctas_per_sm(d.R, MB)) * pass_sms() / G;
   if (P < d.L) P = d.L;  // a range is then at most one level long: <= 2 segments
   if (P > kLstMaxRanges) P = kLstMaxRanges;
   return P;
@@ -942,31 +1223,44 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
     k_fx_cols<float><<<grid_for(nr, 256), 256, 0, s>>>(fx, d.N, d.R, 1, static_cast<float*>(FXt));
   GSP_CHECK_LAUNCH();
   CUtensorMap mT, mF;
-  GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2t(), E128,
-                   elem == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
   GSP_TRY(make_map(&mF, FXt, elem, brows, d.N, brows));
-  int MB = 0;
-  const int G = lst_groups(d, &MB);
-  const int P = tc_lst_ctas(d);
-  const int grid = P * G;
-  const LstCfg cfg = lst_cfg(d.R, split, MB);
-  const size_t smem = cfg.smem;
-  const int stages = cfg.stages, nB = cfg.bslots;
-  const int nAcc = lst_accs(d.R, MB);  // double-buffered chunk accumulator when it fits
+  const bool rows = lst_rows(d, elem, split);
+  const int P = tc_lst_ctas(d, rows);
   const int logN = ilog2(d.N);
+  long long rows_elems = static_cast<long long>(d.B2()) * d.R;
   prof_begin(PROF_MTTKRP_LST, s);
-  if (elem == 4) {
-    GSP_TRY(set_smem(k_lst_tc<4, true>, smem));
-    k_lst_tc<4, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                   MB, G, stages, nB, nAcc, err);
-  } else if (split) {
-    GSP_TRY(set_smem(k_lst_tc<2, true>, smem));
-    k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                   MB, G, stages, nB, nAcc, err);
+  if (rows) {  // T as 16-column boxes, 32-byte swizzle: the MN-major B operand
+    GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2t(), E128, CU_TENSOR_MAP_SWIZZLE_32B, 16));
+    int W = 0;
+    const int G = lst_rows_groups(d, &W);
+    const LstCfg cfg = lst_rows_cfg(W);
+    GSP_TRY(set_smem(k_lst_tc_rows, cfg.smem));
+    k_lst_tc_rows<<<P * G, kThreads, cfg.smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.B2t(),
+                                                     W, G, cfg.stages, cfg.bslots, 2, err);
+    rows_elems = static_cast<long long>(d.B2t()) * d.R;
   } else {
-    GSP_TRY(set_smem(k_lst_tc<2, false>, smem));
-    k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
-                                                    MB, G, stages, nB, nAcc, err);
+    GSP_TRY(make_map(&mT, T, elem, d.L * d.N2(), d.B2t(), E128,
+                     elem == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
+    int MB = 0;
+    const int G = lst_groups(d, &MB);
+    const int grid = P * G;
+    const LstCfg cfg = lst_cfg(d.R, split, MB);
+    const size_t smem = cfg.smem;
+    const int stages = cfg.stages, nB = cfg.bslots;
+    const int nAcc = lst_accs(d.R, MB);  // double-buffered chunk accumulator when it fits
+    if (elem == 4) {
+      GSP_TRY(set_smem(k_lst_tc<4, true>, smem));
+      k_lst_tc<4, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+                                                     MB, G, stages, nB, nAcc, err);
+    } else if (split) {
+      GSP_TRY(set_smem(k_lst_tc<2, true>, smem));
+      k_lst_tc<2, true><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+                                                     MB, G, stages, nB, nAcc, err);
+    } else {
+      GSP_TRY(set_smem(k_lst_tc<2, false>, smem));
+      k_lst_tc<2, false><<<grid, kThreads, smem, s>>>(mT, mF, fy, Zpart, P, logN, d.L, d.B2(), d.R,
+                                                      MB, G, stages, nB, nAcc, err);
+    }
   }
   prof_end(PROF_MTTKRP_LST, s);
   GSP_CHECK_LAUNCH();
@@ -981,7 +1275,8 @@ int tc_mttkrp_lst(const void* T, const float* fx, const float* fy, void* FXt, fl
     sg.level[p][0] = static_cast<int8_t>(l0);
     if (k1 > (l0 + 1) * spl) sg.level[p][1] = static_cast<int8_t>(l0 + 1);
   }
-  k_lst_reduce<<<grid_for(per_level * d.L, 256), 256, 0, s>>>(Zpart, Zp, P, d.L, per_level, sg);
+  k_lst_reduce<<<grid_for(per_level * d.L, 256), 256, 0, s>>>(Zpart, Zp, P, d.L, per_level,
+                                                              rows_elems, sg);
   GSP_CHECK_LAUNCH();
   return GSP_OK;
 }
