@@ -92,7 +92,16 @@ size_t gsp_build_workspace_bytes(int N, int levels, int bins);
  * (x, y, l) covers texels ((x - a + i) mod N, (y - a + j) mod N), 0 <= i, j < 2^l,
  * a = floor(2^l / 2).
  *  d_hist: int32 [levels][N][N][B][B] (C order [l][y][x][s][t]), written.
- *  Counts are exact; sum over (s, t) of every footprint is 4^l. */
+ *  Counts are exact; sum over (s, t) of every footprint is 4^l.
+ *  d_hist NULL (implicit form): no histogram is written; the call bins the
+ *  map into the first N*N*2 bytes of d_ws (uint16 [N][N] = s * B + t, as
+ *  gsp_bin_normals writes it), from which every footprint's histogram is the
+ *  box count above.  gsp_cp_prepare and gsp_cp_decompose generate the MTTKRP
+ *  operand from the normal map the same way, without the int32 tensor
+ *  (L N^2 B^2 x 4 bytes: 47 GB at N = 1024, 11 levels, 32^2 bins).
+ *  d_normal_xy NULL or a bad size: GSP_ERR_INVALID_ARG; d_ws smaller than
+ *  gsp_build_workspace_bytes(): GSP_ERR_WORKSPACE; both before anything is
+ *  enqueued. */
 int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int levels, int bins,
                              int32_t* d_hist, void* d_ws, size_t ws_bytes,
                              uint32_t* d_status, gsp_stream stream);

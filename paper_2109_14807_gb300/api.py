@@ -63,11 +63,15 @@ def bin_normals(normal_xy: torch.Tensor, bins: int, status=None) -> torch.Tensor
 
 
 def build_footprint_ndfs(normal_xy: torch.Tensor, levels: int, bins: int, out=None, status=None,
-                         workspace=None) -> torch.Tensor:
-    """int32 histograms [levels][N][N][B][B] (C order [l][y][x][s][t])."""
+                         workspace=None, implicit=False) -> torch.Tensor:
+    """int32 histograms [levels][N][N][B][B] (C order [l][y][x][s][t]); with
+    `implicit`, no histogram: the bin map int16 [N][N] (s * B + t) in the
+    workspace, of which every footprint histogram is a box count."""
     lib = load()
     N = normal_xy.shape[0]
-    if out is None:
+    if implicit:
+        out = None
+    elif out is None:
         out = torch.empty((levels, N, N, bins, bins), dtype=torch.int32, device=normal_xy.device)
     need = lib.gsp_build_workspace_bytes(N, levels, bins)
     if workspace is None:
@@ -75,6 +79,8 @@ def build_footprint_ndfs(normal_xy: torch.Tensor, levels: int, bins: int, out=No
     check("gsp_build_footprint_ndfs", lib.gsp_build_footprint_ndfs(
         _ptr(normal_xy, torch.float32, "normal_xy"), N, levels, bins, _ptr(out, torch.int32, "out"),
         _ptr(workspace), workspace.numel(), _ptr(status), _stream()))
+    if implicit:
+        return workspace[:N * N * 2].view(torch.int16).view(N, N)
     return out
 
 

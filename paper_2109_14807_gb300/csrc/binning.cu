@@ -917,13 +917,14 @@ extern "C" size_t gsp_build_workspace_bytes(int N, int levels, int bins) {
 extern "C" int gsp_build_footprint_ndfs(const float* d_normal_xy, int N, int levels, int bins,
                                         int32_t* d_hist, void* d_ws, size_t ws_bytes,
                                         uint32_t* d_status, gsp_stream stream) {
-  if (!d_normal_xy || !d_hist || !valid_map(N, levels, bins)) return GSP_ERR_INVALID_ARG;
+  if (!d_normal_xy || !valid_map(N, levels, bins)) return GSP_ERR_INVALID_ARG;
   if (!d_ws || ws_bytes < gsp_build_workspace_bytes(N, levels, bins)) return GSP_ERR_WORKSPACE;
   cudaStream_t s = to_stream(stream);
   uint16_t* bins_map = static_cast<uint16_t*>(d_ws);
   uint32_t* groups = reinterpret_cast<uint32_t*>(
       static_cast<char*>(d_ws) + align_up(static_cast<size_t>(N) * N * sizeof(uint16_t), 256));
   GSP_TRY(launch_bins(d_normal_xy, N, bins, bins_map, d_status, groups, s));
+  if (!d_hist) return GSP_OK;  // implicit form: the bin map, every footprint a box count of it
   HistOut o{};
   o.h = d_hist;
   o.groups = groups;

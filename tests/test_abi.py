@@ -72,6 +72,11 @@ def test_host_side_sizes_and_validation(lib):
     assert lib.gsp_cp_count_bins(None, None, 32, 6, 16, None, 0, None, None, None) == -1
     # argument errors are returned before anything is enqueued
     assert lib.gsp_build_footprint_ndfs(None, 32, 6, 16, None, None, 0, None, None) == -1
+    # a NULL histogram is the implicit form: accepted, so a missing workspace is the error
+    fake = ctypes.c_void_p(4096)
+    assert lib.gsp_build_footprint_ndfs(fake, 32, 6, 16, None, None, 0, None, None) == -3
+    assert lib.gsp_build_footprint_ndfs(fake, 32, 6, 16, None, fake, 2047, None, None) == -3
+    assert lib.gsp_build_footprint_ndfs(fake, 33, 6, 16, None, fake, 1 << 20, None, None) == -1
     assert lib.gsp_range_query(None, 1, None, 10, None, None, None, None, 0, None) == -1
     m = _lib.Material()
     assert lib.gsp_range_query(ctypes.byref(m), 0, None, 0, None, None, None, None, 0, None) == -1

@@ -55,6 +55,25 @@ def test_nonfinite_normal_sets_status():
     assert st & 0x1
 
 
+def test_implicit_build_writes_the_bin_map():
+    # a NULL histogram: the call writes only the bin map, of which every
+    # footprint histogram is a box count (Sec. 4.1); the codes are the oracle's
+    import paper_2109_14807_gb300 as g
+    w = synth.WORKLOADS["flakes32"]
+    m = synth.make_map(w).copy()
+    B = w["bins"]
+    s, t = ndf.bin_index(m, B)
+    st = g.new_status()
+    code = g.build_footprint_ndfs(dev(m), w["levels"], B, status=st, implicit=True)
+    torch.cuda.synchronize()
+    assert g.status_bits(st) == 0
+    assert np.array_equal(code.cpu().numpy().astype(np.int64) & 0xFFFF, s * B + t)
+    m[2, 5, 1] = np.nan
+    st = g.new_status()
+    g.build_footprint_ndfs(dev(m), w["levels"], B, status=st, implicit=True)
+    assert g.status_bits(st) & 0x1
+
+
 @pytest.mark.parametrize("N,L,B,kind", [(32, 6, 16, "flakes"), (64, 7, 32, "brushed"), (8, 4, 8, "flakes")])
 def test_histograms_bit_exact_full(N, L, B, kind):
     import paper_2109_14807_gb300 as g
