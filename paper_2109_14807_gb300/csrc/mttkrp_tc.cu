@@ -11,7 +11,11 @@
 //  Z' pass  D[st][r] = sum_y fy[y][r] sum_x T[l][y][x][st] * fx[x][r]
 //           per (level, map row, st group); the same T tiles are now the
 //           MN-major A operand and FXt (fx, built per sweep) the K-major B
-//           operand; fy scales each map row's sums in the epilogue.
+//           operand; fy scales each map row's sums in the epilogue.  For the
+//           BF16 hi + lo pair at rank 64 (k_lst_tc_rows) the roles are
+//           exchanged, D[r2][st]: FXt's 128 hi and lo rows are the A operand
+//           and the stored st columns the MN-major B operand, so no
+//           accumulator row is padding.
 //
 // Accumulation is chunked: the tensor core's FP32 accumulation does not round
 // to nearest, and over a chain of thousands of MMAs into one accumulator the
