@@ -116,6 +116,36 @@ def test_operand_columns_and_mttkrp_at_every_occupancy(prec, B, n_occ):
     assert torch.equal(ws.operand_view(nb), ws2.operand_view(nb))
 
 
+@pytest.mark.parametrize("n_occ", [200, 256])
+def test_rank64_mttkrp_over_several_st_groups(n_occ):
+    # rank 64 with the BF16 hi + lo pair: the Z' pass splits the stored
+    # columns into groups of at most 80 (208 stored: 3 groups of 80, the last
+    # reaching past the stored columns; 256: 4 groups of 64); all five MTTKRPs
+    # against the dense oracle
+    import paper_2109_14807_gb300 as g
+    N, L, B, R = 64, 7, 16, 64
+    if not _supported("bf16", N, L, B, R):
+        pytest.skip(f"bf16 MTTKRP does not support the shape {(N, L, B, R)}")
+    occ = np.sort(np.argsort(synth.uniform(60 + n_occ, B, B * B))[:n_occ])
+    m = _map_of_bins(N, B, occ, 11 + n_occ)
+    s, t = ndf.bin_index(m, B)
+    assert np.array_equal(np.unique(s * B + t), occ)
+    ws = g.CPWorkspace(N, L, B, R, "bf16")
+    ws.prepare(normal_xy=dev(m))
+    assert ws.operand_cols() == (n_occ, -(-n_occ // 16) * 16)
+    X = ndf.logical(ndf.normalised_tensor(ndf.footprint_histograms(s, t, L, B), B))
+    u = [synth.uniform(800 + n_occ, k, n * R).reshape(n, R).astype(np.float32)
+         for k, n in enumerate((N, N, L, B, B))]
+    outs = ws.mttkrp({k: dev(a) for k, a in zip(("fx", "fy", "fl", "fs", "ft"), u)})
+    torch.cuda.synchronize()
+    A = [a.astype(np.float64) for a in u]
+    for n in range(5):
+        ref = cp.mttkrp_dense(X, A, n)
+        got = outs[n].double().cpu().numpy()
+        err = np.max(np.abs(got - ref) / np.maximum(ref, 1e-30 + np.max(ref) * 1e-6))
+        assert err <= MTTKRP_TOL["bf16"], (n, err)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "tf32"])
 def test_operand_columns_at_128_bins(prec):
     # B = 128 (16384 bins, the largest bin grid): 300 bins occur, 384 operand
