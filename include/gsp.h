@@ -529,7 +529,12 @@ typedef struct gsp_material_grad {
  * then 128 private copies of every material's small gradient tables ((levels
  * + 2 (bins + 1)) rank floats each), which the adjoint's CTAs accumulate into
  * (a copy is shared by at most two CTAs) and one kernel sums afterwards.
- * 0 for invalid arguments. */
+ * 0 when h_mats is NULL or n_mats is outside 1 .. GSP_MAX_MATERIALS.  The
+ * materials' own fields are not checked here (levels, bins and rank are read
+ * as given).  gsp_range_query_backward rejects a malformed material before it
+ * uses the workspace: with GSP_ERR_INVALID_ARG, or with GSP_ERR_WORKSPACE when
+ * ws_bytes is below the size computed from that material (the size test comes
+ * first). */
 size_t gsp_backward_workspace_bytes(const gsp_material* h_mats, int n_mats);
 
 /* Accumulate (+=) d(sum_i g_i q_i)/d(factors) into h_grads[m] for every
